@@ -1,0 +1,117 @@
+"""Pins of the oracle's CKKS scheme and matrix product against what the
+mathematics fixes: decryption within the noise bound, rotation equal to the
+slot permutation, Table 1 operation counts, and the decrypted product against
+FP64 A.B."""
+import numpy as np
+import pytest
+
+from oracle.ckks import CKKS, Params, centred
+from oracle.hmm import HMM, matmul_rot_steps
+
+
+@pytest.fixture(scope="module")
+def small():
+    P = Params(6, [60, 40, 40, 40], [60])
+    he = CKKS(P, 101)
+    return P, he
+
+
+def test_encrypt_decrypt_noise(small):
+    P, he = small
+    z = np.random.default_rng(1).uniform(-1, 1, P.S)
+    m = he.encode(z, P.delta, P.qs(P.L))
+    ct = he.encrypt_poly(m, P.L, P.delta, 1, P.S)
+    # Dec(Enc(m)) - m = v e + e0 + e1 s: bounded by N*19 + 19 + N*19 for ternary v, s
+    d = he.decrypt_poly(ct)
+    diff = centred(((d[0].astype(object) - m[0].astype(object)) % P.q[0]).astype(np.uint64), P.q[0])
+    assert np.abs(diff).max() <= 2 * P.N * 19 + 19
+    assert np.abs(diff).max() > 0
+
+
+def test_rotation_is_slot_permutation_and_keyswitch_noise(small):
+    P, he = small
+    z = np.random.default_rng(2).uniform(-1, 1, P.S)
+    ct = he.encrypt_slots(z, P.L, obj=2)
+    for k in [1, 5, P.S - 1]:
+        he.gen_rotation_key(k)
+        r = he.rotate(ct, k)
+        assert np.abs(he.decrypt_slots(r).real - np.roll(z, -k)).max() < 1e-6
+    # every level
+    for lv in range(P.L + 1):
+        r = he.rotate(he.drop(ct, lv), 1)
+        assert np.abs(he.decrypt_slots(r).real - np.roll(z, -1)).max() < 1e-6
+
+
+def test_mult_relin_rescale(small):
+    P, he = small
+    he.gen_relin_key()
+    rng = np.random.default_rng(3)
+    x, y = rng.uniform(-1, 1, P.S), rng.uniform(-1, 1, P.S)
+    a, b = he.encrypt_slots(x, P.L, obj=3), he.encrypt_slots(y, P.L, obj=4)
+    m = he.rescale(he.mult_relin(a, b))
+    assert m.level == P.L - 1
+    assert abs(m.scale - P.delta ** 2 / P.q[P.L]) < 1e-3
+    assert np.abs(he.decrypt_slots(m).real - x * y).max() < 1e-6
+
+
+def test_refresh_keeps_message(small):
+    P, he = small
+    z = np.random.default_rng(5).uniform(-1, 1, P.S)
+    ct = he.drop(he.encrypt_slots(z, P.L, obj=6), 0)
+    r = he.refresh(ct, 77)
+    assert r.level == P.L
+    assert (he.decrypt_int(r) == he.decrypt_int(ct)).sum() < P.N  # fresh noise differs
+    assert np.abs(he.decrypt_slots(r).real - z).max() < 1e-6
+
+
+def _mm(P, he, n, n1z, n1t, seed):
+    H = HMM(he)
+    for s in matmul_rot_steps(n, n1z, n1t, P.S):
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, (n, n))
+    B = rng.uniform(-1, 1, (n, n))
+    za = np.zeros(P.S); za[: n * n] = A.ravel()
+    zb = np.zeros(P.S); zb[: n * n] = B.ravel()
+    ca = he.encrypt_slots(za, P.L, obj=10)
+    cb = he.encrypt_slots(zb, P.L, obj=11)
+    he.cnt.reset()
+    cc = H.hmatmul(ca, cb, n, n1z, n1t)
+    out = he.decrypt_slots(cc).real[: n * n].reshape(n, n)
+    return A, B, cc, out
+
+
+@pytest.mark.parametrize("logN,n,n1z,n1t", [(6, 4, 2, 2), (8, 8, 4, 2), (9, 16, 4, 4)])
+def test_hmatmul_decrypts_to_product(logN, n, n1z, n1t):
+    P = Params(logN, [60, 40, 40, 40], [60])
+    he = CKKS(P, 7)
+    A, B, cc, out = _mm(P, he, n, n1z, n1t, seed=logN)
+    assert cc.level == P.L - 3
+    assert np.abs(out - A @ B).max() < 1e-4
+    # replicated output: every copy of the n^2 block holds A.B
+    full = he.decrypt_slots(cc).real.reshape(-1, n * n)
+    assert np.abs(full - (A @ B).ravel()).max() < 1e-4
+
+
+def test_hmatmul_operation_counts_table1():
+    # Table 1 "Optimized" rows, counted by the oracle for n=16, n1=4 (no
+    # replication: n^2 = S).  Table 1 counts the trivial j=0 baby / i=0 giant
+    # and the +2 chain steps as operations; the schedule performs:
+    #   Z: MS+Pm n1+2n2-2, Dp 2n2, MD 2n2      T: MS n1+n2-2, Dp n2, MD n2
+    #   C^k: MS 2(n1-1)n2 + 2n2-1, Dp 2n2, MD (n-1) + 2n2-1
+    #   R^k: MS (n1-1)n2 + n2-1, Dp n2, MD n-1 (chain rotations replace the b=0 ones)
+    #   Mult: n relinearisations (MS, Dp, MD each n)
+    n, n1 = 16, 4
+    P = Params(9, [60, 40, 40, 40], [60])
+    he = CKKS(P, 8)
+    _mm(P, he, n, n1, n1, seed=1)
+    n2 = n // n1
+    ms = (n1 + 2 * n2 - 2) + (n1 + n2 - 2) + (2 * (n1 - 1) * n2 + 2 * n2 - 1) + ((n1 - 1) * n2 + n2 - 1) + n
+    dp = 2 * n2 + n2 + 2 * n2 + n2 + n
+    md = 2 * n2 + n2 + (n - 1 + 2 * n2 - 1) + (n - 1) + n
+    assert (he.cnt.MS, he.cnt.Dp, he.cnt.MD) == (ms, dp, md)
+    # within Table 1's bounds: (n1+2n2)+(n1+n2)+(2n-1)+(n-1)+n MS, ...
+    assert he.cnt.MS <= (n1 + 2 * n2) + (n1 + n2) + (2 * n - 1) + (n - 1) + n
+    assert he.cnt.Dp <= (2 * n2 + 1) + (n2 + 1) + (2 * n // n1 + 2) + (n // n1 + 1) + n
+    assert he.cnt.MD <= (2 * n2 + 1) + (n2 + 1) + (2 * n // n1 + n) + (n - 1) + n
