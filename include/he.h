@@ -1,0 +1,191 @@
+/*
+ * he.h -- C ABI of the GB300-native RNS-CKKS homomorphic matrix
+ * multiplication library (one process, one GPU, sm_103a).
+ *
+ * Paper: "Improved Privacy-Preserving PCA Using Optimized Homomorphic Matrix
+ * Multiplication" (arXiv 2305.17341).  The problem statement is the paper's
+ * client/cloud model (Sec. 7.2.1): the client encrypts, the cloud computes on
+ * ciphertexts, the client decrypts.  The primitives follow App. A (full-RNS
+ * CKKS), the matrix product follows eq. 4 with the hoisting of Sec. 4.1.
+ *
+ * Conventions
+ *   - Every function returns int: HE_OK (0) or a negative HE_ERR_* code.
+ *     he_last_error() returns a thread-local message for the last failure.
+ *   - he_ctx and he_ct are opaque, library-owned handles.  Ciphertexts and keys
+ *     live in device memory (HBM) until freed with he_ct_free / he_ctx_destroy.
+ *   - Host arrays passed in are caller-owned and only read or written during
+ *     the call.  Calls that return host data synchronise the context's stream.
+ *   - A context is used from one host thread at a time.
+ *   - Ciphertext residues are exported in coefficient form, limb-major:
+ *     [poly 0..1][limb 0..level][coefficient 0..N-1], each in [0, q_limb).
+ *   - Matrices are packed row-major into slots [0, rows*cols) (Sec. 3.4);
+ *     the remaining slots are zero.
+ */
+#ifndef HE_GB300_H
+#define HE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HE_OK 0
+#define HE_ERR_ARG (-1)         /* invalid argument (null handle, bad size) */
+#define HE_ERR_PARAM (-2)       /* invalid or unsupported parameters */
+#define HE_ERR_LEVEL (-3)       /* not enough levels left for the operation */
+#define HE_ERR_SCALE (-4)       /* operands with different scales */
+#define HE_ERR_KEY_MISSING (-5) /* a rotation or relinearisation key is absent */
+#define HE_ERR_OOM (-6)         /* device allocation failed */
+#define HE_ERR_ADMISSION (-7)   /* rejected by the device-memory budget */
+#define HE_ERR_TIMEOUT (-8)     /* a bounded wait expired */
+#define HE_ERR_CUDA (-9)        /* a CUDA runtime call failed */
+
+typedef struct he_ctx he_ctx;
+typedef struct he_ct he_ct;
+
+/* Setparams (App. A): ring degree N = 2^logN; q_0..q_L and p_0..p_{alpha-1}
+ * are primes = 1 mod 2N of the given bit sizes (q_0 and the p's: the largest
+ * such primes below 2^bits, descending; q_1..q_L alternate around 2^bits:
+ * first above, first below, second above, ...).  Digits of the hybrid key
+ * switch hold alpha = n_p consecutive q's. */
+typedef struct he_params {
+    int logN;         /* 10..17 */
+    int n_q;          /* L + 1, 1..48 */
+    int q_bits[48];   /* each 30..60 */
+    int n_p;          /* alpha, 1..4 */
+    int p_bits[4];    /* each 30..60 */
+    int log_delta;    /* default encoding scale 2^log_delta */
+    double sigma;     /* standard deviation of the error distribution */
+} he_params;
+
+/* Schedule of the hoisted JKLS product (Table 1 "Optimized"): baby-step
+ * counts of the double-hoisted BSGS transforms Z (sigma) and T (tau).  Both
+ * must be powers of two dividing n. */
+typedef struct he_mm_sched {
+    int n1_z;
+    int n1_t;
+} he_mm_sched;
+
+/* One product of a batch: out = A . B for n x n matrices (eq. 4). */
+typedef struct he_mm_job {
+    const he_ct *A;
+    const he_ct *B;
+    int n;
+    he_mm_sched sched;
+} he_mm_job;
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *he_last_error(void);
+
+/* Parameter presets.  cfg_id 1: logN 14, q 60+3x40, p 60 (32x32 products);
+ * 2: logN 16, q 60+20x40, p 2x60 (128x128 products, covariance);
+ * 3: logN 16, q 60+13x40, p 2x60 (PowerMethod chain, Sec. 7.2.3);
+ * 4: logN 15 with the chain of preset 2.  log_delta 40, sigma 3.2. */
+int he_params_default(int cfg_id, he_params *out);
+
+/* Creates a context on the current CUDA device: primes, NTT tables and the
+ * secret/public key pair (SecKeyGen, PubKeyGen of App. A) drawn from the
+ * Philox4x32-10 stream keyed by `seed`.  *out receives the handle. */
+int he_ctx_create(const he_params *prm, uint64_t seed, he_ctx **out);
+int he_ctx_destroy(he_ctx *ctx);
+
+/* Makes the context launch on `stream` (a cudaStream_t; NULL = the context's
+ * own stream).  The caller keeps ownership of a stream it passes. */
+int he_ctx_set_stream(he_ctx *ctx, void *stream);
+
+/* Copies the primes: q_out[0..L] and p_out[0..alpha-1] (host arrays). */
+int he_ctx_primes(const he_ctx *ctx, uint64_t *q_out, uint64_t *p_out);
+
+/* Basic sizes of the context: N, slots, L, alpha, dnum (any pointer may be NULL). */
+int he_ctx_info(const he_ctx *ctx, int *N, int *slots, int *L, int *alpha, int *dnum);
+
+/* Secret key s (SecKeyGen, App. A) as signed coefficients s_i in {-1, 0, 1}
+ * (host array of N entries).  The secret key belongs to the client; this call
+ * is for the client side of the protocol (decryption, refresh) and tests. */
+int he_sk_export(const he_ctx *ctx, int64_t *s_out);
+
+/* SwitchKeyGen (App. A) for the rotation keys rtk_k = swk(s, kappa_{5^k}(s))
+ * of every step in rot_steps[0..n_steps) (taken mod the slot count; 0 is
+ * ignored) and, if want_relin, the relinearisation key swk(s, s^2).  Keys are
+ * generated on the device and stay resident ("loaded into memory prior to the
+ * computation", Sec. 3.3).  Existing keys are kept. */
+int he_keygen(he_ctx *ctx, const int32_t *rot_steps, int n_steps, int want_relin);
+
+/* Lists the rotation steps of the hoisted product schedule for n x n
+ * matrices in `slots` slots: replication steps, Z babies/giants, T
+ * babies/giants, the C^k step -n (Table 1 MinRotKeys).  out must hold 4n+64
+ * entries; *count receives the number written. */
+int he_rot_steps_for_matmul(int n, int n1_z, int n1_t, int slots, int32_t *out, int *count);
+
+/* Steps of the transposition G (BSGS with stride n-1, baby count n1). */
+int he_rot_steps_for_transpose(int n, int n1, int slots, int32_t *out, int *count);
+
+/* Encode (App. A) a real slot vector z[0..nslots) (rest zero) at scale
+ * 2^log_delta and encrypt it (Enc, App. A) at `level` with the public key;
+ * the encryption randomness is the Philox stream at object `enc_counter`. */
+int he_encrypt_slots(he_ctx *ctx, const double *z, int nslots, int level, uint64_t enc_counter, he_ct **out);
+
+/* Row-major matrix A (rows x cols) packed into slots [0, rows*cols), then
+ * he_encrypt_slots. */
+int he_encrypt_matrix(he_ctx *ctx, const double *A, int rows, int cols, int level, uint64_t enc_counter,
+                      he_ct **out);
+
+/* Dec + Decode (App. A): writes nslots real slot values (host). */
+int he_decrypt_slots(he_ctx *ctx, const he_ct *ct, double *z, int nslots);
+int he_decrypt_matrix(he_ctx *ctx, const he_ct *ct, double *out, int rows, int cols);
+
+/* Level, scale and slot period (n^2 after replication, else the slot count). */
+int he_ct_info(const he_ct *ct, int *level, double *scale, int *period);
+
+/* Residues in coefficient form (see Conventions): 2*(level+1)*N words. */
+int he_ct_export(const he_ct *ct, uint64_t *residues);
+
+/* Builds a ciphertext from host residues in coefficient form (upload + NTT). */
+int he_ct_import(he_ctx *ctx, const uint64_t *residues, int level, double scale, int period, he_ct **out);
+
+int he_ct_free(he_ct *ct);
+
+/* Slot rotation rho(ct; step) (App. A Rotation; hoisted key switch with the
+ * Decompose-then-Permute order of Sec. 3.3). */
+int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out);
+
+/* Add (App. A Addition module): same level and scale. */
+int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+
+/* Mult (App. A): tensor product then relinearisation; scale multiplies. */
+int he_mult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
+
+/* Rescale (App. A): round(c / q_l), level l -> l-1, scale / q_l. */
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out);
+
+/* Replicates an n x n matrix ciphertext to slot period n^2:
+ * ct + Rot(ct, -n^2 2^j) for j = 0 .. log2(slots/n^2)-1. */
+int he_replicate(he_ctx *ctx, const he_ct *ct, int n, he_ct **out);
+
+/* Encrypted product of two n x n matrices (eq. 4, DMatrixMult without
+ * decomposition): double-hoisted BSGS Z and T (Sec. 3.3, Table 1), hoisted
+ * C^k / R^k, per-product relinearisation, one final rescale.  Consumes 3
+ * levels; the output is replicated with period n^2. */
+int he_hmatmul(he_ctx *ctx, const he_ct *A, const he_ct *B, int n, const he_mm_sched *sched, he_ct **out);
+
+/* Batched products: jobs are grouped by (context, level, n, schedule); each
+ * group runs as one pass in which every kernel covers all jobs of the group
+ * and every key is read once per group.  outs[i] receives job i's product,
+ * bit-identical to he_hmatmul on the same inputs. */
+int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs);
+
+/* Transposition G (Sec. 3.4) of an n x n matrix ciphertext; consumes 1
+ * level.  Every diagonal is multiplied by `prescale` (1.0 for a plain
+ * transpose). */
+int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, he_ct **out);
+
+/* Counters of the key-switch phases since the last reset: MultSum, Decompose,
+ * ModDown (Table 1 caption), and kernel launches.  Any pointer may be NULL. */
+int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,284 @@
+"""ctypes binding of include/he.h (argument marshalling only).
+
+Every function keeps the C name; all computation runs in libhe_gb300.so.
+Loading fails loudly when the library is missing: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhe_gb300.so")
+
+HE_OK = 0
+ERRORS = {
+    -1: "HE_ERR_ARG", -2: "HE_ERR_PARAM", -3: "HE_ERR_LEVEL", -4: "HE_ERR_SCALE", -5: "HE_ERR_KEY_MISSING",
+    -6: "HE_ERR_OOM", -7: "HE_ERR_ADMISSION", -8: "HE_ERR_TIMEOUT", -9: "HE_ERR_CUDA",
+}
+
+
+class HeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class he_params(ctypes.Structure):
+    _fields_ = [("logN", ctypes.c_int), ("n_q", ctypes.c_int), ("q_bits", ctypes.c_int * 48),
+                ("n_p", ctypes.c_int), ("p_bits", ctypes.c_int * 4), ("log_delta", ctypes.c_int),
+                ("sigma", ctypes.c_double)]
+
+
+class he_mm_sched(ctypes.Structure):
+    _fields_ = [("n1_z", ctypes.c_int), ("n1_t", ctypes.c_int)]
+
+
+class he_mm_job(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("n", ctypes.c_int), ("sched", he_mm_sched)]
+
+
+P = ctypes.POINTER
+vp = ctypes.c_void_p
+ip = ctypes.c_int
+u64p = P(ctypes.c_uint64)
+dblp = P(ctypes.c_double)
+i32p = P(ctypes.c_int32)
+llp = P(ctypes.c_longlong)
+
+# name -> argtypes (restype int unless listed in _RESTYPES)
+SIGNATURES = {
+    "he_last_error": [],
+    "he_params_default": [ip, P(he_params)],
+    "he_ctx_create": [P(he_params), ctypes.c_uint64, P(vp)],
+    "he_ctx_destroy": [vp],
+    "he_ctx_set_stream": [vp, vp],
+    "he_ctx_primes": [vp, u64p, u64p],
+    "he_ctx_info": [vp, P(ip), P(ip), P(ip), P(ip), P(ip)],
+    "he_sk_export": [vp, P(ctypes.c_int64)],
+    "he_keygen": [vp, i32p, ip, ip],
+    "he_rot_steps_for_matmul": [ip, ip, ip, ip, i32p, P(ip)],
+    "he_rot_steps_for_transpose": [ip, ip, ip, i32p, P(ip)],
+    "he_encrypt_slots": [vp, dblp, ip, ip, ctypes.c_uint64, P(vp)],
+    "he_encrypt_matrix": [vp, dblp, ip, ip, ip, ctypes.c_uint64, P(vp)],
+    "he_decrypt_slots": [vp, vp, dblp, ip],
+    "he_decrypt_matrix": [vp, vp, dblp, ip, ip],
+    "he_ct_info": [vp, P(ip), P(ctypes.c_double), P(ip)],
+    "he_ct_export": [vp, u64p],
+    "he_ct_import": [vp, u64p, ip, ctypes.c_double, ip, P(vp)],
+    "he_ct_free": [vp],
+    "he_rotate": [vp, vp, ip, P(vp)],
+    "he_add": [vp, vp, vp, P(vp)],
+    "he_mult": [vp, vp, vp, P(vp)],
+    "he_rescale": [vp, vp, P(vp)],
+    "he_replicate": [vp, vp, ip, P(vp)],
+    "he_hmatmul": [vp, vp, vp, ip, P(he_mm_sched), P(vp)],
+    "he_hmatmul_batch": [P(he_mm_job), ip, P(vp)],
+    "he_transpose": [vp, vp, ip, ip, ctypes.c_double, P(vp)],
+    "he_counters": [vp, llp, llp, llp, llp, ip],
+}
+_RESTYPES = {"he_last_error": ctypes.c_char_p}
+
+_lib = None
+
+
+def lib():
+    """Load libhe_gb300.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhe_gb300.so not built: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = _RESTYPES.get(name, ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != HE_OK:
+        raise HeError(rc, lib().he_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------ wrappers
+def he_params_default(cfg_id):
+    p = he_params()
+    check(lib().he_params_default(cfg_id, ctypes.byref(p)))
+    return p
+
+
+def make_params(logN, qbits, pbits, log_delta=40, sigma=3.2):
+    p = he_params()
+    p.logN = logN
+    p.n_q = len(qbits)
+    for i, b in enumerate(qbits):
+        p.q_bits[i] = b
+    p.n_p = len(pbits)
+    for i, b in enumerate(pbits):
+        p.p_bits[i] = b
+    p.log_delta = log_delta
+    p.sigma = sigma
+    return p
+
+
+def he_ctx_create(params, seed):
+    h = vp()
+    check(lib().he_ctx_create(ctypes.byref(params), seed, ctypes.byref(h)))
+    return h
+
+
+def he_ctx_destroy(ctx):
+    check(lib().he_ctx_destroy(ctx))
+
+
+def he_ctx_set_stream(ctx, stream_ptr):
+    check(lib().he_ctx_set_stream(ctx, stream_ptr))
+
+
+def he_ctx_info(ctx):
+    v = [ctypes.c_int() for _ in range(5)]
+    check(lib().he_ctx_info(ctx, *[ctypes.byref(x) for x in v]))
+    return dict(zip(["N", "slots", "L", "alpha", "dnum"], [x.value for x in v]))
+
+
+def he_ctx_primes(ctx):
+    info = he_ctx_info(ctx)
+    q = np.zeros(info["L"] + 1, dtype=np.uint64)
+    p = np.zeros(info["alpha"], dtype=np.uint64)
+    check(lib().he_ctx_primes(ctx, q.ctypes.data_as(u64p), p.ctypes.data_as(u64p)))
+    return [int(x) for x in q], [int(x) for x in p]
+
+
+def he_sk_export(ctx):
+    N = he_ctx_info(ctx)["N"]
+    out = np.zeros(N, dtype=np.int64)
+    check(lib().he_sk_export(ctx, out.ctypes.data_as(P(ctypes.c_int64))))
+    return out
+
+
+def he_keygen(ctx, steps, want_relin=True):
+    a = np.ascontiguousarray(np.asarray(list(steps), dtype=np.int32))
+    check(lib().he_keygen(ctx, a.ctypes.data_as(i32p), len(a), 1 if want_relin else 0))
+
+
+def he_rot_steps_for_matmul(n, n1z, n1t, slots):
+    out = np.zeros(4 * n + 64, dtype=np.int32)
+    cnt = ctypes.c_int()
+    check(lib().he_rot_steps_for_matmul(n, n1z, n1t, slots, out.ctypes.data_as(i32p), ctypes.byref(cnt)))
+    return [int(x) for x in out[: cnt.value]]
+
+
+def he_rot_steps_for_transpose(n, n1, slots):
+    out = np.zeros(4 * n + 64, dtype=np.int32)
+    cnt = ctypes.c_int()
+    check(lib().he_rot_steps_for_transpose(n, n1, slots, out.ctypes.data_as(i32p), ctypes.byref(cnt)))
+    return [int(x) for x in out[: cnt.value]]
+
+
+def he_encrypt_slots(ctx, z, level, enc_counter):
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    h = vp()
+    check(lib().he_encrypt_slots(ctx, z.ctypes.data_as(dblp), z.size, level, enc_counter, ctypes.byref(h)))
+    return h
+
+
+def he_encrypt_matrix(ctx, A, level, enc_counter):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    h = vp()
+    check(lib().he_encrypt_matrix(ctx, A.ctypes.data_as(dblp), A.shape[0], A.shape[1], level, enc_counter,
+                                  ctypes.byref(h)))
+    return h
+
+
+def he_decrypt_slots(ctx, ct, nslots):
+    out = np.zeros(nslots, dtype=np.float64)
+    check(lib().he_decrypt_slots(ctx, ct, out.ctypes.data_as(dblp), nslots))
+    return out
+
+
+def he_decrypt_matrix(ctx, ct, rows, cols):
+    out = np.zeros((rows, cols), dtype=np.float64)
+    check(lib().he_decrypt_matrix(ctx, ct, out.ctypes.data_as(dblp), rows, cols))
+    return out
+
+
+def he_ct_info(ct):
+    lv, sc, per = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    check(lib().he_ct_info(ct, ctypes.byref(lv), ctypes.byref(sc), ctypes.byref(per)))
+    return lv.value, sc.value, per.value
+
+
+def he_ct_export(ctx, ct):
+    lv, _, _ = he_ct_info(ct)
+    N = he_ctx_info(ctx)["N"]
+    out = np.zeros((2, lv + 1, N), dtype=np.uint64)
+    check(lib().he_ct_export(ct, out.ctypes.data_as(u64p)))
+    return out
+
+
+def he_ct_import(ctx, residues, level, scale, period):
+    r = np.ascontiguousarray(residues, dtype=np.uint64)
+    h = vp()
+    check(lib().he_ct_import(ctx, r.ctypes.data_as(u64p), level, scale, period, ctypes.byref(h)))
+    return h
+
+
+def he_ct_free(ct):
+    check(lib().he_ct_free(ct))
+
+
+def _unary(name, *args):
+    h = vp()
+    check(getattr(lib(), name)(*args, ctypes.byref(h)))
+    return h
+
+
+def he_rotate(ctx, ct, step):
+    return _unary("he_rotate", ctx, ct, step)
+
+
+def he_add(ctx, a, b):
+    return _unary("he_add", ctx, a, b)
+
+
+def he_mult(ctx, a, b):
+    return _unary("he_mult", ctx, a, b)
+
+
+def he_rescale(ctx, a):
+    return _unary("he_rescale", ctx, a)
+
+
+def he_replicate(ctx, ct, n):
+    return _unary("he_replicate", ctx, ct, n)
+
+
+def he_hmatmul(ctx, A, B, n, n1z, n1t):
+    s = he_mm_sched(n1z, n1t)
+    return _unary("he_hmatmul", ctx, A, B, n, ctypes.byref(s))
+
+
+def he_hmatmul_batch(jobs):
+    """jobs: list of (A, B, n, n1z, n1t)."""
+    arr = (he_mm_job * len(jobs))()
+    for i, (A, B, n, n1z, n1t) in enumerate(jobs):
+        arr[i].A = A
+        arr[i].B = B
+        arr[i].n = n
+        arr[i].sched = he_mm_sched(n1z, n1t)
+    outs = (vp * len(jobs))()
+    check(lib().he_hmatmul_batch(arr, len(jobs), outs))
+    return [vp(o) for o in outs]
+
+
+def he_transpose(ctx, ct, n, n1, prescale=1.0):
+    return _unary("he_transpose", ctx, ct, n, n1, prescale)
+
+
+def he_counters(ctx, reset=False):
+    v = [ctypes.c_longlong() for _ in range(4)]
+    check(lib().he_counters(ctx, *[ctypes.byref(x) for x in v], 1 if reset else 0))
+    return dict(zip(["MS", "Dp", "MD", "launches"], [x.value for x in v]))

@@ -1,0 +1,632 @@
+// capi.cu -- the extern "C" boundary declared in include/he.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <set>
+#include <tuple>
+
+#include "eval.h"
+
+using namespace he;
+
+struct he_ctx {
+    Ctx c;
+};
+
+struct he_ct {
+    Ctx *ctx;
+    u64 *d;
+    int level;
+    double scale;
+    int period;
+};
+
+namespace he {
+void build_tables(Ctx *c);
+}
+
+// --------------------------------------------------------------- helpers
+#define GUARD_BEGIN try {
+#define GUARD_END                                                      \
+    }                                                                  \
+    catch (const HeError &e) {                                         \
+        set_error(e.what());                                           \
+        return e.code;                                                 \
+    }                                                                  \
+    catch (const std::bad_alloc &) {                                   \
+        set_error("device or host allocation failed");                 \
+        return HE_ERR_OOM;                                             \
+    }                                                                  \
+    catch (const std::exception &e) {                                  \
+        set_error(e.what());                                           \
+        return HE_ERR_ARG;                                             \
+    }
+
+static int fail(int code, const char *msg) {
+    set_error(msg);
+    return code;
+}
+
+static int cuda_status(Ctx *c) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("CUDA error: ") + cudaGetErrorString(e));
+        return HE_ERR_CUDA;
+    }
+    (void)c;
+    return HE_OK;
+}
+
+static size_t ct_words(const Ctx *c, int level) { return (size_t)2 * (level + 1) * c->N; }
+
+static he_ct *new_ct(Ctx *c, int level, double scale, int period) {
+    he_ct *ct = new he_ct;
+    ct->ctx = c;
+    ct->level = level;
+    ct->scale = scale;
+    ct->period = period;
+    ct->d = (u64 *)c->pool.get(ct_words(c, level) * 8);
+    return ct;
+}
+
+static void free_ct(he_ct *ct) {
+    if (!ct) return;
+    if (ct->d) ct->ctx->pool.put(ct->d);
+    delete ct;
+}
+
+extern "C" {
+
+const char *he_last_error(void) { return last_error(); }
+
+int he_params_default(int cfg_id, he_params *out) {
+    if (!out) return fail(HE_ERR_ARG, "null output");
+    std::memset(out, 0, sizeof(*out));
+    out->log_delta = 40;
+    out->sigma = 3.2;
+    out->q_bits[0] = 60;
+    switch (cfg_id) {
+    case 1:
+        out->logN = 14; out->n_q = 4; out->n_p = 1; out->p_bits[0] = 60;
+        break;
+    case 2: case 4:
+        out->logN = cfg_id == 2 ? 16 : 15; out->n_q = 21; out->n_p = 2;
+        out->p_bits[0] = out->p_bits[1] = 60;
+        break;
+    case 3:
+        out->logN = 16; out->n_q = 14; out->n_p = 2; out->p_bits[0] = out->p_bits[1] = 60;
+        break;
+    default:
+        return fail(HE_ERR_PARAM, "unknown preset");
+    }
+    for (int i = 1; i < out->n_q; i++) out->q_bits[i] = 40;
+    return HE_OK;
+}
+
+int he_ctx_create(const he_params *prm, uint64_t seed, he_ctx **out) {
+    if (!prm || !out) return fail(HE_ERR_ARG, "null argument");
+    if (prm->logN < 10 || prm->logN > 17) return fail(HE_ERR_PARAM, "logN must be in [10, 17]");
+    if (prm->n_q < 1 || prm->n_q > 48 || prm->n_p < 1 || prm->n_p > 4)
+        return fail(HE_ERR_PARAM, "n_q in [1,48], n_p in [1,4]");
+    if (prm->n_q + prm->n_p > 52) return fail(HE_ERR_PARAM, "too many primes");
+    for (int i = 0; i < prm->n_q; i++)
+        if (prm->q_bits[i] < 30 || prm->q_bits[i] > 60) return fail(HE_ERR_PARAM, "q bits in [30, 60]");
+    for (int j = 0; j < prm->n_p; j++)
+        if (prm->p_bits[j] < 30 || prm->p_bits[j] > 60) return fail(HE_ERR_PARAM, "p bits in [30, 60]");
+    if (prm->sigma <= 0 || prm->log_delta < 1 || prm->log_delta > 60) return fail(HE_ERR_PARAM, "sigma / log_delta");
+    GUARD_BEGIN
+    he_ctx *h = new he_ctx;
+    Ctx &c = h->c;
+    c.prm = *prm;
+    c.logN = prm->logN;
+    c.N = 1 << c.logN;
+    c.S = c.N / 2;
+    c.L = prm->n_q - 1;
+    c.alpha = prm->n_p;
+    c.dnum = (c.L + 1 + c.alpha - 1) / c.alpha;
+    c.nprimes = prm->n_q + prm->n_p;
+    c.seed = seed;
+    std::vector<u64> q(prm->n_q), p(prm->n_p);
+    if (h_gen_primes(c.logN, prm->n_q, prm->q_bits, prm->n_p, prm->p_bits, q.data(), p.data()) != 0) {
+        delete h;
+        return fail(HE_ERR_PARAM, "prime search failed");
+    }
+    c.primes = q;
+    c.primes.insert(c.primes.end(), p.begin(), p.end());
+    cudaGetDevice(&c.device);
+    if (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return fail(HE_ERR_CUDA, "stream creation failed");
+    }
+    c.own_stream = true;
+    build_tables(&c);
+    create_keys(&c);
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
+        int rc = cuda_status(&c);
+        delete h;
+        return rc ? rc : HE_ERR_CUDA;
+    }
+    int rc = cuda_status(&c);
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return HE_OK;
+    GUARD_END
+}
+
+int he_ctx_destroy(he_ctx *ctx) {
+    if (!ctx) return HE_OK;
+    Ctx &c = ctx->c;
+    cudaStreamSynchronize(c.stream);
+    for (auto &kv : c.rtk) cudaFree(kv.second);
+    if (c.rlk) cudaFree(c.rlk);
+    for (auto &kv : c.ptcache) cudaFree(kv.second);
+    void *ptrs[] = {c.d_mod, c.d_psi, c.d_psip, c.d_ipsi, c.d_ipsip, c.d_ninv, c.d_dn_pinv, c.d_dn_pmod,
+                    c.d_dn_Pinv, c.d_Pmod, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM, c.d_pkM};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &l : c.lvl) {
+        if (l.d_up_inv) cudaFree(l.d_up_inv);
+        if (l.d_up_mod) cudaFree(l.d_up_mod);
+        if (l.d_rs_inv) cudaFree(l.d_rs_inv);
+        if (l.d_rs_qlmod) cudaFree(l.d_rs_qlmod);
+    }
+    c.pool.release_all();
+    if (c.own_stream) cudaStreamDestroy(c.stream);
+    delete ctx;
+    return HE_OK;
+}
+
+int he_ctx_set_stream(he_ctx *ctx, void *stream) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    Ctx &c = ctx->c;
+    cudaStreamSynchronize(c.stream);
+    if (stream) {
+        if (c.own_stream) cudaStreamDestroy(c.stream);
+        c.own_stream = false;
+        c.stream = (cudaStream_t)stream;
+    } else if (!c.own_stream) {
+        cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+        c.own_stream = true;
+    }
+    return HE_OK;
+}
+
+int he_ctx_primes(const he_ctx *ctx, uint64_t *q_out, uint64_t *p_out) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    const Ctx &c = ctx->c;
+    for (int i = 0; i <= c.L; i++)
+        if (q_out) q_out[i] = c.primes[i];
+    for (int j = 0; j < c.alpha; j++)
+        if (p_out) p_out[j] = c.primes[c.L + 1 + j];
+    return HE_OK;
+}
+
+int he_ctx_info(const he_ctx *ctx, int *N, int *slots, int *L, int *alpha, int *dnum) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    const Ctx &c = ctx->c;
+    if (N) *N = c.N;
+    if (slots) *slots = c.S;
+    if (L) *L = c.L;
+    if (alpha) *alpha = c.alpha;
+    if (dnum) *dnum = c.dnum;
+    return HE_OK;
+}
+
+int he_sk_export(const he_ctx *ctx, int64_t *s_out) {
+    if (!ctx || !s_out) return fail(HE_ERR_ARG, "null argument");
+    const Ctx &c = ctx->c;
+    GUARD_BEGIN
+    Ctx &cc = const_cast<Ctx &>(c);
+    Buf t(&cc.pool, c.N);
+    HE_CUDA_CHECK(cudaMemcpyAsync(t.p, c.d_sk, (size_t)c.N * 8, cudaMemcpyDeviceToDevice, c.stream));
+    RowMap one;
+    one.n = 1;
+    one.p[0] = 0;
+    ntt_inv(&cc, t.p, 1, one, c.stream);
+    std::vector<u64> h(c.N);
+    HE_CUDA_CHECK(cudaMemcpyAsync(h.data(), t.p, (size_t)c.N * 8, cudaMemcpyDeviceToHost, c.stream));
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    u64 q = c.primes[0];
+    for (int i = 0; i < c.N; i++) s_out[i] = h[i] > q / 2 ? -(int64_t)(q - h[i]) : (int64_t)h[i];
+    return HE_OK;
+    GUARD_END
+}
+
+int he_keygen(he_ctx *ctx, const int32_t *rot_steps, int n_steps, int want_relin) {
+    if (!ctx || (n_steps > 0 && !rot_steps) || n_steps < 0) return fail(HE_ERR_ARG, "bad arguments");
+    Ctx &c = ctx->c;
+    GUARD_BEGIN
+    for (int i = 0; i < n_steps; i++) {
+        long s = ((long)rot_steps[i] % c.S + c.S) % c.S;
+        if (s == 0) continue;
+        uint32_t g = galois_of_step(&c, s);
+        if (c.rtk.count(g)) continue;
+        c.rtk[g] = gen_rotation_key(&c, g);
+    }
+    if (want_relin && !c.rlk) c.rlk = gen_relin_key(&c);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    return cuda_status(&c);
+    GUARD_END
+}
+
+static void add_mod(std::set<long> &s, long v, long m) { s.insert(((v % m) + m) % m); }
+
+int he_rot_steps_for_matmul(int n, int n1z, int n1t, int slots, int32_t *out, int *count) {
+    if (!out || !count || n < 1 || n1z < 1 || n1t < 1 || n % n1z || n % n1t || (long)n * n > slots)
+        return fail(HE_ERR_ARG, "bad arguments");
+    long n2 = (long)n * n;
+    std::set<long> st;
+    for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
+    int n2z = n / n1z, n2t = n / n1t;
+    for (int j = 1; j < n1z; j++) add_mod(st, j, n2);
+    for (int i = -n2z; i < n2z; i++)
+        if (i) add_mod(st, (long)n1z * i, n2);
+    for (int j = 1; j < n1t; j++) add_mod(st, (long)n * j, n2);
+    for (int i = 1; i < n2t; i++) add_mod(st, (long)n * n1t * i, n2);
+    add_mod(st, n1z, n2);
+    add_mod(st, -n, n2);
+    if (n2t > 1) add_mod(st, (long)n * n1t, n2);
+    st.erase(0);
+    int k = 0;
+    for (long v : st) out[k++] = (int32_t)v;
+    *count = k;
+    return HE_OK;
+}
+
+int he_rot_steps_for_transpose(int n, int n1, int slots, int32_t *out, int *count) {
+    if (!out || !count || n < 2 || n1 < 1 || n % n1 || (long)n * n > slots) return fail(HE_ERR_ARG, "bad arguments");
+    long n2 = (long)n * n, a = n - 1;
+    std::set<long> st;
+    for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
+    int n2g = n / n1;
+    for (int j = 1; j < n1; j++) add_mod(st, a * j, n2);
+    for (int i = -n2g; i < n2g; i++)
+        if (i) add_mod(st, a * n1 * i, n2);
+    st.erase(0);
+    int k = 0;
+    for (long v : st) out[k++] = (int32_t)v;
+    *count = k;
+    return HE_OK;
+}
+
+int he_encrypt_slots(he_ctx *ctx, const double *z, int nslots, int level, uint64_t enc_counter, he_ct **out) {
+    if (!ctx || !out || (nslots > 0 && !z)) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (nslots < 0 || nslots > c.S) return fail(HE_ERR_ARG, "nslots out of range");
+    if (level < 0 || level > c.L) return fail(HE_ERR_LEVEL, "level out of range");
+    GUARD_BEGIN
+    std::vector<double> host(c.S, 0.0);
+    if (nslots) std::memcpy(host.data(), z, sizeof(double) * nslots);
+    Buf zr(&c.pool, c.S), zi(&c.pool, c.S), m(&c.pool, (size_t)(level + 1) * c.N);
+    HE_CUDA_CHECK(cudaMemcpyAsync(zr.p, host.data(), sizeof(double) * c.S, cudaMemcpyHostToDevice, c.stream));
+    HE_CUDA_CHECK(cudaMemsetAsync(zi.p, 0, sizeof(double) * c.S, c.stream));
+    double delta = std::ldexp(1.0, c.prm.log_delta);
+    encode_to(&c, (double *)zr.p, (double *)zi.p, delta, m.p, level + 1, c.map_q(level));
+    he_ct *ct = new_ct(&c, level, delta, c.S);
+    encrypt_poly(&c, m.p, level, (uint32_t)enc_counter, false, ct->d);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    int rc = cuda_status(&c);
+    if (rc) {
+        free_ct(ct);
+        return rc;
+    }
+    *out = ct;
+    return HE_OK;
+    GUARD_END
+}
+
+int he_encrypt_matrix(he_ctx *ctx, const double *A, int rows, int cols, int level, uint64_t enc_counter,
+                      he_ct **out) {
+    if (!ctx || !A || rows < 1 || cols < 1) return fail(HE_ERR_ARG, "bad arguments");
+    if ((long)rows * cols > ctx->c.S) return fail(HE_ERR_ARG, "matrix larger than the slot count");
+    return he_encrypt_slots(ctx, A, rows * cols, level, enc_counter, out);
+}
+
+int he_decrypt_slots(he_ctx *ctx, const he_ct *ct, double *z, int nslots) {
+    if (!ctx || !ct || (nslots > 0 && !z)) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (ct->ctx != &c) return fail(HE_ERR_ARG, "ciphertext of another context");
+    if (nslots < 0 || nslots > c.S) return fail(HE_ERR_ARG, "nslots out of range");
+    GUARD_BEGIN
+    Buf m(&c.pool, c.N), coef(&c.pool, c.N), zr(&c.pool, c.S), zi(&c.pool, c.S);
+    const u64 *c0 = ct->d, *c1 = ct->d + (size_t)(ct->level + 1) * c.N;
+    launch_dec_q0(&c, c0, c1, m.p, c.stream);
+    RowMap one;
+    one.n = 1;
+    one.p[0] = 0;
+    ntt_inv(&c, m.p, 1, one, c.stream);
+    launch_centre_q0(&c, m.p, (double *)coef.p, c.stream);
+    launch_decode(&c, (double *)coef.p, ct->scale, (double *)zr.p, (double *)zi.p, c.stream);
+    std::vector<double> host(c.S);
+    HE_CUDA_CHECK(cudaMemcpyAsync(host.data(), zr.p, sizeof(double) * c.S, cudaMemcpyDeviceToHost, c.stream));
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (nslots) std::memcpy(z, host.data(), sizeof(double) * nslots);
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_decrypt_matrix(he_ctx *ctx, const he_ct *ct, double *out, int rows, int cols) {
+    if (!ctx || !out || rows < 1 || cols < 1) return fail(HE_ERR_ARG, "bad arguments");
+    if ((long)rows * cols > ctx->c.S) return fail(HE_ERR_ARG, "matrix larger than the slot count");
+    return he_decrypt_slots(ctx, ct, out, rows * cols);
+}
+
+int he_ct_info(const he_ct *ct, int *level, double *scale, int *period) {
+    if (!ct) return fail(HE_ERR_ARG, "null ciphertext");
+    if (level) *level = ct->level;
+    if (scale) *scale = ct->scale;
+    if (period) *period = ct->period;
+    return HE_OK;
+}
+
+int he_ct_export(const he_ct *ct, uint64_t *residues) {
+    if (!ct || !residues) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = *ct->ctx;
+    GUARD_BEGIN
+    size_t w = ct_words(&c, ct->level);
+    Buf t(&c.pool, w);
+    HE_CUDA_CHECK(cudaMemcpyAsync(t.p, ct->d, w * 8, cudaMemcpyDeviceToDevice, c.stream));
+    ntt_inv(&c, t.p, 2L * (ct->level + 1), c.map_q(ct->level), c.stream);
+    HE_CUDA_CHECK(cudaMemcpyAsync(residues, t.p, w * 8, cudaMemcpyDeviceToHost, c.stream));
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_ct_import(he_ctx *ctx, const uint64_t *residues, int level, double scale, int period, he_ct **out) {
+    if (!ctx || !residues || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (level < 0 || level > c.L) return fail(HE_ERR_LEVEL, "level out of range");
+    GUARD_BEGIN
+    he_ct *ct = new_ct(&c, level, scale, period > 0 ? period : c.S);
+    size_t w = ct_words(&c, level);
+    HE_CUDA_CHECK(cudaMemcpyAsync(ct->d, residues, w * 8, cudaMemcpyHostToDevice, c.stream));
+    ntt_fwd(&c, ct->d, 2L * (level + 1), c.map_q(level), c.stream);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    *out = ct;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_ct_free(he_ct *ct) {
+    free_ct(ct);
+    return HE_OK;
+}
+
+static int check_ct(Ctx &c, const he_ct *ct) {
+    if (!ct) return fail(HE_ERR_ARG, "null ciphertext");
+    if (ct->ctx != &c) return fail(HE_ERR_ARG, "ciphertext of another context");
+    return HE_OK;
+}
+
+int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, ct)) return rc;
+    GUARD_BEGIN
+    he_ct *o = new_ct(&c, ct->level, ct->scale, ct->period);
+    try {
+        rotate(&c, ct->d, 1, ct->level, galois_of_step(&c, step), o->d);
+    } catch (...) {
+        free_ct(o);
+        throw;
+    }
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, a)) return rc;
+    if (int rc = check_ct(c, b)) return rc;
+    if (a->level != b->level) return fail(HE_ERR_LEVEL, "operands at different levels");
+    if (a->scale != b->scale) return fail(HE_ERR_SCALE, "operands with different scales");
+    GUARD_BEGIN
+    he_ct *o = new_ct(&c, a->level, a->scale, std::min(a->period, b->period));
+    add(&c, a->d, b->d, 1, a->level, o->d);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_mult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, a)) return rc;
+    if (int rc = check_ct(c, b)) return rc;
+    if (a->level != b->level) return fail(HE_ERR_LEVEL, "operands at different levels");
+    GUARD_BEGIN
+    he_ct *o = new_ct(&c, a->level, a->scale * b->scale, std::min(a->period, b->period));
+    try {
+        mult_relin(&c, a->d, b->d, 1, a->level, o->d);
+    } catch (...) {
+        free_ct(o);
+        throw;
+    }
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, a)) return rc;
+    if (a->level < 1) return fail(HE_ERR_LEVEL, "no level left to rescale");
+    GUARD_BEGIN
+    he_ct *o = new_ct(&c, a->level - 1, a->scale / (double)c.primes[a->level], a->period);
+    rescale(&c, a->d, 1, a->level, o->d);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+static he_ct *clone_ct(Ctx &c, const he_ct *a) {
+    he_ct *o = new_ct(&c, a->level, a->scale, a->period);
+    cudaMemcpyAsync(o->d, a->d, ct_words(&c, a->level) * 8, cudaMemcpyDeviceToDevice, c.stream);
+    return o;
+}
+
+int he_replicate(he_ctx *ctx, const he_ct *ct, int n, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, ct)) return rc;
+    if (n < 1 || (long)n * n > c.S || (c.S % (n * n))) return fail(HE_ERR_ARG, "n^2 must divide the slot count");
+    GUARD_BEGIN
+    he_ct *o = clone_ct(c, ct);
+    if (o->period != n * n) {
+        try {
+            replicate(&c, o->d, 1, o->level, n);
+        } catch (...) {
+            free_ct(o);
+            throw;
+        }
+        o->period = n * n;
+    }
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+static int check_sched(Ctx &c, int n, const he_mm_sched *s) {
+    if (!s) return fail(HE_ERR_ARG, "null schedule");
+    auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
+    if (!pow2(n) || (long)n * n > c.S) return fail(HE_ERR_ARG, "n must be a power of two with n^2 <= slots");
+    if (!pow2(s->n1_z) || !pow2(s->n1_t) || s->n1_z > n || s->n1_t > n || s->n1_z > 32 || s->n1_t > 32)
+        return fail(HE_ERR_ARG, "baby-step counts must be powers of two dividing n (<= 32)");
+    return HE_OK;
+}
+
+// Runs one group of same-shape products: gathers A's and B's, replicates,
+// aligns levels, multiplies, scatters.
+static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::vector<const he_ct *> &Bs, int n,
+                      int n1z, int n1t, int level, std::vector<he_ct *> &outs) {
+    const int Bn = (int)As.size();
+    const size_t w = ct_words(&c, level);
+    Buf A(&c.pool, Bn * w), B(&c.pool, Bn * w);
+    for (int i = 0; i < Bn; i++) {
+        // drop to the common level while gathering (keep limbs 0..level of both polys)
+        cudaMemcpy2DAsync(A.p + i * w, (size_t)(level + 1) * c.N * 8, As[i]->d, (size_t)(As[i]->level + 1) * c.N * 8,
+                          (size_t)(level + 1) * c.N * 8, 2, cudaMemcpyDeviceToDevice, c.stream);
+        cudaMemcpy2DAsync(B.p + i * w, (size_t)(level + 1) * c.N * 8, Bs[i]->d, (size_t)(Bs[i]->level + 1) * c.N * 8,
+                          (size_t)(level + 1) * c.N * 8, 2, cudaMemcpyDeviceToDevice, c.stream);
+    }
+    if (As[0]->period != n * n) replicate(&c, A.p, Bn, level, n);
+    if (Bs[0]->period != n * n) replicate(&c, B.p, Bn, level, n);
+    const size_t wo = ct_words(&c, level - 3);
+    Buf O(&c.pool, Bn * wo);
+    hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p);
+    double q2 = (double)c.primes[level - 2];
+    for (int i = 0; i < Bn; i++) {
+        he_ct *o = new_ct(&c, level - 3, (As[i]->scale * Bs[i]->scale) / q2, n * n);
+        cudaMemcpyAsync(o->d, O.p + i * wo, wo * 8, cudaMemcpyDeviceToDevice, c.stream);
+        outs[i] = o;
+    }
+}
+
+int he_hmatmul(he_ctx *ctx, const he_ct *A, const he_ct *B, int n, const he_mm_sched *sched, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    he_mm_job j{A, B, n, sched ? *sched : he_mm_sched{0, 0}};
+    if (!sched) return fail(HE_ERR_ARG, "null schedule");
+    if (int rc = check_ct(ctx->c, A)) return rc;
+    if (int rc = check_ct(ctx->c, B)) return rc;
+    return he_hmatmul_batch(&j, 1, out);
+}
+
+int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
+    if (!jobs || !outs || n_jobs < 1) return fail(HE_ERR_ARG, "bad arguments");
+    for (int i = 0; i < n_jobs; i++) {
+        if (!jobs[i].A || !jobs[i].B || jobs[i].A->ctx != jobs[i].B->ctx) return fail(HE_ERR_ARG, "bad job operands");
+        if (int rc = check_sched(*jobs[i].A->ctx, jobs[i].n, &jobs[i].sched)) return rc;
+        if (std::min(jobs[i].A->level, jobs[i].B->level) < 3) return fail(HE_ERR_LEVEL, "a product needs 3 levels");
+        outs[i] = nullptr;
+    }
+    GUARD_BEGIN
+    typedef std::tuple<Ctx *, int, int, int, int, int, int> Key;
+    std::map<Key, std::vector<int>> groups;
+    for (int i = 0; i < n_jobs; i++) {
+        const he_mm_job &j = jobs[i];
+        int lv = std::min(j.A->level, j.B->level);
+        groups[Key(j.A->ctx, lv, j.n, j.sched.n1_z, j.sched.n1_t, j.A->period == j.n * j.n,
+                   j.B->period == j.n * j.n)]
+            .push_back(i);
+    }
+    std::vector<he_ct *> res(n_jobs, nullptr);
+    try {
+        for (auto &kv : groups) {
+            Ctx &c = *std::get<0>(kv.first);
+            int lv = std::get<1>(kv.first);
+            std::vector<const he_ct *> As, Bs;
+            for (int i : kv.second) {
+                As.push_back(jobs[i].A);
+                Bs.push_back(jobs[i].B);
+            }
+            std::vector<he_ct *> o(As.size());
+            const he_mm_job &j0 = jobs[kv.second[0]];
+            run_group(c, As, Bs, j0.n, j0.sched.n1_z, j0.sched.n1_t, lv, o);
+            for (size_t t = 0; t < o.size(); t++) res[kv.second[t]] = o[t];
+        }
+        std::set<Ctx *> ctxs;
+        for (auto &kv : groups) ctxs.insert(std::get<0>(kv.first));
+        for (Ctx *c : ctxs) HE_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        for (Ctx *c : ctxs)
+            if (int rc = cuda_status(c)) throw HeError(rc, last_error());
+    } catch (...) {
+        for (he_ct *o : res) free_ct(o);
+        throw;
+    }
+    for (int i = 0; i < n_jobs; i++) outs[i] = res[i];
+    return HE_OK;
+    GUARD_END
+}
+
+int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, ct)) return rc;
+    he_mm_sched s{n1, n1};
+    if (int rc = check_sched(c, n, &s)) return rc;
+    if (ct->level < 1) return fail(HE_ERR_LEVEL, "transpose needs 1 level");
+    GUARD_BEGIN
+    he_ct *tmp = clone_ct(c, ct);
+    he_ct *o = nullptr;
+    try {
+        if (tmp->period != n * n) replicate(&c, tmp->d, 1, tmp->level, n);
+        o = new_ct(&c, ct->level - 1, ct->scale, n * n);
+        lintrans(&c, tmp->d, 1, ct->level, 2, n, n - 1, n1, -(n / n1), n / n1, prescale, o->d);
+    } catch (...) {
+        free_ct(tmp);
+        free_ct(o);
+        throw;
+    }
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    free_ct(tmp);
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    Ctx &c = ctx->c;
+    if (ms) *ms = c.n_ms;
+    if (dp) *dp = c.n_dp;
+    if (md) *md = c.n_md;
+    if (launches) *launches = c.n_launch;
+    if (reset) c.n_ms = c.n_dp = c.n_md = c.n_launch = 0;
+    return HE_OK;
+}
+
+}  // extern "C"

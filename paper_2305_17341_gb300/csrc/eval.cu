@@ -1,0 +1,311 @@
+// eval.cu -- key switching, rotations, products, rescale, the double-hoisted
+// linear transforms and the JKLS matrix product, all on batches of B
+// ciphertexts laid out contiguously as [B][2][level+1][N] (NTT domain).
+#include <algorithm>
+#include <cmath>
+#include <sstream>
+
+#include "eval.h"
+
+namespace he {
+
+static const size_t W = 1;  // words helper
+
+// ------------------------------------------------------------ key switch
+// Decompose (Sec. 3.3): poly of every item (stride item_s) -> digits
+// [B][ndig][l+1+alpha][N] in the NTT domain.
+void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits) {
+    const int N = c->N, nq = level + 1;
+    Buf coef(&c->pool, (size_t)B * nq * N);
+    launch_copy_rows(coef.p, (long)nq * N, poly, item_s, B, (long)nq * N, c->stream);
+    ntt_inv(c, coef.p, (long)B * nq, c->map_q(level), c->stream);
+    launch_modup_bconv(c, coef.p, digits, B, level, c->stream);
+    ntt_fwd(c, digits, (long)B * c->ndig(level) * c->qp_rows(level), c->map_qp(level), c->stream);
+    c->n_dp += B;
+}
+
+// ModDown: items of [rows][N] over Q_l P (contiguous) -> out items of [l+1][N]
+// with item stride out_s.
+void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s) {
+    const int N = c->N, rows = c->qp_rows(level), a = c->alpha;
+    Buf pc(&c->pool, (size_t)items * a * N), conv(&c->pool, (size_t)items * (level + 1) * N);
+    launch_copy_rows(pc.p, (long)a * N, u + (long)(level + 1) * N, (long)rows * N, items, (long)a * N, c->stream);
+    ntt_inv(c, pc.p, (long)items * a, c->map_p(), c->stream);
+    launch_moddown_bconv(c, pc.p, conv.p, items, level, c->stream);
+    ntt_fwd(c, conv.p, (long)items * (level + 1), c->map_q(level), c->stream);
+    launch_moddown_final(c, out, u, conv.p, nullptr, items, level, (long)rows * N, out_s, 0, c->stream);
+}
+
+const u64 *need_key(Ctx *c, uint32_t g) {
+    auto it = c->rtk.find(g);
+    if (it == c->rtk.end()) {
+        std::ostringstream os;
+        os << "rotation key for Galois element " << g << " missing";
+        throw HeError(HE_ERR_KEY_MISSING, os.str());
+    }
+    return it->second;
+}
+
+// Hoisted rotation kept in Q_l P: u = <kappa_g(digits), rtk_g> + (P kappa_g(c0), 0).
+// ct: [B][2][l+1][N]; out: [B][2][rows][N].
+void rot_qp(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out) {
+    const u64 *key = need_key(c, g);
+    launch_multsum(c, out, digits, key, g, B, level, ct, 2L * (level + 1) * c->N, c->stream);
+    c->n_ms += B;
+}
+
+// Full rotation from precomputed digits: ModDown(rot_qp) = kappa(c0) + ModDown(IP0), ModDown(IP1).
+void rotate_digits(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out) {
+    const int rows = c->qp_rows(level);
+    Buf u(&c->pool, (size_t)B * 2 * rows * c->N);
+    rot_qp(c, ct, B, level, digits, g, u.p);
+    moddown(c, u.p, 2 * B, level, out, (long)(level + 1) * c->N);
+    c->n_md += B;
+}
+
+void rotate(Ctx *c, const u64 *ct, int B, int level, uint32_t g, u64 *out) {
+    const int rows = c->qp_rows(level);
+    Buf dg(&c->pool, (size_t)B * c->ndig(level) * rows * c->N);
+    modup(c, ct + (long)(level + 1) * c->N, 2L * (level + 1) * c->N, B, level, dg.p);
+    rotate_digits(c, ct, B, level, dg.p, g, out);
+}
+
+// Rescale (App. A): [B][2][l+1][N] -> [B][2][l][N], round(c / q_l).
+void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out) {
+    const int N = c->N;
+    if (level < 1) throw HeError(HE_ERR_LEVEL, "rescale at level 0");
+    Buf last(&c->pool, (size_t)2 * B * N), t(&c->pool, (size_t)2 * B * level * N);
+    launch_copy_rows(last.p, N, in + (long)level * N, (long)(level + 1) * N, 2 * B, N, c->stream);
+    RowMap one;
+    one.n = 1;
+    one.p[0] = (unsigned char)level;
+    ntt_inv(c, last.p, 2L * B, one, c->stream);
+    launch_rescale_prep(c, last.p, t.p, 2 * B, level, c->stream);
+    ntt_fwd(c, t.p, 2L * B * level, c->map_q(level - 1), c->stream);
+    launch_rescale_final(c, out, in, t.p, 2 * B, level, (long)(level + 1) * N, (long)level * N, c->stream);
+}
+
+// Level drop: keep limbs 0..to of both polys.
+void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out) {
+    const int N = c->N;
+    launch_copy_rows(out, (long)(to + 1) * N, in, (long)(level + 1) * N, 2 * B, (long)(to + 1) * N, c->stream);
+}
+
+// Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk).
+void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out) {
+    if (!c->rlk) throw HeError(HE_ERR_KEY_MISSING, "relinearisation key missing");
+    const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
+    const long cs = 2L * nq * N;
+    Buf d2(&c->pool, (size_t)B * nq * N);
+    launch_tensor(c, out, d2.p, a, b, B, nq, cs, cs, c->map_q(level), c->stream);
+    Buf dg(&c->pool, (size_t)B * c->ndig(level) * rows * N);
+    modup(c, d2.p, (long)nq * N, B, level, dg.p);
+    Buf u(&c->pool, (size_t)B * 2 * rows * N), md(&c->pool, (size_t)B * 2 * nq * N);
+    launch_multsum(c, u.p, dg.p, c->rlk, 1u, B, level, nullptr, 0, c->stream);
+    c->n_ms += B;
+    moddown(c, u.p, 2 * B, level, md.p, (long)nq * N);
+    c->n_md += B;
+    launch_add(c, out, out, md.p, 2L * B * nq, c->map_q(level), c->stream);
+}
+
+void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out) {
+    launch_add(c, out, a, b, 2L * B * (level + 1), c->map_q(level), c->stream);
+}
+
+// --------------------------------------------------- plaintext diagonals
+// Cached encodings (NTT, Montgomery) over Q_l P of a diagonal slot vector at
+// scale q_l.  kind/n/t/rot/value/k as in k_diag_fill.
+const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level) {
+    std::ostringstream os;
+    os << kind << ':' << n << ':' << t << ':' << rot << ':' << k << ':' << level << ':';
+    os.precision(17);
+    os << value;
+    std::string key = os.str();
+    auto it = c->ptcache.find(key);
+    if (it != c->ptcache.end()) return it->second;
+    const int N = c->N, rows = c->qp_rows(level);
+    u64 *pt = nullptr;
+    if (cudaMalloc(&pt, (size_t)rows * N * 8) != cudaSuccess) {
+        cudaGetLastError();
+        throw HeError(HE_ERR_OOM, "plaintext cache allocation failed");
+    }
+    Buf zr(&c->pool, c->S), zi(&c->pool, c->S), m(&c->pool, N);
+    launch_diag_fill(c, (double *)zr.p, kind, n, t, rot, value, k, c->stream);
+    cudaMemsetAsync(zi.p, 0, (size_t)c->S * 8, c->stream);
+    launch_encode(c, (double *)zr.p, (double *)zi.p, (double)c->primes[level], (i64 *)m.p, c->stream);
+    RowMap qp = c->map_qp(level);
+    launch_small_to_rns(c, (const i64 *)m.p, pt, rows, qp, c->stream);
+    ntt_fwd(c, pt, rows, qp, c->stream);
+    launch_to_mont(c, pt, pt, rows, qp, c->stream);
+    c->ptcache[key] = pt;
+    c->ptcache_bytes += (size_t)rows * N * 8;
+    return pt;
+}
+
+// Does diagonal `t` of transform `kind` hold a non-zero entry?
+static bool diag_nonzero(int kind, int n, long t) {
+    switch (kind) {
+    case 0: return t > -n && t < n;                         // Z, eq. 5
+    case 1: return t >= 0 && t % n == 0 && t / n < n;       // T, eq. 6
+    case 2: {                                                // G, (n-1) k
+        long a = n - 1;
+        if (a == 0) return t == 0;
+        if (t % a != 0) return false;
+        long kk = t / a;
+        return kk > -n && kk < n;
+    }
+    }
+    return false;
+}
+
+static long mod_pos(long x, long m) { return ((x % m) + m) % m; }
+
+// Double-hoisted BSGS linear transform (eq. 3', Sec. 3.3):
+//   U m = sum_i rho( sum_j rho(u_{a(n1 i + j)}; -a n1 i) . rho(m; a j) ; a n1 i ),
+// babies kept in Q_l P from one Decompose; giant groups summed in Q_l P,
+// ModDown'd, rotated (kept in Q_l P) and accumulated; one final ModDown and a
+// rescale by q_l (plaintexts at scale q_l keep the ciphertext scale).
+// in: [B][2][l+1][N]; out: [B][2][l][N].
+void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
+              double value, u64 *out) {
+    const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
+    const long n2 = (long)n * n;
+    const size_t qpct = (size_t)2 * rows * N;   // one item over Q_l P
+    Buf dg(&c->pool, (size_t)B * c->ndig(level) * rows * N);
+    modup(c, in + (long)nq * N, 2L * nq * N, B, level, dg.p);
+    std::vector<Buf> R;
+    R.emplace_back(&c->pool, B * qpct);
+    launch_lift_P(c, R[0].p, in, 2 * B, level, (long)nq * N, (long)rows * N, c->stream);
+    for (int j = 1; j < n1; j++) {
+        R.emplace_back(&c->pool, B * qpct);
+        rot_qp(c, in, B, level, dg.p, galois_of_step(c, mod_pos(a * j, n2)), R[j].p);
+    }
+    Buf acc(&c->pool, B * qpct), S(&c->pool, B * qpct), ctmp(&c->pool, (size_t)B * 2 * nq * N),
+        dg2(&c->pool, (size_t)B * c->ndig(level) * rows * N), T(&c->pool, B * qpct);
+    bool have = false;
+    RowMap qp = c->map_qp(level);
+    for (int i = gi0; i < gi1; i++) {
+        std::vector<const u64 *> pts, Rs;
+        for (int j = 0; j < n1; j++) {
+            long t = a * ((long)n1 * i + j);
+            if (!diag_nonzero(kind, n, t)) continue;
+            pts.push_back(get_pt(c, kind, n, t, mod_pos(-a * n1 * i, n2), value, 0, level));
+            Rs.push_back(R[j].p);
+        }
+        if (pts.empty()) continue;
+        launch_pmul_acc(c, S.p, pts.data(), Rs.data(), (int)pts.size(), B, level, (long)qpct, c->stream);
+        const u64 *term = S.p;
+        if (i != 0) {
+            moddown(c, S.p, 2 * B, level, ctmp.p, (long)nq * N);
+            c->n_md += B;
+            modup(c, ctmp.p + (long)nq * N, 2L * nq * N, B, level, dg2.p);
+            rot_qp(c, ctmp.p, B, level, dg2.p, galois_of_step(c, mod_pos(a * n1 * i, n2)), T.p);
+            term = T.p;
+        }
+        if (!have) {
+            cudaMemcpyAsync(acc.p, term, B * qpct * 8, cudaMemcpyDeviceToDevice, c->stream);
+            have = true;
+        } else {
+            launch_add(c, acc.p, acc.p, term, 2L * B * rows, qp, c->stream);
+        }
+    }
+    moddown(c, acc.p, 2 * B, level, ctmp.p, (long)nq * N);
+    c->n_md += B;
+    rescale(c, ctmp.p, B, level, out);
+}
+
+// ct <- ct + Rot(ct, -n^2 2^j) for j = 0 .. log2(S/n^2)-1 (period n^2).
+void replicate(Ctx *c, u64 *ct, int B, int level, int n) {
+    const long n2 = (long)n * n;
+    Buf r(&c->pool, (size_t)B * 2 * (level + 1) * c->N);
+    for (long s = n2; s < c->S; s *= 2) {
+        rotate(c, ct, B, level, galois_of_step(c, c->S - s), r.p);
+        add(c, ct, r.p, B, level, ct);
+    }
+}
+
+// JKLS product (eq. 4) with the hoisting of Sec. 4.1; A, B: [Bn][2][l+1][N]
+// replicated with period n^2; out: [Bn][2][l-2][N].
+void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out) {
+    if (level < 3) throw HeError(HE_ERR_LEVEL, "matrix product needs 3 levels");
+    const int N = c->N;
+    const long n2m = (long)n * n;
+    const int l1 = level - 1, l2 = level - 2;
+    const size_t ct1 = (size_t)2 * (l1 + 1) * N, ct2 = (size_t)2 * (l2 + 1) * N;
+    const int rows1 = c->qp_rows(l1);
+    const size_t qp1 = (size_t)2 * rows1 * N, dig1 = (size_t)c->ndig(l1) * rows1 * N;
+    Buf A0(&c->pool, Bn * ct1), B0(&c->pool, Bn * ct1);
+    lintrans(c, A, Bn, level, 0, n, 1, n1z, -(n / n1z), n / n1z, 1.0, A0.p);
+    lintrans(c, Bm, Bn, level, 1, n, n, n1t, 0, n / n1t, 1.0, B0.p);
+
+    // C^k sources A_g, A'_g and R^k sources B_g with their digits
+    Buf Ag(&c->pool, Bn * ct1), Apg(&c->pool, Bn * ct1), Bg(&c->pool, Bn * ct1);
+    Buf dA(&c->pool, Bn * dig1), dAp(&c->pool, Bn * dig1), dB(&c->pool, Bn * dig1), tmp(&c->pool, Bn * ct1);
+    cudaMemcpyAsync(Ag.p, A0.p, Bn * ct1 * 8, cudaMemcpyDeviceToDevice, c->stream);
+    modup(c, Ag.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dA.p);
+    rotate_digits(c, Ag.p, Bn, l1, dA.p, galois_of_step(c, mod_pos(-n, n2m)), Apg.p);
+    modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dAp.p);
+    cudaMemcpyAsync(Bg.p, B0.p, Bn * ct1 * 8, cudaMemcpyDeviceToDevice, c->stream);
+    modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dB.p);
+    int gA = 0, gB = 0;
+
+    Buf acc(&c->pool, Bn * ct2), Ak(&c->pool, Bn * ct2), Bk(&c->pool, Bn * ct2), prod(&c->pool, Bn * ct2);
+    Buf R1(&c->pool, Bn * qp1), R2(&c->pool, Bn * qp1), S(&c->pool, Bn * qp1), Akp(&c->pool, Bn * ct1),
+        Bkf(&c->pool, Bn * ct1);
+    RowMap q2 = c->map_q(l2);
+    for (int k = 0; k < n; k++) {
+        // ---- A^(k) = C^k A^(0) at level l2
+        int g = k / n1z, b = k % n1z;
+        while (gA < g) {
+            rotate_digits(c, Ag.p, Bn, l1, dA.p, galois_of_step(c, n1z % n2m), tmp.p);
+            std::swap(Ag, tmp);
+            modup(c, Ag.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dA.p);
+            rotate_digits(c, Apg.p, Bn, l1, dAp.p, galois_of_step(c, n1z % n2m), tmp.p);
+            std::swap(Apg, tmp);
+            modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dAp.p);
+            gA++;
+        }
+        if (k == 0) {
+            drop(c, A0.p, Bn, l1, l2, Ak.p);
+        } else {
+            if (b == 0) {
+                launch_lift_P(c, R1.p, Ag.p, 2 * Bn, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
+                launch_lift_P(c, R2.p, Apg.p, 2 * Bn, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
+            } else {
+                uint32_t gb = galois_of_step(c, b % n2m);
+                rot_qp(c, Ag.p, Bn, l1, dA.p, gb, R1.p);
+                rot_qp(c, Apg.p, Bn, l1, dAp.p, gb, R2.p);
+            }
+            const u64 *pts[2] = {get_pt(c, 3, n, 0, 0, 1.0, k, l1), get_pt(c, 4, n, 0, 0, 1.0, k, l1)};
+            const u64 *Rs[2] = {R1.p, R2.p};
+            launch_pmul_acc(c, S.p, pts, Rs, 2, Bn, l1, (long)qp1, c->stream);
+            moddown(c, S.p, 2 * Bn, l1, Akp.p, (long)(l1 + 1) * N);
+            c->n_md += Bn;
+            rescale(c, Akp.p, Bn, l1, Ak.p);
+        }
+        // ---- B^(k) = R^k B^(0), dropped to l2
+        int gb2 = k / n1t, bb = k % n1t;
+        while (gB < gb2) {
+            rotate_digits(c, Bg.p, Bn, l1, dB.p, galois_of_step(c, ((long)n * n1t) % n2m), tmp.p);
+            std::swap(Bg, tmp);
+            modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dB.p);
+            gB++;
+        }
+        if (bb == 0) {
+            drop(c, Bg.p, Bn, l1, l2, Bk.p);
+        } else {
+            rotate_digits(c, Bg.p, Bn, l1, dB.p, galois_of_step(c, ((long)n * bb) % n2m), Bkf.p);
+            drop(c, Bkf.p, Bn, l1, l2, Bk.p);
+        }
+        // ---- product, relinearised, accumulated at level l2
+        if (k == 0) {
+            mult_relin(c, Ak.p, Bk.p, Bn, l2, acc.p);
+        } else {
+            mult_relin(c, Ak.p, Bk.p, Bn, l2, prod.p);
+            launch_add(c, acc.p, acc.p, prod.p, 2L * Bn * (l2 + 1), q2, c->stream);
+        }
+    }
+    rescale(c, acc.p, Bn, l2, out);
+}
+
+}  // namespace he

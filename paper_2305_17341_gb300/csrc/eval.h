@@ -1,0 +1,37 @@
+// eval.h -- batched evaluation routines (see eval.cu).
+#pragma once
+#include <stdexcept>
+
+#include "he_internal.h"
+
+namespace he {
+
+struct HeError : std::runtime_error {
+    int code;
+    HeError(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+uint32_t galois_of_step(const Ctx *c, long step);
+void create_keys(Ctx *c);
+u64 *gen_rotation_key(Ctx *c, uint32_t g);
+u64 *gen_relin_key(Ctx *c);
+void encrypt_poly(Ctx *c, const u64 *m_ntt, int level, uint32_t obj, bool refresh, u64 *out);
+void encode_to(Ctx *c, const double *d_zr, const double *d_zi, double scale, u64 *out, int rows, const RowMap &rm);
+const char *last_error();
+
+void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits);
+void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s);
+void rot_qp(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out);
+void rotate_digits(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out);
+void rotate(Ctx *c, const u64 *ct, int B, int level, uint32_t g, u64 *out);
+void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out);
+void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out);
+void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
+void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
+const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level);
+void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
+              double value, u64 *out);
+void replicate(Ctx *c, u64 *ct, int B, int level, int n);
+void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out);
+
+}  // namespace he

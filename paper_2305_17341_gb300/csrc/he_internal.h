@@ -1,0 +1,219 @@
+// he_internal.h -- internal declarations of the GB300 RNS-CKKS library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/he.h"
+#include "modarith.cuh"
+
+namespace he {
+
+// Row -> global prime index map (row r uses prime p[r % n]); passed by value.
+struct RowMap {
+    int n;
+    unsigned char p[60];
+    __host__ __device__ RowMap shifted(long r0) const {
+        RowMap m = *this;
+        for (int k = 0; k < n; k++) m.p[k] = p[(k + r0) % n];
+        return m;
+    }
+};
+
+// Device pool with size-class free lists (no cudaMalloc/cudaFree in steady state).
+class DevicePool {
+public:
+    void *get(size_t bytes);
+    void put(void *p);
+    void release_all();
+    size_t bytes_in_use() const { return in_use_; }
+    size_t bytes_cached() const { return cached_; }
+    ~DevicePool() { release_all(); }
+
+private:
+    std::multimap<size_t, void *> free_;
+    std::map<void *, size_t> sizes_;
+    size_t in_use_ = 0, cached_ = 0;
+};
+
+// Scratch buffer handle returned to the pool on scope exit.
+struct Buf {
+    DevicePool *pool = nullptr;
+    u64 *p = nullptr;
+    Buf() = default;
+    Buf(DevicePool *pl, size_t words) : pool(pl), p((u64 *)pl->get(words * 8)) {}
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    Buf(Buf &&o) noexcept : pool(o.pool), p(o.p) { o.p = nullptr; }
+    Buf &operator=(Buf &&o) noexcept {
+        if (p) pool->put(p);
+        pool = o.pool; p = o.p; o.p = nullptr;
+        return *this;
+    }
+    ~Buf() { if (p) pool->put(p); }
+};
+
+struct ShoupPair {
+    u64 w, wp;
+};
+
+// Constants of one level l (limbs q_0..q_l, then p's).
+struct LevelConsts {
+    int level = -1;
+    int ndig = 0;
+    // ModUp: per digit d, per source i (alpha max), qhat_inv (pair); per target row r, qhat_mod[d][i][r]
+    ShoupPair *d_up_inv = nullptr;   // [ndig][alpha]
+    ShoupPair *d_up_mod = nullptr;   // [ndig][alpha][l+1+alpha]
+    // Rescale by q_l: q_l^-1 mod q_i, q_l mod q_i (i < l)
+    ShoupPair *d_rs_inv = nullptr;   // [l]
+    u64 *d_rs_qlmod = nullptr;       // [l]
+};
+
+struct Ctx {
+    he_params prm;
+    int logN, N, S, L, alpha, dnum, nprimes;
+    std::vector<u64> primes;       // q_0..q_L, p_0..p_{alpha-1}
+    std::vector<ModQ> hmod;
+    u64 seed;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+
+    ModQ *d_mod = nullptr;         // [nprimes]
+    u64 *d_psi = nullptr, *d_psip = nullptr, *d_ipsi = nullptr, *d_ipsip = nullptr;  // [nprimes][N]
+    u64 *d_ninv = nullptr;         // [nprimes][2]
+    // ModDown constants (level independent)
+    ShoupPair *d_dn_pinv = nullptr;  // [alpha]   (P/p_j)^-1 mod p_j
+    ShoupPair *d_dn_pmod = nullptr;  // [alpha][L+1] (P/p_j) mod q_r
+    ShoupPair *d_dn_Pinv = nullptr;  // [L+1]     P^-1 mod q_r
+    ShoupPair *d_Pmod = nullptr;     // [L+1]     P mod q_r
+    std::vector<LevelConsts> lvl;
+
+    // encoder tables
+    double *d_zeta = nullptr;      // [2N][2] (cos, sin) of pi e / N
+    int *d_slot_t = nullptr;       // [S] t(j) = (5^j mod 2N - 1) / 4
+    u64 gauss_T[20];
+
+    // keys (NTT domain): secret key in normal and Montgomery form over all primes
+    u64 *d_sk = nullptr, *d_skM = nullptr;  // [nprimes][N]
+    u64 *d_pkM = nullptr;                   // [2][L+1][N] Montgomery
+    std::map<uint32_t, u64 *> rtk;          // galois -> [dnum][2][nprimes][N] Montgomery
+    u64 *rlk = nullptr;
+
+    // cached plaintext diagonals (NTT, Montgomery, over Q_l P), keyed by a string id
+    std::map<std::string, u64 *> ptcache;
+    size_t ptcache_bytes = 0;
+
+    DevicePool pool;
+    std::mutex mu;
+
+    // instrumentation
+    long long n_ms = 0, n_dp = 0, n_md = 0, n_launch = 0;
+    bool count_launch = false;
+
+    // helpers
+    int qp_rows(int level) const { return level + 1 + alpha; }
+    int ndig(int level) const { return (level + 1 + alpha - 1) / alpha; }
+    size_t key_words() const { return (size_t)dnum * 2 * nprimes * N; }
+    RowMap map_q(int level) const {
+        RowMap m; m.n = level + 1;
+        for (int i = 0; i <= level; i++) m.p[i] = (unsigned char)i;
+        return m;
+    }
+    RowMap map_qp(int level) const {
+        RowMap m; m.n = level + 1 + alpha;
+        for (int i = 0; i <= level; i++) m.p[i] = (unsigned char)i;
+        for (int j = 0; j < alpha; j++) m.p[level + 1 + j] = (unsigned char)(L + 1 + j);
+        return m;
+    }
+    RowMap map_p() const {
+        RowMap m; m.n = alpha;
+        for (int j = 0; j < alpha; j++) m.p[j] = (unsigned char)(L + 1 + j);
+        return m;
+    }
+    const LevelConsts &lc(int level);
+};
+
+// A ciphertext in the NTT domain: data [2][level+1][N], scale, slot period.
+struct Ct {
+    Ctx *ctx = nullptr;
+    u64 *d = nullptr;
+    int level = 0;
+    double scale = 1.0;
+    int period = 0;
+};
+
+// error handling
+void set_error(const std::string &msg);
+#define HE_CUDA_CHECK(expr)                                                          \
+    do {                                                                             \
+        cudaError_t e__ = (expr);                                                    \
+        if (e__ != cudaSuccess) {                                                    \
+            he::set_error(std::string("CUDA error: ") + cudaGetErrorString(e__) +     \
+                          " at " + __FILE__ + ":" + std::to_string(__LINE__));       \
+            return HE_ERR_CUDA;                                                      \
+        }                                                                            \
+    } while (0)
+
+// host number theory
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_invmod(u64 a, u64 q);
+ShoupPair h_shoup(u64 w, u64 q);
+int h_gen_primes(int logN, int nq, const int *qbits, int np, const int *pbits, u64 *q, u64 *p);
+
+// NTT
+void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st);
+void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st);
+
+// ---- kernels.cu launchers (all asynchronous on st) ----
+void launch_sample_uniform(Ctx *c, u64 *out, int rows, const RowMap &rm, const int *limb_id, uint32_t obj,
+                           uint32_t tag, cudaStream_t st);
+void launch_sample_small(Ctx *c, i64 *out, int kind /*0 ternary 1 gauss*/, uint32_t obj, uint32_t tag,
+                         cudaStream_t st);
+void launch_small_to_rns(Ctx *c, const i64 *x, u64 *out, int rows, const RowMap &rm, cudaStream_t st);
+void launch_encode(Ctx *c, const double *zre, const double *zim, double scale, i64 *m_out,
+                   cudaStream_t st);
+void launch_decode(Ctx *c, const double *coef, double scale, double *zre, double *zim, cudaStream_t st);
+// elementwise over rows with a RowMap
+void launch_add(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st);
+void launch_sub(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st);
+void launch_neg(Ctx *c, u64 *out, const u64 *a, long rows, const RowMap &rm, cudaStream_t st);
+void launch_mul(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st);
+void launch_mulM(Ctx *c, u64 *out, const u64 *a, const u64 *bM, long rows, const RowMap &rm,
+                 cudaStream_t st);
+void launch_to_mont(Ctx *c, u64 *out, const u64 *a, long rows, const RowMap &rm, cudaStream_t st);
+void launch_from_mont(Ctx *c, u64 *out, const u64 *a, long rows, const RowMap &rm, cudaStream_t st);
+void launch_mulconst_rows(Ctx *c, u64 *out, const u64 *a, const ShoupPair *w, long rows, int rows_per_item,
+                          const RowMap &rm, cudaStream_t st);
+void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &rm, uint32_t g,
+                      cudaStream_t st);
+void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long a_item_stride,
+                   long b_item_stride, const RowMap &rm, cudaStream_t st);
+// key switching pieces
+void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st);
+void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st);
+void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const u64 *addend, int items,
+                          int level, long u_item_stride, long out_item_stride, long add_item_stride,
+                          cudaStream_t st);
+void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_t g, int B, int level,
+                    const u64 *c0_for_P, long c0_item_stride, cudaStream_t st);
+void launch_pmul_acc(Ctx *c, u64 *out, const u64 *const *pts, const u64 *const *R, int nterms, int B,
+                     int level, long R_item_stride, cudaStream_t st);
+void launch_lift_P(Ctx *c, u64 *out_qp, const u64 *in_q, int items, int level, long in_item_stride,
+                   long out_item_stride, cudaStream_t st);
+void launch_rescale_prep(Ctx *c, const u64 *lastcoef, u64 *out, int items, int level, cudaStream_t st);
+void launch_rescale_final(Ctx *c, u64 *out, const u64 *in, const u64 *t, int items, int level,
+                          long in_item_stride, long out_item_stride, cudaStream_t st);
+void launch_dec_q0(Ctx *c, const u64 *c0, const u64 *c1, u64 *out, cudaStream_t st);
+void launch_centre_q0(Ctx *c, const u64 *a, double *out, cudaStream_t st);
+void launch_diag_fill(Ctx *c, double *out, int kind, int n, long t, long rot, double value, int k,
+                      cudaStream_t st);
+void launch_copy_rows(u64 *dst, long dst_stride, const u64 *src, long src_stride, int items, long words,
+                      cudaStream_t st);
+
+}  // namespace he

@@ -1,0 +1,630 @@
+// kernels.cu -- element-wise, sampling, encoding and key-switching kernels.
+//
+// Layouts: a polynomial is [limbs][N] u64 (limb-major, coalesced along N);
+// a ciphertext is [2][level+1][N]; an extended polynomial over Q_l P has
+// rows q_0..q_l then p_0..p_{alpha-1}; a batch of B items is contiguous.
+#include <cmath>
+
+#include "he_internal.h"
+
+namespace he {
+
+static inline unsigned nblk(long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// --------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// (multipliers 0xD2511F53, 0xCD9E8D57) with the key bumped by the Weyl
+// constants 0x9E3779B9, 0xBB67AE85 between rounds.
+__device__ __forceinline__ void philox4x32_10(u32 c[4], u32 k0, u32 k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        u32 lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        u32 lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        u32 n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+// uniform residue of limb (global prime index) j at coefficient i:
+// block (i, j, obj, tag) read as hi64:lo64 = (w3 w2):(w1 w0), reduced mod q.
+__global__ void k_sample_uniform(u64 *out, long rows, int N, RowMap rm, const ModQ *mods, u32 obj, u32 tag,
+                                 u32 k0, u32 k1) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * N) return;
+    long row = idx / N;
+    int i = (int)(idx - row * N);
+    int pidx = rm.p[row % rm.n];
+    u32 c[4] = {(u32)i, (u32)pidx, obj, tag};
+    philox4x32_10(c, k0, k1);
+    u64 lo = (u64)c[0] | ((u64)c[1] << 32);
+    u64 hi = (u64)c[2] | ((u64)c[3] << 32);
+    out[idx] = mod128(hi, lo, mods[pidx]);
+}
+
+struct GaussT {
+    u64 T[20];
+};
+
+// kind 0: ternary from w0 mod 3 -> {0, 1, -1}; kind 1: discrete Gaussian by
+// inversion of the cumulative table T on r = (w1:w0) >> 1, sign = w2 bit 0.
+__global__ void k_sample_small(i64 *out, int N, int kind, GaussT gt, u32 obj, u32 tag, u32 k0, u32 k1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    u32 c[4] = {(u32)i, 0u, obj, tag};
+    philox4x32_10(c, k0, k1);
+    if (kind == 0) {
+        u32 r = c[0] % 3u;
+        out[i] = r == 0 ? 0 : (r == 1 ? 1 : -1);
+    } else {
+        u64 r = (((u64)c[1] << 32) | (u64)c[0]) >> 1;
+        int k = 0;
+        while (k < 19 && r >= gt.T[k]) k++;
+        i64 x = k;
+        if (x != 0 && (c[2] & 1u)) x = -x;
+        out[i] = x;
+    }
+}
+
+__global__ void k_small_to_rns(const i64 *x, u64 *out, long rows, int N, RowMap rm, const ModQ *mods) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * N) return;
+    long row = idx / N;
+    int i = (int)(idx - row * N);
+    out[idx] = from_signed(x[i], mods[rm.p[row % rm.n]].q);
+}
+
+void launch_sample_uniform(Ctx *c, u64 *out, int rows, const RowMap &rm, const int *, uint32_t obj,
+                           uint32_t tag, cudaStream_t st) {
+    long n = (long)rows * c->N;
+    k_sample_uniform<<<nblk(n, 256), 256, 0, st>>>(out, rows, c->N, rm, c->d_mod, obj, tag, (u32)c->seed,
+                                                   (u32)(c->seed >> 32));
+}
+
+void launch_sample_small(Ctx *c, i64 *out, int kind, uint32_t obj, uint32_t tag, cudaStream_t st) {
+    GaussT gt;
+    for (int k = 0; k < 20; k++) gt.T[k] = c->gauss_T[k];
+    k_sample_small<<<nblk(c->N, 256), 256, 0, st>>>(out, c->N, kind, gt, obj, tag, (u32)c->seed,
+                                                   (u32)(c->seed >> 32));
+}
+
+void launch_small_to_rns(Ctx *c, const i64 *x, u64 *out, int rows, const RowMap &rm, cudaStream_t st) {
+    long n = (long)rows * c->N;
+    k_small_to_rns<<<nblk(n, 256), 256, 0, st>>>(x, out, rows, c->N, rm, c->d_mod);
+}
+
+// ------------------------------------------------------ encode / decode
+// Inverse canonical embedding (App. A Encode) evaluated in a fixed order so
+// that the integer plaintext is reproducible: slot j goes to position
+// t = (5^j mod 2N - 1)/4, bit-reversal, radix-2 DIT passes with roots
+// conj(zeta^(4 k S/len)), twist by conj(zeta^i), scale by `scale`/S, round
+// half away from zero.  Explicit _rn intrinsics: no contraction into FMA.
+__device__ __forceinline__ int brev_bits(int x, int bits) { return (int)(__brev((unsigned)x) >> (32 - bits)); }
+
+__global__ void k_enc_permute(const double *zr, const double *zi, double *xr, double *xi, const int *slot_t,
+                              int S, int logS) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= S) return;
+    int t = brev_bits(slot_t[j], logS);
+    xr[t] = zr[j];
+    xi[t] = zi[j];
+}
+
+__global__ void k_dft_pass(double *xr, double *xi, const double *zeta, int S, int len, int sign) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int half = len >> 1;
+    if (e >= S / 2) return;
+    int s = (e / half) * len, k = e % half;
+    int ex = k * (4 * (S / len));
+    double wr = zeta[2 * ex], wi = zeta[2 * ex + 1];
+    if (sign < 0) wi = -wi;
+    double br = xr[s + k + half], bi = xi[s + k + half];
+    double tr = __dsub_rn(__dmul_rn(br, wr), __dmul_rn(bi, wi));
+    double ti = __dadd_rn(__dmul_rn(br, wi), __dmul_rn(bi, wr));
+    double ar = xr[s + k], ai = xi[s + k];
+    xr[s + k] = __dadd_rn(ar, tr);
+    xi[s + k] = __dadd_rn(ai, ti);
+    xr[s + k + half] = __dsub_rn(ar, tr);
+    xi[s + k + half] = __dsub_rn(ai, ti);
+}
+
+__global__ void k_enc_final(const double *xr, const double *xi, const double *zeta, double f, i64 *m, int S) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    double wr = zeta[2 * i], wi = -zeta[2 * i + 1];
+    double yr = __dsub_rn(__dmul_rn(xr[i], wr), __dmul_rn(xi[i], wi));
+    double yi = __dadd_rn(__dmul_rn(xr[i], wi), __dmul_rn(xi[i], wr));
+    m[i] = (i64)round(__dmul_rn(yr, f));
+    m[i + S] = (i64)round(__dmul_rn(yi, f));
+}
+
+// Decode (App. A): x_i = u_i zeta^i with u_i = (m_i + I m_{i+S}) / scale,
+// length-S DFT with exponent +1, slot j = x[t(j)].
+__global__ void k_dec_twist(const double *coef, double scale, const double *zeta, double *xr, double *xi, int S,
+                            int logS) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S) return;
+    double ur = coef[i] / scale, ui = coef[i + S] / scale;
+    double wr = zeta[2 * i], wi = zeta[2 * i + 1];
+    int t = brev_bits(i, logS);
+    xr[t] = ur * wr - ui * wi;
+    xi[t] = ur * wi + ui * wr;
+}
+
+__global__ void k_dec_gather(const double *xr, const double *xi, const int *slot_t, double *zr, double *zi, int S) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= S) return;
+    zr[j] = xr[slot_t[j]];
+    zi[j] = xi[slot_t[j]];
+}
+
+void launch_encode(Ctx *c, const double *zre, const double *zim, double scale, i64 *m_out, cudaStream_t st) {
+    int S = c->S, logS = c->logN - 1;
+    Buf tmp(&c->pool, (size_t)S), tmp2(&c->pool, (size_t)S);  // S doubles each
+    double *xr = (double *)tmp.p, *xi = (double *)tmp2.p;
+    k_enc_permute<<<nblk(S, 256), 256, 0, st>>>(zre, zim, xr, xi, c->d_slot_t, S, logS);
+    for (int len = 2; len <= S; len <<= 1)
+        k_dft_pass<<<nblk(S / 2, 256), 256, 0, st>>>(xr, xi, c->d_zeta, S, len, -1);
+    double f = scale / (double)S;
+    k_enc_final<<<nblk(S, 256), 256, 0, st>>>(xr, xi, c->d_zeta, f, m_out, S);
+}
+
+void launch_decode(Ctx *c, const double *coef, double scale, double *zre, double *zim, cudaStream_t st) {
+    int S = c->S, logS = c->logN - 1;
+    Buf tmp(&c->pool, (size_t)S);
+    Buf tmp2(&c->pool, (size_t)S);
+    double *xr = (double *)tmp.p, *xi = (double *)tmp2.p;
+    k_dec_twist<<<nblk(S, 256), 256, 0, st>>>(coef, scale, c->d_zeta, xr, xi, S, logS);
+    for (int len = 2; len <= S; len <<= 1)
+        k_dft_pass<<<nblk(S / 2, 256), 256, 0, st>>>(xr, xi, c->d_zeta, S, len, +1);
+    k_dec_gather<<<nblk(S, 256), 256, 0, st>>>(xr, xi, c->d_slot_t, zre, zim, S);
+}
+
+// ----------------------------------------------------------- elementwise
+#define EW_PROLOGUE                                                   \
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;           \
+    if (idx >= rows * (long)N) return;                                \
+    long row = idx / N;                                               \
+    const ModQ &m = mods[rm.p[row % rm.n]];                           \
+    (void)m;
+
+__global__ void k_add(u64 *o, const u64 *a, const u64 *b, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    o[idx] = addmod(a[idx], b[idx], m.q);
+}
+__global__ void k_sub(u64 *o, const u64 *a, const u64 *b, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    o[idx] = submod(a[idx], b[idx], m.q);
+}
+__global__ void k_neg(u64 *o, const u64 *a, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    u64 v = a[idx];
+    o[idx] = v ? m.q - v : 0;
+}
+__global__ void k_mul(u64 *o, const u64 *a, const u64 *b, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    o[idx] = mulmod(a[idx], b[idx], m);
+}
+__global__ void k_mulM(u64 *o, const u64 *a, const u64 *bM, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    o[idx] = mulmont(a[idx], bM[idx], m);
+}
+__global__ void k_to_mont(u64 *o, const u64 *a, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    o[idx] = mulmont(a[idx], m.r2, m);  // a R^2 R^-1 = a R
+}
+__global__ void k_from_mont(u64 *o, const u64 *a, long rows, int N, RowMap rm, const ModQ *mods) {
+    EW_PROLOGUE
+    o[idx] = redc(a[idx], 0, m);
+}
+
+#define EW_LAUNCH(kern, ...)                                                         \
+    do {                                                                             \
+        long n__ = rows * (long)c->N;                                                \
+        if (n__ > 0) kern<<<nblk(n__, 256), 256, 0, st>>>(__VA_ARGS__, rows, c->N, rm, c->d_mod); \
+    } while (0)
+
+void launch_add(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_add, out, a, b);
+}
+void launch_sub(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_sub, out, a, b);
+}
+void launch_neg(Ctx *c, u64 *out, const u64 *a, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_neg, out, a);
+}
+void launch_mul(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_mul, out, a, b);
+}
+void launch_mulM(Ctx *c, u64 *out, const u64 *a, const u64 *bM, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_mulM, out, a, bM);
+}
+void launch_to_mont(Ctx *c, u64 *out, const u64 *a, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_to_mont, out, a);
+}
+void launch_from_mont(Ctx *c, u64 *out, const u64 *a, long rows, const RowMap &rm, cudaStream_t st) {
+    EW_LAUNCH(k_from_mont, out, a);
+}
+
+// out[row] = a[row] * w[row % rows_per_item] (Shoup constant per row)
+__global__ void k_mulconst_rows(u64 *o, const u64 *a, const ShoupPair *w, int rpi, long rows, int N, RowMap rm,
+                                const ModQ *mods) {
+    EW_PROLOGUE
+    ShoupPair s = w[row % rpi];
+    o[idx] = shoup(a[idx], s.w, s.wp, m.q);
+}
+void launch_mulconst_rows(Ctx *c, u64 *out, const u64 *a, const ShoupPair *w, long rows, int rpi,
+                          const RowMap &rm, cudaStream_t st) {
+    long n = rows * (long)c->N;
+    if (n > 0)
+        k_mulconst_rows<<<nblk(n, 256), 256, 0, st>>>(out, a, w, rpi, rows, c->N, rm, c->d_mod);
+}
+
+// NTT-domain index of the automorphism X -> X^g: output slot x (evaluation
+// point psi^(2 brv(x)+1)) reads input slot brv(((2 brv(x)+1) g mod 2N - 1)/2).
+__device__ __forceinline__ int auto_index(int x, u32 g, int logN) {
+    int N = 1 << logN;
+    u32 e = 2u * (u32)brev_bits(x, logN) + 1u;
+    u32 e2 = (u32)(((u64)e * g) & (u64)(2 * N - 1));
+    return brev_bits((int)((e2 - 1) >> 1), logN);
+}
+
+__global__ void k_automorph(u64 *o, const u64 *in, long rows, int logN, u32 g) {
+    int N = 1 << logN;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * (long)N) return;
+    long row = idx / N;
+    int x = (int)(idx - row * N);
+    o[idx] = in[row * N + auto_index(x, g, logN)];
+}
+void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &, uint32_t g, cudaStream_t st) {
+    long n = rows * (long)c->N;
+    if (n > 0) k_automorph<<<nblk(n, 256), 256, 0, st>>>(out, in, rows, c->logN, g);
+}
+
+// tensor product in the NTT domain: d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1.
+// d01: [B][2][limbs][N] (d0, d1 of each item); d2: [B][limbs][N].
+__global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, int N,
+                         long as, long bs, RowMap rm, const ModQ *mods) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long per = (long)limbs * N;
+    if (idx >= (long)B * per) return;
+    int it = (int)(idx / per);
+    long off = idx - (long)it * per;
+    int limb = (int)(off / N);
+    const ModQ &m = mods[rm.p[limb]];
+    const u64 *pa = a + it * as, *pb = b + it * bs;
+    u64 a0 = pa[off], a1 = pa[per + off], b0 = pb[off], b1 = pb[per + off];
+    U128 acc = {0, 0};
+    mac128(acc, a0, b1);
+    mac128(acc, a1, b0);
+    u64 t1 = redc(acc.lo, acc.hi, m);
+    u64 *o = d01 + (long)it * 2 * per + off;
+    o[0] = mulmod(a0, b0, m);
+    o[per] = redc(t1 * m.r2, mulhi64(t1, m.r2), m);
+    d2[(long)it * per + off] = mulmod(a1, b1, m);
+}
+void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
+                   const RowMap &rm, cudaStream_t st) {
+    long n = (long)B * limbs * c->N;
+    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod);
+}
+
+// ------------------------------------------------------------- ModUp
+// Decompose (Sec. 3.3): per digit d, y_i = [c_i (Q_d/q_i)^-1]_{q_i}; every
+// target row r of Q_l P gets sum_i y_i (Q_d/q_i mod r) mod r, except the
+// digit's own rows, which keep c_r.  In/out in coefficient form.
+// coef: [B][l+1][N]; out: [B][ndig][l+1+alpha][N].
+__global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int alpha, int ndig, int N, RowMap qp,
+                              const ModQ *mods, const ShoupPair *up_inv, const ShoupPair *up_mod) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = (long)B * ndig * N;
+    if (idx >= total) return;
+    int x = (int)(idx % N);
+    long t = idx / N;
+    int d = (int)(t % ndig);
+    int b = (int)(t / ndig);
+    int rows = level + 1 + alpha;
+    const u64 *cb = coef + (long)b * (level + 1) * N;
+    u64 *ob = out + ((long)b * ndig + d) * rows * N;
+    int i0 = d * alpha;
+    int ns = min(alpha, level + 1 - i0);
+    u64 y[4];
+    for (int s = 0; s < ns; s++) {
+        ShoupPair w = up_inv[d * alpha + s];
+        y[s] = shoup(cb[(long)(i0 + s) * N + x], w.w, w.wp, mods[i0 + s].q);
+    }
+    for (int r = 0; r < rows; r++) {
+        u64 v;
+        if (r >= i0 && r < i0 + ns) {
+            v = cb[(long)r * N + x];
+        } else {
+            const ModQ &m = mods[qp.p[r]];
+            v = 0;
+            for (int s = 0; s < ns; s++) {
+                ShoupPair w = up_mod[((long)d * alpha + s) * rows + r];
+                v = addmod(v, shoup(y[s], w.w, w.wp, m.q), m.q);
+            }
+        }
+        ob[(long)r * N + x] = v;
+    }
+}
+void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st) {
+    const LevelConsts &L = c->lc(level);
+    long n = (long)B * L.ndig * c->N;
+    k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, L.ndig, c->N, c->map_qp(level),
+                                                c->d_mod, L.d_up_inv, L.d_up_mod);
+}
+
+// ------------------------------------------------------------- ModDown
+// conv_r = sum_j [u_{p_j} (P/p_j)^-1]_{p_j} (P/p_j mod q_r)  (coefficient form)
+// pcoef: [items][alpha][N]; out: [items][l+1][N]
+__global__ void k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int alpha, int L, int N,
+                                const ModQ *mods, const ShoupPair *pinv, const ShoupPair *pmod) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)items * N) return;
+    int x = (int)(idx % N);
+    int it = (int)(idx / N);
+    u64 y[4];
+    for (int j = 0; j < alpha; j++) {
+        ShoupPair w = pinv[j];
+        y[j] = shoup(pcoef[((long)it * alpha + j) * N + x], w.w, w.wp, mods[L + 1 + j].q);
+    }
+    for (int r = 0; r <= level; r++) {
+        u64 q = mods[r].q, v = 0;
+        for (int j = 0; j < alpha; j++) {
+            ShoupPair w = pmod[j * (L + 1) + r];
+            v = addmod(v, shoup(y[j], w.w, w.wp, q), q);
+        }
+        out[((long)it * (level + 1) + r) * N + x] = v;
+    }
+}
+void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st) {
+    long n = (long)items * c->N;
+    k_moddown_bconv<<<nblk(n, 256), 256, 0, st>>>(pcoef, out, items, level, c->alpha, c->L, c->N, c->d_mod,
+                                                  c->d_dn_pinv, c->d_dn_pmod);
+}
+
+// out_r = (u_r - conv_r) P^-1 mod q_r (+ addend_r), NTT domain, r <= level.
+__global__ void k_moddown_final(u64 *out, const u64 *u, const u64 *conv, const u64 *add, int items, int level,
+                                int N, long us, long os, long as, const ModQ *mods, const ShoupPair *Pinv) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long per = (long)(level + 1) * N;
+    if (idx >= (long)items * per) return;
+    int it = (int)(idx / per);
+    long off = idx - (long)it * per;
+    int r = (int)(off / N);
+    u64 q = mods[r].q;
+    ShoupPair w = Pinv[r];
+    u64 v = shoup(submod(u[it * us + off], conv[idx], q), w.w, w.wp, q);
+    if (add) v = addmod(v, add[it * as + off], q);
+    out[it * os + off] = v;
+}
+void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const u64 *addend, int items, int level,
+                          long us, long os, long as, cudaStream_t st) {
+    long n = (long)items * (level + 1) * c->N;
+    k_moddown_final<<<nblk(n, 256), 256, 0, st>>>(out, u, conv, addend, items, level, c->N, us, os, as, c->d_mod,
+                                                  c->d_dn_Pinv);
+}
+
+// ------------------------------------------------------------- MultSum
+// MultSum + Permute (Sec. 3.3): out[b][k][r][x] = sum_d D[b][d][r][pi_g(x)] * K[d][k][kr(r)][x]
+// with the key in Montgomery form (one REDC per output).  With c0 given,
+// P * kappa_g(c0) is added on the Q rows of poly 0 (the hoisted rotation kept
+// in Q_l P used by double hoisting).  digits: [B][ndig][rows][N];
+// key: [dnum][2][nprimes][N]; out: [B][2][rows][N].
+__global__ void k_multsum(u64 *out, const u64 *digits, const u64 *key, u32 g, int B, int level, int alpha, int L,
+                          int ndig, int nprimes, int logN, RowMap qp, const ModQ *mods, const u64 *c0, long c0s,
+                          const ShoupPair *Pmod) {
+    const int N = 1 << logN;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int rows = level + 1 + alpha;
+    if (idx >= (long)rows * N) return;
+    int r = (int)(idx / N);
+    int x = (int)(idx - (long)r * N);
+    int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ &m = mods[qp.p[r]];
+    int src = (g == 1u) ? x : auto_index(x, g, logN);
+    u64 k0[16], k1[16];
+    for (int d = 0; d < ndig; d++) {
+        k0[d] = key[(((long)d * 2 + 0) * nprimes + kr) * N + x];
+        k1[d] = key[(((long)d * 2 + 1) * nprimes + kr) * N + x];
+    }
+    for (int b = 0; b < B; b++) {
+        const u64 *db = digits + (long)b * ndig * rows * N;
+        U128 a0 = {0, 0}, a1 = {0, 0};
+        for (int d = 0; d < ndig; d++) {
+            u64 v = db[((long)d * rows + r) * N + src];
+            mac128(a0, v, k0[d]);
+            mac128(a1, v, k1[d]);
+        }
+        u64 o0 = redc(a0.lo, a0.hi, m), o1 = redc(a1.lo, a1.hi, m);
+        if (c0 && r <= level) {
+            ShoupPair w = Pmod[r];
+            o0 = addmod(o0, shoup(c0[b * c0s + (long)r * N + src], w.w, w.wp, m.q), m.q);
+        }
+        u64 *ob = out + (long)b * 2 * rows * N;
+        ob[(long)r * N + x] = o0;
+        ob[(long)(rows + r) * N + x] = o1;
+    }
+}
+void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_t g, int B, int level,
+                    const u64 *c0_for_P, long c0s, cudaStream_t st) {
+    int rows = level + 1 + c->alpha;
+    long n = (long)rows * c->N;
+    k_multsum<<<nblk(n, 128), 128, 0, st>>>(out, digits, key, g, B, level, c->alpha, c->L, c->ndig(level),
+                                            c->nprimes, c->logN, c->map_qp(level), c->d_mod, c0_for_P, c0s,
+                                            c->d_Pmod);
+}
+
+// ------------------------------------------------------ double hoisting
+// S[b][k][r][x] = sum_t ptM_t[r][x] * R_t[b][k][r][x] over Q_l P (one REDC).
+struct PtrList {
+    const u64 *p[32];
+};
+__global__ void k_pmul_acc(u64 *out, PtrList pts, PtrList R, int nterms, int B, int rows, int N, long Rs,
+                           RowMap qp, const ModQ *mods) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long per = (long)rows * N;
+    if (idx >= per) return;
+    int r = (int)(idx / N);
+    const ModQ &m = mods[qp.p[r]];
+    for (int b = 0; b < B; b++) {
+        U128 a0 = {0, 0}, a1 = {0, 0};
+        for (int t = 0; t < nterms; t++) {
+            u64 pv = pts.p[t][idx];
+            const u64 *rb = R.p[t] + b * Rs;
+            mac128(a0, pv, rb[idx]);
+            mac128(a1, pv, rb[per + idx]);
+        }
+        u64 *ob = out + (long)b * 2 * per;
+        ob[idx] = redc(a0.lo, a0.hi, m);
+        ob[per + idx] = redc(a1.lo, a1.hi, m);
+    }
+}
+void launch_pmul_acc(Ctx *c, u64 *out, const u64 *const *pts, const u64 *const *R, int nterms, int B, int level,
+                     long Rs, cudaStream_t st) {
+    PtrList a, b;
+    for (int t = 0; t < nterms; t++) { a.p[t] = pts[t]; b.p[t] = R[t]; }
+    int rows = level + 1 + c->alpha;
+    long n = (long)rows * c->N;
+    k_pmul_acc<<<nblk(n, 128), 128, 0, st>>>(out, a, b, nterms, B, rows, c->N, Rs, c->map_qp(level), c->d_mod);
+}
+
+// P * a over Q_l P: rows q_r get (P mod q_r) a_r, the p rows are zero.
+// in: [items][l+1][N] (stride in_s), out: [items][l+1+alpha][N] (stride out_s)
+__global__ void k_lift_P(u64 *out, const u64 *in, int items, int level, int alpha, int N, long is, long os,
+                         const ModQ *mods, const ShoupPair *Pmod) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int rows = level + 1 + alpha;
+    long per = (long)rows * N;
+    if (idx >= (long)items * per) return;
+    int it = (int)(idx / per);
+    long off = idx - (long)it * per;
+    int r = (int)(off / N);
+    u64 v = 0;
+    if (r <= level) {
+        ShoupPair w = Pmod[r];
+        v = shoup(in[it * is + off], w.w, w.wp, mods[r].q);
+    }
+    out[it * os + off] = v;
+}
+void launch_lift_P(Ctx *c, u64 *out_qp, const u64 *in_q, int items, int level, long is, long os, cudaStream_t st) {
+    long n = (long)items * (level + 1 + c->alpha) * c->N;
+    k_lift_P<<<nblk(n, 256), 256, 0, st>>>(out_qp, in_q, items, level, c->alpha, c->N, is, os, c->d_mod,
+                                           c->d_Pmod);
+}
+
+// ------------------------------------------------------------- Rescale
+// t_i = [c_l]_{q_l} mod q_i for i < l (coefficient form): the centred residue
+// of the last limb (reading of App. A Rescaling: round(c / q_l)).
+// last: [items][N]; out: [items][l][N]
+__global__ void k_rescale_prep(const u64 *last, u64 *out, int items, int level, int N, const ModQ *mods,
+                               const u64 *qlmod) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)items * N) return;
+    int x = (int)(idx % N);
+    int it = (int)(idx / N);
+    u64 ql = mods[level].q;
+    u64 v = last[idx];
+    bool neg = v > (ql >> 1);
+    for (int i = 0; i < level; i++) {
+        u64 q = mods[i].q;
+        u64 r = v % q;
+        if (neg) r = submod(r, qlmod[i], q);  // v - q_l
+        out[((long)it * level + i) * N + x] = r;
+    }
+}
+void launch_rescale_prep(Ctx *c, const u64 *lastcoef, u64 *out, int items, int level, cudaStream_t st) {
+    const LevelConsts &L = c->lc(level);
+    long n = (long)items * c->N;
+    k_rescale_prep<<<nblk(n, 256), 256, 0, st>>>(lastcoef, out, items, level, c->N, c->d_mod, L.d_rs_qlmod);
+}
+
+// out_i = (c_i - t_i) q_l^-1 mod q_i (NTT domain), i < l.
+// in: [items][l+1][N] stride is; t: [items][l][N]; out: [items][l][N] stride os
+__global__ void k_rescale_final(u64 *out, const u64 *in, const u64 *t, int items, int level, int N, long is, long os,
+                                const ModQ *mods, const ShoupPair *inv) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long per = (long)level * N;
+    if (idx >= (long)items * per) return;
+    int it = (int)(idx / per);
+    long off = idx - (long)it * per;
+    int i = (int)(off / N);
+    u64 q = mods[i].q;
+    ShoupPair w = inv[i];
+    out[it * os + off] = shoup(submod(in[it * is + off], t[idx], q), w.w, w.wp, q);
+}
+void launch_rescale_final(Ctx *c, u64 *out, const u64 *in, const u64 *t, int items, int level, long is, long os,
+                          cudaStream_t st) {
+    const LevelConsts &L = c->lc(level);
+    long n = (long)items * level * c->N;
+    k_rescale_final<<<nblk(n, 256), 256, 0, st>>>(out, in, t, items, level, c->N, is, os, c->d_mod, L.d_rs_inv);
+}
+
+// ------------------------------------------------------------- decrypt
+// m = c0 + c1 s on limb q_0 (NTT domain), written into out (u64 view).
+__global__ void k_dec_q0(const u64 *c0, const u64 *c1, const u64 *skM, u64 *out, int N, const ModQ *mods) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const ModQ &m = mods[0];
+    out[x] = addmod(c0[x], mulmont(c1[x], skM[x], m), m.q);
+}
+__global__ void k_centre_q0(const u64 *a, double *out, int N, const ModQ *mods) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    u64 q = mods[0].q, v = a[x];
+    out[x] = v > (q >> 1) ? -(double)(q - v) : (double)v;
+}
+
+// -------------------------------------------------------------- diagonals
+// Slot vector (length S, period n^2) of a permutation-matrix diagonal,
+// rotated left by `rot` (mod n^2) and multiplied by `value`:
+//   kind 0  Z (sigma), eq. 5, index t in (-n, n)
+//   kind 1  T (tau), eq. 6, index t = k n
+//   kind 2  G (transpose), index t = (n-1) k, ones where column - row = k
+//   kind 3  C^k mask 1 (columns j < n-k); kind 4  C^k mask 2 (j >= n-k)
+//   kind 5  all ones (constant)
+//   kind 6  first column (j == 0); kind 7  identity (i == j)
+__global__ void k_diag_fill(double *out, int S, int kind, int n, long t, long rot, double value, int k) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S) return;
+    long n2 = (long)n * n;
+    long l = ((long)(p % n2) + rot) % n2;
+    long i = l / n, j = l % n;
+    bool one = false;
+    switch (kind) {
+    case 0:
+        if (t >= 0) one = (l - n * t >= 0) && (l - n * t < n - t);
+        else one = (l - (n + t) * n >= -t) && (l - (n + t) * n < n);
+        break;
+    case 1: one = (j == t / n); break;
+    case 2: one = ((j - i) * (n - 1) == t); break;
+    case 3: one = j < n - k; break;
+    case 4: one = j >= n - k; break;
+    case 5: one = true; break;
+    case 6: one = (j == 0); break;
+    case 7: one = (i == j); break;
+    }
+    out[p] = one ? value : 0.0;
+}
+void launch_diag_fill(Ctx *c, double *out, int kind, int n, long t, long rot, double value, int k, cudaStream_t st) {
+    k_diag_fill<<<nblk(c->S, 256), 256, 0, st>>>(out, c->S, kind, n, t, rot, value, k);
+}
+
+void launch_copy_rows(u64 *dst, long dst_stride, const u64 *src, long src_stride, int items, long words,
+                      cudaStream_t st) {
+    cudaMemcpy2DAsync(dst, dst_stride * 8, src, src_stride * 8, words * 8, items, cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace he
+
+// exported for decrypt
+namespace he {
+void launch_dec_q0(Ctx *c, const u64 *c0, const u64 *c1, u64 *out, cudaStream_t st) {
+    k_dec_q0<<<nblk(c->N, 256), 256, 0, st>>>(c0, c1, c->d_skM, out, c->N, c->d_mod);
+}
+void launch_centre_q0(Ctx *c, const u64 *a, double *out, cudaStream_t st) {
+    k_centre_q0<<<nblk(c->N, 256), 256, 0, st>>>(a, out, c->N, c->d_mod);
+}
+}  // namespace he

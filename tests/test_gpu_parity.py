@@ -1,0 +1,254 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Ciphertext residues are compared element by element in coefficient form
+(bit-exact); decrypted values against FP64 within 1e-4 per matrix entry.
+Sizes: N = 2^14 (config 1 chain) for full residue parity; N = 2^16 with the
+128x128 chain for the launch configuration the bench times (sampled parity
+of a rotation, property checks of the full product)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2305_17341_gb300 as pk
+    pk.build()
+    return pk
+
+
+@pytest.fixture(scope="module")
+def c1(lib):
+    """Config 1 chain: logN 14, q 60+3x40, p 60, seed 101, on both sides."""
+    from oracle.ckks import CKKS, Params
+    prm = lib.he_params_default(1)
+    ctx = lib.he_ctx_create(prm, 101)
+    P = Params(14, [60, 40, 40, 40], [60])
+    he = CKKS(P, 101)
+    yield lib, ctx, P, he
+    lib.he_ctx_destroy(ctx)
+
+
+def residues(he, ct):
+    return np.stack([ct.c0, ct.c1])
+
+
+def test_primes_match_oracle(c1):
+    lib, ctx, P, he = c1
+    q, p = lib.he_ctx_primes(ctx)
+    assert q == P.q and p == P.p
+
+
+def test_secret_key_matches(c1):
+    lib, ctx, P, he = c1
+    assert np.array_equal(lib.he_sk_export(ctx), he.s_int)
+
+
+def test_encrypt_bit_exact_every_level(c1):
+    lib, ctx, P, he = c1
+    rng = np.random.default_rng(11)
+    z = rng.uniform(-1, 1, P.S)
+    for level in range(P.L + 1):
+        g = lib.he_encrypt_slots(ctx, z, level, 1000 + level)
+        o = he.encrypt_slots(z, level, obj=1000 + level)
+        got = lib.he_ct_export(ctx, g)
+        assert np.array_equal(got, residues(he, o)), "level %d" % level
+        assert np.abs(lib.he_decrypt_slots(ctx, g, P.S) - z).max() < 1e-6
+        lib.he_ct_free(g)
+
+
+def test_encrypt_ragged_slot_count(c1):
+    lib, ctx, P, he = c1
+    z = np.random.default_rng(12).uniform(-1, 1, 1000)     # 1000 of 8192 slots, rest zero
+    full = np.zeros(P.S)
+    full[:1000] = z
+    g = lib.he_encrypt_slots(ctx, z, P.L, 7)
+    o = he.encrypt_slots(full, P.L, obj=7)
+    assert np.array_equal(lib.he_ct_export(ctx, g), residues(he, o))
+    lib.he_ct_free(g)
+
+
+def test_import_export_roundtrip(c1):
+    lib, ctx, P, he = c1
+    o = he.encrypt_slots(np.random.default_rng(3).uniform(-1, 1, P.S), 2, obj=5)
+    r = residues(he, o)
+    g = lib.he_ct_import(ctx, r, 2, o.scale, P.S)
+    assert np.array_equal(lib.he_ct_export(ctx, g), r)
+    lib.he_ct_free(g)
+
+
+@pytest.mark.parametrize("step", [1, 7, 4095, 8191])
+def test_rotation_bit_exact(c1, step):
+    lib, ctx, P, he = c1
+    lib.he_keygen(ctx, [step], want_relin=False)
+    he.gen_rotation_key(step)
+    z = np.random.default_rng(step).uniform(-1, 1, P.S)
+    for level in (P.L, 1):
+        o = he.drop(he.encrypt_slots(z, P.L, obj=50 + step), level)
+        g = lib.he_ct_import(ctx, residues(he, o), level, o.scale, P.S)
+        gr = lib.he_rotate(ctx, g, step)
+        orr = he.rotate(o, step)
+        assert np.array_equal(lib.he_ct_export(ctx, gr), residues(he, orr))
+        assert np.abs(lib.he_decrypt_slots(ctx, gr, P.S) - np.roll(z, -step)).max() < 1e-5
+        lib.he_ct_free(g)
+        lib.he_ct_free(gr)
+
+
+def test_mult_relin_rescale_bit_exact(c1):
+    lib, ctx, P, he = c1
+    lib.he_keygen(ctx, [], want_relin=True)
+    he.gen_relin_key()
+    rng = np.random.default_rng(21)
+    x, y = rng.uniform(-1, 1, P.S), rng.uniform(-1, 1, P.S)
+    a, b = he.encrypt_slots(x, P.L, obj=61), he.encrypt_slots(y, P.L, obj=62)
+    ga = lib.he_ct_import(ctx, residues(he, a), P.L, a.scale, P.S)
+    gb = lib.he_ct_import(ctx, residues(he, b), P.L, b.scale, P.S)
+    gm = lib.he_mult(ctx, ga, gb)
+    om = he.mult_relin(a, b)
+    assert np.array_equal(lib.he_ct_export(ctx, gm), residues(he, om))
+    gr = lib.he_rescale(ctx, gm)
+    orr = he.rescale(om)
+    assert np.array_equal(lib.he_ct_export(ctx, gr), residues(he, orr))
+    assert lib.he_ct_info(gr)[1] == orr.scale
+    assert np.abs(lib.he_decrypt_slots(ctx, gr, P.S) - x * y).max() < 1e-6
+    for h in (ga, gb, gm, gr):
+        lib.he_ct_free(h)
+
+
+def _matrix_pair(P, he, lib, ctx, n, seed, level=None):
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, (n, n))
+    B = rng.uniform(-1, 1, (n, n))
+    level = P.L if level is None else level
+    za = np.zeros(P.S); za[: n * n] = A.ravel()
+    zb = np.zeros(P.S); zb[: n * n] = B.ravel()
+    oa, ob = he.encrypt_slots(za, level, obj=seed * 2), he.encrypt_slots(zb, level, obj=seed * 2 + 1)
+    ga = lib.he_encrypt_matrix(ctx, A, level, seed * 2)
+    gb = lib.he_encrypt_matrix(ctx, B, level, seed * 2 + 1)
+    return A, B, oa, ob, ga, gb
+
+
+def test_transpose_bit_exact(c1):
+    from oracle.hmm import HMM, transpose_rot_steps
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    steps = transpose_rot_steps(n, n1, P.S)
+    lib.he_keygen(ctx, steps, want_relin=False)
+    for s in steps:
+        he.gen_rotation_key(s)
+    A, _, oa, _, ga, gb = _matrix_pair(P, he, lib, ctx, n, 31)
+    gt = lib.he_transpose(ctx, ga, n, n1, 1.0)
+    ot = HMM(he).transpose(oa, n, n1)
+    assert np.array_equal(lib.he_ct_export(ctx, gt), residues(he, ot))
+    out = lib.he_decrypt_matrix(ctx, gt, n, n)
+    assert np.abs(out - A.T).max() < TOL
+    for h in (ga, gb, gt):
+        lib.he_ct_free(h)
+
+
+def test_hmatmul_config1_bit_exact(c1):
+    """Config 1: 32x32 product at N=2^14, q 60+3x40, p 60 -- residues
+    bit-exact to the oracle, decrypted product within 1e-4 of FP64 A.B."""
+    from oracle.hmm import HMM, matmul_rot_steps
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    steps = matmul_rot_steps(n, n1, n1, P.S)
+    lib.he_keygen(ctx, steps, want_relin=True)
+    for s in steps:
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    A, B, oa, ob, ga, gb = _matrix_pair(P, he, lib, ctx, n, 41)
+    assert np.array_equal(lib.he_ct_export(ctx, ga), residues(he, oa))
+    gc = lib.he_hmatmul(ctx, ga, gb, n, n1, n1)
+    oc = HMM(he).hmatmul(oa, ob, n, n1, n1)
+    got = lib.he_ct_export(ctx, gc)
+    want = residues(he, oc)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want), "mismatching residues: %d of %d" % ((got != want).sum(), got.size)
+    lv, sc, per = lib.he_ct_info(gc)
+    assert (lv, per) == (0, n * n) and sc == oc.scale
+    out = lib.he_decrypt_matrix(ctx, gc, n, n)
+    assert np.abs(out - A @ B).max() < TOL
+    for h in (ga, gb, gc):
+        lib.he_ct_free(h)
+
+
+def test_hmatmul_batch_equals_single(c1):
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    from oracle.hmm import matmul_rot_steps
+    lib.he_keygen(ctx, matmul_rot_steps(n, n1, n1, P.S), want_relin=True)
+    pairs = [_matrix_pair(P, he, lib, ctx, n, 70 + i) for i in range(3)]
+    singles = [lib.he_hmatmul(ctx, p[4], p[5], n, n1, n1) for p in pairs]
+    batch = lib.he_hmatmul_batch([(p[4], p[5], n, n1, n1) for p in pairs])
+    for s, b, p in zip(singles, batch, pairs):
+        assert np.array_equal(lib.he_ct_export(ctx, s), lib.he_ct_export(ctx, b))
+        assert np.abs(lib.he_decrypt_matrix(ctx, b, n, n) - p[0] @ p[1]).max() < TOL
+    for h in singles + batch + [x for p in pairs for x in p[4:6]]:
+        lib.he_ct_free(h)
+
+
+def test_hmatmul_levels_and_errors(c1):
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    _, _, _, _, ga, gb = _matrix_pair(P, he, lib, ctx, n, 90, level=2)
+    with pytest.raises(lib.HeError) as e:
+        lib.he_hmatmul(ctx, ga, gb, n, n1, n1)
+    assert e.value.code == -3
+    with pytest.raises(lib.HeError):
+        lib.he_hmatmul(ctx, ga, gb, n, 3, n1)
+    lib.he_ct_free(ga)
+    lib.he_ct_free(gb)
+
+
+# ------------------------------------------------ full size: 128x128, N=2^16
+
+@pytest.fixture(scope="module")
+def c2(lib):
+    prm = lib.he_params_default(2)
+    ctx = lib.he_ctx_create(prm, 202)
+    yield lib, ctx
+    lib.he_ctx_destroy(ctx)
+
+
+def test_full_size_rotation_sampled_parity(c2):
+    """One hoisted rotation at N=2^16, level 20, 23 primes: bit-exact to the oracle."""
+    from oracle.ckks import CKKS, Params
+    lib, ctx = c2
+    P = Params(16, [60] + [40] * 20, [60, 60])
+    he = CKKS(P, 202)
+    step = 16
+    lib.he_keygen(ctx, [step], want_relin=False)
+    he.gen_rotation_key(step)
+    z = np.random.default_rng(5).uniform(-1, 1, P.S)
+    o = he.encrypt_slots(z, P.L, obj=3)
+    g = lib.he_encrypt_slots(ctx, z, P.L, 3)
+    assert np.array_equal(lib.he_ct_export(ctx, g), residues(he, o))
+    gr = lib.he_rotate(ctx, g, step)
+    assert np.array_equal(lib.he_ct_export(ctx, gr), residues(he, he.rotate(o, step)))
+    lib.he_ct_free(g)
+    lib.he_ct_free(gr)
+
+
+def test_full_size_hmatmul_properties(c2):
+    """128x128 at N=2^16 (the benchmarked configuration): decrypted product
+    within 1e-4 of FP64 for a batch of 2, and batch == single bit-exact."""
+    lib, ctx = c2
+    n, n1 = 128, 16
+    lib.he_keygen(ctx, lib.he_rot_steps_for_matmul(n, n1, n1, 1 << 15), want_relin=True)
+    rng = np.random.default_rng(9)
+    mats = [(rng.uniform(-1, 1, (n, n)), rng.uniform(-1, 1, (n, n))) for _ in range(2)]
+    cts = [(lib.he_encrypt_matrix(ctx, A, 20, 10 + 2 * i), lib.he_encrypt_matrix(ctx, B, 20, 11 + 2 * i))
+           for i, (A, B) in enumerate(mats)]
+    batch = lib.he_hmatmul_batch([(a, b, n, n1, n1) for a, b in cts])
+    single = lib.he_hmatmul(ctx, cts[0][0], cts[0][1], n, n1, n1)
+    assert np.array_equal(lib.he_ct_export(ctx, single), lib.he_ct_export(ctx, batch[0]))
+    for (A, B), o in zip(mats, batch):
+        err = np.abs(lib.he_decrypt_matrix(ctx, o, n, n) - A @ B).max()
+        assert err < TOL, err
+        assert lib.he_ct_info(o)[0] == 17
+    for h in batch + [single] + [x for c in cts for x in c]:
+        lib.he_ct_free(h)
