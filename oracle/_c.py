@@ -58,6 +58,7 @@ def lib():
             L.or_polymul_sum.argtypes = [ctypes.c_int, ctypes.c_int, u64p, ctypes.c_int, u64p, u64p, u64p]
             L.or_mulconst_limbs.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p, u64p, u64p]
             L.or_bconv.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p, ctypes.c_int, u64p, u64p]
+            L.or_moddown_round.argtypes = [ctypes.c_int, ctypes.c_int, u64p, u64p, ctypes.c_int, u64p, u64p, u64p]
             L.or_encode.argtypes = [ctypes.c_int, dblp, dblp, ctypes.c_double, i64p]
             L.or_decode.argtypes = [ctypes.c_int, dblp, ctypes.c_double, dblp, dblp]
             L.or_encode_direct.argtypes = [ctypes.c_int, dblp, dblp, ctypes.c_double, dblp]
@@ -171,6 +172,18 @@ def bconv(src_q, src, dst_q):
     dq = _u64(np.array(dst_q, dtype=np.uint64))
     out = np.zeros((len(dst_q), N), dtype=np.uint64)
     lib().or_bconv(N, ns, _p(sq, u64p), _p(src, u64p), len(dst_q), _p(dq, u64p), _p(out, u64p))
+    return out
+
+
+def moddown_round(qs, uQ, ps, uP):
+    """round(X / P) over the q's for X given by residues uQ (q's) and uP (p's)."""
+    uQ, uP = _u64(uQ), _u64(uP)
+    nq, N = uQ.shape
+    qa = _u64(np.array(qs, dtype=np.uint64))
+    pa = _u64(np.array(ps, dtype=np.uint64))
+    out = np.zeros_like(uQ)
+    lib().or_moddown_round(N, nq, _p(qa, u64p), _p(uQ, u64p), len(ps), _p(pa, u64p), _p(uP, u64p),
+                           _p(out, u64p))
     return out
 
 

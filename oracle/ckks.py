@@ -15,7 +15,8 @@ Readings of points the paper leaves open (they bind the GPU path too):
   * Hybrid key switching with digits of alpha consecutive q's; the switching
     key is (-a_d s + e_d + P B_d s', a_d) over Q_L P (App. A SwitchKeyGen).
   * Decompose extends every digit with the fast basis conversion; ModDown is
-    (u_Q - BConv(u_P)) P^-1 (App. A KeySwitch, floor-type rounding).
+    the rounding round(u / P) of App. A KeySwitch, computed exactly (the
+    overflow of the basis conversion is removed with an FP64 estimate).
   * Hoisting: Decompose first, then the automorphism on the extended digits
     (Sec. 3.3 hoisting order).
   * Rescale = round(c / q_l) via the centred residue of the last limb.
@@ -300,13 +301,10 @@ class CKKS:
         return self.moddown(u0, level), self.moddown(u1, level)
 
     def moddown(self, u, level):
-        """ModDown: (u_Q - BConv_(P->Q)(u_P)) * P^-1 over Q_level."""
+        """ModDown: round(u / P) over Q_level (App. A KeySwitch, the rounding
+        of the inner product by P^-1), computed exactly as floor((u + (P-1)/2) / P)."""
         P = self.P
-        qs = P.qs(level)
-        conv = _c.bconv(P.p, u[level + 1:], qs)
-        diff = psub(u[: level + 1], conv, qs)
-        pinv = [_c.invmod(P.P % q, q) for q in qs]
-        return pmulconst(diff, pinv, qs)
+        return _c.moddown_round(P.qs(level), u[: level + 1], P.p, u[level + 1:])
 
     def _key_at(self, key, level):
         """Restrict a switching key to the digits and limbs of Q_level P."""

@@ -403,6 +403,65 @@ void or_bconv(int N, int ns, const u64 *sq, const u64 *src, int nd, const u64 *d
     free(qhat_mod);
 }
 
+/*
+ * ModDown with rounding (App. A KeySwitch: round(P^-1 <a, swk>) mod Q_l).
+ * Input: an element X of Q_l P given by residues uQ [nq][N] and uP [np][N].
+ * With h = (P-1)/2 and Y = X + h, the result is floor(Y / P) = round(X / P):
+ *   v_j   = (uP_j + h) mod p_j
+ *   y_j   = [v_j (P/p_j)^-1]_{p_j}
+ *   e     = floor(sum_j y_j / p_j)          (FP64, j ascending, one division
+ *                                             and one addition per term)
+ *   Y mod P = sum_j y_j (P/p_j) - e P       (reduced mod each q_i)
+ *   out_i = ((uQ_i + h) - (Y mod P)) P^-1 mod q_i.
+ * e counts the overflow of the sum of the y_j (P/p_j) past P; its FP64
+ * estimate is wrong only when sum_j y_j/p_j lies within ~1e-15 of an integer.
+ */
+void or_moddown_round(int N, int nq, const u64 *qs, const u64 *uQ, int np, const u64 *ps, const u64 *uP, u64 *out) {
+    u64 hp[8], phat_inv[8], hq[64], Pq[64], Pinv[64], phat_q[8][64];
+    for (int j = 0; j < np; j++) {
+        u64 p = ps[j];
+        u64 Pm = 1, ph = 1;
+        for (int k = 0; k < np; k++) {
+            Pm = mulmod(Pm, ps[k] % p, p);
+            if (k != j) ph = mulmod(ph, ps[k] % p, p);
+        }
+        hp[j] = mulmod(submod(Pm, 1 % p, p), invmod(2, p), p); /* (P-1)/2 mod p */
+        phat_inv[j] = invmod(ph, p);
+        for (int i = 0; i < nq; i++) {
+            u64 q = qs[i], v = 1;
+            for (int k = 0; k < np; k++)
+                if (k != j) v = mulmod(v, ps[k] % q, q);
+            phat_q[j][i] = v;
+        }
+    }
+    for (int i = 0; i < nq; i++) {
+        u64 q = qs[i], Pm = 1;
+        for (int k = 0; k < np; k++) Pm = mulmod(Pm, ps[k] % q, q);
+        Pq[i] = Pm;
+        Pinv[i] = invmod(Pm, q);
+        hq[i] = mulmod(submod(Pm, 1, q), invmod(2, q), q);
+    }
+#pragma omp parallel for
+    for (int x = 0; x < N; x++) {
+        u64 y[8];
+        double e_f = 0.0;
+        for (int j = 0; j < np; j++) {
+            u64 v = addmod(uP[(size_t)j * N + x], hp[j], ps[j]);
+            y[j] = mulmod(v, phat_inv[j], ps[j]);
+            e_f = e_f + (double)y[j] / (double)ps[j];
+        }
+        u64 e = (u64)floor(e_f);
+        for (int i = 0; i < nq; i++) {
+            u64 q = qs[i];
+            u64 conv = 0;
+            for (int j = 0; j < np; j++) conv = addmod(conv, mulmod(y[j] % q, phat_q[j][i], q), q);
+            conv = submod(conv, mulmod(e % q, Pq[i], q), q);
+            u64 t = submod(addmod(uQ[(size_t)i * N + x], hq[i], q), conv, q);
+            out[(size_t)i * N + x] = mulmod(t, Pinv[i], q);
+        }
+    }
+}
+
 /* -------------------------------------------------------- encode / decode
  * Canonical embedding (App. A Encode/Decode): slot j holds m(zeta^(5^j)),
  * zeta = exp(i pi / N), S = N/2 slots.  The inverse map, written as

@@ -176,10 +176,12 @@ def test_fast_bconv_exact_relation():
         assert len(us) == 1  # the same u for every target prime
 
 
-def test_moddown_is_floor_division_minus_small():
-    # ModDown (App. A KeySwitch): result = floor(X / P) - u', 0 <= u' < alpha.
+@pytest.mark.parametrize("pbits", [[60], [60, 60], [60, 50, 45]])
+def test_moddown_is_rounding(pbits):
+    # ModDown (App. A KeySwitch): round(X / P) mod Q_l, exactly, for X the
+    # CRT value over Q_l P (P odd: no ties).
     from oracle.ckks import CKKS
-    P = Params(6, [60, 40, 40], [60, 60])
+    P = Params(8, [60, 40, 40], pbits)
     he = CKKS(P, 9)
     rng = np.random.default_rng(8)
     lv = 2
@@ -190,8 +192,25 @@ def test_moddown_is_floor_division_minus_small():
     for x in range(P.N):
         X, QP = _crt(u[:, x], qp)
         Y, Q = _crt(out[:, x], Qs)
-        base = X // P.P
-        assert any((base - k) % Q == Y for k in range(P.alpha))
+        assert Y == ((2 * X + P.P) // (2 * P.P)) % Q
+
+
+def test_keyswitch_noise_is_centred():
+    # The rounding ModDown leaves no systematic offset in the key-switch
+    # noise: Dec(Rot(ct)) - kappa(Dec(ct)) has mean ~0 (a floor-type ModDown
+    # gives a mean near -alpha * (sum of s) / 2, which decodes to large slot
+    # errors next to slot 0).
+    from oracle.ckks import CKKS, psub
+    P = Params(12, [60] + [40] * 6, [60, 60])
+    he = CKKS(P, 5)
+    z = np.random.default_rng(1).uniform(-1, 1, P.S)
+    ct = he.encrypt_slots(z, P.L, obj=1)
+    he.gen_rotation_key(1)
+    r = he.rotate(ct, 1)
+    want = automorph(he.decrypt_poly(ct), P.galois(1), P.N, P.qs(P.L))
+    noise = centred(psub(he.decrypt_poly(r), want, P.qs(P.L))[0], P.q[0])
+    assert abs(noise.mean()) < 3 * noise.std() / np.sqrt(P.N) + 0.5
+    assert noise.std() < 100
 
 
 def test_rescale_is_rounding():
