@@ -185,6 +185,20 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
  * ModDown (Table 1 caption), and kernel launches.  Any pointer may be NULL. */
 int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset);
 
+/* Kernel tracing.  While enabled, the library records a CUDA event pair on the
+ * context's stream around every launch of the traced kernel classes
+ *   0 MultSum (key-switch inner product), 1 forward NTT, 2 inverse NTT
+ * and adds the launch's algorithmic bytes (words the operation must read and
+ * write once).  he_trace_read synchronises the stream and returns, for one
+ * class, the number of launches, their summed device time (ms) and bytes. */
+int he_trace_enable(he_ctx *ctx, int on);
+
+/* Integer roofline of the NTT: measured rate (butterflies per second) of the
+ * lazy Shoup butterfly with register operands on the current device, `iters`
+ * rounds of 16 butterflies per thread over 8 CTAs of 256 threads per SM. */
+int he_bench_butterfly(int iters, double *bfly_per_s);
+int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, double *bytes, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,9 @@ SIGNATURES = {
     "he_hmatmul_batch": [P(he_mm_job), ip, P(vp)],
     "he_transpose": [vp, vp, ip, ip, ctypes.c_double, P(vp)],
     "he_counters": [vp, llp, llp, llp, llp, ip],
+    "he_trace_enable": [vp, ip],
+    "he_bench_butterfly": [ip, P(ctypes.c_double)],
+    "he_trace_read": [vp, ip, llp, P(ctypes.c_double), P(ctypes.c_double), ip],
 }
 _RESTYPES = {"he_last_error": ctypes.c_char_p}
 
@@ -276,6 +279,25 @@ def he_hmatmul_batch(jobs):
 
 def he_transpose(ctx, ct, n, n1, prescale=1.0):
     return _unary("he_transpose", ctx, ct, n, n1, prescale)
+
+
+TRACE_MULTSUM, TRACE_NTT_FWD, TRACE_NTT_INV = 0, 1, 2
+
+
+def he_trace_enable(ctx, on=True):
+    check(lib().he_trace_enable(ctx, 1 if on else 0))
+
+
+def he_bench_butterfly(iters=2000):
+    v = ctypes.c_double()
+    check(lib().he_bench_butterfly(iters, ctypes.byref(v)))
+    return v.value
+
+
+def he_trace_read(ctx, cls, reset=False):
+    n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    check(lib().he_trace_read(ctx, cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), 1 if reset else 0))
+    return {"count": n.value, "ms": ms.value, "bytes": by.value}
 
 
 def he_counters(ctx, reset=False):

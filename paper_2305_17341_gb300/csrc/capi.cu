@@ -166,7 +166,8 @@ int he_ctx_destroy(he_ctx *ctx) {
     if (c.rlk) cudaFree(c.rlk);
     for (auto &kv : c.ptcache) cudaFree(kv.second);
     void *ptrs[] = {c.d_mod, c.d_psi, c.d_psip, c.d_ipsi, c.d_ipsip, c.d_ninv, c.d_dn_pinv, c.d_dn_pmod,
-                    c.d_dn_Pinv, c.d_Pmod, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM, c.d_pkM};
+                    c.d_dn_Pinv, c.d_Pmod, c.d_dn_hp, c.d_dn_hq, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM,
+                    c.d_pkM};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &l : c.lvl) {
@@ -616,6 +617,36 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
     *out = o;
     return cuda_status(&c);
     GUARD_END
+}
+
+int he_bench_butterfly(int iters, double *bfly_per_s) {
+    if (!bfly_per_s || iters < 1) return fail(HE_ERR_ARG, "bad arguments");
+    *bfly_per_s = bfly_peak(iters);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HE_ERR_CUDA, cudaGetErrorString(e));
+    return HE_OK;
+}
+
+int he_trace_enable(he_ctx *ctx, int on) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    ctx->c.trace_collect();
+    ctx->c.trace = on != 0;
+    return HE_OK;
+}
+
+int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, double *bytes, int reset) {
+    if (!ctx || cls < 0 || cls > 2) return fail(HE_ERR_ARG, "bad arguments");
+    Ctx &c = ctx->c;
+    c.trace_collect();
+    Ctx::TraceClass &t = c.tr[cls];
+    if (count) *count = t.count;
+    if (total_ms) *total_ms = t.total_ms;
+    if (bytes) *bytes = t.bytes;
+    if (reset) {
+        t.count = 0;
+        t.total_ms = t.bytes = 0;
+    }
+    return HE_OK;
 }
 
 int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset) {

@@ -178,6 +178,49 @@ void DevicePool::release_all() {
     in_use_ = cached_ = 0;
 }
 
+// --------------------------------------------------------------- tracing
+cudaEvent_t Ctx::ev_get() {
+    if (!ev_free.empty()) {
+        cudaEvent_t e = ev_free.back();
+        ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Ctx::trace_begin(int cls, cudaEvent_t &e0) {
+    (void)cls;
+    e0 = nullptr;
+    if (!trace) return;
+    e0 = ev_get();
+    cudaEventRecord(e0, stream);
+}
+
+void Ctx::trace_end(int cls, cudaEvent_t e0, double bytes) {
+    if (!trace || !e0) return;
+    cudaEvent_t e1 = ev_get();
+    cudaEventRecord(e1, stream);
+    tr[cls].pending.push_back({e0, e1});
+    tr[cls].bytes += bytes;
+    tr[cls].count++;
+}
+
+void Ctx::trace_collect() {
+    cudaStreamSynchronize(stream);
+    for (auto &c : tr) {
+        for (auto &pr : c.pending) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            c.total_ms += ms;
+            ev_free.push_back(pr.first);
+            ev_free.push_back(pr.second);
+        }
+        c.pending.clear();
+    }
+}
+
 // -------------------------------------------------------------- tables
 template <typename T>
 static T *upload(const std::vector<T> &v) {
@@ -288,6 +331,19 @@ void build_tables(Ctx *c) {
     c->d_dn_pmod = upload(pmod);
     c->d_dn_Pinv = upload(Pinv);
     c->d_Pmod = upload(Pmod);
+    // h = (P-1)/2 reduced mod every prime: 2h = P - 1 exactly (P odd)
+    std::vector<u64> hp(a), hq(L + 1);
+    for (int j = 0; j < a; j++) {
+        u64 pj = c->primes[L + 1 + j], Pm = 1;
+        for (int t = 0; t < a; t++) Pm = h_mulmod(Pm, c->primes[L + 1 + t] % pj, pj);
+        hp[j] = h_mulmod((Pm + pj - 1) % pj, h_invmod(2, pj), pj);
+    }
+    for (int r = 0; r <= L; r++) {
+        u64 qr = c->primes[r];
+        hq[r] = h_mulmod((Pmod[r].w + qr - 1) % qr, h_invmod(2, qr), qr);
+    }
+    c->d_dn_hp = upload(hp);
+    c->d_dn_hq = upload(hq);
     c->lvl.assign(L + 1, LevelConsts());
 
     // encoder: zeta^e = (cos, sin)((pi e) / N); slot j -> t = (5^j mod 2N - 1)/4

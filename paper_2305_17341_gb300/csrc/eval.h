@@ -18,6 +18,7 @@ u64 *gen_relin_key(Ctx *c);
 void encrypt_poly(Ctx *c, const u64 *m_ntt, int level, uint32_t obj, bool refresh, u64 *out);
 void encode_to(Ctx *c, const double *d_zr, const double *d_zi, double scale, u64 *out, int rows, const RowMap &rm);
 const char *last_error();
+double bfly_peak(int iters);
 
 void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits);
 void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s);

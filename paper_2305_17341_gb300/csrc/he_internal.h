@@ -91,6 +91,8 @@ struct Ctx {
     ShoupPair *d_dn_pmod = nullptr;  // [alpha][L+1] (P/p_j) mod q_r
     ShoupPair *d_dn_Pinv = nullptr;  // [L+1]     P^-1 mod q_r
     ShoupPair *d_Pmod = nullptr;     // [L+1]     P mod q_r
+    u64 *d_dn_hp = nullptr;          // [alpha]   (P-1)/2 mod p_j
+    u64 *d_dn_hq = nullptr;          // [L+1]     (P-1)/2 mod q_r
     std::vector<LevelConsts> lvl;
 
     // encoder tables
@@ -113,7 +115,20 @@ struct Ctx {
 
     // instrumentation
     long long n_ms = 0, n_dp = 0, n_md = 0, n_launch = 0;
-    bool count_launch = false;
+    // per-kernel-class tracing: CUDA events on the context stream around each
+    // launch of a traced class, with the launch's algorithmic bytes
+    struct TraceClass {
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+        double total_ms = 0, bytes = 0;
+        long long count = 0;
+    };
+    bool trace = false;
+    TraceClass tr[4];                 // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv
+    std::vector<cudaEvent_t> ev_free;
+    cudaEvent_t ev_get();
+    void trace_begin(int cls, cudaEvent_t &e0);
+    void trace_end(int cls, cudaEvent_t e0, double bytes);
+    void trace_collect();
 
     // helpers
     int qp_rows(int level) const { return level + 1 + alpha; }

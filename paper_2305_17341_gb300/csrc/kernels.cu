@@ -77,6 +77,7 @@ __global__ void k_small_to_rns(const i64 *x, u64 *out, long rows, int N, RowMap 
 void launch_sample_uniform(Ctx *c, u64 *out, int rows, const RowMap &rm, const int *, uint32_t obj,
                            uint32_t tag, cudaStream_t st) {
     long n = (long)rows * c->N;
+    c->n_launch++;
     k_sample_uniform<<<nblk(n, 256), 256, 0, st>>>(out, rows, c->N, rm, c->d_mod, obj, tag, (u32)c->seed,
                                                    (u32)(c->seed >> 32));
 }
@@ -84,12 +85,14 @@ void launch_sample_uniform(Ctx *c, u64 *out, int rows, const RowMap &rm, const i
 void launch_sample_small(Ctx *c, i64 *out, int kind, uint32_t obj, uint32_t tag, cudaStream_t st) {
     GaussT gt;
     for (int k = 0; k < 20; k++) gt.T[k] = c->gauss_T[k];
+    c->n_launch++;
     k_sample_small<<<nblk(c->N, 256), 256, 0, st>>>(out, c->N, kind, gt, obj, tag, (u32)c->seed,
                                                    (u32)(c->seed >> 32));
 }
 
 void launch_small_to_rns(Ctx *c, const i64 *x, u64 *out, int rows, const RowMap &rm, cudaStream_t st) {
     long n = (long)rows * c->N;
+    c->n_launch++;
     k_small_to_rns<<<nblk(n, 256), 256, 0, st>>>(x, out, rows, c->N, rm, c->d_mod);
 }
 
@@ -162,10 +165,14 @@ void launch_encode(Ctx *c, const double *zre, const double *zim, double scale, i
     int S = c->S, logS = c->logN - 1;
     Buf tmp(&c->pool, (size_t)S), tmp2(&c->pool, (size_t)S);  // S doubles each
     double *xr = (double *)tmp.p, *xi = (double *)tmp2.p;
+    c->n_launch++;
     k_enc_permute<<<nblk(S, 256), 256, 0, st>>>(zre, zim, xr, xi, c->d_slot_t, S, logS);
-    for (int len = 2; len <= S; len <<= 1)
+    for (int len = 2; len <= S; len <<= 1) {
+        c->n_launch++;
         k_dft_pass<<<nblk(S / 2, 256), 256, 0, st>>>(xr, xi, c->d_zeta, S, len, -1);
+    }
     double f = scale / (double)S;
+    c->n_launch++;
     k_enc_final<<<nblk(S, 256), 256, 0, st>>>(xr, xi, c->d_zeta, f, m_out, S);
 }
 
@@ -174,9 +181,13 @@ void launch_decode(Ctx *c, const double *coef, double scale, double *zre, double
     Buf tmp(&c->pool, (size_t)S);
     Buf tmp2(&c->pool, (size_t)S);
     double *xr = (double *)tmp.p, *xi = (double *)tmp2.p;
+    c->n_launch++;
     k_dec_twist<<<nblk(S, 256), 256, 0, st>>>(coef, scale, c->d_zeta, xr, xi, S, logS);
-    for (int len = 2; len <= S; len <<= 1)
+    for (int len = 2; len <= S; len <<= 1) {
+        c->n_launch++;
         k_dft_pass<<<nblk(S / 2, 256), 256, 0, st>>>(xr, xi, c->d_zeta, S, len, +1);
+    }
+    c->n_launch++;
     k_dec_gather<<<nblk(S, 256), 256, 0, st>>>(xr, xi, c->d_slot_t, zre, zim, S);
 }
 
@@ -221,7 +232,7 @@ __global__ void k_from_mont(u64 *o, const u64 *a, long rows, int N, RowMap rm, c
 #define EW_LAUNCH(kern, ...)                                                         \
     do {                                                                             \
         long n__ = rows * (long)c->N;                                                \
-        if (n__ > 0) kern<<<nblk(n__, 256), 256, 0, st>>>(__VA_ARGS__, rows, c->N, rm, c->d_mod); \
+        if (n__ > 0) c->n_launch++, kern<<<nblk(n__, 256), 256, 0, st>>>(__VA_ARGS__, rows, c->N, rm, c->d_mod); \
     } while (0)
 
 void launch_add(Ctx *c, u64 *out, const u64 *a, const u64 *b, long rows, const RowMap &rm, cudaStream_t st) {
@@ -257,6 +268,7 @@ void launch_mulconst_rows(Ctx *c, u64 *out, const u64 *a, const ShoupPair *w, lo
                           const RowMap &rm, cudaStream_t st) {
     long n = rows * (long)c->N;
     if (n > 0)
+        c->n_launch++;
         k_mulconst_rows<<<nblk(n, 256), 256, 0, st>>>(out, a, w, rpi, rows, c->N, rm, c->d_mod);
 }
 
@@ -279,6 +291,7 @@ __global__ void k_automorph(u64 *o, const u64 *in, long rows, int logN, u32 g) {
 }
 void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &, uint32_t g, cudaStream_t st) {
     long n = rows * (long)c->N;
+    c->n_launch++;
     if (n > 0) k_automorph<<<nblk(n, 256), 256, 0, st>>>(out, in, rows, c->logN, g);
 }
 
@@ -307,6 +320,7 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
                    const RowMap &rm, cudaStream_t st) {
     long n = (long)B * limbs * c->N;
+    c->n_launch++;
     k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod);
 }
 
@@ -352,37 +366,54 @@ __global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int a
 void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st) {
     const LevelConsts &L = c->lc(level);
     long n = (long)B * L.ndig * c->N;
+    c->n_launch++;
     k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, L.ndig, c->N, c->map_qp(level),
                                                 c->d_mod, L.d_up_inv, L.d_up_mod);
 }
 
 // ------------------------------------------------------------- ModDown
-// conv_r = sum_j [u_{p_j} (P/p_j)^-1]_{p_j} (P/p_j mod q_r)  (coefficient form)
+// Rounding ModDown (App. A KeySwitch: round(P^-1 x)) as floor((x + h) / P),
+// h = (P-1)/2.  With v_j = u_{p_j} + h mod p_j and y_j = [v_j (P/p_j)^-1]_{p_j},
+// the exact residue (x + h) mod P is sum_j y_j (P/p_j) - e P, where the
+// overflow count e = floor(sum_j y_j / p_j) is evaluated in FP64 (j
+// ascending, correctly rounded conversion, division and addition).
+// conv_r = ((x + h) mod P) - h mod q_r, coefficient form (h is added to
+// every coefficient, so it is folded in here, before the forward NTT).
 // pcoef: [items][alpha][N]; out: [items][l+1][N]
 __global__ void k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int alpha, int L, int N,
-                                const ModQ *mods, const ShoupPair *pinv, const ShoupPair *pmod) {
+                                const ModQ *mods, const ShoupPair *pinv, const ShoupPair *pmod, const u64 *hp,
+                                const ShoupPair *Pmod, const u64 *hq) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)items * N) return;
     int x = (int)(idx % N);
     int it = (int)(idx / N);
     u64 y[4];
+    double ef = 0.0;
     for (int j = 0; j < alpha; j++) {
         ShoupPair w = pinv[j];
-        y[j] = shoup(pcoef[((long)it * alpha + j) * N + x], w.w, w.wp, mods[L + 1 + j].q);
+        u64 p = mods[L + 1 + j].q;
+        u64 v = addmod(pcoef[((long)it * alpha + j) * N + x], hp[j], p);
+        y[j] = shoup(v, w.w, w.wp, p);
+        ef = __dadd_rn(ef, __ddiv_rn(__ull2double_rn(y[j]), __ull2double_rn(p)));
     }
+    u64 e = (u64)floor(ef);
     for (int r = 0; r <= level; r++) {
         u64 q = mods[r].q, v = 0;
         for (int j = 0; j < alpha; j++) {
             ShoupPair w = pmod[j * (L + 1) + r];
             v = addmod(v, shoup(y[j], w.w, w.wp, q), q);
         }
+        ShoupPair wP = Pmod[r];
+        v = submod(v, shoup(e, wP.w, wP.wp, q), q);
+        v = submod(v, hq[r], q);
         out[((long)it * (level + 1) + r) * N + x] = v;
     }
 }
 void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st) {
     long n = (long)items * c->N;
+    c->n_launch++;
     k_moddown_bconv<<<nblk(n, 256), 256, 0, st>>>(pcoef, out, items, level, c->alpha, c->L, c->N, c->d_mod,
-                                                  c->d_dn_pinv, c->d_dn_pmod);
+                                                  c->d_dn_pinv, c->d_dn_pmod, c->d_dn_hp, c->d_Pmod, c->d_dn_hq);
 }
 
 // out_r = (u_r - conv_r) P^-1 mod q_r (+ addend_r), NTT domain, r <= level.
@@ -403,6 +434,7 @@ __global__ void k_moddown_final(u64 *out, const u64 *u, const u64 *conv, const u
 void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const u64 *addend, int items, int level,
                           long us, long os, long as, cudaStream_t st) {
     long n = (long)items * (level + 1) * c->N;
+    c->n_launch++;
     k_moddown_final<<<nblk(n, 256), 256, 0, st>>>(out, u, conv, addend, items, level, c->N, us, os, as, c->d_mod,
                                                   c->d_dn_Pinv);
 }
@@ -413,48 +445,115 @@ void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const
 // P * kappa_g(c0) is added on the Q rows of poly 0 (the hoisted rotation kept
 // in Q_l P used by double hoisting).  digits: [B][ndig][rows][N];
 // key: [dnum][2][nprimes][N]; out: [B][2][rows][N].
-__global__ void k_multsum(u64 *out, const u64 *digits, const u64 *key, u32 g, int B, int level, int alpha, int L,
-                          int ndig, int nprimes, int logN, RowMap qp, const ModQ *mods, const u64 *c0, long c0s,
-                          const ShoupPair *Pmod) {
+// Items are processed in chunks of BC held in registers, so each key word is
+// loaded once per chunk; the digit gather pi_g(x) stays inside one aligned
+// 32-word block for 32 consecutive x (the automorphism permutes the low bits
+// of the bit-reversed index only), so the loads remain coalesced.
+template <int BC>
+__global__ void __launch_bounds__(256) k_multsum(u64 *out, const u64 *digits, const u64 *key, u32 g, int B,
+                                                 int level, int alpha, int L, int ndig, int nprimes, int logN,
+                                                 RowMap qp, const ModQ *mods, const u64 *c0, long c0s,
+                                                 const ShoupPair *Pmod) {
     const int N = 1 << logN;
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    int rows = level + 1 + alpha;
+    const int rows = level + 1 + alpha;
     if (idx >= (long)rows * N) return;
-    int r = (int)(idx / N);
-    int x = (int)(idx - (long)r * N);
-    int kr = r <= level ? r : L + 1 + (r - level - 1);
-    const ModQ &m = mods[qp.p[r]];
-    int src = (g == 1u) ? x : auto_index(x, g, logN);
-    u64 k0[16], k1[16];
-    for (int d = 0; d < ndig; d++) {
-        k0[d] = key[(((long)d * 2 + 0) * nprimes + kr) * N + x];
-        k1[d] = key[(((long)d * 2 + 1) * nprimes + kr) * N + x];
-    }
-    for (int b = 0; b < B; b++) {
-        const u64 *db = digits + (long)b * ndig * rows * N;
-        U128 a0 = {0, 0}, a1 = {0, 0};
+    const int r = (int)(idx / N);
+    const int x = (int)(idx - (long)r * N);
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ m = mods[qp.p[r]];
+    const int src = (g == 1u) ? x : auto_index(x, g, logN);
+    const long dstride = (long)rows * N;                  // digit stride
+    const long istride = (long)ndig * rows * N;           // item stride of the digits
+    const u64 *k0p = key + (long)kr * N + x;
+    const long kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    for (int b0 = 0; b0 < B; b0 += BC) {
+        U128 a0[BC], a1[BC];
+#pragma unroll
+        for (int j = 0; j < BC; j++) a0[j] = a1[j] = U128{0, 0};
+        const u64 *dp = digits + (long)b0 * istride + (long)r * N + src;
         for (int d = 0; d < ndig; d++) {
-            u64 v = db[((long)d * rows + r) * N + src];
-            mac128(a0, v, k0[d]);
-            mac128(a1, v, k1[d]);
+            const u64 kv0 = __ldg(k0p + d * kd), kv1 = __ldg(k0p + d * kd + kk);
+#pragma unroll
+            for (int j = 0; j < BC; j++) {
+                if (b0 + j < B) {
+                    u64 v = dp[j * istride + d * dstride];
+                    mac128(a0[j], v, kv0);
+                    mac128(a1[j], v, kv1);
+                }
+            }
         }
-        u64 o0 = redc(a0.lo, a0.hi, m), o1 = redc(a1.lo, a1.hi, m);
-        if (c0 && r <= level) {
-            ShoupPair w = Pmod[r];
-            o0 = addmod(o0, shoup(c0[b * c0s + (long)r * N + src], w.w, w.wp, m.q), m.q);
+#pragma unroll
+        for (int j = 0; j < BC; j++) {
+            int b = b0 + j;
+            if (b >= B) break;
+            u64 o0 = redc(a0[j].lo, a0[j].hi, m), o1 = redc(a1[j].lo, a1[j].hi, m);
+            if (c0 && r <= level) {
+                ShoupPair w = Pmod[r];
+                o0 = addmod(o0, shoup(c0[b * c0s + (long)r * N + src], w.w, w.wp, m.q), m.q);
+            }
+            u64 *ob = out + (long)b * 2 * rows * N;
+            ob[(long)r * N + x] = o0;
+            ob[(long)(rows + r) * N + x] = o1;
         }
-        u64 *ob = out + (long)b * 2 * rows * N;
-        ob[(long)r * N + x] = o0;
-        ob[(long)(rows + r) * N + x] = o1;
     }
 }
+// Item-parallel MultSum: a CTA covers XW = 256/BI consecutive coefficients of
+// one row for BI items (one warp group per item).  The BI groups read the same
+// key words, so each key word comes from HBM once per CTA and from L1
+// afterwards; per-thread state is two 128-bit accumulators.
+__global__ void __launch_bounds__(256) k_multsum_items(u64 *out, const u64 *digits, const u64 *key, u32 g, int B,
+                                                       int BI, int level, int alpha, int L, int ndig, int nprimes,
+                                                       int logN, RowMap qp, const ModQ *mods, const u64 *c0,
+                                                       long c0s, const ShoupPair *Pmod) {
+    const int N = 1 << logN;
+    const int XW = 256 / BI;
+    const int tx = threadIdx.x % XW, ti = threadIdx.x / XW;
+    const int x = blockIdx.x * XW + tx;
+    const int r = blockIdx.y;
+    const int b = blockIdx.z * BI + ti;
+    if (b >= B || x >= N) return;
+    const int rows = level + 1 + alpha;
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ m = mods[qp.p[r]];
+    const int src = (g == 1u) ? x : auto_index(x, g, logN);
+    const long dstride = (long)rows * N;
+    const u64 *dp = digits + (long)b * ndig * dstride + (long)r * N + src;
+    const u64 *kp = key + (long)kr * N + x;
+    const long kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    U128 a0 = {0, 0}, a1 = {0, 0};
+    for (int d = 0; d < ndig; d++) {
+        u64 v = dp[d * dstride];
+        mac128(a0, v, kp[d * kd]);
+        mac128(a1, v, kp[d * kd + kk]);
+    }
+    u64 o0 = redc(a0.lo, a0.hi, m), o1 = redc(a1.lo, a1.hi, m);
+    if (c0 && r <= level) {
+        ShoupPair w = Pmod[r];
+        o0 = addmod(o0, shoup(c0[b * c0s + (long)r * N + src], w.w, w.wp, m.q), m.q);
+    }
+    u64 *ob = out + (long)b * 2 * rows * N;
+    ob[(long)r * N + x] = o0;
+    ob[(long)(rows + r) * N + x] = o1;
+}
+
 void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_t g, int B, int level,
                     const u64 *c0_for_P, long c0s, cudaStream_t st) {
     int rows = level + 1 + c->alpha;
-    long n = (long)rows * c->N;
-    k_multsum<<<nblk(n, 128), 128, 0, st>>>(out, digits, key, g, B, level, c->alpha, c->L, c->ndig(level),
-                                            c->nprimes, c->logN, c->map_qp(level), c->d_mod, c0_for_P, c0s,
-                                            c->d_Pmod);
+    c->n_launch++;
+    cudaEvent_t e0;
+    c->trace_begin(0, e0);
+    int BI = B >= 8 ? 8 : (B >= 4 ? 4 : (B >= 2 ? 2 : 1));
+    int XW = 256 / BI;
+    dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
+    k_multsum_items<<<grid, 256, 0, st>>>(out, digits, key, g, B, BI, level, c->alpha, c->L, c->ndig(level),
+                                          c->nprimes, c->logN, c->map_qp(level), c->d_mod, c0_for_P, c0s,
+                                          c->d_Pmod);
+    // algorithmic bytes: the key (2 polys x ndig digits x rows limbs) read once,
+    // every item's digits read once, both output polys written, c0 read if fused
+    double nd = c->ndig(level), W = (double)c->N * 8.0;
+    double bytes = 2.0 * nd * rows * W + (double)B * (nd * rows * W + 2.0 * rows * W + (c0_for_P ? (level + 1) * W : 0));
+    c->trace_end(0, e0, bytes);
 }
 
 // ------------------------------------------------------ double hoisting
@@ -488,6 +587,7 @@ void launch_pmul_acc(Ctx *c, u64 *out, const u64 *const *pts, const u64 *const *
     for (int t = 0; t < nterms; t++) { a.p[t] = pts[t]; b.p[t] = R[t]; }
     int rows = level + 1 + c->alpha;
     long n = (long)rows * c->N;
+    c->n_launch++;
     k_pmul_acc<<<nblk(n, 128), 128, 0, st>>>(out, a, b, nterms, B, rows, c->N, Rs, c->map_qp(level), c->d_mod);
 }
 
@@ -511,6 +611,7 @@ __global__ void k_lift_P(u64 *out, const u64 *in, int items, int level, int alph
 }
 void launch_lift_P(Ctx *c, u64 *out_qp, const u64 *in_q, int items, int level, long is, long os, cudaStream_t st) {
     long n = (long)items * (level + 1 + c->alpha) * c->N;
+    c->n_launch++;
     k_lift_P<<<nblk(n, 256), 256, 0, st>>>(out_qp, in_q, items, level, c->alpha, c->N, is, os, c->d_mod,
                                            c->d_Pmod);
 }
@@ -538,6 +639,7 @@ __global__ void k_rescale_prep(const u64 *last, u64 *out, int items, int level, 
 void launch_rescale_prep(Ctx *c, const u64 *lastcoef, u64 *out, int items, int level, cudaStream_t st) {
     const LevelConsts &L = c->lc(level);
     long n = (long)items * c->N;
+    c->n_launch++;
     k_rescale_prep<<<nblk(n, 256), 256, 0, st>>>(lastcoef, out, items, level, c->N, c->d_mod, L.d_rs_qlmod);
 }
 
@@ -559,6 +661,7 @@ void launch_rescale_final(Ctx *c, u64 *out, const u64 *in, const u64 *t, int ite
                           cudaStream_t st) {
     const LevelConsts &L = c->lc(level);
     long n = (long)items * level * c->N;
+    c->n_launch++;
     k_rescale_final<<<nblk(n, 256), 256, 0, st>>>(out, in, t, items, level, c->N, is, os, c->d_mod, L.d_rs_inv);
 }
 
@@ -609,6 +712,7 @@ __global__ void k_diag_fill(double *out, int S, int kind, int n, long t, long ro
     out[p] = one ? value : 0.0;
 }
 void launch_diag_fill(Ctx *c, double *out, int kind, int n, long t, long rot, double value, int k, cudaStream_t st) {
+    c->n_launch++;
     k_diag_fill<<<nblk(c->S, 256), 256, 0, st>>>(out, c->S, kind, n, t, rot, value, k);
 }
 
@@ -622,9 +726,11 @@ void launch_copy_rows(u64 *dst, long dst_stride, const u64 *src, long src_stride
 // exported for decrypt
 namespace he {
 void launch_dec_q0(Ctx *c, const u64 *c0, const u64 *c1, u64 *out, cudaStream_t st) {
+    c->n_launch++;
     k_dec_q0<<<nblk(c->N, 256), 256, 0, st>>>(c0, c1, c->d_skM, out, c->N, c->d_mod);
 }
 void launch_centre_q0(Ctx *c, const u64 *a, double *out, cudaStream_t st) {
+    c->n_launch++;
     k_centre_q0<<<nblk(c->N, 256), 256, 0, st>>>(a, out, c->N, c->d_mod);
 }
 }  // namespace he

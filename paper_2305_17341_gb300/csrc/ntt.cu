@@ -166,6 +166,207 @@ __global__ void k_ntt_inv_p1(u64 *data, RowMap rm, const ModQ *mods, const u64 *
     }
 }
 
+// ------------------------------------------------- register-blocked passes
+// One pass transforms W independent length-M sequences per CTA (M = 2^LM,
+// 128 or 256).  Each of the T = M/16 threads of a sequence holds 16 elements:
+// layout A = elements t + T k (k < 16), which covers the 4 stages with spans
+// M/2 .. T in registers; a shared-memory transpose gives layout B = elements
+// 16 t + k, which covers spans T/2 .. 1.  ROWS: sequences are rows of M
+// contiguous coefficients (the last stages of a limb); otherwise columns
+// with stride N/M (the first stages).  The twiddle of the butterfly at local
+// span sp and local group i is psi^brv((M / 2sp) G + i), G = 1 for columns
+// and G = N/M + row for rows.  Global loads and stores are always in layout A
+// (coalesced across the W sequences for columns, along the row for rows).
+template <int LM, bool ROWS>
+struct PassGeom {
+    static constexpr int M = 1 << LM, T = M / 16, W = 256 / T;
+    static constexpr int SM = ROWS ? W * (M + 8) : W * M;
+    __device__ static __forceinline__ int sidx(int r, int w) {
+        if (ROWS) return w * (M + 8) + (r ^ ((r >> 4) & 15));
+        return r * W + w;
+    }
+};
+
+template <int LM, bool ROWS>
+__global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, const ModQ *mods, const u64 *tw,
+                                                      const u64 *twp, int logN) {
+    typedef PassGeom<LM, ROWS> G_;
+    constexpr int M = G_::M, T = G_::T, W = G_::W;
+    __shared__ u64 sm[G_::SM];
+    const int N = 1 << logN;
+    const long row = blockIdx.y;
+    const int pidx = rm.p[row % rm.n];
+    const u64 q = mods[pidx].q;
+    const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
+    int t, w;
+    if (ROWS) { w = threadIdx.x / T; t = threadIdx.x % T; }
+    else { t = threadIdx.x / W; w = threadIdx.x % W; }
+    const long stride = ROWS ? 1 : (N >> LM);
+    const long seq = (long)blockIdx.x * W + w;
+    u64 *p = data + row * (long)N + (ROWS ? seq * M : seq);
+    const long G = ROWS ? ((long)(N >> LM) + seq) : 1;
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = p[(long)(t + T * k) * stride];
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+        const long mb = (long)(M / (2 * T * s)) * G;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (!(k & s)) {
+                long idx = mb + k / (2 * s);
+                bf_fwd(x[k], x[k + s], w_[idx], wp_[idx], q);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[G_::sidx(16 * t + k, w)];
+#pragma unroll
+    for (int sp = T / 2; sp >= 1; sp >>= 1) {
+        const long mb = (long)(M / (2 * sp)) * G + (long)t * (8 / sp);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (!(k & sp)) {
+                long idx = mb + k / (2 * sp);
+                bf_fwd(x[k], x[k + sp], w_[idx], wp_[idx], q);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[G_::sidx(16 * t + k, w)] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        u64 v = sm[G_::sidx(t + T * k, w)];
+        p[(long)(t + T * k) * stride] = ROWS ? reduce4q(v, q) : v;
+    }
+}
+
+template <int LM, bool ROWS>
+__global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, const ModQ *mods, const u64 *tw,
+                                                      const u64 *twp, const u64 *ninv, int logN) {
+    typedef PassGeom<LM, ROWS> G_;
+    constexpr int M = G_::M, T = G_::T, W = G_::W;
+    __shared__ u64 sm[G_::SM];
+    const int N = 1 << logN;
+    const long row = blockIdx.y;
+    const int pidx = rm.p[row % rm.n];
+    const u64 q = mods[pidx].q;
+    const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
+    int t, w;
+    if (ROWS) { w = threadIdx.x / T; t = threadIdx.x % T; }
+    else { t = threadIdx.x / W; w = threadIdx.x % W; }
+    const long stride = ROWS ? 1 : (N >> LM);
+    const long seq = (long)blockIdx.x * W + w;
+    u64 *p = data + row * (long)N + (ROWS ? seq * M : seq);
+    const long G = ROWS ? ((long)(N >> LM) + seq) : 1;
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = p[(long)(t + T * k) * stride];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[G_::sidx(16 * t + k, w)];
+#pragma unroll
+    for (int sp = 1; sp <= T / 2; sp <<= 1) {
+        const long mb = (long)(M / (2 * sp)) * G + (long)t * (8 / sp);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (!(k & sp)) {
+                long idx = mb + k / (2 * sp);
+                bf_inv(x[k], x[k + sp], w_[idx], wp_[idx], q);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[G_::sidx(16 * t + k, w)] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[G_::sidx(t + T * k, w)];
+#pragma unroll
+    for (int s = 1; s <= 8; s <<= 1) {
+        const long mb = (long)(M / (2 * T * s)) * G;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (!(k & s)) {
+                long idx = mb + k / (2 * s);
+                bf_inv(x[k], x[k + s], w_[idx], wp_[idx], q);
+            }
+    }
+    if (!ROWS) {
+        const u64 ni = ninv[2 * pidx], nip = ninv[2 * pidx + 1];
+#pragma unroll
+        for (int k = 0; k < 16; k++) x[k] = shoup(x[k], ni, nip, q);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) p[(long)(t + T * k) * stride] = x[k];
+}
+
+template <int LM, bool ROWS>
+static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st) {
+    typedef PassGeom<LM, ROWS> G_;
+    dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
+    k_ntt_fwd_fast<LM, ROWS><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, ctx->d_psi, ctx->d_psip, ctx->logN);
+}
+
+template <int LM, bool ROWS>
+static void inv_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st) {
+    typedef PassGeom<LM, ROWS> G_;
+    dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
+    k_ntt_inv_fast<LM, ROWS><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, ctx->d_ipsi, ctx->d_ipsip, ctx->d_ninv,
+                                                    ctx->logN);
+}
+
+// ------------------------------------------------------ integer roofline
+// Peak rate of the forward butterfly (one lazy Shoup product and two lazy
+// add/sub) with operands in registers: 16 independent chains per thread,
+// `iters` rounds, every SM filled.  The result is the denominator of the
+// NTT's "alu" roofline.
+__global__ void k_bfly_peak(u64 *sink, int iters, u64 q, u64 w, u64 wp) {
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = (threadIdx.x * 16 + k) % q;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 16; k += 2) bf_fwd(x[k], x[k + 1], w, wp, q);
+#pragma unroll
+        for (int k = 0; k < 16; k += 4) {
+            bf_fwd(x[k], x[k + 2], w, wp, q);
+            bf_fwd(x[k + 1], x[k + 3], w, wp, q);
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc ^= x[k];
+    if (acc == 0x1234567ull) sink[0] = acc;  // keeps the work alive
+}
+
+double bfly_peak(int iters) {
+    const u64 q = 1152921504606748673ull;  // a 60-bit prime = 1 mod 2^15
+    const u64 w = 123456789012345ull % q;
+    ShoupPair sp = h_shoup(w, q);
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    u64 *sink;
+    cudaMalloc(&sink, 8);
+    const int blocks = nsm * 8, threads = 256;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_bfly_peak<<<blocks, threads>>>(sink, 16, q, sp.w, sp.wp);  // warm-up
+    cudaEventRecord(a);
+    k_bfly_peak<<<blocks, threads>>>(sink, iters, q, sp.w, sp.wp);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    double bfly = (double)blocks * threads * iters * 16.0;  // 8 + 8 butterflies per round
+    return bfly / (ms * 1e-3);
+}
+
 // ----------------------------------------------------------------- launch
 static void split(int logN, int &logN1, int &C, int &R) {
     logN1 = logN / 2;
@@ -187,6 +388,16 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st) 
         long nr = rows - r0 < 65535 ? rows - r0 : 65535;
         u64 *d = data + r0 * (long)ctx->N;
         RowMap m = rm.shifted(r0);
+        ctx->n_launch += 2;
+        cudaEvent_t e0;
+        ctx->trace_begin(1, e0);
+        if (logN >= 14 && logN <= 16) {
+            if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st); else fwd_pass<7, false>(ctx, d, nr, m, st);
+            if (logN - logN1 == 8) fwd_pass<8, true>(ctx, d, nr, m, st); else fwd_pass<7, true>(ctx, d, nr, m, st);
+            // algorithmic bytes: every word read and written once (the two passes move twice that)
+            ctx->trace_end(1, e0, 2.0 * nr * ctx->N * 8.0);
+            continue;
+        }
         k_ntt_fwd_p1<<<dim3(N2 / C, (unsigned)nr), 256, N1 * C * 8, st>>>(d, m, ctx->d_mod, ctx->d_psi,
                                                                        ctx->d_psip, logN, logN1, C);
         k_ntt_fwd_p2<<<dim3(N1 / R, (unsigned)nr), 256, R * N2 * 8, st>>>(d, m, ctx->d_mod, ctx->d_psi,
@@ -203,6 +414,15 @@ void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st) 
         long nr = rows - r0 < 65535 ? rows - r0 : 65535;
         u64 *d = data + r0 * (long)ctx->N;
         RowMap m = rm.shifted(r0);
+        ctx->n_launch += 2;
+        cudaEvent_t e0;
+        ctx->trace_begin(2, e0);
+        if (logN >= 14 && logN <= 16) {
+            if (logN - logN1 == 8) inv_pass<8, true>(ctx, d, nr, m, st); else inv_pass<7, true>(ctx, d, nr, m, st);
+            if (logN1 == 8) inv_pass<8, false>(ctx, d, nr, m, st); else inv_pass<7, false>(ctx, d, nr, m, st);
+            ctx->trace_end(2, e0, 2.0 * nr * ctx->N * 8.0);
+            continue;
+        }
         k_ntt_inv_p2<<<dim3(N1 / R, (unsigned)nr), 256, R * N2 * 8, st>>>(d, m, ctx->d_mod, ctx->d_ipsi,
                                                                        ctx->d_ipsip, logN, logN1, R);
         k_ntt_inv_p1<<<dim3(N2 / C, (unsigned)nr), 256, N1 * C * 8, st>>>(d, m, ctx->d_mod, ctx->d_ipsi,

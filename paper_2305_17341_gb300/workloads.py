@@ -1,0 +1,57 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+Only input generation lives here (NumPy PCG64 streams); no part of the
+homomorphic method.  Both the tests' oracle side and the CUDA side draw from
+these functions, so the same bytes reach both.
+
+The paper's datasets (MNIST, Fashion-MNIST, Yale; Sec. 7.2.3) are not
+available; the low-rank-plus-noise matrices below stand in for them with the
+paper's shapes (s samples x 256 pixel features in [0, 1]).
+"""
+import numpy as np
+
+
+def matmul_pair(n, seed):
+    """A, B: n x n, entries i.i.d. uniform[-1, 1] (products of Sec. 4, Table 3)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, (n, n)), rng.uniform(-1.0, 1.0, (n, n))
+
+
+def lowrank_dataset(s, t, seed, decay=0.8, noise=0.01):
+    """X = U diag(decay^i) V^T + noise * N(0, 1), U, V random orthogonal (QR of
+    Gaussian matrices, sign-fixed), globally min-max scaled to [0, 1]."""
+    rng = np.random.default_rng(seed)
+    k = min(s, t)
+    U, Ru = np.linalg.qr(rng.standard_normal((s, k)))
+    U = U * np.sign(np.diag(Ru))
+    V, Rv = np.linalg.qr(rng.standard_normal((t, k)))
+    V = V * np.sign(np.diag(Rv))
+    X = (U * decay ** np.arange(k)) @ V.T + noise * rng.standard_normal((s, t))
+    X = (X - X.min()) / (X.max() - X.min())
+    return X
+
+
+def mixed_matmul_jobs(count, seed, dims=(16, 32, 64, 128), logNs=(15, 16), levels=(3, 20)):
+    """Jobs of a mixed batch: (n, logN, level, A, B) with n, logN, level drawn
+    uniformly; entries uniform[-1, 1]."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for _ in range(count):
+        n = int(rng.choice(dims))
+        logN = int(rng.choice(logNs))
+        level = int(rng.integers(levels[0], levels[1] + 1))
+        A = rng.uniform(-1.0, 1.0, (n, n))
+        B = rng.uniform(-1.0, 1.0, (n, n))
+        jobs.append((n, logN, level, A, B))
+    return jobs
+
+
+def poisson_arrivals(rate, duration, seed):
+    """Arrival times (s) of a Poisson process with the given rate."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return out
+        out.append(t)
