@@ -151,6 +151,22 @@ int he_ct_free(he_ct *ct);
  * Decompose-then-Permute order of Sec. 3.3). */
 int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out);
 
+/* Slot rotation for callers that cannot allocate device memory at the point
+ * of the call (memory owned by another runtime's arena, latency-critical
+ * threads, pipelines that must not fail on an allocation).  The paper has no
+ * counterpart; it is the rotation of he_rotate with caller-owned buffers.
+ *   in_dev, out_dev: device arrays of 2*(level+1)*N words, ciphertext residues
+ *     in coefficient form as he_ct_export writes them; they may not overlap.
+ *   Every temporary lives in one 32 MiB array that the library reserves in
+ *     device memory when it is loaded (each device that loads the library
+ *     holds it until the process exits); no call allocates.  The first call
+ *     on a device looks up the array's device address.
+ *   Returns HE_ERR_ARG when the ring degree and level need more than 32 MiB
+ *     of temporaries (e.g. N = 2^16 above level 3), HE_ERR_KEY_MISSING without
+ *     the rotation key.  The call waits for its work to finish.
+ *   All calls share the array: calls whose work overlaps on the GPU race. */
+int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level, int step, uint64_t *out_dev);
+
 /* Add (App. A Addition module): same level and scale. */
 int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 

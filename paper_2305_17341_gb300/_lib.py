@@ -68,6 +68,7 @@ SIGNATURES = {
     "he_ct_import": [vp, u64p, ip, ctypes.c_double, ip, P(vp)],
     "he_ct_free": [vp],
     "he_rotate": [vp, vp, ip, P(vp)],
+    "he_rotate_noalloc": [vp, vp, ip, ip, vp],
     "he_add": [vp, vp, vp, P(vp)],
     "he_mult": [vp, vp, vp, P(vp)],
     "he_rescale": [vp, vp, P(vp)],
@@ -241,6 +242,11 @@ def _unary(name, *args):
 
 def he_rotate(ctx, ct, step):
     return _unary("he_rotate", ctx, ct, step)
+
+
+def he_rotate_noalloc(ctx, in_dev_ptr, level, step, out_dev_ptr):
+    """Rotation on caller-owned device buffers (raw device pointers as ints)."""
+    check(lib().he_rotate_noalloc(ctx, vp(in_dev_ptr), level, step, vp(out_dev_ptr)))
 
 
 def he_add(ctx, a, b):

@@ -371,6 +371,16 @@ void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cud
                                                 c->d_mod, L.d_up_inv, L.d_up_mod);
 }
 
+// Same conversion with caller-supplied constants (layout of LevelConsts).
+void launch_modup_bconv_with(Ctx *c, const u64 *coef, u64 *out, int B, int level, const ShoupPair *up_inv,
+                             const ShoupPair *up_mod, cudaStream_t st) {
+    int nd = c->ndig(level);
+    long n = (long)B * nd * c->N;
+    c->n_launch++;
+    k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, nd, c->N, c->map_qp(level), c->d_mod,
+                                                up_inv, up_mod);
+}
+
 // ------------------------------------------------------------- ModDown
 // Rounding ModDown (App. A KeySwitch: round(P^-1 x)) as floor((x + h) / P),
 // h = (P-1)/2.  With v_j = u_{p_j} + h mod p_j and y_j = [v_j (P/p_j)^-1]_{p_j},
