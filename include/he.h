@@ -197,6 +197,54 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs);
  * transpose). */
 int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, he_ct **out);
 
+/* State of the interactive modulus refresh (Sec. 7.2.3, App. C): the Philox
+ * object of the next refresh is next_obj + 1; count counts refreshes. */
+typedef struct he_refresh_state {
+    uint32_t next_obj;
+    int count;
+} he_refresh_state;
+
+/* Interactive modulus refresh (the client's step, Sec. 7.2.3): decrypt to the
+ * integer message at q_0, centred lift, re-encrypt the same integers at the
+ * top level with the next refresh object.  Needs the secret key. */
+int he_refresh(he_ctx *ctx, const he_ct *ct, he_refresh_state *rs, he_ct **out);
+
+/* Aggregate (Sec. 5.2): axis 0 sums the rows of an n x n block (rotations
+ * n, 2n, ..., every row becomes the column sums); axis 1 sums within rows
+ * (rotations 1, 2, ..., first-column mask (1 level), rotations -1, -2, ...,
+ * every column becomes the row sums). */
+int he_aggregate(he_ctx *ctx, const he_ct *ct, int axis, int n, he_ct **out);
+
+/* HCovMtrx (Sec. 5.2): blocks[l*k + j] = encrypted X_j[l], the l-th n x n
+ * row block of the j-th feature block of an s x (k n) dataset (zero-padded,
+ * same level >= 6).  cov[a*k + b] receives block (a, b) of
+ * X^T X / s - mu^T mu (or X^T X / s if centered): blocks a <= b by matrix
+ * products summed over row blocks, a > b by transposition, 1/s folded into
+ * the transposition of X, mu from Aggregate.  Consumes 5 levels. */
+int he_covariance(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, int n, int s, int centered,
+                  const he_mm_sched *sched, he_ct **cov);
+
+/* Newton-iteration counts of Lazy Normalization (Sec. 6.1.2): the PowerMethod
+ * simulation with contraction coefficient S, error bound e, precision bound
+ * Bp, interval (0, B2] and the order-1 Taylor start at B2/2 + 1; counts[t]
+ * for t < t_iters (host computation). */
+int he_lazy_normalization_schedule(int t_iters, double S, double e, double Bp, double B2, int max_iters,
+                                   int *counts);
+
+/* HPowerMethod (Sec. 6.1): l_P normalised covariance transformations of the
+ * replicated vector v0[0..k) (axis 0: rows equal, 1: columns equal), Newton
+ * counts per iteration, then one more transformation for the eigenvalue.
+ * Refreshes a ciphertext just before an operation that needs more levels than
+ * it has.  Outputs: lambda (all slots), V[0..k) in *axis_out, VT[0..k) its
+ * flip. */
+int he_power_method(he_ctx *ctx, he_ct *const *cov, int k, int n, he_ct *const *v0, int axis, int l_P,
+                    const int *newton_counts, double B2, he_refresh_state *rs, he_ct **lambda, he_ct **V,
+                    he_ct **VT, int *axis_out);
+
+/* HEigenShift (Sec. 6.2): cov[a*k + b] -= lambda v_a v_b^T in place. */
+int he_eigen_shift(he_ctx *ctx, he_ct **cov, int k, int n, const he_ct *lambda, he_ct *const *V, int axis,
+                   he_ct *const *VT, he_refresh_state *rs);
+
 /* Counters of the key-switch phases since the last reset: MultSum, Decompose,
  * ModDown (Table 1 caption), and kernel launches.  Any pointer may be NULL. */
 int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset);

@@ -38,6 +38,10 @@ class he_mm_job(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("n", ctypes.c_int), ("sched", he_mm_sched)]
 
 
+class he_refresh_state(ctypes.Structure):
+    _fields_ = [("next_obj", ctypes.c_uint32), ("count", ctypes.c_int)]
+
+
 P = ctypes.POINTER
 vp = ctypes.c_void_p
 ip = ctypes.c_int
@@ -76,6 +80,14 @@ SIGNATURES = {
     "he_hmatmul": [vp, vp, vp, ip, P(he_mm_sched), P(vp)],
     "he_hmatmul_batch": [P(he_mm_job), ip, P(vp)],
     "he_transpose": [vp, vp, ip, ip, ctypes.c_double, P(vp)],
+    "he_refresh": [vp, vp, P(he_refresh_state), P(vp)],
+    "he_aggregate": [vp, vp, ip, ip, P(vp)],
+    "he_covariance": [vp, P(vp), ip, ip, ip, ip, ip, P(he_mm_sched), P(vp)],
+    "he_lazy_normalization_schedule": [ip, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip,
+                                       P(ip)],
+    "he_power_method": [vp, P(vp), ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp), P(vp),
+                        P(ip)],
+    "he_eigen_shift": [vp, P(vp), ip, ip, vp, P(vp), ip, P(vp), P(he_refresh_state)],
     "he_counters": [vp, llp, llp, llp, llp, ip],
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
@@ -285,6 +297,56 @@ def he_hmatmul_batch(jobs):
 
 def he_transpose(ctx, ct, n, n1, prescale=1.0):
     return _unary("he_transpose", ctx, ct, n, n1, prescale)
+
+
+def _handles(hs):
+    arr = (vp * len(hs))()
+    for i, h in enumerate(hs):
+        arr[i] = h.value if isinstance(h, vp) else h
+    return arr
+
+
+def he_refresh(ctx, ct, rs):
+    h = vp()
+    check(lib().he_refresh(ctx, ct, ctypes.byref(rs), ctypes.byref(h)))
+    return h
+
+
+def he_aggregate(ctx, ct, axis, n):
+    return _unary("he_aggregate", ctx, ct, axis, n)
+
+
+def he_covariance(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t):
+    """blocks: list of handles in [l][j] order (l-major); returns k*k handles (a*k + b)."""
+    out = (vp * (k * k))()
+    sc = he_mm_sched(n1z, n1t)
+    check(lib().he_covariance(ctx, _handles(blocks), n_row_blocks, k, n, s, 1 if centered else 0,
+                              ctypes.byref(sc), out))
+    return [vp(o) for o in out]
+
+
+def he_lazy_normalization_schedule(t, S=0.5, e=1e-5, Bp=1e-3, B2=2.0 ** 16, max_iters=64):
+    out = (ctypes.c_int * t)()
+    check(lib().he_lazy_normalization_schedule(t, S, e, Bp, B2, max_iters, out))
+    return list(out)
+
+
+def he_power_method(ctx, cov, k, n, v0, axis, l_P, counts, B2, rs):
+    lam = vp()
+    V = (vp * k)()
+    VT = (vp * k)()
+    ax = ctypes.c_int()
+    cs = (ctypes.c_int * len(counts))(*counts)
+    check(lib().he_power_method(ctx, _handles(cov), k, n, _handles(v0), axis, l_P, cs, B2, ctypes.byref(rs),
+                                ctypes.byref(lam), V, VT, ctypes.byref(ax)))
+    return lam, [vp(x) for x in V], [vp(x) for x in VT], ax.value
+
+
+def he_eigen_shift(ctx, cov, k, n, lam, V, axis, VT, rs):
+    """Shifts in place: returns the new list of k*k handles (the old ones are freed)."""
+    arr = _handles(cov)
+    check(lib().he_eigen_shift(ctx, arr, k, n, lam, _handles(V), axis, _handles(VT), ctypes.byref(rs)))
+    return [vp(x) for x in arr]
 
 
 TRACE_MULTSUM, TRACE_NTT_FWD, TRACE_NTT_INV = 0, 1, 2

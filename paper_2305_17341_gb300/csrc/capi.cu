@@ -7,21 +7,9 @@
 #include <set>
 #include <tuple>
 
-#include "eval.h"
+#include "ctapi.h"
 
 using namespace he;
-
-struct he_ctx {
-    Ctx c;
-};
-
-struct he_ct {
-    Ctx *ctx;
-    u64 *d;
-    int level;
-    double scale;
-    int period;
-};
 
 namespace he {
 void build_tables(Ctx *c);
@@ -59,9 +47,10 @@ static int cuda_status(Ctx *c) {
     return HE_OK;
 }
 
-static size_t ct_words(const Ctx *c, int level) { return (size_t)2 * (level + 1) * c->N; }
+namespace he {
+size_t ct_words(const Ctx *c, int level) { return (size_t)2 * (level + 1) * c->N; }
 
-static he_ct *new_ct(Ctx *c, int level, double scale, int period) {
+he_ct *new_ct(Ctx *c, int level, double scale, int period) {
     he_ct *ct = new he_ct;
     ct->ctx = c;
     ct->level = level;
@@ -71,11 +60,12 @@ static he_ct *new_ct(Ctx *c, int level, double scale, int period) {
     return ct;
 }
 
-static void free_ct(he_ct *ct) {
+void free_ct(he_ct *ct) {
     if (!ct) return;
     if (ct->d) ct->ctx->pool.put(ct->d);
     delete ct;
 }
+}  // namespace he
 
 extern "C" {
 

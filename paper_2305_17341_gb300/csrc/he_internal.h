@@ -224,6 +224,10 @@ void launch_lift_P(Ctx *c, u64 *out_qp, const u64 *in_q, int items, int level, l
 void launch_rescale_prep(Ctx *c, const u64 *lastcoef, u64 *out, int items, int level, cudaStream_t st);
 void launch_rescale_final(Ctx *c, u64 *out, const u64 *in, const u64 *t, int items, int level,
                           long in_item_stride, long out_item_stride, cudaStream_t st);
+void launch_scalar_mul_rows(Ctx *c, u64 *out, const u64 *a, long rows, int rpi, const ShoupPair *vals,
+                            const RowMap &rm, cudaStream_t st);
+void launch_scalar_add_rows(Ctx *c, u64 *data, long rows, const u64 *vals, const RowMap &rm, cudaStream_t st);
+void launch_centre_i64_q0(Ctx *c, const u64 *a, i64 *out, cudaStream_t st);
 void launch_dec_q0(Ctx *c, const u64 *c0, const u64 *c1, u64 *out, cudaStream_t st);
 void launch_centre_q0(Ctx *c, const u64 *a, double *out, cudaStream_t st);
 void launch_diag_fill(Ctx *c, double *out, int kind, int n, long t, long rot, double value, int k,

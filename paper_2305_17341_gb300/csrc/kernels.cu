@@ -381,6 +381,54 @@ void launch_modup_bconv_with(Ctx *c, const u64 *coef, u64 *out, int B, int level
                                                 up_inv, up_mod);
 }
 
+// ----------------------------------------------------- constants per limb
+// Multiplying by a constant polynomial m (or adding it) acts on every
+// NTT-domain slot of limb i with the scalar m mod q_i.
+struct ScalarList {
+    ShoupPair w[64];
+};
+__global__ void k_scalar_mul_rows(u64 *o, const u64 *a, long rows, int rpi, int N, ScalarList s, RowMap rm,
+                                  const ModQ *mods) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * (long)N) return;
+    long row = idx / N;
+    int r = (int)(row % rpi);
+    o[idx] = shoup(a[idx], s.w[r].w, s.w[r].wp, mods[rm.p[row % rm.n]].q);
+}
+void launch_scalar_mul_rows(Ctx *c, u64 *out, const u64 *a, long rows, int rpi, const ShoupPair *vals,
+                            const RowMap &rm, cudaStream_t st) {
+    ScalarList s;
+    for (int i = 0; i < rpi && i < 64; i++) s.w[i] = vals[i];
+    long n = rows * (long)c->N;
+    c->n_launch++;
+    k_scalar_mul_rows<<<nblk(n, 256), 256, 0, st>>>(out, a, rows, rpi, c->N, s, rm, c->d_mod);
+}
+__global__ void k_scalar_add_rows(u64 *o, long rows, int N, ScalarList s, RowMap rm, const ModQ *mods) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * (long)N) return;
+    long row = idx / N;
+    u64 q = mods[rm.p[row % rm.n]].q;
+    o[idx] = addmod(o[idx], s.w[row].w, q);
+}
+void launch_scalar_add_rows(Ctx *c, u64 *data, long rows, const u64 *vals, const RowMap &rm, cudaStream_t st) {
+    ScalarList s;
+    for (int i = 0; i < rows && i < 64; i++) s.w[i].w = vals[i];
+    long n = rows * (long)c->N;
+    c->n_launch++;
+    k_scalar_add_rows<<<nblk(n, 256), 256, 0, st>>>(data, rows, c->N, s, rm, c->d_mod);
+}
+// centred lift of a residue mod q_0 to a signed integer
+__global__ void k_centre_i64_q0(const u64 *a, i64 *out, int N, const ModQ *mods) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    u64 q = mods[0].q, v = a[x];
+    out[x] = v > (q >> 1) ? -(i64)(q - v) : (i64)v;
+}
+void launch_centre_i64_q0(Ctx *c, const u64 *a, i64 *out, cudaStream_t st) {
+    c->n_launch++;
+    k_centre_i64_q0<<<nblk(c->N, 256), 256, 0, st>>>(a, out, c->N, c->d_mod);
+}
+
 // ------------------------------------------------------------- ModDown
 // Rounding ModDown (App. A KeySwitch: round(P^-1 x)) as floor((x + h) / P),
 // h = (P-1)/2.  With v_j = u_{p_j} + h mod p_j and y_j = [v_j (P/p_j)^-1]_{p_j},

@@ -1,0 +1,186 @@
+"""CUDA covariance / PowerMethod path against the oracle (bit-exact residues)
+and against FP64 (decrypted values)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+LOGN, QBITS, PBITS = 12, [60] + [40] * 12, [60]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import paper_2305_17341_gb300 as pk
+    from oracle.ckks import CKKS, Params
+    from oracle.hmm import matmul_rot_steps, transpose_rot_steps
+    pk.build()
+    ctx = pk.he_ctx_create(pk.make_params(LOGN, QBITS, PBITS), 13)
+    P = Params(LOGN, QBITS, PBITS)
+    he = CKKS(P, 13)
+    n, n1 = 16, 4
+    steps = set(matmul_rot_steps(n, n1, n1, P.S)) | set(transpose_rot_steps(n, n1, P.S))
+    i = 1
+    while i < n * n:
+        steps |= {i % (n * n), (-i) % (n * n)}
+        i <<= 1
+    steps.discard(0)
+    pk.he_keygen(ctx, sorted(steps), want_relin=True)
+    for s in steps:
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    yield pk, ctx, P, he, n, n1
+    pk.he_ctx_destroy(ctx)
+
+
+def res(ct):
+    return np.stack([ct.c0, ct.c1])
+
+
+def test_aggregate_and_refresh_bit_exact(env):
+    from oracle.hmm import tile
+    from oracle.pca import PCA
+    pk, ctx, P, he, n, n1 = env
+    M = np.random.default_rng(3).uniform(-1, 1, (n, n))
+    z = tile(M.ravel(), n, P.S)
+    o = he.encrypt_slots(z, 5, obj=21, period=n * n)
+    g = pk.he_ct_import(ctx, res(o), 5, o.scale, n * n)
+    pca = PCA(he)
+    for axis in (0, 1):
+        ga = pk.he_aggregate(ctx, g, axis, n)
+        oa = pca.aggregate(o, axis, n)
+        assert np.array_equal(pk.he_ct_export(ctx, ga), res(oa))
+        pk.he_ct_free(ga)
+    rs = pk.he_refresh_state(7, 0)
+    gr = pk.he_refresh(ctx, g, rs)
+    orr = he.refresh(o, 8)
+    assert (rs.next_obj, rs.count) == (8, 1)
+    assert np.array_equal(pk.he_ct_export(ctx, gr), res(orr))
+    assert pk.he_ct_info(gr)[0] == P.L
+    for h in (g, gr):
+        pk.he_ct_free(h)
+
+
+def _dataset_blocks(pk, ctx, P, he, X, n):
+    s, t = X.shape
+    nrb, k = -(-s // n), -(-t // n)
+    Xp = np.zeros((nrb * n, k * n))
+    Xp[:s, :t] = X
+    g, o = [], []
+    for l in range(nrb):
+        row = []
+        for j in range(k):
+            blk = Xp[l * n:(l + 1) * n, j * n:(j + 1) * n]
+            z = np.zeros(P.S)
+            z[: n * n] = blk.ravel()
+            row.append(he.encrypt_slots(z, P.L, obj=300 + l * k + j))
+            g.append(pk.he_encrypt_matrix(ctx, blk, P.L, 300 + l * k + j))
+        o.append(row)
+    return g, o, nrb, k
+
+
+def test_covariance_bit_exact_and_fp64(env):
+    from oracle.pca import PCA
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk, ctx, P, he, n, n1 = env
+    X = lowrank_dataset(40, 32, 2)          # ragged: 40 rows -> 3 row blocks, last zero-padded
+    g, o, nrb, k = _dataset_blocks(pk, ctx, P, he, X, n)
+    C = pk.he_covariance(ctx, g, nrb, k, n, X.shape[0], False, n1, n1)
+    Co = PCA(he).covariance(o, X.shape[0], n, n1, n1)
+    Xc = X - X.mean(0)
+    ref = Xc.T @ Xc / X.shape[0]
+    for a in range(k):
+        for b in range(k):
+            assert np.array_equal(pk.he_ct_export(ctx, C[a * k + b]), res(Co[a][b])), (a, b)
+            d = pk.he_decrypt_matrix(ctx, C[a * k + b], n, n)
+            assert np.abs(d - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max() < 1e-4
+    for h in C + g:
+        pk.he_ct_free(h)
+
+
+def test_power_method_and_eigen_shift_bit_exact(env):
+    from oracle.hmm import tile
+    from oracle.pca import PCA, lazy_normalization_schedule
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk, ctx, P, he, n, n1 = env
+    k = 2
+    t = n * k
+    X = lowrank_dataset(64, t, 4)
+    Xc = X - X.mean(0)
+    Cov = Xc.T @ Xc / 64
+    Cs = Cov * (1.5 / np.linalg.eigvalsh(Cov)[-1])
+    Co, Cg = [], []
+    for a in range(k):
+        row = []
+        for b in range(k):
+            z = tile(Cs[a * n:(a + 1) * n, b * n:(b + 1) * n].ravel(), n, P.S)
+            ct = he.encrypt_slots(z, P.L, obj=500 + a * k + b, period=n * n)
+            row.append(ct)
+            Cg.append(pk.he_ct_import(ctx, res(ct), P.L, ct.scale, n * n))
+        Co.append(row)
+    v0 = np.random.default_rng(7).standard_normal(t)
+    v0 /= np.linalg.norm(v0)
+    V0o = [he.encrypt_slots(tile(np.tile(v0[j * n:(j + 1) * n], n), n, P.S), P.L, obj=900 + j, period=n * n)
+           for j in range(k)]
+    V0g = [pk.he_ct_import(ctx, res(v), P.L, v.scale, n * n) for v in V0o]
+    l_P = 3
+    counts = lazy_normalization_schedule(l_P)
+    pca = PCA(he)
+    pca.refresh_obj = 1 << 20
+    lam_o, V_o, ax_o, VT_o = pca.power_method(Co, V0o, 0, n, l_P, counts, 2.0 ** 16)
+    rs = pk.he_refresh_state(1 << 20, 0)
+    lam_g, V_g, VT_g, ax_g = pk.he_power_method(ctx, Cg, k, n, V0g, 0, l_P, counts, 2.0 ** 16, rs)
+    assert ax_g == ax_o and rs.count == pca.refreshes
+    assert np.array_equal(pk.he_ct_export(ctx, lam_g), res(lam_o))
+    for j in range(k):
+        assert np.array_equal(pk.he_ct_export(ctx, V_g[j]), res(V_o[j]))
+        assert np.array_equal(pk.he_ct_export(ctx, VT_g[j]), res(VT_o[j]))
+    S_o = pca.eigen_shift(Co, lam_o, V_o, ax_o, VT_o, n)
+    S_g = pk.he_eigen_shift(ctx, Cg, k, n, lam_g, V_g, ax_g, VT_g, rs)
+    assert rs.count == pca.refreshes
+    for a in range(k):
+        for b in range(k):
+            assert np.array_equal(pk.he_ct_export(ctx, S_g[a * k + b]), res(S_o[a][b]))
+    for h in S_g + V_g + VT_g + V0g + [lam_g]:
+        pk.he_ct_free(h)
+
+
+def test_lazy_schedule_host_matches_oracle_and_paper():
+    import paper_2305_17341_gb300 as pk
+    from oracle.pca import lazy_normalization_schedule
+    pk.build()
+    for t in (1, 4, 9, 14):
+        assert pk.he_lazy_normalization_schedule(t) == lazy_normalization_schedule(t)
+    assert round(np.mean(pk.he_lazy_normalization_schedule(4)), 1) == 14.5
+    assert round(np.mean(pk.he_lazy_normalization_schedule(14)), 1) == 13.8
+
+
+def test_full_size_covariance_256():
+    """Config 2: 256x256 low-rank dataset, 128x128 blocks at N=2^16, chain
+    60 + 20x40, p 2x60: decrypted covariance within 1e-4 of FP64."""
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk.build()
+    ctx = pk.he_ctx_create(pk.he_params_default(2), 77)
+    try:
+        n, n1 = 128, 16
+        S = 1 << 15
+        steps = set(pk.he_rot_steps_for_matmul(n, n1, n1, S)) | set(pk.he_rot_steps_for_transpose(n, n1, S))
+        i = n
+        while i < n * n:
+            steps.add(i)
+            i <<= 1
+        pk.he_keygen(ctx, sorted(steps), want_relin=True)
+        X = lowrank_dataset(256, 256, 2)
+        blocks = [pk.he_encrypt_matrix(ctx, X[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 10 + 2 * l + j)
+                  for l in range(2) for j in range(2)]
+        C = pk.he_covariance(ctx, blocks, 2, 2, n, 256, False, n1, n1)
+        Xc = X - X.mean(0)
+        ref = Xc.T @ Xc / 256
+        for a in range(2):
+            for b in range(2):
+                d = pk.he_decrypt_matrix(ctx, C[a * 2 + b], n, n)
+                assert np.abs(d - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max() < 1e-4
+        for h in C + blocks:
+            pk.he_ct_free(h)
+    finally:
+        pk.he_ctx_destroy(ctx)
