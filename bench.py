@@ -350,6 +350,140 @@ def run_ours(args, rank, world, dist):
     pk.he_ctx_destroy(ctx)
 
 
+def _cov_keys(pk, ctx, n, n1, S):
+    steps = set(pk.he_rot_steps_for_matmul(n, n1, n1, S)) | set(pk.he_rot_steps_for_transpose(n, n1, S))
+    i = 1
+    while i < n * n:
+        steps |= {i % (n * n), (-i) % (n * n)}
+        i <<= 1
+    steps.discard(0)
+    pk.he_keygen(ctx, sorted(steps), True)
+
+
+def run_covariance(args):
+    """Config 2: encrypted covariance of a 256x256 low-rank dataset (128x128 blocks, N=2^16)."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300 import workloads
+    pk.build()
+    n, n1, s, t = 128, 16, args.rows, 256
+    ctx = pk.he_ctx_create(pk.he_params_default(2), 42)
+    _cov_keys(pk, ctx, n, n1, 1 << 15)
+    X = workloads.lowrank_dataset(s, t, 2)
+    nrb = -(-s // n)
+    Xp = np.zeros((nrb * n, t))
+    Xp[:s] = X
+    blocks = [pk.he_encrypt_matrix(ctx, Xp[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 100 + l * 2 + j)
+              for l in range(nrb) for j in range(2)]
+    C = pk.he_covariance(ctx, blocks, nrb, 2, n, s, False, n1, n1)   # warm-up (diagonal cache)
+    for h in C:
+        pk.he_ct_free(h)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        C = pk.he_covariance(ctx, blocks, nrb, 2, n, s, False, n1, n1)
+        times.append(time.perf_counter() - t0)
+        Cd = [pk.he_decrypt_matrix(ctx, h, n, n) for h in C]
+        for h in C:
+            pk.he_ct_free(h)
+    Xc = X - X.mean(0)
+    ref = Xc.T @ Xc / s
+    err = max(float(np.abs(Cd[a * 2 + b] - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max())
+              for a in range(2) for b in range(2))
+    ms = statistics.median(times) * 1000
+    print(json.dumps({"metric": "encrypted covariance time (HCovMtrx)", "value": ms, "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+                      "config": {"workload": "covariance of a %dx256 low-rank dataset, 128x128 blocks, N=2^16, "
+                                             "q 60+20x40, p 2x60" % s, "matmuls": 3 * nrb},
+                      "check": {"max_abs_err_vs_fp64": err, "tol": 1e-4}}), flush=True)
+    pk.he_ctx_destroy(ctx)
+
+
+def run_pca(args):
+    """Config 3: top-8 eigenvectors by HPowerMethod + HEigenShift on the
+    encrypted 256x256 covariance, chain 60 + 13x40, p 2x60 (Sec. 7.2.3)."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300 import workloads
+    pk.build()
+    n, n1, s, t, k = 128, 16, 256, 256, 2
+    l_E, l_P = args.components, args.pm_iters
+    # covariance in the covariance context (config 2)
+    ctx2 = pk.he_ctx_create(pk.he_params_default(2), 42)
+    _cov_keys(pk, ctx2, n, n1, 1 << 15)
+    X = workloads.lowrank_dataset(s, t, 2)
+    blocks = [pk.he_encrypt_matrix(ctx2, X[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 100 + l * 2 + j)
+              for l in range(2) for j in range(2)]
+    t0 = time.perf_counter()
+    C2 = pk.he_covariance(ctx2, blocks, 2, k, n, s, False, n1, n1)
+    cov_s = time.perf_counter() - t0
+    # interactive refresh into the PowerMethod context, with the public
+    # pre-scale by the feature count d = 256 (norm bound B = b^2 c d, b = 1)
+    ctx3 = pk.he_ctx_create(pk.he_params_default(3), 43)
+    S = 1 << 15
+    steps = set()
+    i = 1
+    while i < n * n:
+        steps |= {i % (n * n), (-i) % (n * n)}
+        i <<= 1
+    r = n * n
+    while r < S:
+        steps.add((-r) % S)
+        r *= 2
+    steps.discard(0)
+    pk.he_keygen(ctx3, sorted(steps), True)
+    C3 = []
+    for a in range(k):
+        for b in range(k):
+            blk = pk.he_decrypt_matrix(ctx2, C2[a * k + b], n, n) * t
+            C3.append(pk.he_replicate(ctx3, pk.he_encrypt_matrix(ctx3, blk, 13, 200 + a * k + b), n))
+    rng = np.random.default_rng(3)
+    v0s = []
+    for m in range(l_E):
+        v0 = rng.standard_normal(t)
+        v0 /= np.linalg.norm(v0)
+        for j in range(k):
+            v0s.append(pk.he_replicate(ctx3, pk.he_encrypt_matrix(ctx3, np.tile(v0[j * n:(j + 1) * n], (n, 1)), 13,
+                                                                  300 + m * k + j), n))
+    counts = pk.he_lazy_normalization_schedule(l_P)
+    rs = pk.he_refresh_state(1 << 20, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lams, Vs, axes = pk.he_pca(ctx3, C3, k, n, l_E, v0s, 0, l_P, counts, 2.0 ** 16, rs)
+    pm_s = time.perf_counter() - t0
+    Xc = X - X.mean(0)
+    w, U = np.linalg.eigh(Xc.T @ Xc / s)
+    w, U = w[::-1], U[:, ::-1]
+    cos, lam_he, vecs = [], [], []
+    for m in range(l_E):
+        parts = []
+        for j in range(k):
+            d = pk.he_decrypt_matrix(ctx3, Vs[m][j], n, n)
+            parts.append(d[0] if axes[m] == 0 else d[:, 0])
+        v = np.concatenate(parts)
+        vecs.append(v)
+        cos.append(float(abs(v @ U[:, m]) / np.linalg.norm(v)))
+        lam_he.append(float(pk.he_decrypt_slots(ctx3, lams[m], 1)[0] / t))
+    Vm = np.array([v / np.linalg.norm(v) * np.sign(v @ U[:, m]) for m, v in enumerate(vecs)])
+    Ut = U[:, :l_E].T
+    r2v = 1 - ((Vm - Ut) ** 2).sum() / ((Ut - Ut.mean()) ** 2).sum()
+    print(json.dumps({"metric": "encrypted PCA time (HPowerMethod + HEigenShift, top-%d)" % l_E, "value": pm_s,
+                      "unit": "s", "higher_is_better": False, "n_gpus": 1,
+                      "config": {"workload": "top-%d eigenvectors of the encrypted covariance of a 256x256 low-rank "
+                                             "dataset; PowerMethod at N=2^16, q 60+13x40, p 2x60; l_P=%d; Newton "
+                                             "counts %s; covariance pre-scaled by d=256" % (l_E, l_P, counts)},
+                      "covariance_s": cov_s, "refreshes": rs.count, "cosine_vs_eigh": cos,
+                      "lambda_he": lam_he, "lambda_fp64": [float(x) for x in w[:l_E]], "R2_V": float(r2v),
+                      "per_pm_iteration_s": pm_s / (l_E * (l_P + 1))}), flush=True)
+    pk.he_ctx_destroy(ctx3)
+    pk.he_ctx_destroy(ctx2)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -360,7 +494,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca"])
+    ap.add_argument("--rows", type=int, default=256)
+    ap.add_argument("--components", type=int, default=8)
+    ap.add_argument("--pm-iters", type=int, default=14)
     args = ap.parse_args()
+    if args.workload == "covariance":
+        return run_covariance(args)
+    if args.workload == "pca":
+        return run_pca(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None

@@ -245,6 +245,13 @@ int he_power_method(he_ctx *ctx, he_ct *const *cov, int k, int n, he_ct *const *
 int he_eigen_shift(he_ctx *ctx, he_ct **cov, int k, int n, const he_ct *lambda, he_ct *const *V, int axis,
                    he_ct *const *VT, he_refresh_state *rs);
 
+/* Privacy-Preserving PCA (Sec. 6.2): for m < l_E, HPowerMethod from the
+ * start vector v0[m*k .. m*k+k) on the current covariance, then HEigenShift
+ * (not after the last component).  cov is left unchanged.  Outputs
+ * lambdas[m], V[m*k + j] and the axis of each eigenvector in axes[m]. */
+int he_pca(he_ctx *ctx, he_ct *const *cov, int k, int n, int l_E, he_ct *const *v0, int axis, int l_P,
+           const int *newton_counts, double B2, he_refresh_state *rs, he_ct **lambdas, he_ct **V, int *axes);
+
 /* Counters of the key-switch phases since the last reset: MultSum, Decompose,
  * ModDown (Table 1 caption), and kernel launches.  Any pointer may be NULL. */
 int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset);

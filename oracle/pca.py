@@ -155,6 +155,9 @@ class PCA:
             elif a.level > b.level and a.scale == b.scale:
                 a = self.he.drop(a, b.level)
             else:
+                # matching the scales spends one level: refresh an operand that has none
+                a = self.need(a, 1)
+                b = self.need(b, 1)
                 lv = min(a.level, b.level) - 1
                 a = self.to_scale(a, lv, a.scale) if a.level != lv else a
                 b = self.to_scale(b, lv, a.scale)

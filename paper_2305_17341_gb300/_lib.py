@@ -88,6 +88,8 @@ SIGNATURES = {
     "he_power_method": [vp, P(vp), ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp), P(vp),
                         P(ip)],
     "he_eigen_shift": [vp, P(vp), ip, ip, vp, P(vp), ip, P(vp), P(he_refresh_state)],
+    "he_pca": [vp, P(vp), ip, ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp),
+               P(ip)],
     "he_counters": [vp, llp, llp, llp, llp, ip],
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
@@ -340,6 +342,17 @@ def he_power_method(ctx, cov, k, n, v0, axis, l_P, counts, B2, rs):
     check(lib().he_power_method(ctx, _handles(cov), k, n, _handles(v0), axis, l_P, cs, B2, ctypes.byref(rs),
                                 ctypes.byref(lam), V, VT, ctypes.byref(ax)))
     return lam, [vp(x) for x in V], [vp(x) for x in VT], ax.value
+
+
+def he_pca(ctx, cov, k, n, l_E, v0, axis, l_P, counts, B2, rs):
+    """Returns (lambdas[l_E], V[l_E][k], axes[l_E])."""
+    lams = (vp * l_E)()
+    V = (vp * (l_E * k))()
+    axes = (ctypes.c_int * l_E)()
+    cs = (ctypes.c_int * len(counts))(*counts)
+    check(lib().he_pca(ctx, _handles(cov), k, n, l_E, _handles(v0), axis, l_P, cs, B2, ctypes.byref(rs), lams, V,
+                       axes))
+    return ([vp(x) for x in lams], [[vp(V[m * k + j]) for j in range(k)] for m in range(l_E)], list(axes))
 
 
 def he_eigen_shift(ctx, cov, k, n, lam, V, axis, VT, rs):

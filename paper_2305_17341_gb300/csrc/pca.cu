@@ -200,6 +200,9 @@ public:
             } else if (a->level > b->level && a->scale == b->scale) {
                 a = dropto(a.p, b->level);
             } else {
+                // matching the scales spends one level: refresh an operand that has none
+                a = need(std::move(a), 1);
+                b = need(std::move(b), 1);
                 const int lv = std::min(a->level, b->level) - 1;
                 const double sa = a->scale;  // read before a is moved into the call
                 if (a->level != lv) a = to_scale(std::move(a), lv, sa);
@@ -576,6 +579,52 @@ int he_power_method(he_ctx *ctx, he_ct *const *cov, int k, int n, he_ct *const *
         VT[j] = VTo[j].release();
     }
     *axis_out = ax;
+    return HE_OK;
+    PCA_GUARD_END
+}
+
+int he_pca(he_ctx *ctx, he_ct *const *cov, int k, int n, int l_E, he_ct *const *v0, int axis, int l_P,
+           const int *newton_counts, double B2, he_refresh_state *rs, he_ct **lambdas, he_ct **V, int *axes) {
+    if (!ctx || !cov || !v0 || !newton_counts || !rs || !lambdas || !V || !axes || k < 1 || !pow2(n) || l_E < 1 ||
+        l_P < 1 || (axis != 0 && axis != 1) || B2 <= 0) {
+        set_error("bad arguments");
+        return HE_ERR_ARG;
+    }
+    Ctx &c = ctx->c;
+    PCA_GUARD_BEGIN
+    RefreshState st{rs->next_obj, rs->count};
+    PcaOps ops(&c, &st);
+    std::vector<HC> C;
+    for (int i = 0; i < k * k; i++) C.push_back(ops.clone(cov[i]));
+    std::vector<HC> lam_out, V_out;
+    std::vector<int> ax_out;
+    for (int m = 0; m < l_E; m++) {
+        std::vector<he_ct *> Cp(k * k);
+        for (int i = 0; i < k * k; i++) Cp[i] = C[i].p;
+        HC lam;
+        std::vector<HC> Vo, VTo;
+        int ax = 0;
+        ops.power_method(Cp.data(), k, n, v0 + (size_t)m * k, axis, l_P, newton_counts, B2, lam, Vo, VTo, ax);
+        if (m + 1 < l_E) {
+            std::vector<he_ct *> Vp(k), VTp(k);
+            for (int j = 0; j < k; j++) {
+                Vp[j] = Vo[j].p;
+                VTp[j] = VTo[j].p;
+            }
+            C = ops.eigen_shift(Cp.data(), k, lam.p, Vp.data(), ax, VTp.data());
+        }
+        lam_out.push_back(std::move(lam));
+        for (auto &v : Vo) V_out.push_back(std::move(v));
+        ax_out.push_back(ax);
+    }
+    if (int rc = sync_status(c)) return rc;
+    rs->next_obj = st.next_obj;
+    rs->count = st.count;
+    for (int m = 0; m < l_E; m++) {
+        lambdas[m] = lam_out[m].release();
+        axes[m] = ax_out[m];
+    }
+    for (size_t i = 0; i < V_out.size(); i++) V[i] = V_out[i].release();
     return HE_OK;
     PCA_GUARD_END
 }

@@ -184,3 +184,54 @@ def test_full_size_covariance_256():
             pk.he_ct_free(h)
     finally:
         pk.he_ctx_destroy(ctx)
+
+
+def test_pca_two_components_bit_exact(env):
+    """he_pca (l_E = 2) equals the oracle's PowerMethod, EigenShift, PowerMethod."""
+    from oracle.hmm import tile
+    from oracle.pca import PCA, lazy_normalization_schedule
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk, ctx, P, he, n, n1 = env
+    k = 2
+    t = n * k
+    X = lowrank_dataset(64, t, 6)
+    Xc = X - X.mean(0)
+    Cs = (Xc.T @ Xc / 64) * t
+    Co, Cg = [], []
+    for a in range(k):
+        row = []
+        for b in range(k):
+            ct = he.encrypt_slots(tile(Cs[a * n:(a + 1) * n, b * n:(b + 1) * n].ravel(), n, P.S), P.L,
+                                  obj=700 + a * k + b, period=n * n)
+            row.append(ct)
+            Cg.append(pk.he_ct_import(ctx, res(ct), P.L, ct.scale, n * n))
+        Co.append(row)
+    rng = np.random.default_rng(9)
+    V0o, V0g = [], []
+    for m in range(2):
+        v0 = rng.standard_normal(t)
+        v0 /= np.linalg.norm(v0)
+        vs = [he.encrypt_slots(tile(np.tile(v0[j * n:(j + 1) * n], n), n, P.S), P.L, obj=800 + 10 * m + j,
+                               period=n * n) for j in range(k)]
+        V0o.append(vs)
+        V0g += [pk.he_ct_import(ctx, res(v), P.L, v.scale, n * n) for v in vs]
+    l_P = 2
+    counts = lazy_normalization_schedule(l_P)
+    pca = PCA(he)
+    C = Co
+    want = []
+    for m in range(2):
+        lam, V, ax, VT = pca.power_method(C, V0o[m], 0, n, l_P, counts, 2.0 ** 16)
+        want.append((lam, V, ax))
+        if m == 0:
+            C = pca.eigen_shift(C, lam, V, ax, VT, n)
+    rs = pk.he_refresh_state(1 << 20, 0)
+    lams, Vs, axes = pk.he_pca(ctx, Cg, k, n, 2, V0g, 0, l_P, counts, 2.0 ** 16, rs)
+    assert rs.count == pca.refreshes
+    for m in range(2):
+        assert axes[m] == want[m][2]
+        assert np.array_equal(pk.he_ct_export(ctx, lams[m]), res(want[m][0]))
+        for j in range(k):
+            assert np.array_equal(pk.he_ct_export(ctx, Vs[m][j]), res(want[m][1][j]))
+    for h in lams + [x for v in Vs for x in v] + Cg + V0g:
+        pk.he_ct_free(h)
