@@ -31,7 +31,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HE 128×128 matmul/s batched vs plain, same GPU, bit-exact; keyswitch % HBM peak"
 UNIT = "matmul/s"
-N_MAT, N1 = 128, 16
+N_MAT = 128
+# baby-step count n1 used for each matrix dimension
+N1_FOR = {16: 4, 32: 8, 64: 8, 128: 16}
 LEVEL = 20
 # per-product operation counts of the hoisted schedule at n=128, n1=16
 # (Table 1 "Optimized" rows as the schedule performs them)
@@ -163,6 +165,7 @@ def run_ours(args, rank, world, dist):
     from paper_2305_17341_gb300 import _lib, workloads
 
     local = env_int("LOCAL_RANK", 0)
+    n_mat, n1 = args.n, N1_FOR[args.n]
     torch.cuda.set_device(local)
     pk.build()
     L = _lib.lib()
@@ -170,12 +173,12 @@ def run_ours(args, rank, world, dist):
     # the library launches on this stream; every CUDA event below is recorded on it
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
-    pk.he_keygen(ctx, pk.he_rot_steps_for_matmul(N_MAT, N1, N1, 1 << 15), True)
+    pk.he_keygen(ctx, pk.he_rot_steps_for_matmul(n_mat, n1, n1, 1 << 15), True)
     B = args.batch
-    mats = [workloads.matmul_pair(N_MAT, 10 * (rank * 1000 + i)) for i in range(B)]
+    mats = [workloads.matmul_pair(n_mat, 10 * (rank * 1000 + i)) for i in range(B)]
     cts = [(pk.he_encrypt_matrix(ctx, A, LEVEL, 2 * i), pk.he_encrypt_matrix(ctx, Bm, LEVEL, 2 * i + 1))
            for i, (A, Bm) in enumerate(mats)]
-    jobs = [(a, b, N_MAT, N1, N1) for a, b in cts]
+    jobs = [(a, b, n_mat, n1, n1) for a, b in cts]
 
     def batched_step():
         outs = pk.he_hmatmul_batch(jobs)
@@ -193,8 +196,8 @@ def run_ours(args, rank, world, dist):
 
     # correctness spot check of the benchmarked configuration (untimed)
     outs = pk.he_hmatmul_batch(jobs[:1])
-    err = float(np.abs(pk.he_decrypt_matrix(ctx, outs[0], N_MAT, N_MAT) - mats[0][0] @ mats[0][1]).max())
-    single = pk.he_hmatmul(ctx, cts[0][0], cts[0][1], N_MAT, N1, N1)
+    err = float(np.abs(pk.he_decrypt_matrix(ctx, outs[0], n_mat, n_mat) - mats[0][0] @ mats[0][1]).max())
+    single = pk.he_hmatmul(ctx, cts[0][0], cts[0][1], n_mat, n1, n1)
     bitexact = bool(np.array_equal(pk.he_ct_export(ctx, single), pk.he_ct_export(ctx, outs[0])))
     pk.he_ct_free(single)
     pk.he_ct_free(outs[0])
@@ -234,7 +237,7 @@ def run_ours(args, rank, world, dist):
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(tstream)
         for a, b in cts:
-            o = pk.he_hmatmul(ctx, a, b, N_MAT, N1, N1)
+            o = pk.he_hmatmul(ctx, a, b, n_mat, n1, n1)
             pk.he_ct_free(o)
         p1.record(tstream)
         torch.cuda.synchronize()
@@ -261,7 +264,7 @@ def run_ours(args, rank, world, dist):
                 ptr = ctypes.cast(host_in[i, j].data_ptr(), u64p)
                 _lib.check(L.he_ct_import(ctx, ptr, LEVEL, scale, 1 << 15, ctypes.byref(h)))
                 hs.append(h)
-        outs = pk.he_hmatmul_batch([(hs[2 * i], hs[2 * i + 1], N_MAT, N1, N1) for i in range(B)])
+        outs = pk.he_hmatmul_batch([(hs[2 * i], hs[2 * i + 1], n_mat, n1, n1) for i in range(B)])
         for i, o in enumerate(outs):
             _lib.check(L.he_ct_export(o, ctypes.cast(host_out[i].data_ptr(), u64p)))
             pk.he_ct_free(o)
@@ -332,8 +335,8 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "batch of %d encrypted 128x128 matmuls, N=2^16, q 60+20x40, p 2x60, level 20, "
-                               "n1_z=n1_t=16" % B, "batch_per_gpu": B, "n": N_MAT, "logN": 16, "level": LEVEL,
+        "config": {"workload": "batch of %d encrypted %dx%d matmuls, N=2^16, q 60+20x40, p 2x60, level 20, "
+                               "n1_z=n1_t=%d" % (B, n_mat, n_mat, n1), "batch_per_gpu": B, "n": n_mat, "logN": 16, "level": LEVEL,
                    "l2": "inputs larger than L2 (14 GB of rotation keys and %d ciphertext pairs streamed per step)" % B,
                    "parallelism": "replicas" if world == 1 else "independent products per rank"},
         "plain": {"value": plain, "unit": UNIT, "note": "same products, one he_hmatmul call each"},
@@ -346,6 +349,8 @@ def run_ours(args, rank, world, dist):
         "clocks": ck, "gpu_launches": launches,
         "check": {"max_abs_err": err, "tol": 1e-4, "batch_equals_single_bitexact": bitexact},
     }
+    if n_mat != N_MAT:
+        line["note"] = "profiling case (n=%d), not the benchmark workload" % n_mat
     print(json.dumps(line), flush=True)
     pk.he_ctx_destroy(ctx)
 
@@ -484,17 +489,73 @@ def run_pca(args):
     pk.he_ctx_destroy(ctx2)
 
 
+
+def run_mixed(args):
+    """Config 4: 96 independent products, n in {16,32,64,128}, N in {2^15, 2^16},
+    remaining level in [3, 20]; plain (one call each) vs one grouped batch."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300 import workloads
+    pk.build()
+    jobs = workloads.mixed_matmul_jobs(args.jobs, 4)
+    ctxs = {15: pk.he_ctx_create(pk.he_params_default(4), 15), 16: pk.he_ctx_create(pk.he_params_default(2), 16)}
+    for logN, ctx in ctxs.items():
+        S = 1 << (logN - 1)
+        steps = set()
+        for n in sorted({j[0] for j in jobs if j[1] == logN}):
+            steps |= set(pk.he_rot_steps_for_matmul(n, N1_FOR[n], N1_FOR[n], S))
+        pk.he_keygen(ctx, sorted(steps), True)
+    cts = []
+    for i, (n, logN, level, A, B) in enumerate(jobs):
+        ctx = ctxs[logN]
+        cts.append((pk.he_encrypt_matrix(ctx, A, level, 2 * i), pk.he_encrypt_matrix(ctx, B, level, 2 * i + 1)))
+    spec = [(a, b, n, N1_FOR[n], N1_FOR[n]) for (a, b), (n, _, _, _, _) in zip(cts, jobs)]
+    outs = pk.he_hmatmul_batch(spec)            # warm-up: plaintext diagonals of every (n, level)
+    for o in outs:
+        pk.he_ct_free(o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [pk.he_hmatmul(ctxs[jobs[i][1]], cts[i][0], cts[i][1], jobs[i][0], N1_FOR[jobs[i][0]],
+                           N1_FOR[jobs[i][0]]) for i in range(len(jobs))]
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch = pk.he_hmatmul_batch(spec)
+    t_batch = time.perf_counter() - t0
+    bitexact = all(np.array_equal(pk.he_ct_export(ctxs[jobs[i][1]], plain[i]),
+                                  pk.he_ct_export(ctxs[jobs[i][1]], batch[i])) for i in range(len(jobs)))
+    err = 0.0
+    for i, (n, logN, level, A, B) in enumerate(jobs):
+        err = max(err, float(np.abs(pk.he_decrypt_matrix(ctxs[logN], batch[i], n, n) - A @ B).max()))
+    groups = len({(logN, level, n) for n, logN, level, _, _ in jobs})
+    print(json.dumps({"metric": "mixed batch of encrypted matmuls/s (batched vs plain)",
+                      "value": len(jobs) / t_batch, "unit": "matmul/s", "higher_is_better": True, "n_gpus": 1,
+                      "plain": len(jobs) / t_plain, "speedup": t_plain / t_batch,
+                      "config": {"workload": "%d products, n in {16,32,64,128}, N in {2^15,2^16}, level in [3,20], "
+                                             "chain 60+20x40, p 2x60" % len(jobs), "groups": groups},
+                      "check": {"batch_equals_plain_bitexact": bitexact, "max_abs_err_vs_fp64": err, "tol": 1e-4}}),
+          flush=True)
+    for h in plain + batch + [x for c in cts for x in c]:
+        pk.he_ct_free(h)
+    for ctx in ctxs.values():
+        pk.he_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--n", type=int, default=N_MAT, choices=[16, 32, 64, 128],
+                    help="matrix dimension (128 is the benchmark; smaller sizes are profiling cases)")
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca"])
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed"])
+    ap.add_argument("--jobs", type=int, default=96)
     ap.add_argument("--rows", type=int, default=256)
     ap.add_argument("--components", type=int, default=8)
     ap.add_argument("--pm-iters", type=int, default=14)
@@ -503,6 +564,8 @@ def main():
         return run_covariance(args)
     if args.workload == "pca":
         return run_pca(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None
