@@ -429,19 +429,7 @@ def run_pca(args):
     cov_s = time.perf_counter() - t0
     # interactive refresh into the PowerMethod context, with the public
     # pre-scale by the feature count d = 256 (norm bound B = b^2 c d, b = 1)
-    ctx3 = pk.he_ctx_create(pk.he_params_default(3), 43)
-    S = 1 << 15
-    steps = set()
-    i = 1
-    while i < n * n:
-        steps |= {i % (n * n), (-i) % (n * n)}
-        i <<= 1
-    r = n * n
-    while r < S:
-        steps.add((-r) % S)
-        r *= 2
-    steps.discard(0)
-    pk.he_keygen(ctx3, sorted(steps), True)
+    ctx3 = _pm_context(pk, n, 1 << 15)
     C3 = []
     for a in range(k):
         for b in range(k):
@@ -488,6 +476,182 @@ def run_pca(args):
     pk.he_ctx_destroy(ctx3)
     pk.he_ctx_destroy(ctx2)
 
+
+
+def _pm_context(pk, n, S):
+    """The PowerMethod context (chain 60 + 13x40, p 2x60) with the rotation
+    keys of Aggregate-style sums (+-2^i) and of replication."""
+    ctx3 = pk.he_ctx_create(pk.he_params_default(3), 43)
+    steps = set()
+    i = 1
+    while i < n * n:
+        steps |= {i % (n * n), (-i) % (n * n)}
+        i <<= 1
+    r = n * n
+    while r < S:
+        steps.add((-r) % S)
+        r *= 2
+    steps.discard(0)
+    pk.he_keygen(ctx3, sorted(steps), True)
+    return ctx3
+
+
+def run_served(args):
+    """Config 5: Poisson arrivals of X^T X row-block jobs (one 128-row block of
+    a 256-feature stream each, accumulated into one encrypted X^T X / s),
+    128x128 products, 256x256 covariances and top-k PCA jobs, served by
+    he_server over resident keys: one worker per context (covariance chain at
+    N=2^16 and the PowerMethod chain), products of all queued jobs merged into
+    batched passes, admission against a device-memory budget."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300 import workloads
+    pk.build()
+    n, n1, k, t = 128, 16, 2, 256
+    mix = workloads.served_job_mix(args.rate, args.duration, 5)
+    ctx2 = pk.he_ctx_create(pk.he_params_default(2), 52)
+    _cov_keys(pk, ctx2, n, n1, 1 << 15)
+    # client side, before the timed region: encrypt every input
+    n_blk = max(1, sum(1 for _, kd in mix if kd == "xtx_block"))
+    Xs = workloads.lowrank_dataset(n * n_blk, t, 6)
+    stream = [[pk.he_encrypt_matrix(ctx2, Xs[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 10000 + 2 * l + j)
+               for j in range(k)] for l in range(n_blk)]
+    pairs = [workloads.matmul_pair(n, 70 + i) for i in range(4)]
+    mm = [(pk.he_encrypt_matrix(ctx2, A, 20, 500 + 2 * i), pk.he_encrypt_matrix(ctx2, B, 20, 501 + 2 * i))
+          for i, (A, B) in enumerate(pairs)]
+    Xc2 = workloads.lowrank_dataset(256, t, 2)
+    cov_in = [pk.he_encrypt_matrix(ctx2, Xc2[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 600 + 2 * l + j)
+              for l in range(2) for j in range(k)]
+    want_pca = any(kd == "pca" for _, kd in mix) and not args.no_pca
+    ctxs = [ctx2]
+    pca_in, counts = [], None
+    if want_pca:
+        ctx3 = _pm_context(pk, n, 1 << 15)
+        ctxs.append(ctx3)
+        Xc = Xc2 - Xc2.mean(0)
+        Cs = Xc.T @ Xc / 256 * t
+        pca_in = [pk.he_replicate(ctx3, pk.he_encrypt_matrix(ctx3, Cs[a * n:(a + 1) * n, b * n:(b + 1) * n], 13,
+                                                             700 + a * k + b), n) for a in range(k) for b in range(k)]
+        rng = np.random.default_rng(3)
+        for m in range(args.components):
+            v0 = rng.standard_normal(t)
+            v0 /= np.linalg.norm(v0)
+            pca_in += [pk.he_replicate(ctx3, pk.he_encrypt_matrix(ctx3, np.tile(v0[j * n:(j + 1) * n], (n, 1)), 13,
+                                                                  800 + m * k + j), n) for j in range(k)]
+        counts = pk.he_lazy_normalization_schedule(args.pm_iters)
+    srv = pk.he_server_create(ctxs, args.budget_gb * 1e9, args.max_batch)
+
+    def submit(kind, idx, acc_id=1):
+        if kind == "xtx_block":
+            return pk.he_server_submit(srv, pk.HE_JOB_XTX_BLOCK, stream[idx], n=n, n1z=n1, n1t=n1, k=k,
+                                       s=n * n_blk, acc_id=acc_id)
+        if kind == "matmul":
+            a, b = mm[idx % len(mm)]
+            return pk.he_server_submit(srv, pk.HE_JOB_MATMUL, [a, b], n=n, n1z=n1, n1t=n1)
+        if kind == "covariance":
+            return pk.he_server_submit(srv, pk.HE_JOB_COVARIANCE, cov_in, n=n, n1z=n1, n1t=n1, n_row_blocks=2, k=k,
+                                       s=256)
+        return pk.he_server_submit(srv, pk.HE_JOB_PCA, pca_in, n=n, k=k, l_E=args.components, l_P=args.pm_iters,
+                                   axis=0, counts=counts, B2=2.0 ** 16, refresh_obj=(1 << 20) + (idx << 16))
+
+    def drain(ids):
+        outs = {}
+        for j, kind in ids:
+            pk.he_server_wait(srv, j, 3600.0)
+            try:
+                outs[j] = (kind, pk.he_server_result(srv, j)[0])
+            except pk.HeError as e:
+                outs[j] = (kind, e)
+        return outs
+
+    # warm-up (plaintext-diagonal caches of every shape and level), untimed
+    warm = [(submit("matmul", 0), "matmul"), (submit("covariance", 0), "covariance"),
+            (submit("xtx_block", 0, acc_id=0), "xtx_block")]
+    warm.append((pk.he_server_submit(srv, pk.HE_JOB_XTX_FINAL, [], ctx=ctx2, n=n, n1z=n1, n1t=n1, k=k, acc_id=0),
+                 "final"))
+    for kind, res in drain(warm).values():
+        if not isinstance(res, Exception):
+            for h in res:
+                pk.he_ct_free(h)
+    pk.he_server_destroy(srv)                 # a fresh server for the timed run (statistics from zero)
+    srv = pk.he_server_create(ctxs, args.budget_gb * 1e9, args.max_batch)
+    torch.cuda.synchronize()
+    # ---- timed: arrivals in real time
+    ids, nb, counters = [], 0, {}
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    for at, kind in mix:
+        dt = t0 + at - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        idx = counters.get(kind, 0)
+        counters[kind] = idx + 1
+        try:
+            ids.append((submit(kind, nb if kind == "xtx_block" else idx), kind))
+            nb += kind == "xtx_block"
+        except pk.HeError as e:
+            if e.code != pk.HE_ERR_ADMISSION:     # counted by the server's statistics
+                raise
+    fin = pk.he_server_submit(srv, pk.HE_JOB_XTX_FINAL, [], ctx=ctx2, n=n, n1z=n1, n1t=n1, k=k, acc_id=1)
+    ids.append((fin, "final"))
+    res = drain(ids)
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    names = {1: "matmul", 2: "covariance", 3: "xtx_block", 4: "xtx_final", 5: "pca"}
+    per_kind = {}
+    for kd, name in names.items():
+        st = pk.he_server_stats(srv, kd)
+        if st["submitted"]:
+            per_kind[name] = {x: st[x] for x in ("submitted", "admitted", "rejected", "completed", "failed",
+                                                 "p50_ms", "p99_ms", "mean_ms", "max_ms")}
+    st = pk.he_server_stats(srv, 0)
+    pk.he_server_destroy(srv)
+    # ---- checks against FP64 (decrypted, untimed)
+    check = {}
+    xtx = res[fin][1]
+    if not isinstance(xtx, Exception):
+        Xb = Xs[:n * nb]
+        ref = Xb.T @ Xb / (n * n_blk)
+        check["xtx_max_abs_err"] = max(float(np.abs(pk.he_decrypt_matrix(ctx2, xtx[a * k + b], n, n) -
+                                                    ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max())
+                                       for a in range(k) for b in range(k))
+    for j, (kind, r) in res.items():
+        if isinstance(r, Exception):
+            continue
+        if kind == "matmul" and "matmul_max_abs_err" not in check:
+            A, B = pairs[[jj for jj, kk in ids if kk == "matmul"].index(j) % len(mm)]
+            check["matmul_max_abs_err"] = float(np.abs(pk.he_decrypt_matrix(ctx2, r[0], n, n) - A @ B).max())
+        if kind == "covariance" and "covariance_max_abs_err" not in check:
+            Xc = Xc2 - Xc2.mean(0)
+            ref = Xc.T @ Xc / 256
+            check["covariance_max_abs_err"] = max(
+                float(np.abs(pk.he_decrypt_matrix(ctx2, r[a * k + b], n, n) - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max())
+                for a in range(k) for b in range(k))
+        for h in r:
+            pk.he_ct_free(h)
+    failed = sum(1 for _, r in res.values() if isinstance(r, Exception))
+    print(json.dumps({
+        "metric": "served encrypted jobs/s (Poisson arrivals; continuous batching over resident keys)",
+        "value": st["jobs_per_s"], "unit": "jobs/s", "higher_is_better": True, "n_gpus": 1,
+        "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"], "max": st["max_ms"]},
+        "per_kind": per_kind,
+        "admitted": st["admitted"], "rejected": st["rejected"], "failed": failed,
+        "ticks": st["ticks"], "products": st["products"],
+        "products_per_tick": st["products"] / max(1, st["ticks"]), "max_products_per_tick": st["max_products_per_tick"],
+        "key_bytes": st["key_bytes"], "wall_s": wall, "clocks": ck,
+        "config": {"workload": "Poisson arrivals at %.2f jobs/s for %.0f s: X^T X row blocks (128x256 each, one "
+                               "accumulator, %d blocks), 128x128 products, 256x256 covariances, top-%d PCA; "
+                               "N=2^16, covariance chain 60+20x40 / PowerMethod chain 60+13x40, p 2x60"
+                               % (args.rate, args.duration, nb, args.components),
+                   "budget_gb": args.budget_gb, "max_batch": args.max_batch, "jobs": len(mix)},
+        "check": dict(check, tol=1e-4)}), flush=True)
+    for h in [x for blk in stream for x in blk] + [x for p in mm for x in p] + cov_in + pca_in:
+        pk.he_ct_free(h)
+    for c in ctxs:
+        pk.he_ctx_destroy(c)
 
 
 def run_mixed(args):
@@ -554,7 +718,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed"])
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served"])
+    ap.add_argument("--rate", type=float, default=1.5, help="served: arrivals per second")
+    ap.add_argument("--duration", type=float, default=30.0, help="served: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
+    ap.add_argument("--max-batch", type=int, default=8, help="served: products per batched pass")
+    ap.add_argument("--no-pca", action="store_true", help="served: leave PCA jobs out of the mix")
     ap.add_argument("--jobs", type=int, default=96)
     ap.add_argument("--rows", type=int, default=256)
     ap.add_argument("--components", type=int, default=8)
@@ -566,6 +735,8 @@ def main():
         return run_pca(args)
     if args.workload == "mixed":
         return run_mixed(args)
+    if args.workload == "served":
+        return run_served(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None

@@ -270,6 +270,102 @@ int he_trace_enable(he_ctx *ctx, int on);
 int he_bench_butterfly(int iters, double *bfly_per_s);
 int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, double *bytes, int reset);
 
+/* ------------------------------------------------------------------ serving
+ * A service over contexts whose keys stay resident (Sec. 2: the keys are on
+ * the server before the computation; the paper's throughput is bounded by
+ * device memory, Sec. 7).  One worker thread per context drains that
+ * context's queue in ticks: every job queued when a tick starts joins it,
+ * the block products of all its matrix-product and covariance jobs run as
+ * batched passes (at most max_batch products per pass), then each job's own
+ * remaining steps run.  Jobs that arrive during a tick join the next one.
+ *
+ * While a server runs, its contexts belong to it: the caller may still call
+ * he_ct_export, he_decrypt_*, he_ct_info and he_ct_free on ciphertexts of
+ * those contexts (from any thread), and nothing else on them.  Input
+ * ciphertexts stay caller-owned and must stay alive and unchanged until the
+ * job completes; results pass to the caller through he_server_result.
+ *
+ * Admission: every job is charged an estimate of the device bytes it holds
+ * from admission until its results are taken (its batched temporaries, the
+ * intermediates of its circuit and its outputs; resident keys are not
+ * charged).  A job whose charge would take the total above hbm_budget_bytes
+ * is rejected with HE_ERR_ADMISSION and counted. */
+typedef struct he_server he_server;
+
+typedef struct he_server_cfg {
+    double hbm_budget_bytes; /* bound on the summed charges of admitted jobs */
+    int max_batch;           /* products per batched pass (>= 1) */
+} he_server_cfg;
+
+#define HE_JOB_MATMUL 1     /* in: A, B; out: A*B (one ciphertext) */
+#define HE_JOB_COVARIANCE 2 /* in: n_row_blocks*k blocks; out: k*k covariance blocks (he_covariance) */
+#define HE_JOB_XTX_BLOCK 3  /* in: the k blocks of one row block; adds X_l^T X_l / s into accumulator acc_id */
+#define HE_JOB_XTX_FINAL 4  /* out: the k*k blocks of the accumulated X^T X / s; the accumulator is consumed */
+#define HE_JOB_PCA 5        /* in: k*k covariance blocks, then l_E*k start vectors; out: l_E eigenvalue
+                             * ciphertexts, then l_E*k eigenvector blocks (he_pca) */
+
+typedef struct he_job {
+    int kind;                  /* HE_JOB_* */
+    he_ctx *ctx;               /* the context of a job without inputs (X^T X final); else NULL or the inputs' */
+    he_ct *const *in;          /* inputs, all of one context served by this server */
+    int n_in;
+    int n;                     /* block dimension (power of two, n*n <= slots) */
+    he_mm_sched sched;         /* baby steps of Z/T (and of G: n1_z) */
+    int n_row_blocks, k, s;    /* covariance / X^T X: row blocks, feature blocks, total rows s */
+    int centered;              /* covariance: the data is already centred */
+    uint64_t acc_id;           /* X^T X accumulator; one accumulation stream per id and context */
+    int l_E, l_P, axis;        /* PCA: components, PowerMethod iterations, start-vector axis */
+    const int *newton_counts;  /* PCA: l_P Newton counts (copied at submission) */
+    double B2;                 /* PCA: Lazy Normalization bound */
+    uint32_t refresh_obj;      /* PCA: first refresh object counter */
+} he_job;
+
+#define HE_JOB_QUEUED 0
+#define HE_JOB_RUNNING 1
+#define HE_JOB_DONE 2
+#define HE_JOB_FAILED 3
+
+typedef struct he_serving_stats {
+    long long submitted, admitted, rejected, completed, failed;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> done latency of completed jobs (nearest rank) */
+    double jobs_per_s;                      /* completed jobs / (last completion - first submission) */
+    long long ticks, products, max_products_per_tick;
+    double charged_bytes;                   /* summed charges of admitted jobs not yet collected */
+    double key_bytes;                       /* resident rotation and relinearisation keys */
+} he_serving_stats;
+
+/* Starts one worker per context.  Errors: HE_ERR_ARG (null, empty, repeated
+ * context, max_batch < 1, budget <= 0). */
+int he_server_create(const he_server_cfg *cfg, he_ctx *const *ctxs, int n_ctx, he_server **out);
+
+/* Validates and queues a job; *job_id identifies it.  Errors, with no job
+ * queued: HE_ERR_ARG (bad kind, operands, sizes or a context not served),
+ * HE_ERR_LEVEL (too few levels), HE_ERR_KEY_MISSING (a rotation key the job
+ * needs is absent), HE_ERR_ADMISSION (over the budget). */
+int he_server_submit(he_server *srv, const he_job *job, uint64_t *job_id);
+
+/* Status (HE_JOB_*) of a job; *error = its HE_ERR_* code if it failed;
+ * *latency_ms = submit -> done once done.  Any output pointer may be NULL. */
+int he_server_poll(he_server *srv, uint64_t job_id, int *status, int *error, double *latency_ms);
+
+/* Waits up to timeout_s seconds (host wait) for a job to finish; returns
+ * HE_ERR_TIMEOUT if it has not. */
+int he_server_wait(he_server *srv, uint64_t job_id, double timeout_s, int *status);
+
+/* Moves a finished job's outputs to the caller (max_outs must hold them all)
+ * and forgets the job, releasing its charge.  aux (may be NULL) receives, for
+ * PCA, the l_E eigenvector axes followed by the number of refreshes.  A
+ * failed job returns its error code (and is forgotten). */
+int he_server_result(he_server *srv, uint64_t job_id, he_ct **outs, int max_outs, int *n_outs, int *aux,
+                     int max_aux, int *n_aux);
+
+/* Counters and latency percentiles over jobs of one kind (0: all kinds). */
+int he_server_stats(he_server *srv, int kind, he_serving_stats *out);
+
+/* Finishes every queued job, stops the workers, frees uncollected outputs
+ * and accumulators. */
+int he_server_destroy(he_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

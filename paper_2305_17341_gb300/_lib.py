@@ -16,6 +16,8 @@ ERRORS = {
     -1: "HE_ERR_ARG", -2: "HE_ERR_PARAM", -3: "HE_ERR_LEVEL", -4: "HE_ERR_SCALE", -5: "HE_ERR_KEY_MISSING",
     -6: "HE_ERR_OOM", -7: "HE_ERR_ADMISSION", -8: "HE_ERR_TIMEOUT", -9: "HE_ERR_CUDA",
 }
+(HE_ERR_ARG, HE_ERR_PARAM, HE_ERR_LEVEL, HE_ERR_SCALE, HE_ERR_KEY_MISSING, HE_ERR_OOM, HE_ERR_ADMISSION,
+ HE_ERR_TIMEOUT, HE_ERR_CUDA) = range(-1, -10, -1)
 
 
 class HeError(RuntimeError):
@@ -41,6 +43,29 @@ class he_mm_job(ctypes.Structure):
 class he_refresh_state(ctypes.Structure):
     _fields_ = [("next_obj", ctypes.c_uint32), ("count", ctypes.c_int)]
 
+
+class he_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_batch", ctypes.c_int)]
+
+
+class he_job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ctx", ctypes.c_void_p), ("in_", ctypes.POINTER(ctypes.c_void_p)),
+                ("n_in", ctypes.c_int), ("n", ctypes.c_int), ("sched", he_mm_sched), ("n_row_blocks", ctypes.c_int),
+                ("k", ctypes.c_int), ("s", ctypes.c_int), ("centered", ctypes.c_int), ("acc_id", ctypes.c_uint64),
+                ("l_E", ctypes.c_int), ("l_P", ctypes.c_int), ("axis", ctypes.c_int),
+                ("newton_counts", ctypes.POINTER(ctypes.c_int)), ("B2", ctypes.c_double),
+                ("refresh_obj", ctypes.c_uint32)]
+
+
+class he_serving_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "rejected", "completed", "failed")] + \
+               [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "jobs_per_s")] + \
+               [(k, ctypes.c_longlong) for k in ("ticks", "products", "max_products_per_tick")] + \
+               [(k, ctypes.c_double) for k in ("charged_bytes", "key_bytes")]
+
+
+HE_JOB_MATMUL, HE_JOB_COVARIANCE, HE_JOB_XTX_BLOCK, HE_JOB_XTX_FINAL, HE_JOB_PCA = 1, 2, 3, 4, 5
+HE_JOB_QUEUED, HE_JOB_RUNNING, HE_JOB_DONE, HE_JOB_FAILED = 0, 1, 2, 3
 
 P = ctypes.POINTER
 vp = ctypes.c_void_p
@@ -94,6 +119,13 @@ SIGNATURES = {
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
     "he_trace_read": [vp, ip, llp, P(ctypes.c_double), P(ctypes.c_double), ip],
+    "he_server_create": [P(he_server_cfg), P(vp), ip, P(vp)],
+    "he_server_submit": [vp, P(he_job), P(ctypes.c_uint64)],
+    "he_server_poll": [vp, ctypes.c_uint64, P(ip), P(ip), P(ctypes.c_double)],
+    "he_server_wait": [vp, ctypes.c_uint64, ctypes.c_double, P(ip)],
+    "he_server_result": [vp, ctypes.c_uint64, P(vp), ip, P(ip), P(ip), ip, P(ip)],
+    "he_server_stats": [vp, ip, P(he_serving_stats)],
+    "he_server_destroy": [vp],
 }
 _RESTYPES = {"he_last_error": ctypes.c_char_p}
 
@@ -385,3 +417,59 @@ def he_counters(ctx, reset=False):
     v = [ctypes.c_longlong() for _ in range(4)]
     check(lib().he_counters(ctx, *[ctypes.byref(x) for x in v], 1 if reset else 0))
     return dict(zip(["MS", "Dp", "MD", "launches"], [x.value for x in v]))
+
+
+# ------------------------------------------------------------- serving
+def he_server_create(ctxs, hbm_budget_bytes, max_batch=8):
+    cfg = he_server_cfg(float(hbm_budget_bytes), max_batch)
+    h = vp()
+    check(lib().he_server_create(ctypes.byref(cfg), _handles(ctxs), len(ctxs), ctypes.byref(h)))
+    return h
+
+
+def he_server_submit(srv, kind, inputs=(), ctx=None, n=0, n1z=1, n1t=1, n_row_blocks=0, k=0, s=0, centered=False,
+                     acc_id=0, l_E=0, l_P=0, axis=0, counts=None, B2=0.0, refresh_obj=0):
+    """Queues one job (see include/he.h, he_job); returns its id.  Raises
+    HeError (HE_ERR_ADMISSION when over the budget)."""
+    arr = _handles(list(inputs)) if len(inputs) else None
+    cs = (ctypes.c_int * len(counts))(*counts) if counts else None
+    j = he_job(kind, ctx.value if isinstance(ctx, vp) else ctx,
+               ctypes.cast(arr, P(vp)) if arr is not None else None, len(inputs), n, he_mm_sched(n1z, n1t),
+               n_row_blocks, k, s, 1 if centered else 0, acc_id, l_E, l_P, axis,
+               ctypes.cast(cs, P(ctypes.c_int)) if cs is not None else None, B2, refresh_obj)
+    jid = ctypes.c_uint64()
+    check(lib().he_server_submit(srv, ctypes.byref(j), ctypes.byref(jid)))
+    return jid.value
+
+
+def he_server_poll(srv, job_id):
+    """Returns (status, error code, latency ms)."""
+    st, err, lat = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    check(lib().he_server_poll(srv, job_id, ctypes.byref(st), ctypes.byref(err), ctypes.byref(lat)))
+    return st.value, err.value, lat.value
+
+
+def he_server_wait(srv, job_id, timeout_s=600.0):
+    st = ctypes.c_int()
+    check(lib().he_server_wait(srv, job_id, timeout_s, ctypes.byref(st)))
+    return st.value
+
+
+def he_server_result(srv, job_id, max_outs=256, max_aux=64):
+    """Returns (outputs, aux); raises HeError with the job's code if it failed."""
+    outs = (vp * max_outs)()
+    aux = (ctypes.c_int * max_aux)()
+    no, na = ctypes.c_int(), ctypes.c_int()
+    check(lib().he_server_result(srv, job_id, outs, max_outs, ctypes.byref(no), aux, max_aux, ctypes.byref(na)))
+    return [vp(outs[i]) for i in range(no.value)], list(aux[:na.value])
+
+
+def he_server_stats(srv, kind=0):
+    st = he_serving_stats()
+    check(lib().he_server_stats(srv, kind, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in he_serving_stats._fields_}
+
+
+def he_server_destroy(srv):
+    check(lib().he_server_destroy(srv))
+

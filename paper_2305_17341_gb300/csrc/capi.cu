@@ -65,6 +65,49 @@ void free_ct(he_ct *ct) {
     if (ct->d) ct->ctx->pool.put(ct->d);
     delete ct;
 }
+
+static void add_mod(std::set<long> &s, long v, long m) { s.insert(((v % m) + m) % m); }
+
+// Table 1 "Optimized" key set of the product: replication steps -n^2 2^j,
+// Z babies j and giants n1z*i (-n2z <= i < n2z), T babies n*j and giants
+// n*n1t*i, and the C^k / R^k source steps n1z, -n and n*n1t.
+std::vector<long> matmul_steps(int n, int n1z, int n1t, long slots) {
+    long n2 = (long)n * n;
+    std::set<long> st;
+    for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
+    int n2z = n / n1z, n2t = n / n1t;
+    for (int j = 1; j < n1z; j++) add_mod(st, j, n2);
+    for (int i = -n2z; i < n2z; i++)
+        if (i) add_mod(st, (long)n1z * i, n2);
+    for (int j = 1; j < n1t; j++) add_mod(st, (long)n * j, n2);
+    for (int i = 1; i < n2t; i++) add_mod(st, (long)n * n1t * i, n2);
+    add_mod(st, n1z, n2);
+    add_mod(st, -n, n2);
+    if (n2t > 1) add_mod(st, (long)n * n1t, n2);
+    st.erase(0);
+    return std::vector<long>(st.begin(), st.end());
+}
+
+// G (transpose) over the diagonals (n-1)k: babies (n-1)j, giants (n-1)n1 i.
+std::vector<long> transpose_steps(int n, int n1, long slots) {
+    long n2 = (long)n * n, a = n - 1;
+    std::set<long> st;
+    for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
+    int n2g = n / n1;
+    for (int j = 1; j < n1; j++) add_mod(st, a * j, n2);
+    for (int i = -n2g; i < n2g; i++)
+        if (i) add_mod(st, a * n1 * i, n2);
+    st.erase(0);
+    return std::vector<long>(st.begin(), st.end());
+}
+
+long first_missing_key(const Ctx *c, const std::vector<long> &steps, long skip_from) {
+    for (long v : steps) {
+        if (v >= skip_from) continue;
+        if (!c->rtk.count(galois_of_step(c, v))) return v;
+    }
+    return 0;
+}
 }  // namespace he
 
 extern "C" {
@@ -245,43 +288,20 @@ int he_keygen(he_ctx *ctx, const int32_t *rot_steps, int n_steps, int want_relin
     GUARD_END
 }
 
-static void add_mod(std::set<long> &s, long v, long m) { s.insert(((v % m) + m) % m); }
-
 int he_rot_steps_for_matmul(int n, int n1z, int n1t, int slots, int32_t *out, int *count) {
     if (!out || !count || n < 1 || n1z < 1 || n1t < 1 || n % n1z || n % n1t || (long)n * n > slots)
         return fail(HE_ERR_ARG, "bad arguments");
-    long n2 = (long)n * n;
-    std::set<long> st;
-    for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
-    int n2z = n / n1z, n2t = n / n1t;
-    for (int j = 1; j < n1z; j++) add_mod(st, j, n2);
-    for (int i = -n2z; i < n2z; i++)
-        if (i) add_mod(st, (long)n1z * i, n2);
-    for (int j = 1; j < n1t; j++) add_mod(st, (long)n * j, n2);
-    for (int i = 1; i < n2t; i++) add_mod(st, (long)n * n1t * i, n2);
-    add_mod(st, n1z, n2);
-    add_mod(st, -n, n2);
-    if (n2t > 1) add_mod(st, (long)n * n1t, n2);
-    st.erase(0);
-    int k = 0;
-    for (long v : st) out[k++] = (int32_t)v;
-    *count = k;
+    std::vector<long> st = matmul_steps(n, n1z, n1t, slots);
+    for (size_t k = 0; k < st.size(); k++) out[k] = (int32_t)st[k];
+    *count = (int)st.size();
     return HE_OK;
 }
 
 int he_rot_steps_for_transpose(int n, int n1, int slots, int32_t *out, int *count) {
     if (!out || !count || n < 2 || n1 < 1 || n % n1 || (long)n * n > slots) return fail(HE_ERR_ARG, "bad arguments");
-    long n2 = (long)n * n, a = n - 1;
-    std::set<long> st;
-    for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
-    int n2g = n / n1;
-    for (int j = 1; j < n1; j++) add_mod(st, a * j, n2);
-    for (int i = -n2g; i < n2g; i++)
-        if (i) add_mod(st, a * n1 * i, n2);
-    st.erase(0);
-    int k = 0;
-    for (long v : st) out[k++] = (int32_t)v;
-    *count = k;
+    std::vector<long> st = transpose_steps(n, n1, slots);
+    for (size_t k = 0; k < st.size(); k++) out[k] = (int32_t)st[k];
+    *count = (int)st.size();
     return HE_OK;
 }
 
@@ -520,10 +540,15 @@ static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::v
     Buf O(&c.pool, Bn * wo);
     hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p);
     double q2 = (double)c.primes[level - 2];
-    for (int i = 0; i < Bn; i++) {
-        he_ct *o = new_ct(&c, level - 3, (As[i]->scale * Bs[i]->scale) / q2, n * n);
-        cudaMemcpyAsync(o->d, O.p + i * wo, wo * 8, cudaMemcpyDeviceToDevice, c.stream);
-        outs[i] = o;
+    try {
+        for (int i = 0; i < Bn; i++) {
+            he_ct *o = new_ct(&c, level - 3, (As[i]->scale * Bs[i]->scale) / q2, n * n);
+            cudaMemcpyAsync(o->d, O.p + i * wo, wo * 8, cudaMemcpyDeviceToDevice, c.stream);
+            outs[i] = o;
+        }
+    } catch (...) {
+        for (he_ct *&o : outs) free_ct(o), o = nullptr;
+        throw;
     }
 }
 
@@ -545,32 +570,14 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
         outs[i] = nullptr;
     }
     GUARD_BEGIN
-    typedef std::tuple<Ctx *, int, int, int, int, int, int> Key;
-    std::map<Key, std::vector<int>> groups;
-    for (int i = 0; i < n_jobs; i++) {
-        const he_mm_job &j = jobs[i];
-        int lv = std::min(j.A->level, j.B->level);
-        groups[Key(j.A->ctx, lv, j.n, j.sched.n1_z, j.sched.n1_t, j.A->period == j.n * j.n,
-                   j.B->period == j.n * j.n)]
-            .push_back(i);
-    }
-    std::vector<he_ct *> res(n_jobs, nullptr);
+    std::vector<ProdSpec> prods;
+    for (int i = 0; i < n_jobs; i++)
+        prods.push_back({jobs[i].A, jobs[i].B, jobs[i].n, jobs[i].sched.n1_z, jobs[i].sched.n1_t});
+    std::vector<he_ct *> res;
+    run_products(prods, res, 0);
     try {
-        for (auto &kv : groups) {
-            Ctx &c = *std::get<0>(kv.first);
-            int lv = std::get<1>(kv.first);
-            std::vector<const he_ct *> As, Bs;
-            for (int i : kv.second) {
-                As.push_back(jobs[i].A);
-                Bs.push_back(jobs[i].B);
-            }
-            std::vector<he_ct *> o(As.size());
-            const he_mm_job &j0 = jobs[kv.second[0]];
-            run_group(c, As, Bs, j0.n, j0.sched.n1_z, j0.sched.n1_t, lv, o);
-            for (size_t t = 0; t < o.size(); t++) res[kv.second[t]] = o[t];
-        }
         std::set<Ctx *> ctxs;
-        for (auto &kv : groups) ctxs.insert(std::get<0>(kv.first));
+        for (auto &p : prods) ctxs.insert(p.A->ctx);
         for (Ctx *c : ctxs) HE_CUDA_CHECK(cudaStreamSynchronize(c->stream));
         for (Ctx *c : ctxs)
             if (int rc = cuda_status(c)) throw HeError(rc, last_error());
@@ -582,6 +589,48 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
     return HE_OK;
     GUARD_END
 }
+
+}  // extern "C"
+
+namespace he {
+void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs, int max_batch) {
+    typedef std::tuple<Ctx *, int, int, int, int, int, int> Key;
+    std::map<Key, std::vector<int>> groups;
+    for (size_t i = 0; i < prods.size(); i++) {
+        const ProdSpec &j = prods[i];
+        int lv = std::min(j.A->level, j.B->level);
+        groups[Key(j.A->ctx, lv, j.n, j.n1z, j.n1t, j.A->period == j.n * j.n, j.B->period == j.n * j.n)]
+            .push_back((int)i);
+    }
+    outs.assign(prods.size(), nullptr);
+    try {
+        for (auto &kv : groups) {
+            Ctx &c = *std::get<0>(kv.first);
+            int lv = std::get<1>(kv.first);
+            const std::vector<int> &ix = kv.second;
+            const int step = max_batch > 0 ? max_batch : (int)ix.size();
+            for (size_t s0 = 0; s0 < ix.size(); s0 += step) {
+                size_t s1 = std::min(ix.size(), s0 + step);
+                std::vector<const he_ct *> As, Bs;
+                for (size_t t = s0; t < s1; t++) {
+                    As.push_back(prods[ix[t]].A);
+                    Bs.push_back(prods[ix[t]].B);
+                }
+                std::vector<he_ct *> o(As.size());
+                const ProdSpec &j0 = prods[ix[s0]];
+                run_group(c, As, Bs, j0.n, j0.n1z, j0.n1t, lv, o);
+                for (size_t t = s0; t < s1; t++) outs[ix[t]] = o[t - s0];
+            }
+        }
+    } catch (...) {
+        for (he_ct *o : outs) free_ct(o);
+        outs.clear();
+        throw;
+    }
+}
+}  // namespace he
+
+extern "C" {
 
 int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, he_ct **out) {
     if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");

@@ -132,6 +132,7 @@ static ModQ make_mod(u64 q) {
 
 // ---------------------------------------------------------------- pool
 void *DevicePool::get(size_t bytes) {
+    std::lock_guard<std::mutex> lk(mu_);
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
     auto it = free_.lower_bound(bytes);
@@ -141,6 +142,7 @@ void *DevicePool::get(size_t bytes) {
         free_.erase(it);
         cached_ -= sz;
         in_use_ += sz;
+        if (in_use_ > peak_) peak_ = in_use_;
         return p;
     }
     void *p = nullptr;
@@ -158,11 +160,13 @@ void *DevicePool::get(size_t bytes) {
     }
     sizes_[p] = bytes;
     in_use_ += bytes;
+    if (in_use_ > peak_) peak_ = in_use_;
     return p;
 }
 
 void DevicePool::put(void *p) {
     if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
     size_t sz = sizes_[p];
     in_use_ -= sz;
     cached_ += sz;
@@ -170,6 +174,7 @@ void DevicePool::put(void *p) {
 }
 
 void DevicePool::release_all() {
+    std::lock_guard<std::mutex> lk(mu_);
     if (sizes_.empty()) return;
     cudaDeviceSynchronize();
     for (auto &kv : sizes_) cudaFree(kv.first);

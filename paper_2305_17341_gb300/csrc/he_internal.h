@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -32,12 +33,15 @@ public:
     void release_all();
     size_t bytes_in_use() const { return in_use_; }
     size_t bytes_cached() const { return cached_; }
+    size_t bytes_peak() const { return peak_; }
     ~DevicePool() { release_all(); }
 
 private:
+    // get/put may be called from a serving worker and the caller's thread
+    std::mutex mu_;
     std::multimap<size_t, void *> free_;
     std::map<void *, size_t> sizes_;
-    size_t in_use_ = 0, cached_ = 0;
+    size_t in_use_ = 0, cached_ = 0, peak_ = 0;
 };
 
 // Scratch buffer handle returned to the pool on scope exit.
@@ -114,7 +118,7 @@ struct Ctx {
     std::mutex mu;
 
     // instrumentation
-    long long n_ms = 0, n_dp = 0, n_md = 0, n_launch = 0;
+    std::atomic<long long> n_ms{0}, n_dp{0}, n_md{0}, n_launch{0};
     // per-kernel-class tracing: CUDA events on the context stream around each
     // launch of a traced class, with the launch's algorithmic bytes
     struct TraceClass {

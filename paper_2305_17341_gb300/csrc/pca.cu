@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ctapi.h"
+#include "stages.h"
 
 namespace he {
 
@@ -51,6 +52,9 @@ static u64 mod_signed(long long m, u64 q) {
     long long r = m % (long long)q;
     return (u64)(r < 0 ? r + (long long)q : r);
 }
+
+// products per batched pass inside one covariance (bounds the temporaries)
+static const int kCovBatch = 16;
 
 class PcaOps {
 public:
@@ -258,49 +262,80 @@ public:
     }
 
     // ---------------------------------------------------------- covariance
-    std::vector<HC> covariance(he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z,
-                               int n1t) {
-        const double inv_s = 1.0 / s;
-        const int N = c->N;
-        std::vector<HC> XT(nrb * k), Xr(nrb * k);
-        for (int l = 0; l < nrb; l++)
+    // HCovMtrx (Sec. 5.3) in three stages, so that a server can merge the
+    // block products of several jobs into one batched pass:
+    //   1. cov_prepare: X_j[l]^T with 1/s folded into the G diagonals, and
+    //      the replicated X_j[l]; appends the products X_a[l]^T X_b[l]
+    //      (a <= b) in the order a, b, l
+    //   2. cov_upper: C[a][b] = sum over l of those products
+    //   3. cov_finish: the blocks below the diagonal as G(C[b][a]), one
+    //      common level, and (not centred) minus mu_a^T mu_b
+    struct CovPlan {
+        int nrb = 0, k = 0, n = 0, s = 0, n1z = 0, n1t = 0;
+        bool centered = true;
+        std::vector<he_ct *> blocks;
+        std::vector<HC> XT, Xr;
+    };
+
+    void cov_prepare(CovPlan &P, std::vector<ProdSpec> &prods) {
+        const double inv_s = 1.0 / P.s;
+        const int k = P.k;
+        P.XT.clear();
+        P.Xr.clear();
+        P.XT.resize(P.nrb * k);
+        P.Xr.resize(P.nrb * k);
+        for (int l = 0; l < P.nrb; l++)
             for (int j = 0; j < k; j++) {
-                XT[l * k + j] = transpose(blocks[l * k + j], n, n1z, inv_s);
-                Xr[l * k + j] = replicated(blocks[l * k + j], n);
+                P.XT[l * k + j] = transpose(P.blocks[l * k + j], P.n, P.n1z, inv_s);
+                P.Xr[l * k + j] = replicated(P.blocks[l * k + j], P.n);
             }
-        const int lx = XT[0]->level;
-        const size_t w = ct_words(c, lx), wo = ct_words(c, lx - 3);
+        for (int a = 0; a < k; a++)
+            for (int b = a; b < k; b++)
+                for (int l = 0; l < P.nrb; l++)
+                    prods.push_back({P.XT[l * k + a].p, P.Xr[l * k + b].p, P.n, P.n1z, P.n1t});
+    }
+
+    // Takes ownership of the products made from cov_prepare's list.
+    std::vector<HC> cov_upper(CovPlan &P, he_ct *const *outs) {
+        const int k = P.k;
+        std::vector<HC> own;
+        for (int t = 0; t < k * (k + 1) / 2 * P.nrb; t++) own.emplace_back(outs[t]);
         std::vector<HC> C(k * k);
-        Buf A(&c->pool, nrb * w), B(&c->pool, nrb * w), O(&c->pool, nrb * wo);
+        size_t t = 0;
         for (int a = 0; a < k; a++)
             for (int b = a; b < k; b++) {
-                for (int l = 0; l < nrb; l++) {
-                    cudaMemcpyAsync(A.p + l * w, XT[l * k + a]->d, w * 8, cudaMemcpyDeviceToDevice, c->stream);
-                    drop(c, Xr[l * k + b]->d, 1, Xr[l * k + b]->level, lx, B.p + l * w);
+                HC acc = std::move(own[t++]);
+                for (int l = 1; l < P.nrb; l++) {
+                    HC o = std::move(own[t++]);
+                    add(c, acc->d, o->d, 1, acc->level, acc->d);
                 }
-                hmatmul(c, A.p, B.p, nrb, lx, n, n1z, n1t, O.p);
-                double sc = (XT[a]->scale * Xr[b]->scale) / (double)c->primes[lx - 2];
-                HC acc = make(lx - 3, sc, n * n);
-                cudaMemcpyAsync(acc->d, O.p, wo * 8, cudaMemcpyDeviceToDevice, c->stream);
-                for (int l = 1; l < nrb; l++) add(c, acc->d, O.p + l * wo, 1, lx - 3, acc->d);
                 C[a * k + b] = std::move(acc);
             }
+        P.XT.clear();
+        P.Xr.clear();
+        return C;
+    }
+
+    std::vector<HC> cov_finish(const CovPlan &P, std::vector<HC> C) {
+        const int k = P.k, n = P.n, nrb = P.nrb;
         for (int a = 0; a < k; a++)
-            for (int b = 0; b < a; b++) C[a * k + b] = transpose(C[b * k + a].p, n, n1z, 1.0);
+            for (int b = 0; b < a; b++) C[a * k + b] = transpose(C[b * k + a].p, n, P.n1z, 1.0);
         int lv = C[0]->level;
         for (auto &x : C) lv = std::min(lv, x->level);
         for (auto &x : C)
             if (x->level != lv) x = dropto(x.p, lv);
-        if (centered) return C;
+        if (P.centered) return C;
+        const double inv_s = 1.0 / P.s;
         std::vector<HC> mu, muT;
         for (int j = 0; j < k; j++) {
-            HC acc = clone(blocks[j]);
-            for (int l = 1; l < nrb; l++) acc = add_ct(acc.p, blocks[l * k + j]);
+            HC acc = clone(P.blocks[j]);
+            for (int l = 1; l < nrb; l++) acc = add_ct(acc.p, P.blocks[l * k + j]);
             HC m = aggregate(acc.p, 0, n);
             mu.push_back(mul_const(std::move(m), inv_s));
         }
-        for (int j = 0; j < k; j++) muT.push_back(transpose(mu[j].p, n, n1z, 1.0));
-        const int pl = lx - 2;
+        for (int j = 0; j < k; j++) muT.push_back(transpose(mu[j].p, n, P.n1z, 1.0));
+        // the mean product is taken at the level of the block products' inputs minus 2
+        const int pl = P.blocks[0]->level - 3;
         for (int a = 0; a < k; a++)
             for (int b = 0; b < k; b++) {
                 HC x = dropto(muT[a].p, pl), y = dropto(mu[b].p, pl);
@@ -309,8 +344,25 @@ public:
                 HC tr = rescale_ct(t.p, false);
                 C[a * k + b] = sub_matched(std::move(C[a * k + b]), std::move(tr));
             }
-        (void)N;
         return C;
+    }
+
+    std::vector<HC> covariance(he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z,
+                               int n1t) {
+        CovPlan P;
+        P.nrb = nrb;
+        P.k = k;
+        P.n = n;
+        P.s = s;
+        P.n1z = n1z;
+        P.n1t = n1t;
+        P.centered = centered;
+        P.blocks.assign(blocks, blocks + (size_t)nrb * k);
+        std::vector<ProdSpec> prods;
+        cov_prepare(P, prods);
+        std::vector<he_ct *> outs;
+        run_products(prods, outs, kCovBatch);
+        return cov_finish(P, cov_upper(P, outs.data()));
     }
 
     // -------------------------------------------------------- PowerMethod
@@ -412,7 +464,94 @@ public:
             }
         return out;
     }
+
+    // Privacy-Preserving PCA (Sec. 6.2): l_E rounds of PowerMethod and
+    // EigenShift on a private copy of the covariance blocks.
+    void pca(he_ct *const *cov, int k, int n, int l_E, he_ct *const *v0, int axis, int l_P, const int *counts,
+             double B2, std::vector<HC> &lam_out, std::vector<HC> &V_out, std::vector<int> &ax_out) {
+        std::vector<HC> C;
+        for (int i = 0; i < k * k; i++) C.push_back(clone(cov[i]));
+        for (int m = 0; m < l_E; m++) {
+            std::vector<he_ct *> Cp(k * k);
+            for (int i = 0; i < k * k; i++) Cp[i] = C[i].p;
+            HC lam;
+            std::vector<HC> Vo, VTo;
+            int ax = 0;
+            power_method(Cp.data(), k, n, v0 + (size_t)m * k, axis, l_P, counts, B2, lam, Vo, VTo, ax);
+            if (m + 1 < l_E) {
+                std::vector<he_ct *> Vp(k), VTp(k);
+                for (int j = 0; j < k; j++) {
+                    Vp[j] = Vo[j].p;
+                    VTp[j] = VTo[j].p;
+                }
+                C = eigen_shift(Cp.data(), k, lam.p, Vp.data(), ax, VTp.data());
+            }
+            lam_out.push_back(std::move(lam));
+            for (auto &v : Vo) V_out.push_back(std::move(v));
+            ax_out.push_back(ax);
+        }
+    }
 };
+
+// ------------------------------------------------------ stages for serving
+struct CovStage {
+    PcaOps::CovPlan plan;
+};
+
+CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z, int n1t,
+                    std::vector<ProdSpec> &prods) {
+    RefreshState st{0, 0};
+    PcaOps ops(c, &st);
+    CovStage *S = new CovStage;
+    PcaOps::CovPlan &P = S->plan;
+    P.nrb = nrb;
+    P.k = k;
+    P.n = n;
+    P.s = s;
+    P.n1z = n1z;
+    P.n1t = n1t;
+    P.centered = centered;
+    P.blocks.assign(blocks, blocks + (size_t)nrb * k);
+    try {
+        ops.cov_prepare(P, prods);
+    } catch (...) {
+        delete S;
+        throw;
+    }
+    return S;
+}
+
+void cov_upper(Ctx *c, CovStage *S, he_ct *const *outs, std::vector<he_ct *> &upper) {
+    RefreshState st{0, 0};
+    PcaOps ops(c, &st);
+    std::vector<HC> C = ops.cov_upper(S->plan, outs);
+    upper.assign(C.size(), nullptr);
+    for (size_t i = 0; i < C.size(); i++) upper[i] = C[i].release();
+}
+
+void cov_finish(Ctx *c, CovStage *S, std::vector<he_ct *> &blocks_io) {
+    RefreshState st{0, 0};
+    PcaOps ops(c, &st);
+    std::vector<HC> C(blocks_io.size());
+    for (size_t i = 0; i < C.size(); i++) C[i] = HC(blocks_io[i]), blocks_io[i] = nullptr;
+    C = ops.cov_finish(S->plan, std::move(C));
+    for (size_t i = 0; i < C.size(); i++) blocks_io[i] = C[i].release();
+}
+
+void cov_free(CovStage *S) { delete S; }
+
+void pca_run(Ctx *c, he_ct *const *cov, int k, int n, int l_E, he_ct *const *v0, int axis, int l_P,
+             const int *counts, double B2, uint32_t &next_obj, int &count, std::vector<he_ct *> &lams,
+             std::vector<he_ct *> &V, std::vector<int> &axes) {
+    RefreshState st{next_obj, count};
+    PcaOps ops(c, &st);
+    std::vector<HC> lo, vo;
+    ops.pca(cov, k, n, l_E, v0, axis, l_P, counts, B2, lo, vo, axes);
+    next_obj = st.next_obj;
+    count = st.count;
+    for (auto &x : lo) lams.push_back(x.release());
+    for (auto &x : vo) V.push_back(x.release());
+}
 
 // Lazy Normalization's PowerMethod simulation (Sec. 6.1.2)
 int lazy_schedule(int t, double S, double e, double Bp, double B2, int max_iters, int *counts) {
@@ -594,29 +733,9 @@ int he_pca(he_ctx *ctx, he_ct *const *cov, int k, int n, int l_E, he_ct *const *
     PCA_GUARD_BEGIN
     RefreshState st{rs->next_obj, rs->count};
     PcaOps ops(&c, &st);
-    std::vector<HC> C;
-    for (int i = 0; i < k * k; i++) C.push_back(ops.clone(cov[i]));
     std::vector<HC> lam_out, V_out;
     std::vector<int> ax_out;
-    for (int m = 0; m < l_E; m++) {
-        std::vector<he_ct *> Cp(k * k);
-        for (int i = 0; i < k * k; i++) Cp[i] = C[i].p;
-        HC lam;
-        std::vector<HC> Vo, VTo;
-        int ax = 0;
-        ops.power_method(Cp.data(), k, n, v0 + (size_t)m * k, axis, l_P, newton_counts, B2, lam, Vo, VTo, ax);
-        if (m + 1 < l_E) {
-            std::vector<he_ct *> Vp(k), VTp(k);
-            for (int j = 0; j < k; j++) {
-                Vp[j] = Vo[j].p;
-                VTp[j] = VTo[j].p;
-            }
-            C = ops.eigen_shift(Cp.data(), k, lam.p, Vp.data(), ax, VTp.data());
-        }
-        lam_out.push_back(std::move(lam));
-        for (auto &v : Vo) V_out.push_back(std::move(v));
-        ax_out.push_back(ax);
-    }
+    ops.pca(cov, k, n, l_E, v0, axis, l_P, newton_counts, B2, lam_out, V_out, ax_out);
     if (int rc = sync_status(c)) return rc;
     rs->next_obj = st.next_obj;
     rs->count = st.count;

@@ -55,3 +55,15 @@ def poisson_arrivals(rate, duration, seed):
         if t >= duration:
             return out
         out.append(t)
+
+
+def served_job_mix(rate, duration, seed, weights=(("xtx_block", 0.60), ("matmul", 0.25), ("covariance", 0.12),
+                                                  ("pca", 0.03))):
+    """A served workload: Poisson arrivals, each labelled with a job kind drawn
+    from `weights`.  Returns [(t, kind)] in arrival order."""
+    ts = poisson_arrivals(rate, duration, seed)
+    rng = np.random.default_rng(seed + 1)
+    kinds = [k for k, _ in weights]
+    p = np.array([w for _, w in weights], dtype=float)
+    p /= p.sum()
+    return [(t, kinds[int(rng.choice(len(kinds), p=p))]) for t in ts]
