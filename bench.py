@@ -654,6 +654,57 @@ def run_served(args):
         pk.he_ctx_destroy(c)
 
 
+def run_ntt(args):
+    """The NTT alone (he_ntt) on R rows at N = 2^16 over the primes of the
+    covariance chain at level 20 (R = 2024 is the forward transform of one
+    batched Decompose of 8 products: 8 x 11 digits x 23 rows), device time of
+    every launch from the library's CUDA-event trace, against the measured
+    butterfly peak.  Also the small case for kernel profiles."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    pk.build()
+    ctx = pk.he_ctx_create(pk.he_params_default(2), 9)
+    tstream = torch.cuda.Stream()
+    pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
+    q, p = pk.he_ctx_primes(ctx)
+    primes = list(q) + list(p)
+    R, N, level = args.ntt_rows, 1 << 16, 20
+    rng = np.random.default_rng(12)
+    host = np.stack([rng.integers(0, primes[r % len(primes)], N, dtype=np.uint64) for r in range(R)])
+    dev = torch.from_numpy(host.view(np.int64)).cuda()
+    del host
+    for _ in range(max(3, args.warmup)):
+        pk.he_ntt(ctx, dev.data_ptr(), R, level)
+        pk.he_ntt(ctx, dev.data_ptr(), R, level, inverse=True)
+    pk.he_trace_enable(ctx, True)
+    for c in (1, 2):
+        pk.he_trace_read(ctx, c, reset=True)
+    for _ in range(args.steps):
+        pk.he_ntt(ctx, dev.data_ptr(), R, level)
+        pk.he_ntt(ctx, dev.data_ptr(), R, level, inverse=True)
+    tr = {c: pk.he_trace_read(ctx, c, reset=True) for c in (1, 2)}
+    pk.he_trace_enable(ctx, False)
+    peak = pk.he_bench_butterfly(4000) / 1e9
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    out = {}
+    for c, name in ((1, "forward"), (2, "inverse")):
+        t = tr[c]
+        avg = t["ms"] / t["count"] / 1e3
+        bfly = R * (N // 2) * 16 / avg / 1e9
+        out[name] = {"avg_us": avg * 1e6, "gbfly_s": bfly, "frac_of_measured_peak": bfly / peak,
+                     "algorithmic_gbs": t["bytes"] / t["count"] / avg / 1e9,
+                     "hbm_frac_of_measured": t["bytes"] / t["count"] / avg / 1e9 / hbm}
+    print(json.dumps({"metric": "NTT butterflies/s (N=2^16, %d rows)" % R, "value": out["forward"]["gbfly_s"],
+                      "unit": "Gbutterfly/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+                      "peak_gbfly_s": peak, "peak_source": "measured lazy-Shoup butterfly microbenchmark",
+                      "forward": out["forward"], "inverse": out["inverse"],
+                      "config": {"workload": "%d rows x 2^16 words, primes of q 60+20x40 and p 2x60 cycled"
+                                             % R}}), flush=True)
+    pk.he_ctx_destroy(ctx)
+
+
 def run_mixed(args):
     """Config 4: 96 independent products, n in {16,32,64,128}, N in {2^15, 2^16},
     remaining level in [3, 20]; plain (one call each) vs one grouped batch."""
@@ -718,7 +769,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served"])
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served", "ntt"])
+    ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
     ap.add_argument("--rate", type=float, default=1.5, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="served: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
@@ -737,6 +789,8 @@ def main():
         return run_mixed(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "ntt":
+        return run_ntt(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None

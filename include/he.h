@@ -252,6 +252,18 @@ int he_eigen_shift(he_ctx *ctx, he_ct **cov, int k, int n, const he_ct *lambda, 
 int he_pca(he_ctx *ctx, he_ct *const *cov, int k, int n, int l_E, he_ct *const *v0, int axis, int l_P,
            const int *newton_counts, double B2, he_refresh_state *rs, he_ct **lambdas, he_ct **V, int *axes);
 
+/* Negacyclic NTT over rows in device memory: the transform that puts
+ * polynomials in the NTT domain where the full-RNS CKKS of App. A multiplies
+ * them (Sec. 3.2); Decompose and ModDown spend most of their time in it
+ * (Sec. 3.3.1).  rows_dev holds n_rows rows of N words; row r is reduced
+ * modulo prime r mod (level+1+alpha) of Q_level P (q_0..q_level, then
+ * p_0..p_{alpha-1}).  Forward: coefficients in [0, q) -> evaluations in
+ * bit-reversed order, in [0, q).  Inverse (inverse != 0): the converse.
+ * Runs on the context's stream and returns when it is done.
+ * Errors: HE_ERR_ARG (null or negative sizes), HE_ERR_LEVEL (level outside
+ * 0..L), HE_ERR_CUDA. */
+int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inverse);
+
 /* Counters of the key-switch phases since the last reset: MultSum, Decompose,
  * ModDown (Table 1 caption), and kernel launches.  Any pointer may be NULL. */
 int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset);

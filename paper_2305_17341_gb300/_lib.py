@@ -115,6 +115,7 @@ SIGNATURES = {
     "he_eigen_shift": [vp, P(vp), ip, ip, vp, P(vp), ip, P(vp), P(he_refresh_state)],
     "he_pca": [vp, P(vp), ip, ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp),
                P(ip)],
+    "he_ntt": [vp, vp, ctypes.c_longlong, ip, ip],
     "he_counters": [vp, llp, llp, llp, llp, ip],
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
@@ -395,6 +396,11 @@ def he_eigen_shift(ctx, cov, k, n, lam, V, axis, VT, rs):
 
 
 TRACE_MULTSUM, TRACE_NTT_FWD, TRACE_NTT_INV = 0, 1, 2
+
+
+def he_ntt(ctx, rows_dev_ptr, n_rows, level, inverse=False):
+    """In-place NTT (or inverse) of n_rows device rows (see include/he.h)."""
+    check(lib().he_ntt(ctx, rows_dev_ptr, n_rows, level, 1 if inverse else 0))
 
 
 def he_trace_enable(ctx, on=True):

@@ -658,6 +658,20 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
     GUARD_END
 }
 
+int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inverse) {
+    if (!ctx || (n_rows > 0 && !rows_dev) || n_rows < 0) return fail(HE_ERR_ARG, "bad arguments");
+    Ctx &c = ctx->c;
+    if (level < 0 || level > c.L) return fail(HE_ERR_LEVEL, "level out of range");
+    GUARD_BEGIN
+    if (inverse)
+        ntt_inv(&c, (u64 *)rows_dev, n_rows, c.map_qp(level), c.stream);
+    else
+        ntt_fwd(&c, (u64 *)rows_dev, n_rows, c.map_qp(level), c.stream);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    return cuda_status(&c);
+    GUARD_END
+}
+
 int he_bench_butterfly(int iters, double *bfly_per_s) {
     if (!bfly_per_s || iters < 1) return fail(HE_ERR_ARG, "bad arguments");
     *bfly_per_s = bfly_peak(iters);

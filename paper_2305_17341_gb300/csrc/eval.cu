@@ -19,8 +19,21 @@ void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits) 
     Buf coef(&c->pool, (size_t)B * nq * N);
     launch_copy_rows(coef.p, (long)nq * N, poly, item_s, B, (long)nq * N, c->stream);
     ntt_inv(c, coef.p, (long)B * nq, c->map_q(level), c->stream);
-    launch_modup_bconv(c, coef.p, digits, B, level, c->stream);
-    ntt_fwd(c, digits, (long)B * c->ndig(level) * c->qp_rows(level), c->map_qp(level), c->stream);
+    const long rows = (long)B * c->ndig(level) * c->qp_rows(level);
+    if (c->logN >= 14 && c->logN <= 16) {
+        // the digit's own rows are the input's NTT-domain rows: copy them and
+        // transform only the extended rows
+        launch_modup_bconv(c, coef.p, digits, B, level, c->stream, poly, item_s);
+        RowSkip sk;
+        sk.rows_per_digit = c->qp_rows(level);
+        sk.ndig = c->ndig(level);
+        sk.alpha = c->alpha;
+        sk.nq = nq;
+        ntt_fwd(c, digits, rows, c->map_qp(level), c->stream, &sk);
+    } else {
+        launch_modup_bconv(c, coef.p, digits, B, level, c->stream);
+        ntt_fwd(c, digits, rows, c->map_qp(level), c->stream);
+    }
     c->n_dp += B;
 }
 

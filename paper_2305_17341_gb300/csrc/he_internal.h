@@ -25,6 +25,22 @@ struct RowMap {
     }
 };
 
+// Rows a forward NTT leaves untouched: in Decompose output laid out as
+// [item][digit][rows_per_digit][N], the digit's own rows r in
+// [d alpha, min(d alpha + alpha, nq)) are already in the NTT domain.
+// rows_per_digit == 0 disables the skip; row0 is the absolute index of the
+// launch's first row.
+struct RowSkip {
+    int rows_per_digit = 0, ndig = 0, alpha = 0, nq = 0;
+    long row0 = 0;
+    __host__ __device__ bool skip(long row) const {
+        if (!rows_per_digit) return false;
+        long a = row0 + row;
+        int r = (int)(a % rows_per_digit), d = (int)((a / rows_per_digit) % ndig), i0 = d * alpha;
+        return r >= i0 && r < i0 + alpha && r < nq;
+    }
+};
+
 // Device pool with size-class free lists (no cudaMalloc/cudaFree in steady state).
 class DevicePool {
 public:
@@ -186,7 +202,7 @@ ShoupPair h_shoup(u64 w, u64 q);
 int h_gen_primes(int logN, int nq, const int *qbits, int np, const int *pbits, u64 *q, u64 *p);
 
 // NTT
-void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st);
+void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const RowSkip *skip = nullptr);
 void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st);
 
 // ---- kernels.cu launchers (all asynchronous on st) ----
@@ -214,7 +230,11 @@ void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long a_item_stride,
                    long b_item_stride, const RowMap &rm, cudaStream_t st);
 // key switching pieces
-void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st);
+// own_ntt (may be null): the input in the NTT domain, item stride own_s; the
+// digit's own rows are then copied from it (and the forward NTT must skip
+// them), else from coef.
+void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st,
+                        const u64 *own_ntt = nullptr, long own_s = 0);
 void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st);
 void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const u64 *addend, int items,
                           int level, long u_item_stride, long out_item_stride, long add_item_stride,

@@ -330,7 +330,8 @@ void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B,
 // digit's own rows, which keep c_r.  In/out in coefficient form.
 // coef: [B][l+1][N]; out: [B][ndig][l+1+alpha][N].
 __global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int alpha, int ndig, int N, RowMap qp,
-                              const ModQ *mods, const ShoupPair *up_inv, const ShoupPair *up_mod) {
+                              const ModQ *mods, const ShoupPair *up_inv, const ShoupPair *up_mod,
+                              const u64 *own_ntt, long own_s) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long total = (long)B * ndig * N;
     if (idx >= total) return;
@@ -351,7 +352,7 @@ __global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int a
     for (int r = 0; r < rows; r++) {
         u64 v;
         if (r >= i0 && r < i0 + ns) {
-            v = cb[(long)r * N + x];
+            v = own_ntt ? own_ntt[(long)b * own_s + (long)r * N + x] : cb[(long)r * N + x];
         } else {
             const ModQ &m = mods[qp.p[r]];
             v = 0;
@@ -363,12 +364,13 @@ __global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int a
         ob[(long)r * N + x] = v;
     }
 }
-void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st) {
+void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st, const u64 *own_ntt,
+                        long own_s) {
     const LevelConsts &L = c->lc(level);
     long n = (long)B * L.ndig * c->N;
     c->n_launch++;
     k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, L.ndig, c->N, c->map_qp(level),
-                                                c->d_mod, L.d_up_inv, L.d_up_mod);
+                                                c->d_mod, L.d_up_inv, L.d_up_mod, own_ntt, own_s);
 }
 
 // Same conversion with caller-supplied constants (layout of LevelConsts).
@@ -378,7 +380,7 @@ void launch_modup_bconv_with(Ctx *c, const u64 *coef, u64 *out, int B, int level
     long n = (long)B * nd * c->N;
     c->n_launch++;
     k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, nd, c->N, c->map_qp(level), c->d_mod,
-                                                up_inv, up_mod);
+                                                up_inv, up_mod, nullptr, 0);
 }
 
 // ----------------------------------------------------- constants per limb

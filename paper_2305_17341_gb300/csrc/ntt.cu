@@ -15,6 +15,8 @@
 // equal index mod N2, C columns per CTA, staged in shared memory); pass 2 runs
 // the remaining log2(N2) stages on rows of N2 contiguous coefficients.  Both
 // passes read and write HBM once.
+#include <stdexcept>
+
 #include "he_internal.h"
 
 namespace he {
@@ -189,12 +191,13 @@ struct PassGeom {
 
 template <int LM, bool ROWS>
 __global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, const ModQ *mods, const u64 *tw,
-                                                      const u64 *twp, int logN) {
+                                                      const u64 *twp, int logN, RowSkip skip) {
     typedef PassGeom<LM, ROWS> G_;
     constexpr int M = G_::M, T = G_::T, W = G_::W;
     __shared__ u64 sm[G_::SM];
     const int N = 1 << logN;
     const long row = blockIdx.y;
+    if (skip.skip(row)) return;  // uniform over the CTA
     const int pidx = rm.p[row % rm.n];
     const u64 q = mods[pidx].q;
     const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
@@ -302,10 +305,10 @@ __global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, cons
 }
 
 template <int LM, bool ROWS>
-static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st) {
+static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk) {
     typedef PassGeom<LM, ROWS> G_;
     dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
-    k_ntt_fwd_fast<LM, ROWS><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, ctx->d_psi, ctx->d_psip, ctx->logN);
+    k_ntt_fwd_fast<LM, ROWS><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, ctx->d_psi, ctx->d_psip, ctx->logN, sk);
 }
 
 template <int LM, bool ROWS>
@@ -379,7 +382,7 @@ static void split(int logN, int &logN1, int &C, int &R) {
     if (R > N1) R = N1;
 }
 
-void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st) {
+void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const RowSkip *skip) {
     if (rows <= 0) return;
     int logN = ctx->logN, logN1, C, R;
     split(logN, logN1, C, R);
@@ -392,12 +395,22 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st) 
         cudaEvent_t e0;
         ctx->trace_begin(1, e0);
         if (logN >= 14 && logN <= 16) {
-            if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st); else fwd_pass<7, false>(ctx, d, nr, m, st);
-            if (logN - logN1 == 8) fwd_pass<8, true>(ctx, d, nr, m, st); else fwd_pass<7, true>(ctx, d, nr, m, st);
-            // algorithmic bytes: every word read and written once (the two passes move twice that)
-            ctx->trace_end(1, e0, 2.0 * nr * ctx->N * 8.0);
+            RowSkip sk;
+            long done = nr;
+            if (skip) {
+                sk = *skip;
+                sk.row0 = r0;
+                done = 0;
+                for (long r = 0; r < nr; r++) done += !sk.skip(r);
+            }
+            if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st, sk); else fwd_pass<7, false>(ctx, d, nr, m, st, sk);
+            if (logN - logN1 == 8) fwd_pass<8, true>(ctx, d, nr, m, st, sk); else fwd_pass<7, true>(ctx, d, nr, m, st, sk);
+            // algorithmic bytes: every transformed word read and written once
+            // (the two passes move twice that)
+            ctx->trace_end(1, e0, 2.0 * done * ctx->N * 8.0);
             continue;
         }
+        if (skip) throw std::logic_error("row skipping needs the register-blocked NTT (logN 14..16)");
         k_ntt_fwd_p1<<<dim3(N2 / C, (unsigned)nr), 256, N1 * C * 8, st>>>(d, m, ctx->d_mod, ctx->d_psi,
                                                                        ctx->d_psip, logN, logN1, C);
         k_ntt_fwd_p2<<<dim3(N1 / R, (unsigned)nr), 256, R * N2 * 8, st>>>(d, m, ctx->d_mod, ctx->d_psi,

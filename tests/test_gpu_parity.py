@@ -252,3 +252,42 @@ def test_full_size_hmatmul_properties(c2):
         assert lib.he_ct_info(o)[0] == 17
     for h in batch + [single] + [x for c in cts for x in c]:
         lib.he_ct_free(h)
+
+
+@pytest.mark.parametrize("logN,qbits,pbits", [(12, [60, 40, 40], [60]), (16, [60] + [40] * 20, [60, 60])])
+def test_ntt_negacyclic_product_and_roundtrip(lib, logN, qbits, pbits):
+    """he_ntt (generic smem path at 2^12, register-blocked two-pass path at
+    2^16): NTT, pointwise product, inverse NTT equals the oracle's
+    negacyclic product in Z_q[X]/(X^N + 1); inverse(forward(x)) = x; every
+    output in [0, q).  Rows cycle through the primes of Q_l P."""
+    import torch
+    from oracle import _c
+    ctx = lib.he_ctx_create(lib.make_params(logN, qbits, pbits), 5)
+    try:
+        q, p = lib.he_ctx_primes(ctx)
+        level = len(qbits) - 1
+        primes = list(q) + list(p)
+        pick = [0, 1, len(primes) - 1]                      # q0, a 40-bit q, the last special prime
+        N = 1 << logN
+        rng = np.random.default_rng(logN)
+        a = np.stack([rng.integers(0, primes[i], N, dtype=np.uint64) for i in range(len(primes))])
+        b = np.stack([rng.integers(0, primes[i], N, dtype=np.uint64) for i in range(len(primes))])
+        da = torch.from_numpy(a.view(np.int64).copy()).cuda()
+        db = torch.from_numpy(b.view(np.int64).copy()).cuda()
+        lib.he_ntt(ctx, da.data_ptr(), len(primes), level)
+        lib.he_ntt(ctx, db.data_ptr(), len(primes), level)
+        fa = da.cpu().numpy().view(np.uint64)
+        fb = db.cpu().numpy().view(np.uint64)
+        for i in range(len(primes)):
+            assert int(fa[i].max()) < primes[i] and int(fb[i].max()) < primes[i]
+        prod = np.stack([np.array([(int(x) * int(y)) % primes[i] if i in pick else 0
+                                   for x, y in zip(fa[i], fb[i])], dtype=np.uint64) for i in range(len(primes))])
+        dp = torch.from_numpy(prod.view(np.int64).copy()).cuda()
+        lib.he_ntt(ctx, dp.data_ptr(), len(primes), level, inverse=True)
+        got = dp.cpu().numpy().view(np.uint64)
+        for i in pick:
+            assert np.array_equal(got[i], _c.polymul(primes[i], a[i], b[i])), "prime %d" % i
+        lib.he_ntt(ctx, da.data_ptr(), len(primes), level, inverse=True)
+        assert np.array_equal(da.cpu().numpy().view(np.uint64), a)
+    finally:
+        lib.he_ctx_destroy(ctx)
