@@ -32,6 +32,14 @@ sys.path.insert(0, ROOT)
 METRIC = "HE 128×128 matmul/s batched vs plain, same GPU, bit-exact; keyswitch % HBM peak"
 UNIT = "matmul/s"
 N_MAT = 128
+# DRAM bytes per algorithmic byte, from ncu captures of the same kernels
+# (dram__bytes_read.sum + dram__bytes_write.sum of the launch over the bytes
+# the traced class counts): the forward NTT's two passes each read and write
+# the rows once (512-row capture: 1020.6 MB against 536.9 MB); MultSum reads
+# the key, the digits and c0 once and writes its outputs once (8-item capture
+# at level 20: 1618.1 MB against 1607.5 MB).  Traffic grows with the rows /
+# items of a launch, so per launch it is this ratio times the launch's bytes.
+TRAFFIC_RATIO = {"ntt_fwd": 1020.6 / 536.9, "multsum": 1618.1 / 1607.5}
 # baby-step count n1 used for each matrix dimension
 N1_FOR = {16: 4, 32: 8, 64: 8, 128: 16}
 LEVEL = 20
@@ -165,18 +173,22 @@ def run_ours(args, rank, world, dist):
     from paper_2305_17341_gb300 import _lib, workloads
 
     local = env_int("LOCAL_RANK", 0)
-    n_mat, n1 = args.n, N1_FOR[args.n]
+    if args.preset == 1:     # N = 2^14, q 60+3x40, p 60: 32x32 products from the top level
+        logN, level, n_mat, n1 = 14, 3, 32, 8
+    else:
+        logN, level, n_mat, n1 = 16, LEVEL, args.n, N1_FOR[args.n]
+    Nn, S = 1 << logN, 1 << (logN - 1)
     torch.cuda.set_device(local)
     pk.build()
     L = _lib.lib()
-    ctx = pk.he_ctx_create(pk.he_params_default(2), 1000 + rank)
+    ctx = pk.he_ctx_create(pk.he_params_default(args.preset), 1000 + rank)
     # the library launches on this stream; every CUDA event below is recorded on it
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
-    pk.he_keygen(ctx, pk.he_rot_steps_for_matmul(n_mat, n1, n1, 1 << 15), True)
+    pk.he_keygen(ctx, pk.he_rot_steps_for_matmul(n_mat, n1, n1, S), True)
     B = args.batch
     mats = [workloads.matmul_pair(n_mat, 10 * (rank * 1000 + i)) for i in range(B)]
-    cts = [(pk.he_encrypt_matrix(ctx, A, LEVEL, 2 * i), pk.he_encrypt_matrix(ctx, Bm, LEVEL, 2 * i + 1))
+    cts = [(pk.he_encrypt_matrix(ctx, A, level, 2 * i), pk.he_encrypt_matrix(ctx, Bm, level, 2 * i + 1))
            for i, (A, Bm) in enumerate(mats)]
     jobs = [(a, b, n_mat, n1, n1) for a, b in cts]
 
@@ -197,9 +209,8 @@ def run_ours(args, rank, world, dist):
     # correctness spot check of the benchmarked configuration (untimed)
     outs = pk.he_hmatmul_batch(jobs[:1])
     err = float(np.abs(pk.he_decrypt_matrix(ctx, outs[0], n_mat, n_mat) - mats[0][0] @ mats[0][1]).max())
-    single = pk.he_hmatmul(ctx, cts[0][0], cts[0][1], n_mat, n1, n1)
-    bitexact = bool(np.array_equal(pk.he_ct_export(ctx, single), pk.he_ct_export(ctx, outs[0])))
-    pk.he_ct_free(single)
+    single_ref = pk.he_hmatmul(ctx, cts[0][0], cts[0][1], n_mat, n1, n1)
+    bitexact = bool(np.array_equal(pk.he_ct_export(ctx, single_ref), pk.he_ct_export(ctx, outs[0])))
     pk.he_ct_free(outs[0])
 
     # ---- timed region: K batched steps
@@ -244,10 +255,36 @@ def run_ours(args, rank, world, dist):
         ptimes.append(p0.elapsed_time(p1))
     plain = B / (statistics.median(ptimes) / 1000.0)
 
+    # ---- the same batched step replayed as one captured CUDA graph
+    graph = None
+    if not args.no_graph:
+        plan = pk.he_mm_plan_create(jobs)
+        ginfo = pk.he_mm_plan_info(plan)
+        for _ in range(3):
+            for o in pk.he_mm_plan_run(plan):
+                pk.he_ct_free(o)
+        outs_g = pk.he_mm_plan_run(plan)
+        gbit = bool(np.array_equal(pk.he_ct_export(ctx, outs_g[0]), pk.he_ct_export(ctx, single_ref)))
+        for o in outs_g:
+            pk.he_ct_free(o)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(tstream)
+        for _ in range(args.steps):
+            for o in pk.he_mm_plan_run(plan):
+                pk.he_ct_free(o)
+        g1.record(tstream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1)
+        graph = {"value": B * args.steps / (gms / 1000.0), "unit": UNIT, "ms_per_step": gms / args.steps,
+                 "launches_per_step": ginfo["launches"], "plan_bytes": ginfo["bytes"],
+                 "bitexact_vs_batch": gbit}
+        pk.he_mm_plan_destroy(plan)
+    pk.he_ct_free(single_ref)
+
     # ---- e2e through the C ABI from pinned host memory
-    Nn = 1 << 16
-    w_in = 2 * (LEVEL + 1) * Nn
-    w_out = 2 * (LEVEL - 3 + 1) * Nn
+    w_in = 2 * (level + 1) * Nn
+    w_out = 2 * (level - 3 + 1) * Nn
     host_in = torch.empty((B, 2, w_in), dtype=torch.int64, pin_memory=True)
     host_out = torch.empty((B, w_out), dtype=torch.int64, pin_memory=True)
     u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -262,7 +299,7 @@ def run_ours(args, rank, world, dist):
             for j in range(2):
                 h = ctypes.c_void_p()
                 ptr = ctypes.cast(host_in[i, j].data_ptr(), u64p)
-                _lib.check(L.he_ct_import(ctx, ptr, LEVEL, scale, 1 << 15, ctypes.byref(h)))
+                _lib.check(L.he_ct_import(ctx, ptr, level, scale, S, ctypes.byref(h)))
                 hs.append(h)
         outs = pk.he_hmatmul_batch([(hs[2 * i], hs[2 * i + 1], n_mat, n1, n1) for i in range(B)])
         for i, o in enumerate(outs):
@@ -298,23 +335,26 @@ def run_ours(args, rank, world, dist):
         avg_s = t["ms"] / t["count"] / 1000.0
         ach = t["bytes"] / t["count"] / avg_s / 1e9
         return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "peak_source": hbm_src, "traffic": None, "launches": t["count"], "avg_us": avg_s * 1e6}
+                "peak_source": hbm_src,
+                "traffic": TRAFFIC_RATIO["multsum"] * t["bytes"] / t["count"] if args.preset == 2 else None,
+                "launches": t["count"], "avg_us": avg_s * 1e6}
 
-    def ntt_roof(t):
+    def ntt_roof(t, ratio=None):
         if not t["count"]:
             return None
         avg_s = t["ms"] / t["count"] / 1000.0
         words = t["bytes"] / t["count"] / 16.0                     # rows * N per launch
-        bfly = words / 2.0 * 16                                     # (N/2) log2 N per row, logN = 16
+        bfly = words / 2.0 * logN                                   # (N/2) log2 N per row
         ach = bfly / avg_s / 1e9
         peak = bfly_peak / 1e9
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gbutterfly/s", "frac": ach / peak,
-                "peak_source": "measured lazy-Shoup butterfly microbenchmark on this GPU", "traffic": None,
+                "peak_source": "measured lazy-Shoup butterfly microbenchmark on this GPU",
+                "traffic": ratio * t["bytes"] / t["count"] if ratio else None,
                 "launches": t["count"], "avg_us": avg_s * 1e6,
                 "hbm_gbs": t["bytes"] / t["count"] / avg_s / 1e9}
 
     roof_ms = hbm_roof(tr[0])
-    roof_nf = ntt_roof(tr[1])
+    roof_nf = ntt_roof(tr[1], TRAFFIC_RATIO["ntt_fwd"] if args.preset == 2 else None)
     roof_ni = ntt_roof(tr[2])
     totals = {"multsum": tr[0]["ms"], "ntt_fwd": tr[1]["ms"], "ntt_inv": tr[2]["ms"]}
     dominant = max(totals, key=totals.get)
@@ -324,7 +364,7 @@ def run_ours(args, rank, world, dist):
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu:
+    if world == 1 and not args.no_cpu and args.preset == 2 and n_mat == N_MAT:
         v, spent, threads, per = oracle_sample()
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "oracle Decompose + MultSum + ModDown once each at logN 16, level 19, 23 primes "
@@ -335,14 +375,18 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "batch of %d encrypted %dx%d matmuls, N=2^16, q 60+20x40, p 2x60, level 20, "
-                               "n1_z=n1_t=%d" % (B, n_mat, n_mat, n1), "batch_per_gpu": B, "n": n_mat, "logN": 16, "level": LEVEL,
-                   "l2": "inputs larger than L2 (14 GB of rotation keys and %d ciphertext pairs streamed per step)" % B,
+        "config": {"workload": "batch of %d encrypted %dx%d matmuls, N=2^%d, %s, level %d, n1_z=n1_t=%d"
+                               % (B, n_mat, n_mat, logN, "q 60+20x40, p 2x60" if args.preset == 2 else
+                                  "q 60+3x40, p 60", level, n1),
+                   "batch_per_gpu": B, "n": n_mat, "logN": logN, "level": level,
+                   "l2": ("inputs larger than L2 (rotation keys and %d ciphertext pairs streamed per step)" % B
+                          if args.preset == 2 else "no flush: keys and ciphertexts fit in L2 (small-ring case)"),
                    "parallelism": "replicas" if world == 1 else "independent products per rank"},
         "plain": {"value": plain, "unit": UNIT, "note": "same products, one he_hmatmul call each"},
         "batched_over_plain": value / world / plain,
         "roofline": roof, "roofline_keyswitch": roof_ms, "roofline_ntt_fwd": roof_nf, "roofline_ntt_inv": roof_ni,
         "kernel_time_ms": totals,
+        "graph": graph,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": B * 2 * w_in * 8,
                 "d2h_bytes_per_step": B * w_out * 8},
@@ -763,6 +807,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--preset", type=int, default=2, choices=[1, 2],
+                    help="matmul: 2 = 128x128 at N=2^16 (the benchmark), 1 = 32x32 at N=2^14")
+    ap.add_argument("--no-graph", action="store_true", help="matmul: skip the captured-graph replay")
     ap.add_argument("--n", type=int, default=N_MAT, choices=[16, 32, 64, 128],
                     help="matrix dimension (128 is the benchmark; smaller sizes are profiling cases)")
     ap.add_argument("--plain-steps", type=int, default=1)

@@ -120,6 +120,10 @@ SIGNATURES = {
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
     "he_trace_read": [vp, ip, llp, P(ctypes.c_double), P(ctypes.c_double), ip],
+    "he_mm_plan_create": [P(he_mm_job), ip, P(vp)],
+    "he_mm_plan_run": [vp, P(vp)],
+    "he_mm_plan_info": [vp, llp, P(ctypes.c_double)],
+    "he_mm_plan_destroy": [vp],
     "he_server_create": [P(he_server_cfg), P(vp), ip, P(vp)],
     "he_server_submit": [vp, P(he_job), P(ctypes.c_uint64)],
     "he_server_poll": [vp, ctypes.c_uint64, P(ip), P(ip), P(ctypes.c_double)],
@@ -478,4 +482,37 @@ def he_server_stats(srv, kind=0):
 
 def he_server_destroy(srv):
     check(lib().he_server_destroy(srv))
+
+
+# ---------------------------------------------------------- graph plans
+def _mm_jobs(jobs):
+    arr = (he_mm_job * len(jobs))()
+    for i, (a, b, n, n1z, n1t) in enumerate(jobs):
+        arr[i] = he_mm_job(a.value if isinstance(a, vp) else a, b.value if isinstance(b, vp) else b, n,
+                           he_mm_sched(n1z, n1t))
+    return arr
+
+
+def he_mm_plan_create(jobs):
+    """jobs: list of (A, B, n, n1z, n1t); returns a plan handle."""
+    h = vp()
+    check(lib().he_mm_plan_create(_mm_jobs(jobs), len(jobs), ctypes.byref(h)))
+    h.n_jobs = len(jobs)
+    return h
+
+
+def he_mm_plan_run(plan):
+    outs = (vp * plan.n_jobs)()
+    check(lib().he_mm_plan_run(plan, outs))
+    return [vp(o) for o in outs]
+
+
+def he_mm_plan_info(plan):
+    n, b = ctypes.c_longlong(), ctypes.c_double()
+    check(lib().he_mm_plan_info(plan, ctypes.byref(n), ctypes.byref(b)))
+    return {"launches": n.value, "bytes": b.value}
+
+
+def he_mm_plan_destroy(plan):
+    check(lib().he_mm_plan_destroy(plan))
 

@@ -131,7 +131,23 @@ static ModQ make_mod(u64 q) {
 }
 
 // ---------------------------------------------------------------- pool
+void DevicePool::set_redirect(DevicePool *r) {
+    std::lock_guard<std::mutex> lk(mu_);
+    redirect_ = r;
+}
+
+bool DevicePool::owns(void *p) {
+    std::lock_guard<std::mutex> lk(mu_);
+    return sizes_.count(p) != 0;
+}
+
 void *DevicePool::get(size_t bytes) {
+    DevicePool *r;
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        r = redirect_;
+    }
+    if (r) return r->get(bytes);
     std::lock_guard<std::mutex> lk(mu_);
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
@@ -166,6 +182,15 @@ void *DevicePool::get(size_t bytes) {
 
 void DevicePool::put(void *p) {
     if (!p) return;
+    DevicePool *r;
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        r = redirect_;
+    }
+    if (r && r->owns(p)) {
+        r->put(p);
+        return;
+    }
     std::lock_guard<std::mutex> lk(mu_);
     size_t sz = sizes_[p];
     in_use_ -= sz;

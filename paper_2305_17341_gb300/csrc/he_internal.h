@@ -50,9 +50,14 @@ public:
     size_t bytes_in_use() const { return in_use_; }
     size_t bytes_cached() const { return cached_; }
     size_t bytes_peak() const { return peak_; }
+    // While set, get() serves from `r` and put() returns r's blocks to it
+    // (the private scratch of a graph being recorded).
+    void set_redirect(DevicePool *r);
+    bool owns(void *p);
     ~DevicePool() { release_all(); }
 
 private:
+    DevicePool *redirect_ = nullptr;
     // get/put may be called from a serving worker and the caller's thread
     std::mutex mu_;
     std::multimap<size_t, void *> free_;
