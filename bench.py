@@ -109,6 +109,23 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------ multi-rank
+def max_over_ranks(x, dist, device):
+    """The slowest rank's time (every rank gets it); x itself without a group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, units_per_rank, seconds):
+    """Whole-job throughput when every rank processes its own units (no data
+    exchange): all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # -------------------------------------------------------------- cpu oracle
 def oracle_sample(ops_per_step=1):
     """Time the oracle's Decompose, MultSum and ModDown once each at logN 16,
@@ -234,12 +251,8 @@ def run_ours(args, rank, world, dist):
     tr = [pk.he_trace_read(ctx, c, reset=True) for c in range(3)]
     pk.he_trace_enable(ctx, False)
     launches = pk.he_counters(ctx, reset=True)["launches"]
-    t_max = ms_total
-    if dist is not None:
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * B * args.steps / (t_max / 1000.0)
+    t_max = max_over_ranks(ms_total, dist, "cuda")
+    value = weak_scaling_value(world, B * args.steps, t_max / 1000.0)
 
     # ---- plain: the same products one call at a time (untraced)
     ptimes = []
@@ -315,12 +328,8 @@ def run_ours(args, rank, world, dist):
     for _ in range(max(1, args.e2e_steps)):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([e2e_dt], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_dt = float(tt.item())
-    e2e_val = world * B * max(1, args.e2e_steps) / e2e_dt
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_val = weak_scaling_value(world, B * max(1, args.e2e_steps), e2e_dt)
 
     # ---- rooflines
     pk_ = peaks()
