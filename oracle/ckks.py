@@ -365,19 +365,29 @@ class CKKS:
     def rotate(self, ct, step):
         return self.rotate_hoisted(ct, self.modup(ct.c1, ct.level), step)
 
-    def mult_relin(self, a, b):
-        """Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk).
-        Scale = scale_a * scale_b; the caller rescales."""
+    def tensor(self, a, b):
+        """The tensor of Mult (App. A): (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1),
+        decrypting as d0 + d1 s + d2 s^2 = (a0 + a1 s)(b0 + b1 s)."""
         assert a.level == b.level
-        lv = a.level
-        qs = self.P.qs(lv)
+        qs = self.P.qs(a.level)
         d0 = pmul(a.c0, b.c0, qs)
         d1 = _c.polymul_sum(qs, np.stack([a.c0, a.c1]), np.stack([b.c1, b.c0]))
         d2 = pmul(a.c1, b.c1, qs)
+        return d0, d1, d2
+
+    def relin(self, d0, d1, d2, lv, scale, period):
+        """(d0, d1) + KeySwitch(d2, rlk) (App. A Mult)."""
+        qs = self.P.qs(lv)
         digits = self.modup(d2, lv)
         u0, u1 = self.multsum(digits, self.rlk, lv)
         m0, m1 = self.moddown2(u0, u1, lv)
-        return Ct(padd(d0, m0, qs), padd(d1, m1, qs), lv, a.scale * b.scale, min(a.period, b.period))
+        return Ct(padd(d0, m0, qs), padd(d1, m1, qs), lv, scale, period)
+
+    def mult_relin(self, a, b):
+        """Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk).
+        Scale = scale_a * scale_b; the caller rescales."""
+        d0, d1, d2 = self.tensor(a, b)
+        return self.relin(d0, d1, d2, a.level, a.scale * b.scale, min(a.period, b.period))
 
     def refresh(self, ct, obj):
         """Interactive modulus refresh (Sec. 7.2, App. C): decrypt to the

@@ -210,9 +210,14 @@ class HMM:
             return u * prescale
         return self.lintrans(ct, d, a, n, n1, range(-n2g, n2g))
 
-    def hmatmul(self, ctA, ctB, n, n1z, n1t):
+    def hmatmul(self, ctA, ctB, n, n1z, n1t, relin_once=False):
         """JKLS product (eq. 4) with the hoisting of Sec. 4.1 (DMatrixMult with
-        no decomposition, reading C11).  Consumes 3 levels."""
+        no decomposition, reading C11).  Consumes 3 levels.
+
+        relin_once: instead of DMatrixMult's relinearised Mult per k, sum the
+        tensors (d0, d1, d2) of the n products (exact modular sums: decryption
+        d0 + d1 s + d2 s^2 is linear) and relinearise the sum once (App. A
+        Mult applied to the sum).  Not in the paper; n - 1 fewer key switches."""
         he, P = self.he, self.P
         n2m = n * n
         A = self.replicate(ctA, n)
@@ -281,6 +286,14 @@ class HMM:
             else:
                 Bk = he.rotate_hoisted(B_src[g], B_dig[g], (n * b) % n2m)
             Bk = he.drop(Bk, l1 - 1)
-            prod = he.mult_relin(Ak, Bk)
-            acc = prod if acc is None else he.add(acc, prod)
+            if relin_once:
+                t = he.tensor(Ak, Bk)
+                qs = P.qs(Ak.level)
+                acc = t if acc is None else tuple(padd(x, y, qs) for x, y in zip(acc, t))
+                scale, period = Ak.scale * Bk.scale, min(Ak.period, Bk.period)
+            else:
+                prod = he.mult_relin(Ak, Bk)
+                acc = prod if acc is None else he.add(acc, prod)
+        if relin_once:
+            acc = he.relin(acc[0], acc[1], acc[2], l1 - 1, scale, period)
         return he.rescale(acc)

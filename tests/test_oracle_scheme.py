@@ -64,7 +64,7 @@ def test_refresh_keeps_message(small):
     assert np.abs(he.decrypt_slots(r).real - z).max() < 1e-6
 
 
-def _mm(P, he, n, n1z, n1t, seed):
+def _mm(P, he, n, n1z, n1t, seed, relin_once=False):
     H = HMM(he)
     for s in matmul_rot_steps(n, n1z, n1t, P.S):
         he.gen_rotation_key(s)
@@ -77,7 +77,7 @@ def _mm(P, he, n, n1z, n1t, seed):
     ca = he.encrypt_slots(za, P.L, obj=10)
     cb = he.encrypt_slots(zb, P.L, obj=11)
     he.cnt.reset()
-    cc = H.hmatmul(ca, cb, n, n1z, n1t)
+    cc = H.hmatmul(ca, cb, n, n1z, n1t, relin_once=relin_once)
     out = he.decrypt_slots(cc).real[: n * n].reshape(n, n)
     return A, B, cc, out
 
@@ -115,3 +115,42 @@ def test_hmatmul_operation_counts_table1():
     assert he.cnt.MS <= (n1 + 2 * n2) + (n1 + n2) + (2 * n - 1) + (n - 1) + n
     assert he.cnt.Dp <= (2 * n2 + 1) + (n2 + 1) + (2 * n // n1 + 2) + (n // n1 + 1) + n
     assert he.cnt.MD <= (2 * n2 + 1) + (n2 + 1) + (2 * n // n1 + n) + (n - 1) + n
+
+
+def test_tensor_decrypts_to_product_of_decryptions(small):
+    """(d0, d1, d2) of Mult (App. A) satisfies d0 + d1 s + d2 s^2 =
+    (a0 + a1 s)(b0 + b1 s) in every limb; the right side is computed from the
+    two decryptions with the oracle's negacyclic product (pinned against
+    schoolbook convolution)."""
+    from oracle import _c
+    from oracle.ckks import to_rns
+    P, he = small
+    rng = np.random.default_rng(5)
+    a = he.encrypt_slots(rng.uniform(-1, 1, P.S), 2, obj=30)
+    b = he.encrypt_slots(rng.uniform(-1, 1, P.S), 2, obj=31)
+    d0, d1, d2 = he.tensor(a, b)
+    s = to_rns(he.s_int, P.qs(2))
+    for i, q in enumerate(P.qs(2)):
+        ma = (a.c0[i].astype(object) + np.array(_c.polymul(q, a.c1[i], s[i]), dtype=object)) % q
+        mb = (b.c0[i].astype(object) + np.array(_c.polymul(q, b.c1[i], s[i]), dtype=object)) % q
+        want = np.array(_c.polymul(q, ma.astype(np.uint64), mb.astype(np.uint64)), dtype=object)
+        s2 = np.array(_c.polymul(q, s[i], s[i]), dtype=np.uint64)
+        got = (d0[i].astype(object) + np.array(_c.polymul(q, d1[i], s[i]), dtype=object)
+               + np.array(_c.polymul(q, d2[i], s2), dtype=object)) % q
+        assert np.array_equal(got, want)
+
+
+def test_hmatmul_single_relinearisation():
+    """relin_once: the product still decrypts to A.B, with n - 1 fewer
+    MultSum, Decompose and ModDown than the per-product schedule."""
+    n, n1 = 16, 4
+    P = Params(9, [60, 40, 40, 40], [60])
+    he = CKKS(P, 8)
+    A, B, cc, out = _mm(P, he, n, n1, n1, seed=1, relin_once=True)
+    assert cc.level == P.L - 3
+    assert np.abs(out - A @ B).max() < 1e-4
+    got = (he.cnt.MS, he.cnt.Dp, he.cnt.MD)
+    he2 = CKKS(P, 8)
+    _mm(P, he2, n, n1, n1, seed=1)
+    assert got == (he2.cnt.MS - (n - 1), he2.cnt.Dp - (n - 1), he2.cnt.MD - (n - 1))
+
