@@ -61,11 +61,18 @@ typedef struct he_params {
 } he_params;
 
 /* Schedule of the hoisted JKLS product (Table 1 "Optimized"): baby-step
- * counts of the double-hoisted BSGS transforms Z (sigma) and T (tau).  Both
- * must be powers of two dividing n. */
+ * counts of the double-hoisted BSGS transforms Z (sigma) and T (tau), both
+ * powers of two dividing n, and the relinearisation placement:
+ *   relin_once = 0  every product A^(k) B^(k) is relinearised (DMatrixMult's
+ *                   Mult, Sec. 4.3) before the sum -- the paper's circuit;
+ *   relin_once = 1  the n tensors (d0, d1, d2) are summed and relinearised
+ *                   once (App. A Mult applied to the sum; not in the paper:
+ *                   n - 1 fewer key switches, different noise, so different
+ *                   bits). */
 typedef struct he_mm_sched {
     int n1_z;
     int n1_t;
+    int relin_once;
 } he_mm_sched;
 
 /* One product of a batch: out = A . B for n x n matrices (eq. 4). */

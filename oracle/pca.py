@@ -189,8 +189,9 @@ class PCA:
         return A
 
     # --- HCovMtrx (Sec. 5.2) -----------------------------------------------------
-    def covariance(self, blocks, s, n, n1z, n1t, centered=False):
-        """blocks[l][j] = ct(X_j[l]); returns C[a][b] for a, b < k."""
+    def covariance(self, blocks, s, n, n1z, n1t, centered=False, relin_once=False):
+        """blocks[l][j] = ct(X_j[l]); returns C[a][b] for a, b < k.  relin_once
+        selects the block products' relinearisation (HMM.hmatmul)."""
         he, H = self.he, self.H
         nrb, k = len(blocks), len(blocks[0])
         inv_s = 1.0 / s
@@ -203,7 +204,7 @@ class PCA:
                 for l in range(nrb):
                     A = XT[l][a]
                     B = he.drop(Xr[l][b], A.level)
-                    p = H.hmatmul(A, B, n, n1z, n1t)
+                    p = H.hmatmul(A, B, n, n1z, n1t, relin_once=relin_once)
                     acc = p if acc is None else he.add(acc, p)
                 C[a][b] = acc
         for a in range(k):

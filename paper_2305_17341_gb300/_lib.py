@@ -33,7 +33,7 @@ class he_params(ctypes.Structure):
 
 
 class he_mm_sched(ctypes.Structure):
-    _fields_ = [("n1_z", ctypes.c_int), ("n1_t", ctypes.c_int)]
+    _fields_ = [("n1_z", ctypes.c_int), ("n1_t", ctypes.c_int), ("relin_once", ctypes.c_int)]
 
 
 class he_mm_job(ctypes.Structure):
@@ -316,21 +316,15 @@ def he_replicate(ctx, ct, n):
     return _unary("he_replicate", ctx, ct, n)
 
 
-def he_hmatmul(ctx, A, B, n, n1z, n1t):
-    s = he_mm_sched(n1z, n1t)
+def he_hmatmul(ctx, A, B, n, n1z, n1t, relin_once=False):
+    s = he_mm_sched(n1z, n1t, 1 if relin_once else 0)
     return _unary("he_hmatmul", ctx, A, B, n, ctypes.byref(s))
 
 
 def he_hmatmul_batch(jobs):
-    """jobs: list of (A, B, n, n1z, n1t)."""
-    arr = (he_mm_job * len(jobs))()
-    for i, (A, B, n, n1z, n1t) in enumerate(jobs):
-        arr[i].A = A
-        arr[i].B = B
-        arr[i].n = n
-        arr[i].sched = he_mm_sched(n1z, n1t)
+    """jobs: list of (A, B, n, n1z, n1t[, relin_once])."""
     outs = (vp * len(jobs))()
-    check(lib().he_hmatmul_batch(arr, len(jobs), outs))
+    check(lib().he_hmatmul_batch(_mm_jobs(jobs), len(jobs), outs))
     return [vp(o) for o in outs]
 
 
@@ -355,10 +349,10 @@ def he_aggregate(ctx, ct, axis, n):
     return _unary("he_aggregate", ctx, ct, axis, n)
 
 
-def he_covariance(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t):
+def he_covariance(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t, relin_once=False):
     """blocks: list of handles in [l][j] order (l-major); returns k*k handles (a*k + b)."""
     out = (vp * (k * k))()
-    sc = he_mm_sched(n1z, n1t)
+    sc = he_mm_sched(n1z, n1t, 1 if relin_once else 0)
     check(lib().he_covariance(ctx, _handles(blocks), n_row_blocks, k, n, s, 1 if centered else 0,
                               ctypes.byref(sc), out))
     return [vp(o) for o in out]
@@ -438,13 +432,14 @@ def he_server_create(ctxs, hbm_budget_bytes, max_batch=8):
 
 
 def he_server_submit(srv, kind, inputs=(), ctx=None, n=0, n1z=1, n1t=1, n_row_blocks=0, k=0, s=0, centered=False,
-                     acc_id=0, l_E=0, l_P=0, axis=0, counts=None, B2=0.0, refresh_obj=0):
+                     acc_id=0, l_E=0, l_P=0, axis=0, counts=None, B2=0.0, refresh_obj=0, relin_once=False):
     """Queues one job (see include/he.h, he_job); returns its id.  Raises
     HeError (HE_ERR_ADMISSION when over the budget)."""
     arr = _handles(list(inputs)) if len(inputs) else None
     cs = (ctypes.c_int * len(counts))(*counts) if counts else None
     j = he_job(kind, ctx.value if isinstance(ctx, vp) else ctx,
-               ctypes.cast(arr, P(vp)) if arr is not None else None, len(inputs), n, he_mm_sched(n1z, n1t),
+               ctypes.cast(arr, P(vp)) if arr is not None else None, len(inputs), n,
+               he_mm_sched(n1z, n1t, 1 if relin_once else 0),
                n_row_blocks, k, s, 1 if centered else 0, acc_id, l_E, l_P, axis,
                ctypes.cast(cs, P(ctypes.c_int)) if cs is not None else None, B2, refresh_obj)
     jid = ctypes.c_uint64()
@@ -486,10 +481,13 @@ def he_server_destroy(srv):
 
 # ---------------------------------------------------------- graph plans
 def _mm_jobs(jobs):
+    """(A, B, n, n1z, n1t[, relin_once]) tuples -> he_mm_job array."""
     arr = (he_mm_job * len(jobs))()
-    for i, (a, b, n, n1z, n1t) in enumerate(jobs):
+    for i, j in enumerate(jobs):
+        a, b, n, n1z, n1t = j[:5]
+        once = 1 if len(j) > 5 and j[5] else 0
         arr[i] = he_mm_job(a.value if isinstance(a, vp) else a, b.value if isinstance(b, vp) else b, n,
-                           he_mm_sched(n1z, n1t))
+                           he_mm_sched(n1z, n1t, once))
     return arr
 
 

@@ -523,7 +523,7 @@ static int check_sched(Ctx &c, int n, const he_mm_sched *s) {
 // Runs one group of same-shape products: gathers A's and B's, replicates,
 // aligns levels, multiplies, scatters.
 static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::vector<const he_ct *> &Bs, int n,
-                      int n1z, int n1t, int level, std::vector<he_ct *> &outs) {
+                      int n1z, int n1t, int level, std::vector<he_ct *> &outs, bool relin_once) {
     const int Bn = (int)As.size();
     const size_t w = ct_words(&c, level);
     Buf A(&c.pool, Bn * w), B(&c.pool, Bn * w);
@@ -538,7 +538,7 @@ static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::v
     if (Bs[0]->period != n * n) replicate(&c, B.p, Bn, level, n);
     const size_t wo = ct_words(&c, level - 3);
     Buf O(&c.pool, Bn * wo);
-    hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p);
+    hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p, relin_once);
     double q2 = (double)c.primes[level - 2];
     try {
         for (int i = 0; i < Bn; i++) {
@@ -554,7 +554,7 @@ static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::v
 
 int he_hmatmul(he_ctx *ctx, const he_ct *A, const he_ct *B, int n, const he_mm_sched *sched, he_ct **out) {
     if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
-    he_mm_job j{A, B, n, sched ? *sched : he_mm_sched{0, 0}};
+    he_mm_job j{A, B, n, sched ? *sched : he_mm_sched{0, 0, 0}};
     if (!sched) return fail(HE_ERR_ARG, "null schedule");
     if (int rc = check_ct(ctx->c, A)) return rc;
     if (int rc = check_ct(ctx->c, B)) return rc;
@@ -572,7 +572,8 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
     GUARD_BEGIN
     std::vector<ProdSpec> prods;
     for (int i = 0; i < n_jobs; i++)
-        prods.push_back({jobs[i].A, jobs[i].B, jobs[i].n, jobs[i].sched.n1_z, jobs[i].sched.n1_t});
+        prods.push_back({jobs[i].A, jobs[i].B, jobs[i].n, jobs[i].sched.n1_z, jobs[i].sched.n1_t,
+                         jobs[i].sched.relin_once != 0});
     std::vector<he_ct *> res;
     run_products(prods, res, 0);
     try {
@@ -594,12 +595,13 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
 
 namespace he {
 void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs, int max_batch) {
-    typedef std::tuple<Ctx *, int, int, int, int, int, int> Key;
+    typedef std::tuple<Ctx *, int, int, int, int, int, int, int> Key;
     std::map<Key, std::vector<int>> groups;
     for (size_t i = 0; i < prods.size(); i++) {
         const ProdSpec &j = prods[i];
         int lv = std::min(j.A->level, j.B->level);
-        groups[Key(j.A->ctx, lv, j.n, j.n1z, j.n1t, j.A->period == j.n * j.n, j.B->period == j.n * j.n)]
+        groups[Key(j.A->ctx, lv, j.n, j.n1z, j.n1t, j.A->period == j.n * j.n, j.B->period == j.n * j.n,
+                   j.relin_once)]
             .push_back((int)i);
     }
     outs.assign(prods.size(), nullptr);
@@ -618,7 +620,7 @@ void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs
                 }
                 std::vector<he_ct *> o(As.size());
                 const ProdSpec &j0 = prods[ix[s0]];
-                run_group(c, As, Bs, j0.n, j0.n1z, j0.n1t, lv, o);
+                run_group(c, As, Bs, j0.n, j0.n1z, j0.n1t, lv, o, j0.relin_once);
                 for (size_t t = s0; t < s1; t++) outs[ix[t]] = o[t - s0];
             }
         }

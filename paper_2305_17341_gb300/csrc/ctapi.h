@@ -26,6 +26,7 @@ namespace he {
 struct ProdSpec {
     const he_ct *A, *B;
     int n, n1z, n1t;
+    bool relin_once = false;
 };
 
 // Runs every product of `prods`, grouping those that share (context, level,

@@ -104,6 +104,20 @@ void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out) {
     launch_copy_rows(out, (long)(to + 1) * N, in, (long)(level + 1) * N, 2 * B, (long)(to + 1) * N, c->stream);
 }
 
+// out (holding (d0, d1)) += KeySwitch(d2, rlk): the relinearisation of Mult.
+static void relin_into(Ctx *c, const u64 *d2, int B, int level, u64 *out) {
+    if (!c->rlk) throw HeError(HE_ERR_KEY_MISSING, "relinearisation key missing");
+    const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
+    Buf dg(&c->pool, (size_t)B * c->ndig(level) * rows * N);
+    modup(c, d2, (long)nq * N, B, level, dg.p);
+    Buf u(&c->pool, (size_t)B * 2 * rows * N), md(&c->pool, (size_t)B * 2 * nq * N);
+    launch_multsum(c, u.p, dg.p, c->rlk, 1u, B, level, nullptr, 0, c->stream);
+    c->n_ms += B;
+    moddown(c, u.p, 2 * B, level, md.p, (long)nq * N);
+    c->n_md += B;
+    launch_add(c, out, out, md.p, 2L * B * nq, c->map_q(level), c->stream);
+}
+
 // Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk).
 void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out) {
     if (!c->rlk) throw HeError(HE_ERR_KEY_MISSING, "relinearisation key missing");
@@ -239,7 +253,8 @@ void replicate(Ctx *c, u64 *ct, int B, int level, int n) {
 
 // JKLS product (eq. 4) with the hoisting of Sec. 4.1; A, B: [Bn][2][l+1][N]
 // replicated with period n^2; out: [Bn][2][l-2][N].
-void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out) {
+void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
+             bool relin_once) {
     if (level < 3) throw HeError(HE_ERR_LEVEL, "matrix product needs 3 levels");
     const int N = c->N;
     const long n2m = (long)n * n;
@@ -263,6 +278,8 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
     int gA = 0, gB = 0;
 
     Buf acc(&c->pool, Bn * ct2), Ak(&c->pool, Bn * ct2), Bk(&c->pool, Bn * ct2), prod(&c->pool, Bn * ct2);
+    // relin_once: the summed d2 of the n tensors (d0, d1 are summed in acc)
+    Buf acc2(&c->pool, relin_once ? (size_t)Bn * (l2 + 1) * N : 1);
     Buf R1(&c->pool, Bn * qp1), R2(&c->pool, Bn * qp1), S(&c->pool, Bn * qp1), Akp(&c->pool, Bn * ct1),
         Bkf(&c->pool, Bn * ct1);
     RowMap q2 = c->map_q(l2);
@@ -311,13 +328,17 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
             drop(c, Bkf.p, Bn, l1, l2, Bk.p);
         }
         // ---- product, relinearised, accumulated at level l2
-        if (k == 0) {
+        if (relin_once) {
+            const long cs = 2L * (l2 + 1) * N;
+            launch_tensor(c, acc.p, acc2.p, Ak.p, Bk.p, Bn, l2 + 1, cs, cs, q2, c->stream, k > 0);
+        } else if (k == 0) {
             mult_relin(c, Ak.p, Bk.p, Bn, l2, acc.p);
         } else {
             mult_relin(c, Ak.p, Bk.p, Bn, l2, prod.p);
             launch_add(c, acc.p, acc.p, prod.p, 2L * Bn * (l2 + 1), q2, c->stream);
         }
     }
+    if (relin_once) relin_into(c, acc2.p, Bn, l2, acc.p);
     rescale(c, acc.p, Bn, l2, out);
 }
 

@@ -33,6 +33,7 @@ const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k
 void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
               double value, u64 *out);
 void replicate(Ctx *c, u64 *ct, int B, int level, int n);
-void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out);
+void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
+             bool relin_once = false);
 
 }  // namespace he

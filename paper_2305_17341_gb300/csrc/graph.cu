@@ -21,7 +21,7 @@ namespace {
 struct Group {
     std::vector<int> idx;        // job indices
     int level = 0, n = 0, n1z = 0, n1t = 0;
-    bool repA = false, repB = false;
+    bool repA = false, repB = false, relin_once = false;
     u64 *O = nullptr;            // [items][2][level-2][N], plan memory
     size_t wo = 0;
 };
@@ -61,7 +61,7 @@ static void record(he_mm_plan *P) {
         }
         if (g.repA) replicate(&c, A.p, Bn, g.level, g.n);
         if (g.repB) replicate(&c, B.p, Bn, g.level, g.n);
-        hmatmul(&c, A.p, B.p, Bn, g.level, g.n, g.n1z, g.n1t, g.O);
+        hmatmul(&c, A.p, B.p, Bn, g.level, g.n, g.n1z, g.n1t, g.O, g.relin_once);
     }
 }
 
@@ -90,17 +90,18 @@ int he_mm_plan_create(const he_mm_job *jobs, int n_jobs, he_mm_plan **out) {
     if (!P) return plan_fail(HE_ERR_OOM, "host allocation failed");
     P->c = c;
     P->jobs.assign(jobs, jobs + n_jobs);
-    typedef std::tuple<int, int, int, int, bool, bool> Key;
+    typedef std::tuple<int, int, int, int, bool, bool, bool> Key;
     std::map<Key, int> gi;
     for (int i = 0; i < n_jobs; i++) {
         const he_mm_job &j = jobs[i];
         const int n = j.n, lv = std::min(j.A->level, j.B->level);
-        Key k(lv, n, j.sched.n1_z, j.sched.n1_t, j.A->period != n * n, j.B->period != n * n);
+        Key k(lv, n, j.sched.n1_z, j.sched.n1_t, j.A->period != n * n, j.B->period != n * n,
+              j.sched.relin_once != 0);
         auto it = gi.find(k);
         if (it == gi.end()) {
             Group g;
             g.level = lv, g.n = n, g.n1z = j.sched.n1_z, g.n1t = j.sched.n1_t;
-            g.repA = std::get<4>(k), g.repB = std::get<5>(k);
+            g.repA = std::get<4>(k), g.repB = std::get<5>(k), g.relin_once = std::get<6>(k);
             it = gi.emplace(k, (int)P->groups.size()).first;
             P->groups.push_back(g);
         }

@@ -232,8 +232,10 @@ void launch_mulconst_rows(Ctx *c, u64 *out, const u64 *a, const ShoupPair *w, lo
                           const RowMap &rm, cudaStream_t st);
 void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &rm, uint32_t g,
                       cudaStream_t st);
+// (d0, d1) -> d01 [B][2][limbs][N], d2 -> [B][limbs][N]; accumulate adds
+// the tensor to what d01 and d2 already hold.
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long a_item_stride,
-                   long b_item_stride, const RowMap &rm, cudaStream_t st);
+                   long b_item_stride, const RowMap &rm, cudaStream_t st, bool accumulate = false);
 // key switching pieces
 // own_ntt (may be null): the input in the NTT domain, item stride own_s; the
 // digit's own rows are then copied from it (and the forward NTT must skip

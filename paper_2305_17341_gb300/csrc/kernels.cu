@@ -298,7 +298,7 @@ void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &
 // tensor product in the NTT domain: d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1.
 // d01: [B][2][limbs][N] (d0, d1 of each item); d2: [B][limbs][N].
 __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, int N,
-                         long as, long bs, RowMap rm, const ModQ *mods) {
+                         long as, long bs, RowMap rm, const ModQ *mods, int accumulate) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long per = (long)limbs * N;
     if (idx >= (long)B * per) return;
@@ -313,15 +313,22 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
     mac128(acc, a1, b0);
     u64 t1 = redc(acc.lo, acc.hi, m);
     u64 *o = d01 + (long)it * 2 * per + off;
-    o[0] = mulmod(a0, b0, m);
-    o[per] = redc(t1 * m.r2, mulhi64(t1, m.r2), m);
-    d2[(long)it * per + off] = mulmod(a1, b1, m);
+    u64 v0 = mulmod(a0, b0, m), v1 = redc(t1 * m.r2, mulhi64(t1, m.r2), m), v2 = mulmod(a1, b1, m);
+    u64 *o2 = d2 + (long)it * per + off;
+    if (accumulate) {
+        v0 = addmod(v0, o[0], m.q);
+        v1 = addmod(v1, o[per], m.q);
+        v2 = addmod(v2, o2[0], m.q);
+    }
+    o[0] = v0;
+    o[per] = v1;
+    o2[0] = v2;
 }
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
-                   const RowMap &rm, cudaStream_t st) {
+                   const RowMap &rm, cudaStream_t st, bool accumulate) {
     long n = (long)B * limbs * c->N;
     c->n_launch++;
-    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod);
+    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod, accumulate ? 1 : 0);
 }
 
 // ------------------------------------------------------------- ModUp

@@ -272,7 +272,7 @@ public:
     //      common level, and (not centred) minus mu_a^T mu_b
     struct CovPlan {
         int nrb = 0, k = 0, n = 0, s = 0, n1z = 0, n1t = 0;
-        bool centered = true;
+        bool centered = true, relin_once = false;
         std::vector<he_ct *> blocks;
         std::vector<HC> XT, Xr;
     };
@@ -292,7 +292,7 @@ public:
         for (int a = 0; a < k; a++)
             for (int b = a; b < k; b++)
                 for (int l = 0; l < P.nrb; l++)
-                    prods.push_back({P.XT[l * k + a].p, P.Xr[l * k + b].p, P.n, P.n1z, P.n1t});
+                    prods.push_back({P.XT[l * k + a].p, P.Xr[l * k + b].p, P.n, P.n1z, P.n1t, P.relin_once});
     }
 
     // Takes ownership of the products made from cov_prepare's list.
@@ -348,8 +348,9 @@ public:
     }
 
     std::vector<HC> covariance(he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z,
-                               int n1t) {
+                               int n1t, bool relin_once = false) {
         CovPlan P;
+        P.relin_once = relin_once;
         P.nrb = nrb;
         P.k = k;
         P.n = n;
@@ -499,7 +500,7 @@ struct CovStage {
 };
 
 CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z, int n1t,
-                    std::vector<ProdSpec> &prods) {
+                    std::vector<ProdSpec> &prods, bool relin_once) {
     RefreshState st{0, 0};
     PcaOps ops(c, &st);
     CovStage *S = new CovStage;
@@ -511,6 +512,7 @@ CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, 
     P.n1z = n1z;
     P.n1t = n1t;
     P.centered = centered;
+    P.relin_once = relin_once;
     P.blocks.assign(blocks, blocks + (size_t)nrb * k);
     try {
         ops.cov_prepare(P, prods);
@@ -674,7 +676,8 @@ int he_covariance(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, in
     PCA_GUARD_BEGIN
     RefreshState st{0, 0};
     PcaOps ops(&c, &st);
-    std::vector<HC> C = ops.covariance(blocks, n_row_blocks, k, n, s, centered != 0, sched->n1_z, sched->n1_t);
+    std::vector<HC> C = ops.covariance(blocks, n_row_blocks, k, n, s, centered != 0, sched->n1_z, sched->n1_t,
+                                       sched->relin_once != 0);
     if (int rc = sync_status(c)) return rc;
     for (int i = 0; i < k * k; i++) cov[i] = C[i].release();
     return HE_OK;

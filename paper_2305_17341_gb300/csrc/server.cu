@@ -45,7 +45,7 @@ struct Job {
 };
 
 struct Accum {
-    int k = 0, n = 0, n1z = 0, n1t = 0, s = 0, level = -1;
+    int k = 0, n = 0, n1z = 0, n1t = 0, s = 0, level = -1, relin_once = 0;
     CovStage *stage = nullptr;    // plan of the first row block (used for the final mirror)
     std::vector<he_ct *> upper;   // k*k, entries a <= b
 };
@@ -141,12 +141,13 @@ void he_server::tick(Worker *w, std::vector<Job *> &batch) {
         j->p0 = prods.size();
         guarded(j, [&] {
             if (s.kind == HE_JOB_MATMUL) {
-                prods.push_back({j->in[0], j->in[1], s.n, s.sched.n1_z, s.sched.n1_t});
+                prods.push_back({j->in[0], j->in[1], s.n, s.sched.n1_z, s.sched.n1_t, s.sched.relin_once != 0});
             } else if (s.kind == HE_JOB_COVARIANCE) {
                 j->stage = cov_begin(c, j->in.data(), s.n_row_blocks, s.k, s.n, s.s, s.centered != 0, s.sched.n1_z,
-                                     s.sched.n1_t, prods);
+                                     s.sched.n1_t, prods, s.sched.relin_once != 0);
             } else if (s.kind == HE_JOB_XTX_BLOCK) {
-                j->stage = cov_begin(c, j->in.data(), 1, s.k, s.n, s.s, true, s.sched.n1_z, s.sched.n1_t, prods);
+                j->stage = cov_begin(c, j->in.data(), 1, s.k, s.n, s.s, true, s.sched.n1_z, s.sched.n1_t, prods,
+                                     s.sched.relin_once != 0);
             }
         });
         if (j->status == HE_JOB_FAILED) prods.resize(j->p0);
@@ -202,6 +203,7 @@ void he_server::tick(Worker *w, std::vector<Job *> &batch) {
                 if (it == w->acc.end()) {
                     Accum a;
                     a.k = s.k, a.n = s.n, a.n1z = s.sched.n1_z, a.n1t = s.sched.n1_t, a.s = s.s;
+                    a.relin_once = s.sched.relin_once != 0;
                     a.level = U[0]->level;
                     a.stage = j->stage;
                     j->stage = nullptr;
@@ -210,7 +212,7 @@ void he_server::tick(Worker *w, std::vector<Job *> &batch) {
                 } else {
                     Accum &a = it->second;
                     bool same = a.k == s.k && a.n == s.n && a.n1z == s.sched.n1_z && a.n1t == s.sched.n1_t &&
-                                a.s == s.s && a.level == U[0]->level;
+                                a.s == s.s && a.level == U[0]->level && a.relin_once == (s.sched.relin_once != 0);
                     if (!same) {
                         for (he_ct *u : U) free_ct(u);
                         throw HeError(HE_ERR_ARG, "row block does not match its accumulator (shape, rows or level)");

@@ -149,9 +149,12 @@ def test_transpose_bit_exact(c1):
         lib.he_ct_free(h)
 
 
-def test_hmatmul_config1_bit_exact(c1):
+@pytest.mark.parametrize("relin_once", [False, True])
+def test_hmatmul_config1_bit_exact(c1, relin_once):
     """Config 1: 32x32 product at N=2^14, q 60+3x40, p 60 -- residues
-    bit-exact to the oracle, decrypted product within 1e-4 of FP64 A.B."""
+    bit-exact to the oracle, decrypted product within 1e-4 of FP64 A.B; with
+    the per-product relinearisation of DMatrixMult and with one
+    relinearisation of the summed tensors."""
     from oracle.hmm import HMM, matmul_rot_steps
     lib, ctx, P, he = c1
     n, n1 = 32, 8
@@ -162,8 +165,12 @@ def test_hmatmul_config1_bit_exact(c1):
     he.gen_relin_key()
     A, B, oa, ob, ga, gb = _matrix_pair(P, he, lib, ctx, n, 41)
     assert np.array_equal(lib.he_ct_export(ctx, ga), residues(he, oa))
-    gc = lib.he_hmatmul(ctx, ga, gb, n, n1, n1)
-    oc = HMM(he).hmatmul(oa, ob, n, n1, n1)
+    lib.he_counters(ctx, reset=True)
+    gc = lib.he_hmatmul(ctx, ga, gb, n, n1, n1, relin_once=relin_once)
+    cnt = lib.he_counters(ctx)
+    he.cnt.reset()
+    oc = HMM(he).hmatmul(oa, ob, n, n1, n1, relin_once=relin_once)
+    assert (cnt["MS"], cnt["Dp"], cnt["MD"]) == (he.cnt.MS, he.cnt.Dp, he.cnt.MD)
     got = lib.he_ct_export(ctx, gc)
     want = residues(he, oc)
     assert got.shape == want.shape
@@ -291,3 +298,20 @@ def test_ntt_negacyclic_product_and_roundtrip(lib, logN, qbits, pbits):
         assert np.array_equal(da.cpu().numpy().view(np.uint64), a)
     finally:
         lib.he_ctx_destroy(ctx)
+
+
+def test_hmatmul_batch_relin_once_equals_single(c1):
+    """Batched products with one relinearisation each equal the single calls."""
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    from oracle.hmm import matmul_rot_steps
+    lib.he_keygen(ctx, matmul_rot_steps(n, n1, n1, P.S), want_relin=True)
+    pairs = [_matrix_pair(P, he, lib, ctx, n, 80 + i) for i in range(3)]
+    singles = [lib.he_hmatmul(ctx, p[4], p[5], n, n1, n1, relin_once=True) for p in pairs]
+    batch = lib.he_hmatmul_batch([(p[4], p[5], n, n1, n1, True) for p in pairs])
+    for s, b, p in zip(singles, batch, pairs):
+        assert np.array_equal(lib.he_ct_export(ctx, s), lib.he_ct_export(ctx, b))
+        assert np.abs(lib.he_decrypt_matrix(ctx, b, n, n) - p[0] @ p[1]).max() < TOL
+    for h in singles + batch + [x for p in pairs for x in p[4:6]]:
+        lib.he_ct_free(h)
+
