@@ -714,6 +714,64 @@ def run_served(args):
         pk.he_ctx_destroy(c)
 
 
+def run_keyswitch(args):
+    """Hoisted key-switched rotations alone (he_rotate_hoisted): B ciphertexts
+    at level 20 of the 60 + 20x40 / 2x60 chain (N = 2^16), each Decomposed
+    once and rotated by R steps; every MultSum launch reads one rotation key
+    for all B ciphertexts.  Device time of the traced kernel classes; the
+    MultSum roofline is the key switch's HBM roofline."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    pk.build()
+    ctx = pk.he_ctx_create(pk.he_params_default(2), 11)
+    tstream = torch.cuda.Stream()
+    pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
+    R, B = args.rot_steps, args.batch
+    steps = [1 + 37 * i for i in range(R)]
+    pk.he_keygen(ctx, steps, False)
+    rng = np.random.default_rng(13)
+    cts = [pk.he_encrypt_slots(ctx, rng.uniform(-1, 1, 1 << 15), LEVEL, 7000 + i) for i in range(B)]
+
+    def step():
+        for row in pk.he_rotate_hoisted(ctx, cts, steps):
+            for h in row:
+                pk.he_ct_free(h)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    pk.he_trace_enable(ctx, True)
+    for c in range(3):
+        pk.he_trace_read(ctx, c, reset=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(tstream)
+    for _ in range(args.steps):
+        step()
+    e1.record(tstream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tr = [pk.he_trace_read(ctx, c, reset=True) for c in range(3)]
+    pk.he_trace_enable(ctx, False)
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    t = tr[0]
+    avg = t["ms"] / t["count"] / 1e3
+    ach = t["bytes"] / t["count"] / avg / 1e9
+    print(json.dumps({"metric": "hoisted key-switched rotations/s (N=2^16, level 20)",
+                      "value": B * R * args.steps / (ms / 1e3), "unit": "rotations/s", "higher_is_better": True,
+                      "n_gpus": 1, "steps": args.steps, "ms_per_step": ms / args.steps,
+                      "roofline_keyswitch": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                             "frac": ach / hbm, "launches": t["count"], "avg_us": avg * 1e6,
+                                             "algorithmic_bytes_per_launch": t["bytes"] / t["count"]},
+                      "kernel_time_ms": {"multsum": tr[0]["ms"], "ntt_fwd": tr[1]["ms"], "ntt_inv": tr[2]["ms"]},
+                      "config": {"workload": "%d ciphertexts x %d rotation steps, one Decompose per ciphertext" % (B, R)}}),
+          flush=True)
+    for h in cts:
+        pk.he_ct_free(h)
+    pk.he_ctx_destroy(ctx)
+
+
 def run_ntt(args):
     """The NTT alone (he_ntt) on R rows at N = 2^16 over the primes of the
     covariance chain at level 20 (R = 2024 is the forward transform of one
@@ -834,8 +892,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served", "ntt"])
+    ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served", "ntt",
+                                                           "keyswitch"])
     ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
+    ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
     ap.add_argument("--rate", type=float, default=1.5, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="served: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
@@ -856,6 +916,8 @@ def main():
         return run_served(args)
     if args.workload == "ntt":
         return run_ntt(args)
+    if args.workload == "keyswitch":
+        return run_keyswitch(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None

@@ -102,6 +102,13 @@ int he_ctx_destroy(he_ctx *ctx);
  * own stream).  The caller keeps ownership of a stream it passes. */
 int he_ctx_set_stream(he_ctx *ctx, void *stream);
 
+/* Launch-geometry autotuner (on by default): the first MultSum launch of
+ * each (level, batch size) times its launch variants -- items per CTA, cached
+ * or streaming digit loads -- on that very launch and keeps the fastest for
+ * the context.  Variants compute identical words; only speed differs.
+ * on = 0 uses the fixed default (8 items per CTA, cached loads). */
+int he_ctx_set_autotune(he_ctx *ctx, int on);
+
 /* Copies the primes: q_out[0..L] and p_out[0..alpha-1] (host arrays). */
 int he_ctx_primes(const he_ctx *ctx, uint64_t *q_out, uint64_t *p_out);
 
@@ -175,6 +182,14 @@ int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out);
 int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level, int step, uint64_t *out_dev);
 
 /* Add (App. A Addition module): same level and scale. */
+/* Hoisted rotations (Sec. 3.3.1): every ciphertext is Decomposed once and
+ * that Decompose output serves all n_steps rotations; ciphertexts of one
+ * level run as one batch, so each rotation key is read once per batch.
+ * outs[i*n_steps + s] = Rot(cts[i], steps[s]) (caller frees).  Bit-identical
+ * to he_rotate.  Errors: HE_ERR_ARG, HE_ERR_KEY_MISSING (no outputs made). */
+int he_rotate_hoisted(he_ctx *ctx, const he_ct *const *cts, int n_cts, const int32_t *steps, int n_steps,
+                      he_ct **outs);
+
 int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out);
 
 /* Mult (App. A): tensor product then relinearisation; scale multiplies. */

@@ -83,6 +83,7 @@ SIGNATURES = {
     "he_ctx_destroy": [vp],
     "he_ctx_set_stream": [vp, vp],
     "he_ctx_primes": [vp, u64p, u64p],
+    "he_ctx_set_autotune": [vp, ip],
     "he_ctx_info": [vp, P(ip), P(ip), P(ip), P(ip), P(ip)],
     "he_sk_export": [vp, P(ctypes.c_int64)],
     "he_keygen": [vp, i32p, ip, ip],
@@ -98,6 +99,7 @@ SIGNATURES = {
     "he_ct_free": [vp],
     "he_rotate": [vp, vp, ip, P(vp)],
     "he_rotate_noalloc": [vp, vp, ip, ip, vp],
+    "he_rotate_hoisted": [vp, P(vp), ip, i32p, ip, P(vp)],
     "he_add": [vp, vp, vp, P(vp)],
     "he_mult": [vp, vp, vp, P(vp)],
     "he_rescale": [vp, vp, P(vp)],
@@ -191,6 +193,10 @@ def he_ctx_destroy(ctx):
 
 def he_ctx_set_stream(ctx, stream_ptr):
     check(lib().he_ctx_set_stream(ctx, stream_ptr))
+
+
+def he_ctx_set_autotune(ctx, on=True):
+    check(lib().he_ctx_set_autotune(ctx, 1 if on else 0))
 
 
 def he_ctx_info(ctx):
@@ -298,6 +304,14 @@ def he_rotate(ctx, ct, step):
 def he_rotate_noalloc(ctx, in_dev_ptr, level, step, out_dev_ptr):
     """Rotation on caller-owned device buffers (raw device pointers as ints)."""
     check(lib().he_rotate_noalloc(ctx, vp(in_dev_ptr), level, step, vp(out_dev_ptr)))
+
+
+def he_rotate_hoisted(ctx, cts, steps):
+    """Returns outs[i][s] = Rot(cts[i], steps[s]) with one Decompose per ciphertext."""
+    st = (ctypes.c_int32 * len(steps))(*steps)
+    outs = (vp * (len(cts) * len(steps)))()
+    check(lib().he_rotate_hoisted(ctx, _handles(cts), len(cts), st, len(steps), outs))
+    return [[vp(outs[i * len(steps) + s]) for s in range(len(steps))] for i in range(len(cts))]
 
 
 def he_add(ctx, a, b):

@@ -230,6 +230,12 @@ int he_ctx_set_stream(he_ctx *ctx, void *stream) {
     return HE_OK;
 }
 
+int he_ctx_set_autotune(he_ctx *ctx, int on) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    ctx->c.autotune = on != 0;
+    return HE_OK;
+}
+
 int he_ctx_primes(const he_ctx *ctx, uint64_t *q_out, uint64_t *p_out) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
     const Ctx &c = ctx->c;
@@ -258,9 +264,7 @@ int he_sk_export(const he_ctx *ctx, int64_t *s_out) {
     Ctx &cc = const_cast<Ctx &>(c);
     Buf t(&cc.pool, c.N);
     HE_CUDA_CHECK(cudaMemcpyAsync(t.p, c.d_sk, (size_t)c.N * 8, cudaMemcpyDeviceToDevice, c.stream));
-    RowMap one;
-    one.n = 1;
-    one.p[0] = 0;
+    RowMap one = RowMap::single(0);
     ntt_inv(&cc, t.p, 1, one, c.stream);
     std::vector<u64> h(c.N);
     HE_CUDA_CHECK(cudaMemcpyAsync(h.data(), t.p, (size_t)c.N * 8, cudaMemcpyDeviceToHost, c.stream));
@@ -347,9 +351,7 @@ int he_decrypt_slots(he_ctx *ctx, const he_ct *ct, double *z, int nslots) {
     Buf m(&c.pool, c.N), coef(&c.pool, c.N), zr(&c.pool, c.S), zi(&c.pool, c.S);
     const u64 *c0 = ct->d, *c1 = ct->d + (size_t)(ct->level + 1) * c.N;
     launch_dec_q0(&c, c0, c1, m.p, c.stream);
-    RowMap one;
-    one.n = 1;
-    one.p[0] = 0;
+    RowMap one = RowMap::single(0);
     ntt_inv(&c, m.p, 1, one, c.stream);
     launch_centre_q0(&c, m.p, (double *)coef.p, c.stream);
     launch_decode(&c, (double *)coef.p, ct->scale, (double *)zr.p, (double *)zi.p, c.stream);
@@ -430,6 +432,48 @@ int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out) {
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
     *out = o;
     return cuda_status(&c);
+    GUARD_END
+}
+
+int he_rotate_hoisted(he_ctx *ctx, const he_ct *const *cts, int n_cts, const int32_t *steps, int n_steps,
+                      he_ct **outs) {
+    if (!ctx || !cts || !steps || !outs || n_cts < 1 || n_steps < 1) return fail(HE_ERR_ARG, "bad arguments");
+    Ctx &c = ctx->c;
+    for (int i = 0; i < n_cts; i++)
+        if (int rc = check_ct(c, cts[i])) return rc;
+    for (int s = 0; s < n_steps; s++)
+        if (!c.rtk.count(galois_of_step(&c, steps[s]))) return fail(HE_ERR_KEY_MISSING, "rotation key missing");
+    GUARD_BEGIN
+    std::map<int, std::vector<int>> by_level;
+    for (int i = 0; i < n_cts; i++) by_level[cts[i]->level].push_back(i);
+    std::vector<he_ct *> res((size_t)n_cts * n_steps, nullptr);
+    try {
+        for (auto &kv : by_level) {
+            const int lv = kv.first, Bn = (int)kv.second.size();
+            const size_t w = ct_words(&c, lv);
+            Buf A(&c.pool, Bn * w), O(&c.pool, Bn * w);
+            Buf dg(&c.pool, (size_t)Bn * c.ndig(lv) * c.qp_rows(lv) * c.N);
+            for (int t = 0; t < Bn; t++)
+                cudaMemcpyAsync(A.p + t * w, cts[kv.second[t]]->d, w * 8, cudaMemcpyDeviceToDevice, c.stream);
+            modup(&c, A.p + (long)(lv + 1) * c.N, (long)w, Bn, lv, dg.p);
+            for (int s = 0; s < n_steps; s++) {
+                rotate_digits(&c, A.p, Bn, lv, dg.p, galois_of_step(&c, steps[s]), O.p);
+                for (int t = 0; t < Bn; t++) {
+                    const he_ct *in = cts[kv.second[t]];
+                    he_ct *o = new_ct(&c, lv, in->scale, in->period);
+                    res[(size_t)kv.second[t] * n_steps + s] = o;
+                    cudaMemcpyAsync(o->d, O.p + t * w, w * 8, cudaMemcpyDeviceToDevice, c.stream);
+                }
+            }
+        }
+        HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+        if (int rc = cuda_status(&c)) throw HeError(rc, last_error());
+    } catch (...) {
+        for (he_ct *o : res) free_ct(o);
+        throw;
+    }
+    for (size_t i = 0; i < res.size(); i++) outs[i] = res[i];
+    return HE_OK;
     GUARD_END
 }
 

@@ -414,8 +414,7 @@ enum { TAG_SK = 1, TAG_PK_A = 2, TAG_PK_E = 3, TAG_ENC_V = 4, TAG_ENC_E0 = 5, TA
 
 static RowMap map_all(const Ctx *c) {
     RowMap m;
-    m.n = c->nprimes;
-    for (int k = 0; k < c->nprimes; k++) m.p[k] = (unsigned char)k;
+    m.n = c->nprimes, m.lq = c->nprimes - 1;   // every prime, in global order
     return m;
 }
 
@@ -470,9 +469,7 @@ static u64 *gen_swk(Ctx *c, const u64 *sprime, uint32_t obj) {
         launch_mulM(c, k0, k1, c->d_skM, np, all, c->stream);  // a s
         launch_sub(c, k0, e.p, k0, np, all, c->stream);          // e - a s
         for (int i = d * c->alpha; i < std::min((d + 1) * c->alpha, c->L + 1); i++) {
-            RowMap one;
-            one.n = 1;
-            one.p[0] = (unsigned char)i;
+            RowMap one = RowMap::single(i);
             // t = (P mod q_i) s'_i ; k0_i += t
             launch_mulconst_rows(c, t.p, sprime + (size_t)i * N, c->d_Pmod + i, 1, 1, one, c->stream);
             launch_add(c, k0 + (size_t)i * N, k0 + (size_t)i * N, t.p, 1, one, c->stream);

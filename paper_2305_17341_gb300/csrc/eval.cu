@@ -89,9 +89,7 @@ void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out) {
     if (level < 1) throw HeError(HE_ERR_LEVEL, "rescale at level 0");
     Buf last(&c->pool, (size_t)2 * B * N), t(&c->pool, (size_t)2 * B * level * N);
     launch_copy_rows(last.p, N, in + (long)level * N, (long)(level + 1) * N, 2 * B, N, c->stream);
-    RowMap one;
-    one.n = 1;
-    one.p[0] = (unsigned char)level;
+    RowMap one = RowMap::single(level);
     ntt_inv(c, last.p, 2L * B, one, c->stream);
     launch_rescale_prep(c, last.p, t.p, 2 * B, level, c->stream);
     ntt_fwd(c, t.p, 2L * B * level, c->map_q(level - 1), c->stream);

@@ -15,12 +15,25 @@
 namespace he {
 
 // Row -> global prime index map (row r uses prime p[r % n]); passed by value.
+// Prime of each row of a multi-row launch (global prime index: q_0..q_L,
+// then p_0..p_{alpha-1}).  Row k, after a cyclic shift, is k' = (k + shift)
+// mod n; rows k' <= lq are q_{base_q + k'}, the others prime
+// base_p + (k' - lq - 1).  Plain integers, so a kernel evaluates it in
+// registers (no per-thread copy of a parameter array).
 struct RowMap {
-    int n;
-    unsigned char p[60];
+    int n = 1, shift = 0, lq = 0, base_q = 0, base_p = 0;
+    __host__ __device__ __forceinline__ int at(long k) const {
+        int kk = (int)((k + shift) % n);
+        return kk <= lq ? base_q + kk : base_p + (kk - lq - 1);
+    }
     __host__ __device__ RowMap shifted(long r0) const {
         RowMap m = *this;
-        for (int k = 0; k < n; k++) m.p[k] = p[(k + r0) % n];
+        m.shift = (int)((shift + r0) % n);
+        return m;
+    }
+    static RowMap single(int prime) {
+        RowMap m;
+        m.base_q = prime;
         return m;
     }
 };
@@ -148,6 +161,10 @@ struct Ctx {
         long long count = 0;
     };
     bool trace = false;
+    // launch-geometry autotuner: per (kernel, shape) the fastest variant,
+    // timed on first use (variants compute identical words)
+    bool autotune = true;
+    std::map<std::pair<int, int>, int> tune_multsum;   // (level, items) -> variant
     TraceClass tr[4];                 // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv
     std::vector<cudaEvent_t> ev_free;
     cudaEvent_t ev_get();
@@ -160,19 +177,18 @@ struct Ctx {
     int ndig(int level) const { return (level + 1 + alpha - 1) / alpha; }
     size_t key_words() const { return (size_t)dnum * 2 * nprimes * N; }
     RowMap map_q(int level) const {
-        RowMap m; m.n = level + 1;
-        for (int i = 0; i <= level; i++) m.p[i] = (unsigned char)i;
+        RowMap m;
+        m.n = level + 1, m.lq = level;
         return m;
     }
     RowMap map_qp(int level) const {
-        RowMap m; m.n = level + 1 + alpha;
-        for (int i = 0; i <= level; i++) m.p[i] = (unsigned char)i;
-        for (int j = 0; j < alpha; j++) m.p[level + 1 + j] = (unsigned char)(L + 1 + j);
+        RowMap m;
+        m.n = level + 1 + alpha, m.lq = level, m.base_p = L + 1;
         return m;
     }
     RowMap map_p() const {
-        RowMap m; m.n = alpha;
-        for (int j = 0; j < alpha; j++) m.p[j] = (unsigned char)(L + 1 + j);
+        RowMap m;
+        m.n = alpha, m.lq = -1, m.base_p = L + 1;
         return m;
     }
     const LevelConsts &lc(int level);

@@ -5,6 +5,8 @@
 // rows q_0..q_l then p_0..p_{alpha-1}; a batch of B items is contiguous.
 #include <cmath>
 
+#include <set>
+
 #include "he_internal.h"
 
 namespace he {
@@ -34,7 +36,7 @@ __global__ void k_sample_uniform(u64 *out, long rows, int N, RowMap rm, const Mo
     if (idx >= rows * N) return;
     long row = idx / N;
     int i = (int)(idx - row * N);
-    int pidx = rm.p[row % rm.n];
+    int pidx = rm.at(row);
     u32 c[4] = {(u32)i, (u32)pidx, obj, tag};
     philox4x32_10(c, k0, k1);
     u64 lo = (u64)c[0] | ((u64)c[1] << 32);
@@ -71,7 +73,7 @@ __global__ void k_small_to_rns(const i64 *x, u64 *out, long rows, int N, RowMap 
     if (idx >= rows * N) return;
     long row = idx / N;
     int i = (int)(idx - row * N);
-    out[idx] = from_signed(x[i], mods[rm.p[row % rm.n]].q);
+    out[idx] = from_signed(x[i], mods[rm.at(row)].q);
 }
 
 void launch_sample_uniform(Ctx *c, u64 *out, int rows, const RowMap &rm, const int *, uint32_t obj,
@@ -196,7 +198,7 @@ void launch_decode(Ctx *c, const double *coef, double scale, double *zre, double
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;           \
     if (idx >= rows * (long)N) return;                                \
     long row = idx / N;                                               \
-    const ModQ &m = mods[rm.p[row % rm.n]];                           \
+    const ModQ &m = mods[rm.at(row)];                           \
     (void)m;
 
 __global__ void k_add(u64 *o, const u64 *a, const u64 *b, long rows, int N, RowMap rm, const ModQ *mods) {
@@ -305,7 +307,7 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
     int it = (int)(idx / per);
     long off = idx - (long)it * per;
     int limb = (int)(off / N);
-    const ModQ &m = mods[rm.p[limb]];
+    const ModQ &m = mods[rm.at(limb)];
     const u64 *pa = a + it * as, *pb = b + it * bs;
     u64 a0 = pa[off], a1 = pa[per + off], b0 = pb[off], b1 = pb[per + off];
     U128 acc = {0, 0};
@@ -351,21 +353,29 @@ __global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int a
     u64 *ob = out + ((long)b * ndig + d) * rows * N;
     int i0 = d * alpha;
     int ns = min(alpha, level + 1 - i0);
-    u64 y[4];
-    for (int s = 0; s < ns; s++) {
-        ShoupPair w = up_inv[d * alpha + s];
-        y[s] = shoup(cb[(long)(i0 + s) * N + x], w.w, w.wp, mods[i0 + s].q);
+    // alpha <= 4; fixed trip counts keep y in registers
+    u64 y[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        if (s < ns) {
+            ShoupPair w = up_inv[d * alpha + s];
+            y[s] = shoup(cb[(long)(i0 + s) * N + x], w.w, w.wp, mods[i0 + s].q);
+        }
     }
     for (int r = 0; r < rows; r++) {
         u64 v;
         if (r >= i0 && r < i0 + ns) {
             v = own_ntt ? own_ntt[(long)b * own_s + (long)r * N + x] : cb[(long)r * N + x];
         } else {
-            const ModQ &m = mods[qp.p[r]];
+            // qp is unshifted: rows <= level are q_r, the rest p_{r-level-1}
+            const ModQ &m = mods[r <= qp.lq ? r : qp.base_p + (r - qp.lq - 1)];
             v = 0;
-            for (int s = 0; s < ns; s++) {
-                ShoupPair w = up_mod[((long)d * alpha + s) * rows + r];
-                v = addmod(v, shoup(y[s], w.w, w.wp, m.q), m.q);
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                if (s < ns) {
+                    ShoupPair w = up_mod[((long)d * alpha + s) * rows + r];
+                    v = addmod(v, shoup(y[s], w.w, w.wp, m.q), m.q);
+                }
             }
         }
         ob[(long)r * N + x] = v;
@@ -402,7 +412,7 @@ __global__ void k_scalar_mul_rows(u64 *o, const u64 *a, long rows, int rpi, int 
     if (idx >= rows * (long)N) return;
     long row = idx / N;
     int r = (int)(row % rpi);
-    o[idx] = shoup(a[idx], s.w[r].w, s.w[r].wp, mods[rm.p[row % rm.n]].q);
+    o[idx] = shoup(a[idx], s.w[r].w, s.w[r].wp, mods[rm.at(row)].q);
 }
 void launch_scalar_mul_rows(Ctx *c, u64 *out, const u64 *a, long rows, int rpi, const ShoupPair *vals,
                             const RowMap &rm, cudaStream_t st) {
@@ -416,7 +426,7 @@ __global__ void k_scalar_add_rows(u64 *o, long rows, int N, ScalarList s, RowMap
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * (long)N) return;
     long row = idx / N;
-    u64 q = mods[rm.p[row % rm.n]].q;
+    u64 q = mods[rm.at(row)].q;
     o[idx] = addmod(o[idx], s.w[row].w, q);
 }
 void launch_scalar_add_rows(Ctx *c, u64 *data, long rows, const u64 *vals, const RowMap &rm, cudaStream_t st) {
@@ -454,21 +464,28 @@ __global__ void k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level
     if (idx >= (long)items * N) return;
     int x = (int)(idx % N);
     int it = (int)(idx / N);
-    u64 y[4];
+    // alpha <= 4; fixed trip counts keep y in registers
+    u64 y[4] = {0, 0, 0, 0};
     double ef = 0.0;
-    for (int j = 0; j < alpha; j++) {
-        ShoupPair w = pinv[j];
-        u64 p = mods[L + 1 + j].q;
-        u64 v = addmod(pcoef[((long)it * alpha + j) * N + x], hp[j], p);
-        y[j] = shoup(v, w.w, w.wp, p);
-        ef = __dadd_rn(ef, __ddiv_rn(__ull2double_rn(y[j]), __ull2double_rn(p)));
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (j < alpha) {
+            ShoupPair w = pinv[j];
+            u64 p = mods[L + 1 + j].q;
+            u64 v = addmod(pcoef[((long)it * alpha + j) * N + x], hp[j], p);
+            y[j] = shoup(v, w.w, w.wp, p);
+            ef = __dadd_rn(ef, __ddiv_rn(__ull2double_rn(y[j]), __ull2double_rn(p)));
+        }
     }
     u64 e = (u64)floor(ef);
     for (int r = 0; r <= level; r++) {
         u64 q = mods[r].q, v = 0;
-        for (int j = 0; j < alpha; j++) {
-            ShoupPair w = pmod[j * (L + 1) + r];
-            v = addmod(v, shoup(y[j], w.w, w.wp, q), q);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (j < alpha) {
+                ShoupPair w = pmod[j * (L + 1) + r];
+                v = addmod(v, shoup(y[j], w.w, w.wp, q), q);
+            }
         }
         ShoupPair wP = Pmod[r];
         v = submod(v, shoup(e, wP.w, wP.wp, q), q);
@@ -528,7 +545,7 @@ __global__ void __launch_bounds__(256) k_multsum(u64 *out, const u64 *digits, co
     const int r = (int)(idx / N);
     const int x = (int)(idx - (long)r * N);
     const int kr = r <= level ? r : L + 1 + (r - level - 1);
-    const ModQ m = mods[qp.p[r]];
+    const ModQ m = mods[qp.at(r)];
     const int src = (g == 1u) ? x : auto_index(x, g, logN);
     const long dstride = (long)rows * N;                  // digit stride
     const long istride = (long)ndig * rows * N;           // item stride of the digits
@@ -569,6 +586,7 @@ __global__ void __launch_bounds__(256) k_multsum(u64 *out, const u64 *digits, co
 // one row for BI items (one warp group per item).  The BI groups read the same
 // key words, so each key word comes from HBM once per CTA and from L1
 // afterwards; per-thread state is two 128-bit accumulators.
+template <bool STREAM>
 __global__ void __launch_bounds__(256) k_multsum_items(u64 *out, const u64 *digits, const u64 *key, u32 g, int B,
                                                        int BI, int level, int alpha, int L, int ndig, int nprimes,
                                                        int logN, RowMap qp, const ModQ *mods, const u64 *c0,
@@ -582,17 +600,35 @@ __global__ void __launch_bounds__(256) k_multsum_items(u64 *out, const u64 *digi
     if (b >= B || x >= N) return;
     const int rows = level + 1 + alpha;
     const int kr = r <= level ? r : L + 1 + (r - level - 1);
-    const ModQ m = mods[qp.p[r]];
+    const ModQ m = mods[qp.at(r)];
     const int src = (g == 1u) ? x : auto_index(x, g, logN);
     const long dstride = (long)rows * N;
     const u64 *dp = digits + (long)b * ndig * dstride + (long)r * N + src;
     const u64 *kp = key + (long)kr * N + x;
     const long kd = 2L * nprimes * N, kk = (long)nprimes * N;
     U128 a0 = {0, 0}, a1 = {0, 0};
-    for (int d = 0; d < ndig; d++) {
-        u64 v = dp[d * dstride];
-        mac128(a0, v, kp[d * kd]);
-        mac128(a1, v, kp[d * kd + kk]);
+    // four digits per round: all twelve loads are issued before the products
+    // (more bytes in flight per thread); key words are shared by the CTA's
+    // items (cached); STREAM marks the digit loads evict-first (read once)
+    int d = 0;
+    for (; d + 4 <= ndig; d += 4) {
+        u64 v[4], k0[4], k1[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            v[u] = STREAM ? __ldcs(dp + (long)(d + u) * dstride) : __ldg(dp + (long)(d + u) * dstride);
+            k0[u] = __ldg(kp + (long)(d + u) * kd);
+            k1[u] = __ldg(kp + (long)(d + u) * kd + kk);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            mac128(a0, v[u], k0[u]);
+            mac128(a1, v[u], k1[u]);
+        }
+    }
+    for (; d < ndig; d++) {
+        u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
+        mac128(a0, v, __ldg(kp + (long)d * kd));
+        mac128(a1, v, __ldg(kp + (long)d * kd + kk));
     }
     u64 o0 = redc(a0.lo, a0.hi, m), o1 = redc(a1.lo, a1.hi, m);
     if (c0 && r <= level) {
@@ -604,18 +640,72 @@ __global__ void __launch_bounds__(256) k_multsum_items(u64 *out, const u64 *digi
     ob[(long)(rows + r) * N + x] = o1;
 }
 
+// MultSum launch variants: items per CTA (BI) and streaming digit loads.
+static void multsum_variant(int v, int B, int &BI, bool &stream) {
+    static const int bis[4] = {8, 4, 2, 1};
+    BI = bis[(v >> 1) & 3];
+    while (BI > 1 && BI > B) BI >>= 1;
+    stream = v & 1;
+}
+
 void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_t g, int B, int level,
                     const u64 *c0_for_P, long c0s, cudaStream_t st) {
     int rows = level + 1 + c->alpha;
-    c->n_launch++;
+    auto launch = [&](int v) {
+        int BI;
+        bool stream;
+        multsum_variant(v, B, BI, stream);
+        int XW = 256 / BI;
+        dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
+        if (stream)
+            k_multsum_items<true><<<grid, 256, 0, st>>>(out, digits, key, g, B, BI, level, c->alpha, c->L,
+                                                        c->ndig(level), c->nprimes, c->logN, c->map_qp(level),
+                                                        c->d_mod, c0_for_P, c0s, c->d_Pmod);
+        else
+            k_multsum_items<false><<<grid, 256, 0, st>>>(out, digits, key, g, B, BI, level, c->alpha, c->L,
+                                                         c->ndig(level), c->nprimes, c->logN, c->map_qp(level),
+                                                         c->d_mod, c0_for_P, c0s, c->d_Pmod);
+        c->n_launch++;
+    };
+    int v = 0;  // 8 items per CTA (capped by B), cached digit loads
+    if (c->autotune) {
+        auto key2 = std::make_pair(level, B);
+        auto it = c->tune_multsum.find(key2);
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        if (it != c->tune_multsum.end()) {
+            v = it->second;
+        } else if (cap == cudaStreamCaptureStatusNone) {
+            // time each distinct variant twice on this very launch (the
+            // output does not depend on the variant) and keep the fastest
+            cudaEvent_t a = c->ev_get(), b = c->ev_get();
+            float best = 1e30f;
+            std::set<std::pair<int, bool>> seen;
+            for (int cand = 0; cand < 8; cand++) {
+                int BI;
+                bool stream;
+                multsum_variant(cand, B, BI, stream);
+                if (!seen.insert({BI, stream}).second) continue;
+                float t = 1e30f;
+                for (int rep = 0; rep < 2; rep++) {
+                    cudaEventRecord(a, st);
+                    launch(cand);
+                    cudaEventRecord(b, st);
+                    cudaEventSynchronize(b);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, a, b);
+                    t = std::min(t, ms);
+                }
+                if (t < best) best = t, v = cand;
+            }
+            c->ev_free.push_back(a);
+            c->ev_free.push_back(b);
+            c->tune_multsum[key2] = v;
+        }
+    }
     cudaEvent_t e0;
     c->trace_begin(0, e0);
-    int BI = B >= 8 ? 8 : (B >= 4 ? 4 : (B >= 2 ? 2 : 1));
-    int XW = 256 / BI;
-    dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
-    k_multsum_items<<<grid, 256, 0, st>>>(out, digits, key, g, B, BI, level, c->alpha, c->L, c->ndig(level),
-                                          c->nprimes, c->logN, c->map_qp(level), c->d_mod, c0_for_P, c0s,
-                                          c->d_Pmod);
+    launch(v);
     // algorithmic bytes: the key (2 polys x ndig digits x rows limbs) read once,
     // every item's digits read once, both output polys written, c0 read if fused
     double nd = c->ndig(level), W = (double)c->N * 8.0;
@@ -634,7 +724,7 @@ __global__ void k_pmul_acc(u64 *out, PtrList pts, PtrList R, int nterms, int B, 
     long per = (long)rows * N;
     if (idx >= per) return;
     int r = (int)(idx / N);
-    const ModQ &m = mods[qp.p[r]];
+    const ModQ &m = mods[qp.at(r)];
     for (int b = 0; b < B; b++) {
         U128 a0 = {0, 0}, a1 = {0, 0};
         for (int t = 0; t < nterms; t++) {

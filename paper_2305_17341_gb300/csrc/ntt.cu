@@ -44,7 +44,7 @@ __global__ void k_ntt_fwd_p1(u64 *data, RowMap rm, const ModQ *mods, const u64 *
     extern __shared__ u64 sm[];
     const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
     const long row = blockIdx.y;
-    const int pidx = rm.p[row % rm.n];
+    const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
     u64 *base = data + row * (long)N + (long)blockIdx.x * C;
     const u64 *w = tw + (long)pidx * N, *wp = twp + (long)pidx * N;
@@ -76,7 +76,7 @@ __global__ void k_ntt_fwd_p2(u64 *data, RowMap rm, const ModQ *mods, const u64 *
     extern __shared__ u64 sm[];
     const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
     const long row = blockIdx.y;
-    const int pidx = rm.p[row % rm.n];
+    const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
     const int hi0 = blockIdx.x * R;
     u64 *base = data + row * (long)N + (long)hi0 * N2;
@@ -107,7 +107,7 @@ __global__ void k_ntt_inv_p2(u64 *data, RowMap rm, const ModQ *mods, const u64 *
     extern __shared__ u64 sm[];
     const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
     const long row = blockIdx.y;
-    const int pidx = rm.p[row % rm.n];
+    const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
     const int hi0 = blockIdx.x * R;
     u64 *base = data + row * (long)N + (long)hi0 * N2;
@@ -139,7 +139,7 @@ __global__ void k_ntt_inv_p1(u64 *data, RowMap rm, const ModQ *mods, const u64 *
     extern __shared__ u64 sm[];
     const int N = 1 << logN, N1 = 1 << logN1, N2 = N >> logN1;
     const long row = blockIdx.y;
-    const int pidx = rm.p[row % rm.n];
+    const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
     u64 *base = data + row * (long)N + (long)blockIdx.x * C;
     const u64 *w = tw + (long)pidx * N, *wp = twp + (long)pidx * N;
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, cons
     const int N = 1 << logN;
     const long row = blockIdx.y;
     if (skip.skip(row)) return;  // uniform over the CTA
-    const int pidx = rm.p[row % rm.n];
+    const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
     const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
     int t, w;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, cons
     __shared__ u64 sm[G_::SM];
     const int N = 1 << logN;
     const long row = blockIdx.y;
-    const int pidx = rm.p[row % rm.n];
+    const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
     const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
     int t, w;

@@ -82,9 +82,7 @@ public:
         const int N = c->N, L = c->L;
         Buf m(&c->pool, N), mi(&c->pool, N), rns(&c->pool, (size_t)(L + 1) * N);
         launch_dec_q0(c, a->d, a->d + (size_t)(a->level + 1) * N, m.p, c->stream);
-        RowMap one;
-        one.n = 1;
-        one.p[0] = 0;
+        RowMap one = RowMap::single(0);
         ntt_inv(c, m.p, 1, one, c->stream);
         launch_centre_i64_q0(c, m.p, (i64 *)mi.p, c->stream);
         launch_small_to_rns(c, (const i64 *)mi.p, rns.p, L + 1, c->map_q(L), c->stream);

@@ -315,3 +315,53 @@ def test_hmatmul_batch_relin_once_equals_single(c1):
     for h in singles + batch + [x for p in pairs for x in p[4:6]]:
         lib.he_ct_free(h)
 
+
+
+def test_rotate_hoisted_batch_bit_exact(c1):
+    """he_rotate_hoisted: three ciphertexts (two levels) x three steps, one
+    Decompose per ciphertext, each output equal to the oracle's hoisted
+    rotation and to he_rotate."""
+    lib, ctx, P, he = c1
+    steps = [1, 7, P.S - 3]
+    lib.he_keygen(ctx, steps, want_relin=False)
+    for s in steps:
+        he.gen_rotation_key(s)
+    rng = np.random.default_rng(99)
+    os_, gs = [], []
+    for i, level in enumerate((P.L, 2, P.L)):
+        o = he.drop(he.encrypt_slots(rng.uniform(-1, 1, P.S), P.L, obj=400 + i), level)
+        os_.append(o)
+        gs.append(lib.he_ct_import(ctx, residues(he, o), level, o.scale, P.S))
+    outs = lib.he_rotate_hoisted(ctx, gs, steps)
+    for i, o in enumerate(os_):
+        dg = he.modup(o.c1, o.level)
+        for j, s in enumerate(steps):
+            want = he.rotate_hoisted(o, dg, s)
+            assert np.array_equal(lib.he_ct_export(ctx, outs[i][j]), residues(he, want)), (i, s)
+            single = lib.he_rotate(ctx, gs[i], s)
+            assert np.array_equal(lib.he_ct_export(ctx, single), lib.he_ct_export(ctx, outs[i][j]))
+            lib.he_ct_free(single)
+    for h in gs + [x for row in outs for x in row]:
+        lib.he_ct_free(h)
+
+
+def test_autotuned_launches_compute_the_same_words(c1):
+    """The MultSum variants the autotuner chooses among (items per CTA, load
+    caching) give identical residues: a product with the tuner on equals the
+    same product with the fixed default launch."""
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    from oracle.hmm import matmul_rot_steps
+    lib.he_keygen(ctx, matmul_rot_steps(n, n1, n1, P.S), want_relin=True)
+    pairs = [_matrix_pair(P, he, lib, ctx, n, 120 + i) for i in range(3)]
+    jobs = [(p[4], p[5], n, n1, n1) for p in pairs]
+    tuned = lib.he_hmatmul_batch(jobs)
+    lib.he_ctx_set_autotune(ctx, False)
+    try:
+        fixed = lib.he_hmatmul_batch(jobs)
+    finally:
+        lib.he_ctx_set_autotune(ctx, True)
+    for a, b in zip(tuned, fixed):
+        assert np.array_equal(lib.he_ct_export(ctx, a), lib.he_ct_export(ctx, b))
+    for h in tuned + fixed + [x for p in pairs for x in p[4:6]]:
+        lib.he_ct_free(h)
