@@ -102,12 +102,19 @@ int he_ctx_destroy(he_ctx *ctx);
  * own stream).  The caller keeps ownership of a stream it passes. */
 int he_ctx_set_stream(he_ctx *ctx, void *stream);
 
-/* Launch-geometry autotuner (on by default): the first MultSum launch of
- * each (level, batch size) times its launch variants -- items per CTA, cached
- * or streaming digit loads -- on that very launch and keeps the fastest for
- * the context.  Variants compute identical words; only speed differs.
- * on = 0 uses the fixed default (8 items per CTA, cached loads). */
+/* Launch-geometry autotuner (on by default): the first MultSum of each
+ * (level, batch size, number of hoisted rotations) times its launch plans --
+ * rotations per launch (1, 2, 4 or 8 sharing one read of the digits), items
+ * per CTA, cached or streaming digit loads -- on those very launches and keeps
+ * the fastest for the context.  Plans compute identical words; only speed
+ * differs.  on = 0 uses the fixed default (8 rotations per launch, 8 items per
+ * CTA, cached loads). */
 int he_ctx_set_autotune(he_ctx *ctx, int on);
+
+/* The autotuner's record: one line per timed launch plan (kernel, shape,
+ * plan, best of two device times in ms).  Copies at most cap - 1 bytes and a
+ * terminating NUL into out; *len (may be NULL) receives the full length. */
+int he_autotune_log(const he_ctx *ctx, char *out, int cap, int *len);
 
 /* Copies the primes: q_out[0..L] and p_out[0..alpha-1] (host arrays). */
 int he_ctx_primes(const he_ctx *ctx, uint64_t *q_out, uint64_t *p_out);

@@ -84,6 +84,7 @@ SIGNATURES = {
     "he_ctx_set_stream": [vp, vp],
     "he_ctx_primes": [vp, u64p, u64p],
     "he_ctx_set_autotune": [vp, ip],
+    "he_autotune_log": [vp, ctypes.c_char_p, ip, P(ip)],
     "he_ctx_info": [vp, P(ip), P(ip), P(ip), P(ip), P(ip)],
     "he_sk_export": [vp, P(ctypes.c_int64)],
     "he_keygen": [vp, i32p, ip, ip],
@@ -197,6 +198,14 @@ def he_ctx_set_stream(ctx, stream_ptr):
 
 def he_ctx_set_autotune(ctx, on=True):
     check(lib().he_ctx_set_autotune(ctx, 1 if on else 0))
+
+
+def he_autotune_log(ctx):
+    n = ctypes.c_int()
+    check(lib().he_autotune_log(ctx, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    check(lib().he_autotune_log(ctx, buf, n.value + 1, None))
+    return buf.value.decode()
 
 
 def he_ctx_info(ctx):

@@ -236,6 +236,18 @@ int he_ctx_set_autotune(he_ctx *ctx, int on) {
     return HE_OK;
 }
 
+int he_autotune_log(const he_ctx *ctx, char *out, int cap, int *len) {
+    if (!ctx || (cap > 0 && !out)) return fail(HE_ERR_ARG, "bad arguments");
+    const std::string &s = ctx->c.tune_log;
+    if (len) *len = (int)s.size();
+    if (cap > 0) {
+        size_t n = std::min(s.size(), (size_t)cap - 1);
+        std::memcpy(out, s.data(), n);
+        out[n] = 0;
+    }
+    return HE_OK;
+}
+
 int he_ctx_primes(const he_ctx *ctx, uint64_t *q_out, uint64_t *p_out) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
     const Ctx &c = ctx->c;
@@ -451,20 +463,30 @@ int he_rotate_hoisted(he_ctx *ctx, const he_ct *const *cts, int n_cts, const int
         for (auto &kv : by_level) {
             const int lv = kv.first, Bn = (int)kv.second.size();
             const size_t w = ct_words(&c, lv);
-            Buf A(&c.pool, Bn * w), O(&c.pool, Bn * w);
+            Buf A(&c.pool, Bn * w);
             Buf dg(&c.pool, (size_t)Bn * c.ndig(lv) * c.qp_rows(lv) * c.N);
             for (int t = 0; t < Bn; t++)
                 cudaMemcpyAsync(A.p + t * w, cts[kv.second[t]]->d, w * 8, cudaMemcpyDeviceToDevice, c.stream);
             modup(&c, A.p + (long)(lv + 1) * c.N, (long)w, Bn, lv, dg.p);
+            // all steps from one MultSum pass over the digits, one ModDown
+            const size_t qp = (size_t)2 * c.qp_rows(lv) * c.N;
+            Buf U(&c.pool, (size_t)n_steps * Bn * qp), M(&c.pool, (size_t)n_steps * Bn * w);
+            std::vector<uint32_t> gs;
+            std::vector<u64 *> uo;
             for (int s = 0; s < n_steps; s++) {
-                rotate_digits(&c, A.p, Bn, lv, dg.p, galois_of_step(&c, steps[s]), O.p);
+                gs.push_back(galois_of_step(&c, steps[s]));
+                uo.push_back(U.p + (size_t)s * Bn * qp);
+            }
+            rot_qp_multi(&c, A.p, Bn, lv, dg.p, gs.data(), n_steps, uo.data());
+            moddown(&c, U.p, 2 * Bn * n_steps, lv, M.p, (long)(lv + 1) * c.N);
+            c.n_md += (long long)Bn * n_steps;
+            for (int s = 0; s < n_steps; s++)
                 for (int t = 0; t < Bn; t++) {
                     const he_ct *in = cts[kv.second[t]];
                     he_ct *o = new_ct(&c, lv, in->scale, in->period);
                     res[(size_t)kv.second[t] * n_steps + s] = o;
-                    cudaMemcpyAsync(o->d, O.p + t * w, w * 8, cudaMemcpyDeviceToDevice, c.stream);
+                    cudaMemcpyAsync(o->d, M.p + ((size_t)s * Bn + t) * w, w * 8, cudaMemcpyDeviceToDevice, c.stream);
                 }
-            }
         }
         HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
         if (int rc = cuda_status(&c)) throw HeError(rc, last_error());

@@ -480,11 +480,18 @@ static u64 *gen_swk(Ctx *c, const u64 *sprime, uint32_t obj) {
     return key;
 }
 
+// The key of kappa_g, stored in the permuted layout MultSum reads (every row
+// r of the key at index pi_g(x) holds the switching key's word x).
 u64 *gen_rotation_key(Ctx *c, uint32_t g) {
     RowMap all = map_all(c);
     Buf sp(&c->pool, (size_t)c->nprimes * c->N);
     launch_automorph(c, sp.p, c->d_sk, c->nprimes, all, g, c->stream);   // kappa_g(s)
-    return gen_swk(c, sp.p, g);
+    u64 *key = gen_swk(c, sp.p, g);
+    const long rows = (long)c->dnum * 2 * c->nprimes;
+    Buf tmp(&c->pool, (size_t)rows * c->N);
+    cudaMemcpyAsync(tmp.p, key, (size_t)rows * c->N * 8, cudaMemcpyDeviceToDevice, c->stream);
+    launch_permute_key(c, key, tmp.p, rows, g, c->stream);
+    return key;
 }
 
 u64 *gen_relin_key(Ctx *c) {

@@ -67,6 +67,17 @@ void rot_qp(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t
     c->n_ms += B;
 }
 
+// G hoisted rotations of the same Decompose output, kept in Q_l P; the
+// digits are read once per launch for up to kMultSumMaxKeys keys.
+void rot_qp_multi(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, const uint32_t *gs, int G,
+                  u64 *const *outs) {
+    if (G <= 0) return;
+    std::vector<const u64 *> keys(G);
+    for (int k = 0; k < G; k++) keys[k] = need_key(c, gs[k]);
+    launch_multsum_multi(c, outs, digits, keys.data(), gs, G, B, level, ct, 2L * (level + 1) * c->N, c->stream);
+    c->n_ms += (long long)B * G;
+}
+
 // Full rotation from precomputed digits: ModDown(rot_qp) = kappa(c0) + ModDown(IP0), ModDown(IP1).
 void rotate_digits(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out) {
     const int rows = c->qp_rows(level);
@@ -201,10 +212,14 @@ void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, 
     std::vector<Buf> R;
     R.emplace_back(&c->pool, B * qpct);
     launch_lift_P(c, R[0].p, in, 2 * B, level, (long)nq * N, (long)rows * N, c->stream);
+    std::vector<uint32_t> gs;
+    std::vector<u64 *> outs;
     for (int j = 1; j < n1; j++) {
         R.emplace_back(&c->pool, B * qpct);
-        rot_qp(c, in, B, level, dg.p, galois_of_step(c, mod_pos(a * j, n2)), R[j].p);
+        gs.push_back(galois_of_step(c, mod_pos(a * j, n2)));
+        outs.push_back(R[j].p);
     }
+    rot_qp_multi(c, in, B, level, dg.p, gs.data(), (int)gs.size(), outs.data());
     Buf acc(&c->pool, B * qpct), S(&c->pool, B * qpct), ctmp(&c->pool, (size_t)B * 2 * nq * N),
         dg2(&c->pool, (size_t)B * c->ndig(level) * rows * N), T(&c->pool, B * qpct);
     bool have = false;
@@ -278,9 +293,42 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
     Buf acc(&c->pool, Bn * ct2), Ak(&c->pool, Bn * ct2), Bk(&c->pool, Bn * ct2), prod(&c->pool, Bn * ct2);
     // relin_once: the summed d2 of the n tensors (d0, d1 are summed in acc)
     Buf acc2(&c->pool, relin_once ? (size_t)Bn * (l2 + 1) * N : 1);
-    Buf R1(&c->pool, Bn * qp1), R2(&c->pool, Bn * qp1), S(&c->pool, Bn * qp1), Akp(&c->pool, Bn * ct1),
-        Bkf(&c->pool, Bn * ct1);
+    Buf R1(&c->pool, Bn * qp1), R2(&c->pool, Bn * qp1), S(&c->pool, Bn * qp1), Akp(&c->pool, Bn * ct1);
     RowMap q2 = c->map_q(l2);
+
+    // The babies of a source are all its hoisted rotations at once (one
+    // read of the source's digits per kMultSumMaxKeys keys):
+    //   C^k: rotations by b of A_g and A'_g kept in Q_l P, b = 1..n1z-1;
+    //   R^k: rotations by n b of B_g (ModDown'd), b = 1..n1t-1.
+    const int nbA = n1z - 1, nbB = n1t - 1;
+    Buf RA(&c->pool, (size_t)std::max(1, nbA) * Bn * qp1), RAp(&c->pool, (size_t)std::max(1, nbA) * Bn * qp1);
+    Buf UB(&c->pool, (size_t)std::max(1, nbB) * Bn * qp1), BB(&c->pool, (size_t)std::max(1, nbB) * Bn * ct1);
+    auto babies_A = [&]() {
+        std::vector<uint32_t> gs;
+        std::vector<u64 *> o1, o2;
+        for (int b = 1; b <= nbA; b++) {
+            gs.push_back(galois_of_step(c, b % n2m));
+            o1.push_back(RA.p + (size_t)(b - 1) * Bn * qp1);
+            o2.push_back(RAp.p + (size_t)(b - 1) * Bn * qp1);
+        }
+        rot_qp_multi(c, Ag.p, Bn, l1, dA.p, gs.data(), nbA, o1.data());
+        rot_qp_multi(c, Apg.p, Bn, l1, dAp.p, gs.data(), nbA, o2.data());
+    };
+    auto babies_B = [&]() {
+        std::vector<uint32_t> gs;
+        std::vector<u64 *> o;
+        for (int b = 1; b <= nbB; b++) {
+            gs.push_back(galois_of_step(c, ((long)n * b) % n2m));
+            o.push_back(UB.p + (size_t)(b - 1) * Bn * qp1);
+        }
+        rot_qp_multi(c, Bg.p, Bn, l1, dB.p, gs.data(), nbB, o.data());
+        if (nbB > 0) {
+            moddown(c, UB.p, 2 * Bn * nbB, l1, BB.p, (long)(l1 + 1) * N);
+            c->n_md += (long long)Bn * nbB;
+        }
+    };
+    if (nbA > 0) babies_A();
+    if (nbB > 0) babies_B();
     for (int k = 0; k < n; k++) {
         // ---- A^(k) = C^k A^(0) at level l2
         int g = k / n1z, b = k % n1z;
@@ -292,6 +340,7 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
             std::swap(Apg, tmp);
             modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dAp.p);
             gA++;
+            if (nbA > 0) babies_A();
         }
         if (k == 0) {
             drop(c, A0.p, Bn, l1, l2, Ak.p);
@@ -299,13 +348,10 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
             if (b == 0) {
                 launch_lift_P(c, R1.p, Ag.p, 2 * Bn, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
                 launch_lift_P(c, R2.p, Apg.p, 2 * Bn, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
-            } else {
-                uint32_t gb = galois_of_step(c, b % n2m);
-                rot_qp(c, Ag.p, Bn, l1, dA.p, gb, R1.p);
-                rot_qp(c, Apg.p, Bn, l1, dAp.p, gb, R2.p);
             }
             const u64 *pts[2] = {get_pt(c, 3, n, 0, 0, 1.0, k, l1), get_pt(c, 4, n, 0, 0, 1.0, k, l1)};
-            const u64 *Rs[2] = {R1.p, R2.p};
+            const u64 *Rs[2] = {b == 0 ? R1.p : RA.p + (size_t)(b - 1) * Bn * qp1,
+                                b == 0 ? R2.p : RAp.p + (size_t)(b - 1) * Bn * qp1};
             launch_pmul_acc(c, S.p, pts, Rs, 2, Bn, l1, (long)qp1, c->stream);
             moddown(c, S.p, 2 * Bn, l1, Akp.p, (long)(l1 + 1) * N);
             c->n_md += Bn;
@@ -318,12 +364,12 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
             std::swap(Bg, tmp);
             modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dB.p);
             gB++;
+            if (nbB > 0) babies_B();
         }
         if (bb == 0) {
             drop(c, Bg.p, Bn, l1, l2, Bk.p);
         } else {
-            rotate_digits(c, Bg.p, Bn, l1, dB.p, galois_of_step(c, ((long)n * bb) % n2m), Bkf.p);
-            drop(c, Bkf.p, Bn, l1, l2, Bk.p);
+            drop(c, BB.p + (size_t)(bb - 1) * Bn * ct1, Bn, l1, l2, Bk.p);
         }
         // ---- product, relinearised, accumulated at level l2
         if (relin_once) {

@@ -23,6 +23,8 @@ double bfly_peak(int iters);
 void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits);
 void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s);
 void rot_qp(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out);
+void rot_qp_multi(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, const uint32_t *gs, int G,
+                  u64 *const *outs);
 void rotate_digits(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out);
 void rotate(Ctx *c, const u64 *ct, int B, int level, uint32_t g, u64 *out);
 void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out);

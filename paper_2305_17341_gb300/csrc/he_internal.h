@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/he.h"
@@ -164,7 +165,8 @@ struct Ctx {
     // launch-geometry autotuner: per (kernel, shape) the fastest variant,
     // timed on first use (variants compute identical words)
     bool autotune = true;
-    std::map<std::pair<int, int>, int> tune_multsum;   // (level, items) -> variant
+    std::map<std::tuple<int, int, int>, int> tune_multsum;
+    std::string tune_log;   // every timed plan: "multsum level B G chunk BI stream ms"   // (level, items, keys) -> (keys per launch << 8) | variant
     TraceClass tr[4];                 // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv
     std::vector<cudaEvent_t> ev_free;
     cudaEvent_t ev_get();
@@ -264,6 +266,12 @@ void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const
                           cudaStream_t st);
 void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_t g, int B, int level,
                     const u64 *c0_for_P, long c0_item_stride, cudaStream_t st);
+// Up to kMultSumMaxKeys rotations per launch share one read of the digits
+// (longer lists are split); keys must be in the permuted layout.
+constexpr int kMultSumMaxKeys = 8;
+void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64 *const *keys, const uint32_t *gs,
+                          int G, int B, int level, const u64 *c0_for_P, long c0s, cudaStream_t st);
+void launch_permute_key(Ctx *c, u64 *out, const u64 *in, long rows, uint32_t g, cudaStream_t st);
 void launch_pmul_acc(Ctx *c, u64 *out, const u64 *const *pts, const u64 *const *R, int nterms, int B,
                      int level, long R_item_stride, cudaStream_t st);
 void launch_lift_P(Ctx *c, u64 *out_qp, const u64 *in_q, int items, int level, long in_item_stride,

@@ -5,7 +5,9 @@
 // rows q_0..q_l then p_0..p_{alpha-1}; a batch of B items is contiguous.
 #include <cmath>
 
+#include <cstdio>
 #include <set>
+#include <stdexcept>
 
 #include "he_internal.h"
 
@@ -524,193 +526,212 @@ void launch_moddown_final(Ctx *c, u64 *out, const u64 *u, const u64 *conv, const
 }
 
 // ------------------------------------------------------------- MultSum
-// MultSum + Permute (Sec. 3.3): out[b][k][r][x] = sum_d D[b][d][r][pi_g(x)] * K[d][k][kr(r)][x]
-// with the key in Montgomery form (one REDC per output).  With c0 given,
-// P * kappa_g(c0) is added on the Q rows of poly 0 (the hoisted rotation kept
-// in Q_l P used by double hoisting).  digits: [B][ndig][rows][N];
-// key: [dnum][2][nprimes][N]; out: [B][2][rows][N].
-// Items are processed in chunks of BC held in registers, so each key word is
-// loaded once per chunk; the digit gather pi_g(x) stays inside one aligned
-// 32-word block for 32 consecutive x (the automorphism permutes the low bits
-// of the bit-reversed index only), so the loads remain coalesced.
-template <int BC>
-__global__ void __launch_bounds__(256) k_multsum(u64 *out, const u64 *digits, const u64 *key, u32 g, int B,
-                                                 int level, int alpha, int L, int ndig, int nprimes, int logN,
-                                                 RowMap qp, const ModQ *mods, const u64 *c0, long c0s,
-                                                 const ShoupPair *Pmod) {
-    const int N = 1 << logN;
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int rows = level + 1 + alpha;
-    if (idx >= (long)rows * N) return;
-    const int r = (int)(idx / N);
-    const int x = (int)(idx - (long)r * N);
-    const int kr = r <= level ? r : L + 1 + (r - level - 1);
-    const ModQ m = mods[qp.at(r)];
-    const int src = (g == 1u) ? x : auto_index(x, g, logN);
-    const long dstride = (long)rows * N;                  // digit stride
-    const long istride = (long)ndig * rows * N;           // item stride of the digits
-    const u64 *k0p = key + (long)kr * N + x;
-    const long kd = 2L * nprimes * N, kk = (long)nprimes * N;
-    for (int b0 = 0; b0 < B; b0 += BC) {
-        U128 a0[BC], a1[BC];
-#pragma unroll
-        for (int j = 0; j < BC; j++) a0[j] = a1[j] = U128{0, 0};
-        const u64 *dp = digits + (long)b0 * istride + (long)r * N + src;
-        for (int d = 0; d < ndig; d++) {
-            const u64 kv0 = __ldg(k0p + d * kd), kv1 = __ldg(k0p + d * kd + kk);
-#pragma unroll
-            for (int j = 0; j < BC; j++) {
-                if (b0 + j < B) {
-                    u64 v = dp[j * istride + d * dstride];
-                    mac128(a0[j], v, kv0);
-                    mac128(a1[j], v, kv1);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < BC; j++) {
-            int b = b0 + j;
-            if (b >= B) break;
-            u64 o0 = redc(a0[j].lo, a0[j].hi, m), o1 = redc(a1[j].lo, a1[j].hi, m);
-            if (c0 && r <= level) {
-                ShoupPair w = Pmod[r];
-                o0 = addmod(o0, shoup(c0[b * c0s + (long)r * N + src], w.w, w.wp, m.q), m.q);
-            }
-            u64 *ob = out + (long)b * 2 * rows * N;
-            ob[(long)r * N + x] = o0;
-            ob[(long)(rows + r) * N + x] = o1;
-        }
-    }
-}
-// Item-parallel MultSum: a CTA covers XW = 256/BI consecutive coefficients of
-// one row for BI items (one warp group per item).  The BI groups read the same
-// key words, so each key word comes from HBM once per CTA and from L1
-// afterwards; per-thread state is two 128-bit accumulators.
-template <bool STREAM>
-__global__ void __launch_bounds__(256) k_multsum_items(u64 *out, const u64 *digits, const u64 *key, u32 g, int B,
-                                                       int BI, int level, int alpha, int L, int ndig, int nprimes,
-                                                       int logN, RowMap qp, const ModQ *mods, const u64 *c0,
-                                                       long c0s, const ShoupPair *Pmod) {
+// MultSum + Permute (Sec. 3.3.1) for G rotations that share one Decompose
+// output (hoisting).  Rotation keys are stored permuted, K'_g[y] = K_g[x]
+// with y = pi_g(x) the NTT-domain index of kappa_g, so that
+//   out_g[x] = sum_d D[d][pi_g(x)] K_g[d][x] = T_g[pi_g(x)],
+//   T_g[y]   = sum_d D[d][y] K'_g[d][y]
+// (the same products, summed in the same order, for every output word).
+// Each digit word is loaded once and multiplied into all G accumulators; the
+// result is written to x = pi_g^{-1}(y), which stays inside the aligned
+// 32-word block of y (kappa permutes the low bits of the bit-reversed index
+// only), so stores remain coalesced.  Keys in Montgomery form (one REDC per
+// output).  With c0 given, P * c0[y] is added on the Q rows of poly 0 (the
+// hoisted rotation kept in Q_l P of double hoisting).
+// digits: [B][ndig][rows][N]; key_k: [dnum][2][nprimes][N];
+// out_k: [B][2][rows][N].
+template <int G>
+struct MultiKeys {
+    const u64 *key[G];
+    u64 *out[G];
+    u32 ginv[G];   // pi_g^{-1} = pi_{g^{-1} mod 2N}; 1 = identity
+};
+
+// Each digit word is loaded once and multiplied into the 2G accumulators of
+// the G keys (2G independent accumulation chains per thread).
+template <int G, bool STREAM>
+__global__ void __launch_bounds__(256) k_multsum_multi(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
+                                                       int alpha, int L, int ndig, int nprimes, int logN,
+                                                       const ModQ *mods, const u64 *c0, long c0s,
+                                                       const ShoupPair *Pmod) {
     const int N = 1 << logN;
     const int XW = 256 / BI;
     const int tx = threadIdx.x % XW, ti = threadIdx.x / XW;
-    const int x = blockIdx.x * XW + tx;
+    const int y = blockIdx.x * XW + tx;
     const int r = blockIdx.y;
     const int b = blockIdx.z * BI + ti;
-    if (b >= B || x >= N) return;
+    if (b >= B || y >= N) return;
     const int rows = level + 1 + alpha;
-    const int kr = r <= level ? r : L + 1 + (r - level - 1);
-    const ModQ m = mods[qp.at(r)];
-    const int src = (g == 1u) ? x : auto_index(x, g, logN);
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);   // the row's global prime
+    const ModQ m = mods[kr];
     const long dstride = (long)rows * N;
-    const u64 *dp = digits + (long)b * ndig * dstride + (long)r * N + src;
-    const u64 *kp = key + (long)kr * N + x;
-    const long kd = 2L * nprimes * N, kk = (long)nprimes * N;
-    U128 a0 = {0, 0}, a1 = {0, 0};
-    // four digits per round: all twelve loads are issued before the products
-    // (more bytes in flight per thread); key words are shared by the CTA's
-    // items (cached); STREAM marks the digit loads evict-first (read once)
-    int d = 0;
-    for (; d + 4 <= ndig; d += 4) {
-        u64 v[4], k0[4], k1[4];
+    const u64 *dp = digits + (long)b * ndig * dstride + (long)r * N + y;
+    const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    U128 a0[G], a1[G];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            v[u] = STREAM ? __ldcs(dp + (long)(d + u) * dstride) : __ldg(dp + (long)(d + u) * dstride);
-            k0[u] = __ldg(kp + (long)(d + u) * kd);
-            k1[u] = __ldg(kp + (long)(d + u) * kd + kk);
-        }
+    for (int k = 0; k < G; k++) a0[k] = U128{0, 0}, a1[k] = U128{0, 0};
+    for (int d = 0; d < ndig; d++) {
+        const u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            mac128(a0, v[u], k0[u]);
-            mac128(a1, v[u], k1[u]);
+        for (int k = 0; k < G; k++) {
+            const u64 *kp = mk.key[k] + (long)d * kd + koff;
+            mac128(a0[k], v, __ldg(kp));
+            mac128(a1[k], v, __ldg(kp + kk));
         }
     }
-    for (; d < ndig; d++) {
-        u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
-        mac128(a0, v, __ldg(kp + (long)d * kd));
-        mac128(a1, v, __ldg(kp + (long)d * kd + kk));
-    }
-    u64 o0 = redc(a0.lo, a0.hi, m), o1 = redc(a1.lo, a1.hi, m);
-    if (c0 && r <= level) {
+    u64 pc0 = 0;
+    const bool with_c0 = c0 && r <= level;
+    if (with_c0) {
         ShoupPair w = Pmod[r];
-        o0 = addmod(o0, shoup(c0[b * c0s + (long)r * N + src], w.w, w.wp, m.q), m.q);
+        pc0 = shoup(c0[b * c0s + (long)r * N + y], w.w, w.wp, m.q);
     }
-    u64 *ob = out + (long)b * 2 * rows * N;
-    ob[(long)r * N + x] = o0;
-    ob[(long)(rows + r) * N + x] = o1;
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        u64 o0 = redc(a0[k].lo, a0[k].hi, m), o1 = redc(a1[k].lo, a1[k].hi, m);
+        if (with_c0) o0 = addmod(o0, pc0, m.q);
+        const int x = mk.ginv[k] == 1u ? y : auto_index(y, mk.ginv[k], logN);
+        u64 *ob = mk.out[k] + (long)b * 2 * rows * N;
+        ob[(long)r * N + x] = o0;
+        ob[(long)(rows + r) * N + x] = o1;
+    }
 }
 
-// MultSum launch variants: items per CTA (BI) and streaming digit loads.
+// Permutes key rows into the layout above: out[row][pi_g(x)] = in[row][x].
+__global__ void k_permute_key(u64 *out, const u64 *in, long rows, int logN, u32 g) {
+    const int N = 1 << logN;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * (long)N) return;
+    long row = idx / N;
+    int x = (int)(idx - row * N);
+    out[row * N + auto_index(x, g, logN)] = in[idx];
+}
+void launch_permute_key(Ctx *c, u64 *out, const u64 *in, long rows, uint32_t g, cudaStream_t st) {
+    long n = rows * (long)c->N;
+    c->n_launch++;
+    k_permute_key<<<nblk(n, 256), 256, 0, st>>>(out, in, rows, c->logN, g);
+}
+
+// MultSum launch variants: items per CTA (BI), streaming digit loads.
 static void multsum_variant(int v, int B, int &BI, bool &stream) {
     static const int bis[4] = {8, 4, 2, 1};
-    BI = bis[(v >> 1) & 3];
+    BI = bis[v & 3];
     while (BI > 1 && BI > B) BI >>= 1;
-    stream = v & 1;
+    stream = (v >> 2) & 1;
+}
+
+template <int G>
+static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits, const u64 *const *keys,
+                             const uint32_t *gs, int B, int level, const u64 *c0, long c0s, cudaStream_t st) {
+    MultiKeys<G> mk;
+    const u32 M = 2u * (u32)c->N;
+    for (int k = 0; k < G; k++) {
+        mk.key[k] = keys[k];
+        mk.out[k] = outs[k];
+        // inverse of the odd g modulo 2N: Newton iteration on 32-bit words
+        u32 g = gs[k], inv = g;
+        for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
+        mk.ginv[k] = inv & (M - 1);
+    }
+    int BI;
+    bool stream;
+    multsum_variant(v, B, BI, stream);
+    const int rows = level + 1 + c->alpha, XW = 256 / BI;
+    dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
+    if (stream)
+        k_multsum_multi<G, true><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L, c->ndig(level),
+                                                       c->nprimes, c->logN, c->d_mod, c0, c0s, c->d_Pmod);
+    else
+        k_multsum_multi<G, false><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L, c->ndig(level),
+                                                        c->nprimes, c->logN, c->d_mod, c0, c0s, c->d_Pmod);
+    c->n_launch++;
+}
+
+static void multsum_launch(Ctx *c, int v, int G, u64 *const *outs, const u64 *digits, const u64 *const *keys,
+                           const uint32_t *gs, int B, int level, const u64 *c0, long c0s, cudaStream_t st) {
+    switch (G) {
+    case 1: multsum_launch_g<1>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    case 2: multsum_launch_g<2>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    case 3: multsum_launch_g<3>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    case 4: multsum_launch_g<4>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    case 5: multsum_launch_g<5>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    case 6: multsum_launch_g<6>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    case 7: multsum_launch_g<7>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    default: multsum_launch_g<8>(c, v, outs, digits, keys, gs, B, level, c0, c0s, st); break;
+    }
+}
+
+void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64 *const *keys, const uint32_t *gs,
+                          int G, int B, int level, const u64 *c0_for_P, long c0s, cudaStream_t st) {
+    if (G <= 0) return;
+    const int rows = level + 1 + c->alpha;
+    // a launch plan: keys per launch (chunk) and the launch variant
+    auto run = [&](int chunk, int v, bool traced) {
+        for (int k0 = 0; k0 < G; k0 += chunk) {
+            const int g = std::min(chunk, G - k0);
+            cudaEvent_t e0 = nullptr;
+            if (traced) c->trace_begin(0, e0);
+            multsum_launch(c, v, g, outs + k0, digits, keys + k0, gs + k0, B, level, c0_for_P, c0s, st);
+            if (traced) {
+                // algorithmic bytes: every key (2 polys x ndig digits x rows
+                // limbs) read once, every item's digits read once for the g
+                // keys, both output polys of every (item, key) written, c0
+                // read once if fused
+                double nd = c->ndig(level), W = (double)c->N * 8.0;
+                double bytes = g * 2.0 * nd * rows * W +
+                               (double)B * (nd * rows * W + g * 2.0 * rows * W + (c0_for_P ? (level + 1) * W : 0));
+                c->trace_end(0, e0, bytes);
+            }
+        }
+    };
+    int chunk = std::min(G, kMultSumMaxKeys), v = 0;  // default: 8 keys, 8 items per CTA, cached loads
+    if (c->autotune) {
+        auto key3 = std::make_tuple(level, B, G);
+        auto it = c->tune_multsum.find(key3);
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        if (it != c->tune_multsum.end()) {
+            chunk = it->second >> 8, v = it->second & 255;
+        } else if (cap == cudaStreamCaptureStatusNone) {
+            // time every (keys per launch, variant) twice on these very
+            // launches (the outputs do not depend on the plan); keep the fastest
+            cudaEvent_t a = c->ev_get(), b = c->ev_get();
+            float best = 1e30f;
+            std::set<std::tuple<int, int, bool>> seen;
+            for (int ch : {8, 4, 2, 1}) {
+                const int cc = std::min(ch, G);
+                for (int cand = 0; cand < 8; cand++) {
+                    int BI;
+                    bool stream;
+                    multsum_variant(cand, B, BI, stream);
+                    if (!seen.insert(std::make_tuple(cc, BI, stream)).second) continue;
+                    float t = 1e30f;
+                    for (int rep = 0; rep < 2; rep++) {
+                        cudaEventRecord(a, st);
+                        run(cc, cand, false);
+                        cudaEventRecord(b, st);
+                        cudaEventSynchronize(b);
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, a, b);
+                        t = std::min(t, ms);
+                    }
+                    if (t < best) best = t, chunk = cc, v = cand;
+                    char line[128];
+                    snprintf(line, sizeof line, "multsum level %d B %d G %d chunk %d BI %d stream %d ms %.4f\n",
+                             level, B, G, cc, BI, (int)stream, t);
+                    c->tune_log += line;
+                }
+            }
+            c->ev_free.push_back(a);
+            c->ev_free.push_back(b);
+            c->tune_multsum[key3] = (chunk << 8) | v;
+        }
+    }
+    run(chunk, v, true);
 }
 
 void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_t g, int B, int level,
                     const u64 *c0_for_P, long c0s, cudaStream_t st) {
-    int rows = level + 1 + c->alpha;
-    auto launch = [&](int v) {
-        int BI;
-        bool stream;
-        multsum_variant(v, B, BI, stream);
-        int XW = 256 / BI;
-        dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
-        if (stream)
-            k_multsum_items<true><<<grid, 256, 0, st>>>(out, digits, key, g, B, BI, level, c->alpha, c->L,
-                                                        c->ndig(level), c->nprimes, c->logN, c->map_qp(level),
-                                                        c->d_mod, c0_for_P, c0s, c->d_Pmod);
-        else
-            k_multsum_items<false><<<grid, 256, 0, st>>>(out, digits, key, g, B, BI, level, c->alpha, c->L,
-                                                         c->ndig(level), c->nprimes, c->logN, c->map_qp(level),
-                                                         c->d_mod, c0_for_P, c0s, c->d_Pmod);
-        c->n_launch++;
-    };
-    int v = 0;  // 8 items per CTA (capped by B), cached digit loads
-    if (c->autotune) {
-        auto key2 = std::make_pair(level, B);
-        auto it = c->tune_multsum.find(key2);
-        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-        cudaStreamIsCapturing(st, &cap);
-        if (it != c->tune_multsum.end()) {
-            v = it->second;
-        } else if (cap == cudaStreamCaptureStatusNone) {
-            // time each distinct variant twice on this very launch (the
-            // output does not depend on the variant) and keep the fastest
-            cudaEvent_t a = c->ev_get(), b = c->ev_get();
-            float best = 1e30f;
-            std::set<std::pair<int, bool>> seen;
-            for (int cand = 0; cand < 8; cand++) {
-                int BI;
-                bool stream;
-                multsum_variant(cand, B, BI, stream);
-                if (!seen.insert({BI, stream}).second) continue;
-                float t = 1e30f;
-                for (int rep = 0; rep < 2; rep++) {
-                    cudaEventRecord(a, st);
-                    launch(cand);
-                    cudaEventRecord(b, st);
-                    cudaEventSynchronize(b);
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, a, b);
-                    t = std::min(t, ms);
-                }
-                if (t < best) best = t, v = cand;
-            }
-            c->ev_free.push_back(a);
-            c->ev_free.push_back(b);
-            c->tune_multsum[key2] = v;
-        }
-    }
-    cudaEvent_t e0;
-    c->trace_begin(0, e0);
-    launch(v);
-    // algorithmic bytes: the key (2 polys x ndig digits x rows limbs) read once,
-    // every item's digits read once, both output polys written, c0 read if fused
-    double nd = c->ndig(level), W = (double)c->N * 8.0;
-    double bytes = 2.0 * nd * rows * W + (double)B * (nd * rows * W + 2.0 * rows * W + (c0_for_P ? (level + 1) * W : 0));
-    c->trace_end(0, e0, bytes);
+    launch_multsum_multi(c, &out, digits, &key, &g, 1, B, level, c0_for_P, c0s, st);
 }
 
 // ------------------------------------------------------ double hoisting

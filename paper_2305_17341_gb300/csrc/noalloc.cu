@@ -122,8 +122,9 @@ extern "C" int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level,
         }
     }
     cudaStream_t st = c.stream;
-    const bool tr = c.trace;
-    c.trace = false;  // tracing would create CUDA events
+    const bool tr = c.trace, at = c.autotune;
+    c.trace = false;     // tracing would create CUDA events
+    c.autotune = false;  // so would the launch tuner
     cudaMemcpyAsync(d_inv, h_inv, sizeof(ShoupPair) * (nd * a + (size_t)nd * a * rows), cudaMemcpyHostToDevice, st);
     // Decompose c1 (the input is in coefficient form already), extend, NTT
     const u64 *in = (const u64 *)in_dev;
@@ -142,6 +143,7 @@ extern "C" int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level,
     ntt_inv(&c, S_ct, 2L * nq, c.map_q(level), st);
     cudaMemcpyAsync(out_dev, S_ct, wct * 8, cudaMemcpyDeviceToDevice, st);
     c.trace = tr;
+    c.autotune = at;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
