@@ -106,9 +106,10 @@ int he_ctx_set_stream(he_ctx *ctx, void *stream);
  * (level, batch size, number of hoisted rotations) times its launch plans --
  * rotations per launch (1, 2, 4 or 8 sharing one read of the digits), items
  * per CTA, cached or streaming digit loads -- on those very launches and keeps
- * the fastest for the context.  Plans compute identical words; only speed
- * differs.  on = 0 uses the fixed default (8 rotations per launch, 8 items per
- * CTA, cached loads). */
+ * the fastest for the context; the first NTT of the context times the NTT
+ * passes compiled for 2 and for 3 CTAs per SM on scratch rows.  Plans compute
+ * identical words; only speed differs.  on = 0 uses the fixed defaults (8
+ * rotations per launch, 8 items per CTA, cached loads; 2 NTT CTAs per SM). */
 int he_ctx_set_autotune(he_ctx *ctx, int on);
 
 /* The autotuner's record: one line per timed launch plan (kernel, shape,

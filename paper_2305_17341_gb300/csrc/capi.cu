@@ -198,7 +198,8 @@ int he_ctx_destroy(he_ctx *ctx) {
     for (auto &kv : c.rtk) cudaFree(kv.second);
     if (c.rlk) cudaFree(c.rlk);
     for (auto &kv : c.ptcache) cudaFree(kv.second);
-    void *ptrs[] = {c.d_mod, c.d_psi, c.d_psip, c.d_ipsi, c.d_ipsip, c.d_ninv, c.d_dn_pinv, c.d_dn_pmod,
+    void *ptrs[] = {c.d_mod, c.d_psi, c.d_psip, c.d_ipsi, c.d_ipsip, c.d_psi2, c.d_ipsi2, c.d_ninv, c.d_dn_pinv,
+                    c.d_dn_pmod,
                     c.d_dn_Pinv, c.d_Pmod, c.d_dn_hp, c.d_dn_hq, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM,
                     c.d_pkM};
     for (void *p : ptrs)

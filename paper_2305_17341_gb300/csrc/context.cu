@@ -330,6 +330,15 @@ void build_tables(Ctx *c) {
     c->d_psip = upload(psip);
     c->d_ipsi = upload(ipsi);
     c->d_ipsip = upload(ipsip);
+    {
+        std::vector<u64> t2(2 * psi.size()), it2(2 * psi.size());
+        for (size_t i = 0; i < psi.size(); i++) {
+            t2[2 * i] = psi[i], t2[2 * i + 1] = psip[i];
+            it2[2 * i] = ipsi[i], it2[2 * i + 1] = ipsip[i];
+        }
+        c->d_psi2 = upload(t2);
+        c->d_ipsi2 = upload(it2);
+    }
     c->d_ninv = upload(ninv);
     c->hmod.resize(c->nprimes);
     for (int k = 0; k < c->nprimes; k++) c->hmod[k] = make_mod(c->primes[k]);

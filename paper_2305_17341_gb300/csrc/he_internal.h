@@ -124,6 +124,7 @@ struct Ctx {
 
     ModQ *d_mod = nullptr;         // [nprimes]
     u64 *d_psi = nullptr, *d_psip = nullptr, *d_ipsi = nullptr, *d_ipsip = nullptr;  // [nprimes][N]
+    u64 *d_psi2 = nullptr, *d_ipsi2 = nullptr;   // [nprimes][N][2]: (w, w') pairs, one 16-byte load each
     u64 *d_ninv = nullptr;         // [nprimes][2]
     // ModDown constants (level independent)
     ShoupPair *d_dn_pinv = nullptr;  // [alpha]   (P/p_j)^-1 mod p_j
@@ -165,6 +166,8 @@ struct Ctx {
     // launch-geometry autotuner: per (kernel, shape) the fastest variant,
     // timed on first use (variants compute identical words)
     bool autotune = true;
+    int ntt_minb = 2;        // CTAs per SM the register-blocked NTT is compiled for (2 or 3)
+    bool ntt_tuned = false;
     std::map<std::tuple<int, int, int>, int> tune_multsum;
     std::string tune_log;   // every timed plan: "multsum level B G chunk BI stream ms"   // (level, items, keys) -> (keys per launch << 8) | variant
     TraceClass tr[4];                 // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv

@@ -15,6 +15,7 @@
 // equal index mod N2, C columns per CTA, staged in shared memory); pass 2 runs
 // the remaining log2(N2) stages on rows of N2 contiguous coefficients.  Both
 // passes read and write HBM once.
+#include <cstdio>
 #include <stdexcept>
 
 #include "he_internal.h"
@@ -189,9 +190,9 @@ struct PassGeom {
     }
 };
 
-template <int LM, bool ROWS>
-__global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, const ModQ *mods, const u64 *tw,
-                                                      const u64 *twp, int logN, RowSkip skip) {
+template <int LM, bool ROWS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm, const ModQ *mods,
+                                                            const ulonglong2 *tw2, int logN, RowSkip skip) {
     typedef PassGeom<LM, ROWS> G_;
     constexpr int M = G_::M, T = G_::T, W = G_::W;
     __shared__ u64 sm[G_::SM];
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, cons
     if (skip.skip(row)) return;  // uniform over the CTA
     const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
-    const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
+    const ulonglong2 *w2_ = tw2 + (long)pidx * N;
     int t, w;
     if (ROWS) { w = threadIdx.x / T; t = threadIdx.x % T; }
     else { t = threadIdx.x / W; w = threadIdx.x % W; }
@@ -217,8 +218,8 @@ __global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, cons
 #pragma unroll
         for (int k = 0; k < 16; k++)
             if (!(k & s)) {
-                long idx = mb + k / (2 * s);
-                bf_fwd(x[k], x[k + s], w_[idx], wp_[idx], q);
+                const ulonglong2 w = __ldg(w2_ + mb + k / (2 * s));
+                bf_fwd(x[k], x[k + s], w.x, w.y, q);
             }
     }
 #pragma unroll
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, cons
 #pragma unroll
         for (int k = 0; k < 16; k++)
             if (!(k & sp)) {
-                long idx = mb + k / (2 * sp);
-                bf_fwd(x[k], x[k + sp], w_[idx], wp_[idx], q);
+                const ulonglong2 w = __ldg(w2_ + mb + k / (2 * sp));
+                bf_fwd(x[k], x[k + sp], w.x, w.y, q);
             }
     }
 #pragma unroll
@@ -246,9 +247,9 @@ __global__ void __launch_bounds__(256) k_ntt_fwd_fast(u64 *data, RowMap rm, cons
     }
 }
 
-template <int LM, bool ROWS>
-__global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, const ModQ *mods, const u64 *tw,
-                                                      const u64 *twp, const u64 *ninv, int logN) {
+template <int LM, bool ROWS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ntt_inv_fast(u64 *data, RowMap rm, const ModQ *mods,
+                                                            const ulonglong2 *tw2, const u64 *ninv, int logN) {
     typedef PassGeom<LM, ROWS> G_;
     constexpr int M = G_::M, T = G_::T, W = G_::W;
     __shared__ u64 sm[G_::SM];
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, cons
     const long row = blockIdx.y;
     const int pidx = rm.at(row);
     const u64 q = mods[pidx].q;
-    const u64 *w_ = tw + (long)pidx * N, *wp_ = twp + (long)pidx * N;
+    const ulonglong2 *w2_ = tw2 + (long)pidx * N;
     int t, w;
     if (ROWS) { w = threadIdx.x / T; t = threadIdx.x % T; }
     else { t = threadIdx.x / W; w = threadIdx.x % W; }
@@ -276,8 +277,8 @@ __global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, cons
 #pragma unroll
         for (int k = 0; k < 16; k++)
             if (!(k & sp)) {
-                long idx = mb + k / (2 * sp);
-                bf_inv(x[k], x[k + sp], w_[idx], wp_[idx], q);
+                const ulonglong2 w = __ldg(w2_ + mb + k / (2 * sp));
+                bf_inv(x[k], x[k + sp], w.x, w.y, q);
             }
     }
 #pragma unroll
@@ -291,8 +292,8 @@ __global__ void __launch_bounds__(256) k_ntt_inv_fast(u64 *data, RowMap rm, cons
 #pragma unroll
         for (int k = 0; k < 16; k++)
             if (!(k & s)) {
-                long idx = mb + k / (2 * s);
-                bf_inv(x[k], x[k + s], w_[idx], wp_[idx], q);
+                const ulonglong2 w = __ldg(w2_ + mb + k / (2 * s));
+                bf_inv(x[k], x[k + s], w.x, w.y, q);
             }
     }
     if (!ROWS) {
@@ -308,15 +309,22 @@ template <int LM, bool ROWS>
 static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk) {
     typedef PassGeom<LM, ROWS> G_;
     dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
-    k_ntt_fwd_fast<LM, ROWS><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, ctx->d_psi, ctx->d_psip, ctx->logN, sk);
+    const ulonglong2 *t2 = (const ulonglong2 *)ctx->d_psi2;
+    if (ctx->ntt_minb == 3)
+        k_ntt_fwd_fast<LM, ROWS, 3><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk);
+    else
+        k_ntt_fwd_fast<LM, ROWS, 2><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk);
 }
 
 template <int LM, bool ROWS>
 static void inv_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st) {
     typedef PassGeom<LM, ROWS> G_;
     dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
-    k_ntt_inv_fast<LM, ROWS><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, ctx->d_ipsi, ctx->d_ipsip, ctx->d_ninv,
-                                                    ctx->logN);
+    const ulonglong2 *t2 = (const ulonglong2 *)ctx->d_ipsi2;
+    if (ctx->ntt_minb == 3)
+        k_ntt_inv_fast<LM, ROWS, 3><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
+    else
+        k_ntt_inv_fast<LM, ROWS, 2><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
 }
 
 // ------------------------------------------------------ integer roofline
@@ -382,8 +390,56 @@ static void split(int logN, int &logN1, int &C, int &R) {
     if (R > N1) R = N1;
 }
 
+// Picks the register budget of the register-blocked passes (2 or 3 CTAs per
+// SM) by timing a forward and an inverse transform of 256 scratch rows with
+// each; runs once per context, outside stream capture.
+static void tune_ntt(Ctx *ctx, cudaStream_t st) {
+    ctx->ntt_tuned = true;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    if (cap != cudaStreamCaptureStatusNone) {
+        ctx->ntt_tuned = false;
+        return;
+    }
+    const long R = 256;
+    Buf scratch(&ctx->pool, (size_t)R * ctx->N);
+    cudaMemsetAsync(scratch.p, 0, (size_t)R * ctx->N * 8, st);
+    int logN1, C, Rr;
+    split(ctx->logN, logN1, C, Rr);
+    RowMap m = ctx->map_q(0);
+    RowSkip none;
+    cudaEvent_t a = ctx->ev_get(), b = ctx->ev_get();
+    float best = 1e30f;
+    int pick = 2;
+    for (int minb : {2, 3}) {
+        ctx->ntt_minb = minb;
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; rep++) {
+            cudaEventRecord(a, st);
+            if (logN1 == 8) fwd_pass<8, false>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, false>(ctx, scratch.p, R, m, st, none);
+            if (ctx->logN - logN1 == 8) fwd_pass<8, true>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, true>(ctx, scratch.p, R, m, st, none);
+            if (ctx->logN - logN1 == 8) inv_pass<8, true>(ctx, scratch.p, R, m, st); else inv_pass<7, true>(ctx, scratch.p, R, m, st);
+            if (logN1 == 8) inv_pass<8, false>(ctx, scratch.p, R, m, st); else inv_pass<7, false>(ctx, scratch.p, R, m, st);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            t = std::min(t, ms);
+        }
+        ctx->n_launch += 8;
+        char line[96];
+        snprintf(line, sizeof line, "ntt logN %d rows %ld ctas_per_sm %d ms %.4f\n", ctx->logN, R, minb, t);
+        ctx->tune_log += line;
+        if (t < best) best = t, pick = minb;
+    }
+    ctx->ntt_minb = pick;
+    ctx->ev_free.push_back(a);
+    ctx->ev_free.push_back(b);
+}
+
 void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const RowSkip *skip) {
     if (rows <= 0) return;
+    if (ctx->autotune && !ctx->ntt_tuned && ctx->logN >= 14 && ctx->logN <= 16) tune_ntt(ctx, st);
     int logN = ctx->logN, logN1, C, R;
     split(logN, logN1, C, R);
     int N1 = 1 << logN1, N2 = 1 << (logN - logN1);
@@ -420,6 +476,7 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, 
 
 void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st) {
     if (rows <= 0) return;
+    if (ctx->autotune && !ctx->ntt_tuned && ctx->logN >= 14 && ctx->logN <= 16) tune_ntt(ctx, st);
     int logN = ctx->logN, logN1, C, R;
     split(logN, logN1, C, R);
     int N1 = 1 << logN1, N2 = 1 << (logN - logN1);
