@@ -298,6 +298,33 @@ def run_ours(args, rank, world, dist):
         pk.he_mm_plan_destroy(plan)
     pk.he_ct_free(single_ref)
 
+    # ---- the same products with one relinearisation each (not the paper's
+    #      DMatrixMult: n - 1 fewer key switches per product)
+    once_line = None
+    if not once and not args.no_once:
+        jobs1 = [(a, b, n_mat, n1, n1, True) for a, b in cts]
+        for _ in range(2):
+            for o in pk.he_hmatmul_batch(jobs1):
+                pk.he_ct_free(o)
+        o1 = pk.he_hmatmul_batch(jobs1[:1])
+        s1 = pk.he_hmatmul(ctx, cts[0][0], cts[0][1], n_mat, n1, n1, relin_once=True)
+        ob = bool(np.array_equal(pk.he_ct_export(ctx, o1[0]), pk.he_ct_export(ctx, s1)))
+        oerr = float(np.abs(pk.he_decrypt_matrix(ctx, o1[0], n_mat, n_mat) - mats[0][0] @ mats[0][1]).max())
+        pk.he_ct_free(o1[0])
+        pk.he_ct_free(s1)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(tstream)
+        for _ in range(args.steps):
+            for o in pk.he_hmatmul_batch(jobs1):
+                pk.he_ct_free(o)
+        r1.record(tstream)
+        torch.cuda.synchronize()
+        rms = r0.elapsed_time(r1)
+        once_line = {"value": B * args.steps / (rms / 1000.0), "unit": UNIT, "ms_per_step": rms / args.steps,
+                     "batch_equals_single_bitexact": ob, "max_abs_err": oerr,
+                     "note": "relin_once=1: the n tensors summed, one key switch per product (not DMatrixMult)"}
+
     # ---- e2e through the C ABI from pinned host memory
     w_in = 2 * (level + 1) * Nn
     w_out = 2 * (level - 3 + 1) * Nn
@@ -404,6 +431,7 @@ def run_ours(args, rank, world, dist):
         "roofline": roof, "roofline_keyswitch": roof_ms, "roofline_ntt_fwd": roof_nf, "roofline_ntt_inv": roof_ni,
         "kernel_time_ms": totals,
         "graph": graph,
+        "relin_once": once_line,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": B * 2 * w_in * 8,
                 "d2h_bytes_per_step": B * w_out * 8},
@@ -774,6 +802,74 @@ def run_keyswitch(args):
     pk.he_ctx_destroy(ctx)
 
 
+# Table 3 (dh-BSGS rows): the paper's Z and T transform times of a 128x128
+# matrix ciphertext, logN 15, 14 levels, Lattigo v4.1.0 on an AMD Ryzen 7
+# 7735HS CPU (seconds; thread count not stated)
+PAPER_TABLE3 = {("Z", 8): 2.004, ("Z", 16): 1.286, ("T", 8): 1.049, ("T", 16): 0.725}
+
+
+def run_transforms(args):
+    """The Z (sigma) and T (tau) transforms alone, as Table 3 measures them:
+    one 128x128 matrix ciphertext at N = 2^15 (n^2 = slots, no replication),
+    chain 60 + 14x40 with 2x60 special primes, input at level 11 so that the
+    run ends at level 10, n1 in {8, 16}; device time per transform."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300 import workloads
+    pk.build()
+    ctx = pk.he_ctx_create(pk.make_params(15, [60] + [40] * 14, [60, 60]), 21)
+    tstream = torch.cuda.Stream()
+    pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
+    n, S = 128, 1 << 14
+    steps = set()
+    for n1 in (8, 16):
+        steps |= set(pk.he_rot_steps_for_matmul(n, n1, n1, S))
+    pk.he_keygen(ctx, sorted(steps), False)
+    A, _ = workloads.matmul_pair(n, 5)
+    ct = pk.he_encrypt_matrix(ctx, A, 11, 1)
+    info = pk.he_ctx_info(ctx)
+    key_mb = None
+    out = {}
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for name, kind in (("Z", 0), ("T", 1)):
+        for n1 in (8, 16):
+            for _ in range(max(2, args.warmup)):
+                pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(tstream)
+            for _ in range(args.steps):
+                pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1))
+            e1.record(tstream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            r = pk.he_linear_transform(ctx, ct, kind, n, n1)
+            d = pk.he_decrypt_matrix(ctx, r, n, n)
+            ref = A[i, (i + j) % n] if kind == 0 else A[(i + j) % n, j]
+            err = float(np.abs(d - ref).max())
+            lv = pk.he_ct_info(r)[0]
+            pk.he_ct_free(r)
+            n2 = n // n1
+            keys = (n1 + 2 * n2 - 2) if kind == 0 else (n1 + n2 - 2)
+            out["%s_n1_%d" % (name, n1)] = {"ms": ms, "end_level": lv, "max_abs_err": err,
+                                            "rotation_keys": keys,
+                                            "paper_s": PAPER_TABLE3[(name, n1)],
+                                            "speedup_vs_paper": PAPER_TABLE3[(name, n1)] * 1e3 / ms}
+    # one rotation key: dnum digits x 2 polys x (L+1+alpha) limbs x N words
+    N, L, alpha, dnum = info["N"], info["L"], info["alpha"], info["dnum"]
+    key_mb = dnum * 2 * (L + 1 + alpha) * N * 8 / 2 ** 20
+    print(json.dumps({"metric": "Z / T linear transform time (Table 3 setting)", "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "results": out,
+                      "rotation_key_mib": key_mb,
+                      "paper_hardware": "Lattigo v4.1.0, AMD Ryzen 7 7735HS (CPU), logN 15, logQP 760, 14 levels",
+                      "config": {"workload": "one 128x128 matrix ciphertext, N=2^15, q 60+14x40, p 2x60 "
+                                             "(logQP 740), level 11 -> 10, n1 in {8, 16}"}}), flush=True)
+    pk.he_ct_free(ct)
+    pk.he_ctx_destroy(ctx)
+
+
 def run_ntt(args):
     """The NTT alone (he_ntt) on R rows at N = 2^16 over the primes of the
     covariance chain at level 20 (R = 2024 is the forward transform of one
@@ -886,6 +982,7 @@ def main():
     ap.add_argument("--preset", type=int, default=2, choices=[1, 2],
                     help="matmul: 2 = 128x128 at N=2^16 (the benchmark), 1 = 32x32 at N=2^14")
     ap.add_argument("--no-graph", action="store_true", help="matmul: skip the captured-graph replay")
+    ap.add_argument("--no-once", action="store_true", help="matmul: skip the single-relinearisation measurement")
     ap.add_argument("--relin-once", action="store_true",
                     help="matmul: relinearise the summed tensors once per product (not the paper's DMatrixMult)")
     ap.add_argument("--n", type=int, default=N_MAT, choices=[16, 32, 64, 128],
@@ -895,7 +992,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served", "ntt",
-                                                           "keyswitch"])
+                                                           "keyswitch", "transforms"])
     ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
     ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
     ap.add_argument("--rate", type=float, default=1.5, help="served: arrivals per second")
@@ -920,6 +1017,8 @@ def main():
         return run_ntt(args)
     if args.workload == "keyswitch":
         return run_keyswitch(args)
+    if args.workload == "transforms":
+        return run_transforms(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None

@@ -227,6 +227,18 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs);
  * transpose). */
 int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, he_ct **out);
 
+/* One double-hoisted BSGS linear transform of eq. 3' on a matrix ciphertext
+ * (Sec. 3.3.1, Table 1 "Optimized" rows): kind 0 = sigma (the Z transform
+ * of eq. 5, diagonals k, -n < k < n), 1 = tau (T of eq. 6, diagonals n k,
+ * 0 <= k < n), 2 = the transpose G (diagonals (n - 1) k); n1 baby steps.
+ * Replicates a zero-padded input to period n^2 first; consumes one level
+ * (the plaintext diagonals are encoded at scale q_l and rescaled away, so
+ * the scale is kept).  Errors: HE_ERR_ARG, HE_ERR_LEVEL, HE_ERR_KEY_MISSING. */
+#define HE_LT_SIGMA 0
+#define HE_LT_TAU 1
+#define HE_LT_TRANSPOSE 2
+int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, he_ct **out);
+
 /* State of the interactive modulus refresh (Sec. 7.2.3, App. C): the Philox
  * object of the next refresh is next_obj + 1; count counts refreshes. */
 typedef struct he_refresh_state {

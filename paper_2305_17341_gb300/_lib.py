@@ -108,6 +108,7 @@ SIGNATURES = {
     "he_hmatmul": [vp, vp, vp, ip, P(he_mm_sched), P(vp)],
     "he_hmatmul_batch": [P(he_mm_job), ip, P(vp)],
     "he_transpose": [vp, vp, ip, ip, ctypes.c_double, P(vp)],
+    "he_linear_transform": [vp, vp, ip, ip, ip, P(vp)],
     "he_refresh": [vp, vp, P(he_refresh_state), P(vp)],
     "he_aggregate": [vp, vp, ip, ip, P(vp)],
     "he_covariance": [vp, P(vp), ip, ip, ip, ip, ip, P(he_mm_sched), P(vp)],
@@ -353,6 +354,13 @@ def he_hmatmul_batch(jobs):
 
 def he_transpose(ctx, ct, n, n1, prescale=1.0):
     return _unary("he_transpose", ctx, ct, n, n1, prescale)
+
+
+HE_LT_SIGMA, HE_LT_TAU, HE_LT_TRANSPOSE = 0, 1, 2
+
+
+def he_linear_transform(ctx, ct, kind, n, n1):
+    return _unary("he_linear_transform", ctx, ct, kind, n, n1)
 
 
 def _handles(hs):

@@ -727,6 +727,36 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
     GUARD_END
 }
 
+int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    if (kind < 0 || kind > 2) return fail(HE_ERR_ARG, "kind must be 0 (sigma), 1 (tau) or 2 (transpose)");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, ct)) return rc;
+    he_mm_sched s{n1, n1, 0};
+    if (int rc = check_sched(c, n, &s)) return rc;
+    if (ct->level < 1) return fail(HE_ERR_LEVEL, "a linear transform needs 1 level");
+    GUARD_BEGIN
+    he_ct *tmp = clone_ct(c, ct);
+    he_ct *o = nullptr;
+    try {
+        if (tmp->period != n * n) replicate(&c, tmp->d, 1, tmp->level, n);
+        o = new_ct(&c, ct->level - 1, ct->scale, n * n);
+        const int n2 = n / n1;
+        if (kind == 0) lintrans(&c, tmp->d, 1, ct->level, 0, n, 1, n1, -n2, n2, 1.0, o->d);
+        else if (kind == 1) lintrans(&c, tmp->d, 1, ct->level, 1, n, n, n1, 0, n2, 1.0, o->d);
+        else lintrans(&c, tmp->d, 1, ct->level, 2, n, n - 1, n1, -n2, n2, 1.0, o->d);
+    } catch (...) {
+        free_ct(tmp);
+        free_ct(o);
+        throw;
+    }
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    free_ct(tmp);
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
 int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inverse) {
     if (!ctx || (n_rows > 0 && !rows_dev) || n_rows < 0) return fail(HE_ERR_ARG, "bad arguments");
     Ctx &c = ctx->c;

@@ -365,3 +365,29 @@ def test_autotuned_launches_compute_the_same_words(c1):
         assert np.array_equal(lib.he_ct_export(ctx, a), lib.he_ct_export(ctx, b))
     for h in tuned + fixed + [x for p in pairs for x in p[4:6]]:
         lib.he_ct_free(h)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_linear_transform_bit_exact(c1, kind):
+    """sigma (Z), tau (T) and G alone through he_linear_transform, bit-exact
+    to the oracle's double-hoisted BSGS transforms; the decrypted sigma/tau
+    match the index maps of eq. 5 / eq. 6 and G the transpose."""
+    from oracle.hmm import HMM, matmul_rot_steps, transpose_rot_steps
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    steps = sorted(set(matmul_rot_steps(n, n1, n1, P.S)) | set(transpose_rot_steps(n, n1, P.S)))
+    lib.he_keygen(ctx, steps, want_relin=False)
+    for s in steps:
+        he.gen_rotation_key(s)
+    A, B, oa, ob, ga, gb = _matrix_pair(P, he, lib, ctx, n, 140 + kind)
+    H = HMM(he)
+    r = H.replicate(oa, n)
+    want = H.sigma(r, n, n1) if kind == 0 else H.tau(r, n, n1) if kind == 1 else H.transpose(oa, n, n1)
+    got = lib.he_linear_transform(ctx, ga, kind, n, n1)
+    assert np.array_equal(lib.he_ct_export(ctx, got), residues(he, want))
+    out = lib.he_decrypt_matrix(ctx, got, n, n)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ref = A[i, (i + j) % n] if kind == 0 else A[(i + j) % n, j] if kind == 1 else A.T
+    assert np.abs(out - ref).max() < TOL
+    for h in (ga, gb, got):
+        lib.he_ct_free(h)
