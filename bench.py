@@ -244,8 +244,10 @@ def run_ours(args, rank, world, dist):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(tstream)
+    torch.cuda.nvtx.range_push("timed")      # profilers select the timed launches by this range
     for _ in range(args.steps):
         batched_step()
+    torch.cuda.nvtx.range_pop()
     e1.record(tstream)
     torch.cuda.synchronize()
     barrier()
@@ -776,8 +778,10 @@ def run_keyswitch(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(tstream)
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         step()
+    torch.cuda.nvtx.range_pop()
     e1.record(tstream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -897,9 +901,11 @@ def run_ntt(args):
     pk.he_trace_enable(ctx, True)
     for c in (1, 2):
         pk.he_trace_read(ctx, c, reset=True)
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
         pk.he_ntt(ctx, dev.data_ptr(), R, level)
         pk.he_ntt(ctx, dev.data_ptr(), R, level, inverse=True)
+    torch.cuda.nvtx.range_pop()
     tr = {c: pk.he_trace_read(ctx, c, reset=True) for c in (1, 2)}
     pk.he_trace_enable(ctx, False)
     peak = pk.he_bench_butterfly(4000) / 1e9
