@@ -45,8 +45,16 @@ void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s) {
     launch_copy_rows(pc.p, (long)a * N, u + (long)(level + 1) * N, (long)rows * N, items, (long)a * N, c->stream);
     ntt_inv(c, pc.p, (long)items * a, c->map_p(), c->stream);
     launch_moddown_bconv(c, pc.p, conv.p, items, level, c->stream);
-    ntt_fwd(c, conv.p, (long)items * (level + 1), c->map_q(level), c->stream);
-    launch_moddown_final(c, out, u, conv.p, nullptr, items, level, (long)rows * N, out_s, 0, c->stream);
+    if (c->logN >= 14 && c->logN <= 16) {
+        // the NTT's last pass writes out = (u_Q - conv) P^-1 directly
+        SubScale ep;
+        ep.u = u, ep.us = (long)rows * N, ep.out = out, ep.os = out_s, ep.w = c->d_dn_Pinv;
+        ep.rows_per_item = level + 1;
+        ntt_fwd_subscale(c, conv.p, (long)items * (level + 1), c->map_q(level), c->stream, ep);
+    } else {
+        ntt_fwd(c, conv.p, (long)items * (level + 1), c->map_q(level), c->stream);
+        launch_moddown_final(c, out, u, conv.p, nullptr, items, level, (long)rows * N, out_s, 0, c->stream);
+    }
 }
 
 const u64 *need_key(Ctx *c, uint32_t g) {
@@ -103,8 +111,16 @@ void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out) {
     RowMap one = RowMap::single(level);
     ntt_inv(c, last.p, 2L * B, one, c->stream);
     launch_rescale_prep(c, last.p, t.p, 2 * B, level, c->stream);
-    ntt_fwd(c, t.p, 2L * B * level, c->map_q(level - 1), c->stream);
-    launch_rescale_final(c, out, in, t.p, 2 * B, level, (long)(level + 1) * N, (long)level * N, c->stream);
+    if (c->logN >= 14 && c->logN <= 16) {
+        // the NTT's last pass writes out = (in - t) q_l^-1 directly
+        SubScale ep;
+        ep.u = in, ep.us = (long)(level + 1) * N, ep.out = out, ep.os = (long)level * N, ep.w = c->lc(level).d_rs_inv;
+        ep.rows_per_item = level;
+        ntt_fwd_subscale(c, t.p, 2L * B * level, c->map_q(level - 1), c->stream, ep);
+    } else {
+        ntt_fwd(c, t.p, 2L * B * level, c->map_q(level - 1), c->stream);
+        launch_rescale_final(c, out, in, t.p, 2 * B, level, (long)(level + 1) * N, (long)level * N, c->stream);
+    }
 }
 
 // Level drop: keep limbs 0..to of both polys.

@@ -229,6 +229,19 @@ int h_gen_primes(int logN, int nq, const int *qbits, int np, const int *pbits, u
 
 // NTT
 void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const RowSkip *skip = nullptr);
+// Epilogue of a forward NTT that finishes ModDown or Rescale: the transform
+// v of row (item it, limb r) is not stored; instead
+//   out[it*os + r*N + x] = (u[it*us + r*N + x] - v) * w[r]  mod q_r.
+struct SubScale {
+    const u64 *u = nullptr;
+    long us = 0;
+    u64 *out = nullptr;
+    long os = 0;
+    const ShoupPair *w = nullptr;
+    int rows_per_item = 1;
+    long row0 = 0;   // absolute index of the launch's first row
+};
+void ntt_fwd_subscale(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const SubScale &ep);
 void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st);
 
 // ---- kernels.cu launchers (all asynchronous on st) ----

@@ -340,28 +340,39 @@ void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B,
 // target row r of Q_l P gets sum_i y_i (Q_d/q_i mod r) mod r, except the
 // digit's own rows, which keep c_r.  In/out in coefficient form.
 // coef: [B][l+1][N]; out: [B][ndig][l+1+alpha][N].
-__global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int alpha, int ndig, int N, RowMap qp,
-                              const ModQ *mods, const ShoupPair *up_inv, const ShoupPair *up_mod,
-                              const u64 *own_ntt, long own_s) {
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long total = (long)B * ndig * N;
-    if (idx >= total) return;
-    int x = (int)(idx % N);
-    long t = idx / N;
-    int d = (int)(t % ndig);
-    int b = (int)(t / ndig);
-    int rows = level + 1 + alpha;
+__global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int alpha,
+                                                     int ndig, int N, RowMap qp, const ModQ *mods,
+                                                     const ShoupPair *up_inv, const ShoupPair *up_mod,
+                                                     const u64 *own_ntt, long own_s) {
+    // 256 | N, so the CTA's 256 coefficients share one (item, digit): its
+    // conversion constants and row primes are staged in shared memory
+    __shared__ ShoupPair s_mod[4 * 64];   // [s][r], alpha <= 4, rows <= 64
+    __shared__ u64 s_q[64];
+    const long base = (long)blockIdx.x * blockDim.x;
+    const long t = base / N;
+    const int d = (int)(t % ndig), b = (int)(t / ndig);
+    const int rows = level + 1 + alpha;
+    const int i0 = d * alpha;
+    const int ns = min(alpha, level + 1 - i0);
+    for (int e = threadIdx.x; e < ns * rows; e += blockDim.x) {
+        const int sd = e / rows, r = e - sd * rows;
+        s_mod[e] = up_mod[((long)d * alpha + sd) * rows + r];
+    }
+    for (int r = threadIdx.x; r < rows; r += blockDim.x)
+        s_q[r] = mods[r <= qp.lq ? r : qp.base_p + (r - qp.lq - 1)].q;   // qp is unshifted
+    __syncthreads();
+    const long idx = base + threadIdx.x;
+    if (idx >= (long)B * ndig * N) return;
+    const int x = (int)(idx - t * N);
     const u64 *cb = coef + (long)b * (level + 1) * N;
     u64 *ob = out + ((long)b * ndig + d) * rows * N;
-    int i0 = d * alpha;
-    int ns = min(alpha, level + 1 - i0);
     // alpha <= 4; fixed trip counts keep y in registers
     u64 y[4] = {0, 0, 0, 0};
 #pragma unroll
-    for (int s = 0; s < 4; s++) {
-        if (s < ns) {
-            ShoupPair w = up_inv[d * alpha + s];
-            y[s] = shoup(cb[(long)(i0 + s) * N + x], w.w, w.wp, mods[i0 + s].q);
+    for (int sd = 0; sd < 4; sd++) {
+        if (sd < ns) {
+            ShoupPair w = up_inv[d * alpha + sd];
+            y[sd] = shoup(cb[(long)(i0 + sd) * N + x], w.w, w.wp, mods[i0 + sd].q);
         }
     }
     for (int r = 0; r < rows; r++) {
@@ -369,14 +380,13 @@ __global__ void k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int a
         if (r >= i0 && r < i0 + ns) {
             v = own_ntt ? own_ntt[(long)b * own_s + (long)r * N + x] : cb[(long)r * N + x];
         } else {
-            // qp is unshifted: rows <= level are q_r, the rest p_{r-level-1}
-            const ModQ &m = mods[r <= qp.lq ? r : qp.base_p + (r - qp.lq - 1)];
+            const u64 q = s_q[r];
             v = 0;
 #pragma unroll
-            for (int s = 0; s < 4; s++) {
-                if (s < ns) {
-                    ShoupPair w = up_mod[((long)d * alpha + s) * rows + r];
-                    v = addmod(v, shoup(y[s], w.w, w.wp, m.q), m.q);
+            for (int sd = 0; sd < 4; sd++) {
+                if (sd < ns) {
+                    const ShoupPair w = s_mod[sd * rows + r];
+                    v = addmod(v, shoup(y[sd], w.w, w.wp, q), q);
                 }
             }
         }
@@ -459,9 +469,19 @@ void launch_centre_i64_q0(Ctx *c, const u64 *a, i64 *out, cudaStream_t st) {
 // conv_r = ((x + h) mod P) - h mod q_r, coefficient form (h is added to
 // every coefficient, so it is folded in here, before the forward NTT).
 // pcoef: [items][alpha][N]; out: [items][l+1][N]
-__global__ void k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int alpha, int L, int N,
-                                const ModQ *mods, const ShoupPair *pinv, const ShoupPair *pmod, const u64 *hp,
-                                const ShoupPair *Pmod, const u64 *hq) {
+__global__ void __launch_bounds__(256) k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int alpha,
+                                                       int L, int N, const ModQ *mods, const ShoupPair *pinv,
+                                                       const ShoupPair *pmod, const u64 *hp, const ShoupPair *Pmod,
+                                                       const u64 *hq) {
+    // per-row constants of the conversion, staged once per CTA
+    __shared__ ShoupPair s_pmod[4 * 64], s_P[64];
+    __shared__ u64 s_q[64], s_hq[64];
+    for (int e = threadIdx.x; e < alpha * (level + 1); e += blockDim.x) {
+        const int j = e / (level + 1), r = e - j * (level + 1);
+        s_pmod[e] = pmod[j * (L + 1) + r];
+    }
+    for (int r = threadIdx.x; r <= level; r += blockDim.x) s_q[r] = mods[r].q, s_P[r] = Pmod[r], s_hq[r] = hq[r];
+    __syncthreads();
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)items * N) return;
     int x = (int)(idx % N);
@@ -481,17 +501,17 @@ __global__ void k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level
     }
     u64 e = (u64)floor(ef);
     for (int r = 0; r <= level; r++) {
-        u64 q = mods[r].q, v = 0;
+        u64 q = s_q[r], v = 0;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             if (j < alpha) {
-                ShoupPair w = pmod[j * (L + 1) + r];
+                ShoupPair w = s_pmod[j * (level + 1) + r];
                 v = addmod(v, shoup(y[j], w.w, w.wp, q), q);
             }
         }
-        ShoupPair wP = Pmod[r];
+        ShoupPair wP = s_P[r];
         v = submod(v, shoup(e, wP.w, wP.wp, q), q);
-        v = submod(v, hq[r], q);
+        v = submod(v, s_hq[r], q);
         out[((long)it * (level + 1) + r) * N + x] = v;
     }
 }

@@ -190,9 +190,10 @@ struct PassGeom {
     }
 };
 
-template <int LM, bool ROWS, int MINB>
+template <int LM, bool ROWS, int MINB, bool SUBSC>
 __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm, const ModQ *mods,
-                                                            const ulonglong2 *tw2, int logN, RowSkip skip) {
+                                                            const ulonglong2 *tw2, int logN, RowSkip skip,
+                                                            SubScale ep) {
     typedef PassGeom<LM, ROWS> G_;
     constexpr int M = G_::M, T = G_::T, W = G_::W;
     __shared__ u64 sm[G_::SM];
@@ -240,6 +241,21 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
 #pragma unroll
     for (int k = 0; k < 16; k++) sm[G_::sidx(16 * t + k, w)] = x[k];
     __syncthreads();
+    if (ROWS && SUBSC) {
+        const long arow = ep.row0 + row;
+        const long it = arow / ep.rows_per_item;
+        const int r = (int)(arow - it * ep.rows_per_item);
+        const ShoupPair wr = ep.w[r];
+        const long off = (long)r * N + seq * M;
+        const u64 *up = ep.u + it * ep.us + off;
+        u64 *op = ep.out + it * ep.os + off;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const u64 v = reduce4q(sm[G_::sidx(t + T * k, w)], q);
+            op[t + T * k] = shoup(submod(up[t + T * k], v, q), wr.w, wr.wp, q);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = sm[G_::sidx(t + T * k, w)];
@@ -306,14 +322,22 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_inv_fast(u64 *data, RowMap rm
 }
 
 template <int LM, bool ROWS>
-static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk) {
+static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk,
+                     const SubScale *ep = nullptr) {
     typedef PassGeom<LM, ROWS> G_;
     dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
     const ulonglong2 *t2 = (const ulonglong2 *)ctx->d_psi2;
-    if (ctx->ntt_minb == 3)
-        k_ntt_fwd_fast<LM, ROWS, 3><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk);
-    else
-        k_ntt_fwd_fast<LM, ROWS, 2><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk);
+    const SubScale e = ep ? *ep : SubScale();
+    if (ROWS && ep) {
+        if (ctx->ntt_minb == 3)
+            k_ntt_fwd_fast<LM, ROWS, 3, true><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
+        else
+            k_ntt_fwd_fast<LM, ROWS, 2, true><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
+    } else if (ctx->ntt_minb == 3) {
+        k_ntt_fwd_fast<LM, ROWS, 3, false><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
+    } else {
+        k_ntt_fwd_fast<LM, ROWS, 2, false><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
+    }
 }
 
 template <int LM, bool ROWS>
@@ -471,6 +495,31 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, 
                                                                        ctx->d_psip, logN, logN1, C);
         k_ntt_fwd_p2<<<dim3(N1 / R, (unsigned)nr), 256, R * N2 * 8, st>>>(d, m, ctx->d_mod, ctx->d_psi,
                                                                        ctx->d_psip, logN, logN1, R);
+    }
+}
+
+void ntt_fwd_subscale(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const SubScale &ep) {
+    if (rows <= 0) return;
+    if (ctx->autotune && !ctx->ntt_tuned && ctx->logN >= 14 && ctx->logN <= 16) tune_ntt(ctx, st);
+    int logN = ctx->logN, logN1, C, R;
+    split(logN, logN1, C, R);
+    if (logN < 14 || logN > 16) throw std::logic_error("the fused NTT epilogue needs the register-blocked NTT");
+    for (long r0 = 0; r0 < rows; r0 += 65535) {
+        long nr = rows - r0 < 65535 ? rows - r0 : 65535;
+        u64 *d = data + r0 * (long)ctx->N;
+        RowMap m = rm.shifted(r0);
+        SubScale e = ep;
+        e.row0 = ep.row0 + r0;
+        ctx->n_launch += 2;
+        cudaEvent_t e0;
+        ctx->trace_begin(1, e0);
+        RowSkip none;
+        if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st, none); else fwd_pass<7, false>(ctx, d, nr, m, st, none);
+        if (logN - logN1 == 8) fwd_pass<8, true>(ctx, d, nr, m, st, none, &e); else fwd_pass<7, true>(ctx, d, nr, m, st, none, &e);
+        // algorithmic bytes of the transform: every word read and written once
+        // (the fused epilogue's read of u is not counted, so butterflies per
+        // traced byte stay those of a plain transform)
+        ctx->trace_end(1, e0, 2.0 * nr * ctx->N * 8.0);
     }
 }
 
