@@ -127,6 +127,7 @@ static ModQ make_mod(u64 q) {
     u64 R = (u64)(((u128)1 << 64) % q);
     m.r2 = h_mulmod(R, R, q);
     m.twoq = 2 * q;
+    m.wone = (u64)(((u128)1 << 64) / q);
     return m;
 }
 

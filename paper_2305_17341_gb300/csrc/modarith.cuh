@@ -19,6 +19,7 @@ struct ModQ {
     u64 qinv;    // -q^-1 mod 2^64 (Montgomery)
     u64 r2;      // 2^128 mod q
     u64 twoq;
+    u64 wone;    // floor(2^64 / q): the Shoup companion of 1
 };
 
 __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }
@@ -35,6 +36,13 @@ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wp, u64 q) {
 }
 
 __device__ __forceinline__ u64 reduce2q(u64 a, u64 q) { return a >= q ? a - q : a; }
+
+// a mod q for any 64-bit a: Shoup's product by 1 lands in [0, 2q), then one
+// conditional subtraction.
+__device__ __forceinline__ u64 reduce_any(u64 a, u64 q, u64 wone) {
+    u64 r = a - mulhi64(a, wone) * q;
+    return r >= q ? r - q : r;
+}
 
 __device__ __forceinline__ u64 reduce4q(u64 a, u64 q) {
     a = a >= 2 * q ? a - 2 * q : a;

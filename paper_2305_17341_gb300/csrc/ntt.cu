@@ -190,6 +190,56 @@ struct PassGeom {
     }
 };
 
+// Forward butterfly without the reduction of x: x' = x + t, y' = x - t + 2q
+// (t = w y mod q in [0, 2q)).  Both outputs grow by less than 2q per stage,
+// so from inputs below 4q the 16 stages of a limb stay below 36q < 2^64 for
+// every prime below 2^58 (all the 40-bit levels); larger primes use bf_fwd.
+__device__ __forceinline__ void bf_fwd_nored(u64 &x, u64 &y, u64 w, u64 wp, u64 q) {
+    u64 t = shoup_lazy(y, w, wp, q);
+    u64 a = x;
+    x = a + t;
+    y = a - t + 2 * q;
+}
+
+// The 8 stages of one pass (4 in registers in layout A, a shared-memory
+// transpose, 4 in layout B), leaving the result in shared memory (layout B).
+template <int LM, bool ROWS, bool RED>
+__device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulonglong2 *w2_, long G, int t, int w,
+                                              u64 q) {
+    typedef PassGeom<LM, ROWS> G_;
+    constexpr int M = G_::M, T = G_::T;
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+        const long mb = (long)(M / (2 * T * s)) * G;
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (!(k & s)) {
+                const ulonglong2 wv = __ldg(w2_ + mb + k / (2 * s));
+                if (RED) bf_fwd(x[k], x[k + s], wv.x, wv.y, q);
+                else bf_fwd_nored(x[k], x[k + s], wv.x, wv.y, q);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[G_::sidx(16 * t + k, w)];
+#pragma unroll
+    for (int sp = T / 2; sp >= 1; sp >>= 1) {
+        const long mb = (long)(M / (2 * sp)) * G + (long)t * (8 / sp);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            if (!(k & sp)) {
+                const ulonglong2 wv = __ldg(w2_ + mb + k / (2 * sp));
+                if (RED) bf_fwd(x[k], x[k + sp], wv.x, wv.y, q);
+                else bf_fwd_nored(x[k], x[k + sp], wv.x, wv.y, q);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[G_::sidx(16 * t + k, w)] = x[k];
+    __syncthreads();
+}
+
 template <int LM, bool ROWS, int MINB, bool SUBSC>
 __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm, const ModQ *mods,
                                                             const ulonglong2 *tw2, int logN, RowSkip skip,
@@ -213,34 +263,12 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[(long)(t + T * k) * stride];
-#pragma unroll
-    for (int s = 8; s >= 1; s >>= 1) {
-        const long mb = (long)(M / (2 * T * s)) * G;
-#pragma unroll
-        for (int k = 0; k < 16; k++)
-            if (!(k & s)) {
-                const ulonglong2 w = __ldg(w2_ + mb + k / (2 * s));
-                bf_fwd(x[k], x[k + s], w.x, w.y, q);
-            }
-    }
-#pragma unroll
-    for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = x[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 16; k++) x[k] = sm[G_::sidx(16 * t + k, w)];
-#pragma unroll
-    for (int sp = T / 2; sp >= 1; sp >>= 1) {
-        const long mb = (long)(M / (2 * sp)) * G + (long)t * (8 / sp);
-#pragma unroll
-        for (int k = 0; k < 16; k++)
-            if (!(k & sp)) {
-                const ulonglong2 w = __ldg(w2_ + mb + k / (2 * sp));
-                bf_fwd(x[k], x[k + sp], w.x, w.y, q);
-            }
-    }
-#pragma unroll
-    for (int k = 0; k < 16; k++) sm[G_::sidx(16 * t + k, w)] = x[k];
-    __syncthreads();
+    const bool red = q >= (1ull << 58);   // uniform over the CTA
+    if (red) fwd_pass_body<LM, ROWS, true>(x, sm, w2_, G, t, w, q);
+    else fwd_pass_body<LM, ROWS, false>(x, sm, w2_, G, t, w, q);
+    // the row pass ends with exact residues: [0, 4q) after reducing
+    // butterflies, below 36q after the others
+    const u64 wone = mods[pidx].wone;
     if (ROWS && SUBSC) {
         const long arow = ep.row0 + row;
         const long it = arow / ep.rows_per_item;
@@ -251,7 +279,8 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
         u64 *op = ep.out + it * ep.os + off;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
-            const u64 v = reduce4q(sm[G_::sidx(t + T * k, w)], q);
+            const u64 s = sm[G_::sidx(t + T * k, w)];
+            const u64 v = red ? reduce4q(s, q) : reduce_any(s, q, wone);
             op[t + T * k] = shoup(submod(up[t + T * k], v, q), wr.w, wr.wp, q);
         }
         return;
@@ -259,7 +288,8 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = sm[G_::sidx(t + T * k, w)];
-        p[(long)(t + T * k) * stride] = ROWS ? reduce4q(v, q) : v;
+        if (ROWS) v = red ? reduce4q(v, q) : reduce_any(v, q, wone);
+        p[(long)(t + T * k) * stride] = v;
     }
 }
 
