@@ -616,6 +616,11 @@ def run_served(args):
     Xc2 = workloads.lowrank_dataset(256, t, 2)
     cov_in = [pk.he_encrypt_matrix(ctx2, Xc2[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 600 + 2 * l + j)
               for l in range(2) for j in range(k)]
+    big_rows = 4096
+    want_big = any(kd == "covariance_large" for _, kd in mix)
+    Xbig = workloads.lowrank_dataset(big_rows, t, 7) if want_big else None
+    cov_big = ([pk.he_encrypt_matrix(ctx2, Xbig[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 20000 + 2 * l + j)
+                for l in range(big_rows // n) for j in range(k)] if want_big else [])
     want_pca = any(kd == "pca" for _, kd in mix) and not args.no_pca
     ctxs = [ctx2]
     pca_in, counts = [], None
@@ -645,6 +650,9 @@ def run_served(args):
         if kind == "covariance":
             return pk.he_server_submit(srv, pk.HE_JOB_COVARIANCE, cov_in, n=n, n1z=n1, n1t=n1, n_row_blocks=2, k=k,
                                        s=256)
+        if kind == "covariance_large":
+            return pk.he_server_submit(srv, pk.HE_JOB_COVARIANCE, cov_big, n=n, n1z=n1, n1t=n1,
+                                       n_row_blocks=big_rows // n, k=k, s=big_rows)
         return pk.he_server_submit(srv, pk.HE_JOB_PCA, pca_in, n=n, k=k, l_E=args.components, l_P=args.pm_iters,
                                    axis=0, counts=counts, B2=2.0 ** 16, refresh_obj=(1 << 20) + (idx << 16))
 
@@ -692,13 +700,13 @@ def run_served(args):
     res = drain(ids)
     wall = time.perf_counter() - t0
     ck = clocks.stop()
-    names = {1: "matmul", 2: "covariance", 3: "xtx_block", 4: "xtx_final", 5: "pca"}
+    names = {1: "matmul", 2: "covariance (both sizes)", 3: "xtx_block", 4: "xtx_final", 5: "pca"}
     per_kind = {}
     for kd, name in names.items():
         st = pk.he_server_stats(srv, kd)
         if st["submitted"]:
-            per_kind[name] = {x: st[x] for x in ("submitted", "admitted", "rejected", "completed", "failed",
-                                                 "p50_ms", "p99_ms", "mean_ms", "max_ms")}
+            per_kind[name] = {x: st[x] for x in ("submitted", "admitted", "waited", "rejected", "completed",
+                                                 "failed", "p50_ms", "p99_ms", "mean_ms", "max_ms")}
     st = pk.he_server_stats(srv, 0)
     pk.he_server_destroy(srv)
     # ---- checks against FP64 (decrypted, untimed)
@@ -716,6 +724,12 @@ def run_served(args):
         if kind == "matmul" and "matmul_max_abs_err" not in check:
             A, B = pairs[[jj for jj, kk in ids if kk == "matmul"].index(j) % len(mm)]
             check["matmul_max_abs_err"] = float(np.abs(pk.he_decrypt_matrix(ctx2, r[0], n, n) - A @ B).max())
+        if kind == "covariance_large" and "covariance_large_max_abs_err" not in check:
+            Xc = Xbig - Xbig.mean(0)
+            ref = Xc.T @ Xc / big_rows
+            check["covariance_large_max_abs_err"] = max(
+                float(np.abs(pk.he_decrypt_matrix(ctx2, r[a * k + b], n, n) - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max())
+                for a in range(k) for b in range(k))
         if kind == "covariance" and "covariance_max_abs_err" not in check:
             Xc = Xc2 - Xc2.mean(0)
             ref = Xc.T @ Xc / 256
@@ -730,17 +744,17 @@ def run_served(args):
         "value": st["jobs_per_s"], "unit": "jobs/s", "higher_is_better": True, "n_gpus": 1,
         "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"], "max": st["max_ms"]},
         "per_kind": per_kind,
-        "admitted": st["admitted"], "rejected": st["rejected"], "failed": failed,
+        "admitted": st["admitted"], "waited": st["waited"], "rejected": st["rejected"], "failed": failed,
         "ticks": st["ticks"], "products": st["products"],
         "products_per_tick": st["products"] / max(1, st["ticks"]), "max_products_per_tick": st["max_products_per_tick"],
         "key_bytes": st["key_bytes"], "wall_s": wall, "clocks": ck,
         "config": {"workload": "Poisson arrivals at %.2f jobs/s for %.0f s: X^T X row blocks (128x256 each, one "
-                               "accumulator, %d blocks), 128x128 products, 256x256 covariances, top-%d PCA; "
-                               "N=2^16, covariance chain 60+20x40 / PowerMethod chain 60+13x40, p 2x60"
+                               "accumulator, %d blocks), 128x128 products, 256x256 and 4096x256 covariances, "
+                               "top-%d PCA; N=2^16, covariance chain 60+20x40 / PowerMethod chain 60+13x40, p 2x60"
                                % (args.rate, args.duration, nb, args.components),
                    "budget_gb": args.budget_gb, "max_batch": args.max_batch, "jobs": len(mix)},
         "check": dict(check, tol=1e-4)}), flush=True)
-    for h in [x for blk in stream for x in blk] + [x for p in mm for x in p] + cov_in + pca_in:
+    for h in [x for blk in stream for x in blk] + [x for p in mm for x in p] + cov_in + cov_big + pca_in:
         pk.he_ct_free(h)
     for c in ctxs:
         pk.he_ctx_destroy(c)
@@ -1002,8 +1016,8 @@ def main():
                                                            "keyswitch", "transforms"])
     ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
     ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
-    ap.add_argument("--rate", type=float, default=1.5, help="served: arrivals per second")
-    ap.add_argument("--duration", type=float, default=30.0, help="served: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")
+    ap.add_argument("--duration", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
     ap.add_argument("--max-batch", type=int, default=8, help="served: products per batched pass")
     ap.add_argument("--no-pca", action="store_true", help="served: leave PCA jobs out of the mix")

@@ -364,13 +364,17 @@ int he_mm_plan_destroy(he_mm_plan *plan);
  * Admission: every job is charged an estimate of the device bytes it holds
  * from admission until its results are taken (its batched temporaries, the
  * intermediates of its circuit and its outputs; resident keys are not
- * charged).  A job whose charge would take the total above hbm_budget_bytes
- * is rejected with HE_ERR_ADMISSION and counted. */
+ * charged).  A job whose charge alone exceeds hbm_budget_bytes is rejected
+ * with HE_ERR_ADMISSION.  A job that fits the budget but not what is left of
+ * it waits (HE_JOB_WAITING) and is admitted, in submission order, as earlier
+ * jobs give their charges back (completion without outputs, or
+ * he_server_result) -- unless reject_when_full is set, which rejects it. */
 typedef struct he_server he_server;
 
 typedef struct he_server_cfg {
     double hbm_budget_bytes; /* bound on the summed charges of admitted jobs */
     int max_batch;           /* products per batched pass (>= 1) */
+    int reject_when_full;    /* 0: a job that does not fit now waits; 1: it is rejected */
 } he_server_cfg;
 
 #define HE_JOB_MATMUL 1     /* in: A, B; out: A*B (one ciphertext) */
@@ -400,9 +404,11 @@ typedef struct he_job {
 #define HE_JOB_RUNNING 1
 #define HE_JOB_DONE 2
 #define HE_JOB_FAILED 3
+#define HE_JOB_WAITING 4  /* accepted, waiting for device memory to be admitted */
 
 typedef struct he_serving_stats {
     long long submitted, admitted, rejected, completed, failed;
+    long long waited;                       /* jobs that waited for admission */
     double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> done latency of completed jobs (nearest rank) */
     double jobs_per_s;                      /* completed jobs / (last completion - first submission) */
     long long ticks, products, max_products_per_tick;

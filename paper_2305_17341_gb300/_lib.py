@@ -45,7 +45,7 @@ class he_refresh_state(ctypes.Structure):
 
 
 class he_server_cfg(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_batch", ctypes.c_int)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_batch", ctypes.c_int), ("reject_when_full", ctypes.c_int)]
 
 
 class he_job(ctypes.Structure):
@@ -58,14 +58,15 @@ class he_job(ctypes.Structure):
 
 
 class he_serving_stats(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "rejected", "completed", "failed")] + \
+    _fields_ = [(k, ctypes.c_longlong) for k in ("submitted", "admitted", "rejected", "completed", "failed",
+                                                 "waited")] + \
                [(k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "jobs_per_s")] + \
                [(k, ctypes.c_longlong) for k in ("ticks", "products", "max_products_per_tick")] + \
                [(k, ctypes.c_double) for k in ("charged_bytes", "key_bytes")]
 
 
 HE_JOB_MATMUL, HE_JOB_COVARIANCE, HE_JOB_XTX_BLOCK, HE_JOB_XTX_FINAL, HE_JOB_PCA = 1, 2, 3, 4, 5
-HE_JOB_QUEUED, HE_JOB_RUNNING, HE_JOB_DONE, HE_JOB_FAILED = 0, 1, 2, 3
+HE_JOB_QUEUED, HE_JOB_RUNNING, HE_JOB_DONE, HE_JOB_FAILED, HE_JOB_WAITING = 0, 1, 2, 3, 4
 
 P = ctypes.POINTER
 vp = ctypes.c_void_p
@@ -455,8 +456,8 @@ def he_counters(ctx, reset=False):
 
 
 # ------------------------------------------------------------- serving
-def he_server_create(ctxs, hbm_budget_bytes, max_batch=8):
-    cfg = he_server_cfg(float(hbm_budget_bytes), max_batch)
+def he_server_create(ctxs, hbm_budget_bytes, max_batch=8, reject_when_full=False):
+    cfg = he_server_cfg(float(hbm_budget_bytes), max_batch, 1 if reject_when_full else 0)
     h = vp()
     check(lib().he_server_create(ctypes.byref(cfg), _handles(ctxs), len(ctxs), ctypes.byref(h)))
     return h

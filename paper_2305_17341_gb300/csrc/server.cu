@@ -36,7 +36,6 @@ struct Job {
     std::string msg;
     double t_submit = 0, t_done = 0;
     double charge = 0;            // released when the results are taken
-    double acc_charge = 0;        // accumulator bytes released when a FINAL completes
     std::vector<he_ct *> out;
     std::vector<int> aux;
     // per-tick state
@@ -75,6 +74,8 @@ double key_bytes(const Ctx *c) {
 
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+bool finished(const Job *J) { return J->status == HE_JOB_DONE || J->status == HE_JOB_FAILED; }
+
 }  // namespace
 
 struct he_server {
@@ -83,6 +84,7 @@ struct he_server {
     std::condition_variable cv_work, cv_done;
     std::vector<std::unique_ptr<Worker>> workers;
     std::unordered_map<uint64_t, Job *> jobs;
+    std::deque<Job *> waiting;                          // accepted, not yet admitted (FIFO)
     std::set<std::pair<Ctx *, uint64_t>> acc_charged;   // accumulators already charged
     std::map<std::pair<Ctx *, uint64_t>, double> acc_bytes;
     uint64_t next_id = 1;
@@ -90,7 +92,8 @@ struct he_server {
     bool stop = false;
     Clock::time_point t0 = Clock::now();
     // statistics, per kind (index 0: all)
-    long long submitted[6] = {}, admitted[6] = {}, rejected[6] = {}, completed[6] = {}, failed[6] = {};
+    long long submitted[6] = {}, admitted[6] = {}, rejected[6] = {}, completed[6] = {}, failed[6] = {},
+              waited[6] = {};
     std::vector<double> lat[6];
     double first_submit[6], last_done[6];
     long long ticks = 0, products = 0, max_tick_products = 0;
@@ -106,6 +109,36 @@ struct he_server {
     }
     void run(Worker *w);
     void tick(Worker *w, std::vector<Job *> &batch);
+    // accumulator bytes a row-block job adds when it is admitted (caller holds m)
+    double acc_extra(const Job *J) const {
+        if (J->spec.kind != HE_JOB_XTX_BLOCK || acc_charged.count(std::make_pair(J->c, J->spec.acc_id))) return 0;
+        return (double)J->spec.k * (J->spec.k + 1) / 2 * ct_bytes(J->c, J->in[0]->level - 4);
+    }
+    // charges the job and queues it on its context's worker (caller holds m)
+    void admit(Job *J) {
+        const double extra = acc_extra(J);
+        charged += J->charge;
+        if (extra > 0) {
+            auto key = std::make_pair(J->c, J->spec.acc_id);
+            acc_charged.insert(key);
+            acc_bytes[key] = extra;
+            charged += extra;
+        }
+        const int kd = J->spec.kind;
+        for (int x : {0, kd}) admitted[x]++;
+        J->status = HE_JOB_QUEUED;
+        worker_of(J->c)->q.push_back(J);
+        cv_work.notify_all();
+    }
+    // admits waiting jobs, in order, while they fit (caller holds m)
+    void admit_waiting() {
+        while (!waiting.empty()) {
+            Job *J = waiting.front();
+            if (charged + J->charge + acc_extra(J) > cfg.hbm_budget_bytes) break;
+            waiting.pop_front();
+            admit(J);
+        }
+    }
 };
 
 // --------------------------------------------------------------- one tick
@@ -289,6 +322,7 @@ void he_server::tick(Worker *w, std::vector<Job *> &batch) {
             acc_charged.erase(key);
         }
     }
+    admit_waiting();
     cv_done.notify_all();
 }
 
@@ -458,16 +492,7 @@ int he_server_submit(he_server *S, const he_job *j, uint64_t *job_id) {
         return rc;
     }
     if (S->stop) return reject("the server is stopping", HE_ERR_ARG);
-    auto acc_key = std::make_pair(c, j->acc_id);
-    double acc_extra = 0;
-    if (kind == HE_JOB_XTX_BLOCK && !S->acc_charged.count(acc_key))
-        acc_extra = (double)j->k * (j->k + 1) / 2 * ct_bytes(c, j->in[0]->level - 4);
-    if (S->charged + charge + acc_extra > S->cfg.hbm_budget_bytes) {
-        for (int x : {0, kind}) S->rejected[x]++;
-        return reject("rejected by the device-memory budget", HE_ERR_ADMISSION);
-    }
     Job *J = new Job;
-    J->id = S->next_id++;
     J->spec = *j;
     J->in.assign(j->in, j->in + j->n_in);
     J->spec.in = nullptr;
@@ -477,21 +502,26 @@ int he_server_submit(he_server *S, const he_job *j, uint64_t *job_id) {
     }
     J->c = c;
     J->charge = charge;
+    const double extra = S->acc_extra(J);
+    const bool fits_now = S->waiting.empty() && S->charged + charge + extra <= S->cfg.hbm_budget_bytes;
+    if (charge + extra > S->cfg.hbm_budget_bytes || (!fits_now && S->cfg.reject_when_full)) {
+        delete J;
+        for (int x : {0, kind}) S->rejected[x]++;
+        return reject("rejected by the device-memory budget", HE_ERR_ADMISSION);
+    }
+    J->id = S->next_id++;
     J->t_submit = S->now();
-    S->charged += charge;
-    if (acc_extra > 0) {
-        S->acc_charged.insert(acc_key);
-        S->acc_bytes[acc_key] = acc_extra;
-        S->charged += acc_extra;
-    }
-    for (int x : {0, kind}) {
-        S->admitted[x]++;
+    for (int x : {0, kind})
         if (S->first_submit[x] < 0) S->first_submit[x] = J->t_submit;
-    }
     S->jobs[J->id] = J;
-    S->worker_of(c)->q.push_back(J);
+    if (fits_now) {
+        S->admit(J);
+    } else {
+        J->status = HE_JOB_WAITING;
+        S->waiting.push_back(J);
+        for (int x : {0, kind}) S->waited[x]++;
+    }
     *job_id = J->id;
-    S->cv_work.notify_all();
     return HE_OK;
 }
 
@@ -503,7 +533,7 @@ int he_server_poll(he_server *S, uint64_t id, int *status, int *error, double *l
     Job *J = it->second;
     if (status) *status = J->status;
     if (error) *error = J->err;
-    if (latency_ms) *latency_ms = J->status >= HE_JOB_DONE ? 1000.0 * (J->t_done - J->t_submit) : 0.0;
+    if (latency_ms) *latency_ms = finished(J) ? 1000.0 * (J->t_done - J->t_submit) : 0.0;
     return HE_OK;
 }
 
@@ -514,7 +544,7 @@ int he_server_wait(he_server *S, uint64_t id, double timeout_s, int *status) {
     if (it == S->jobs.end()) return reject("unknown job id", HE_ERR_ARG);
     Job *J = it->second;
     bool ok = S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
-                                  [&] { return J->status >= HE_JOB_DONE; });
+                                  [&] { return finished(J); });
     if (status) *status = J->status;
     if (!ok) return reject("timed out waiting for the job", HE_ERR_TIMEOUT);
     return HE_OK;
@@ -527,13 +557,14 @@ int he_server_result(he_server *S, uint64_t id, he_ct **outs, int max_outs, int 
     auto it = S->jobs.find(id);
     if (it == S->jobs.end()) return reject("unknown job id", HE_ERR_ARG);
     Job *J = it->second;
-    if (J->status < HE_JOB_DONE) return reject("the job has not finished", HE_ERR_ARG);
+    if (!finished(J)) return reject("the job has not finished", HE_ERR_ARG);
     if (J->status == HE_JOB_FAILED) {
         int code = J->err ? J->err : HE_ERR_ARG;
         set_error(J->msg);
         S->charged -= J->charge;
         S->jobs.erase(it);
         delete J;
+        S->admit_waiting();
         return code;
     }
     if ((int)J->out.size() > max_outs) return reject("max_outs is smaller than the job's outputs", HE_ERR_ARG);
@@ -546,6 +577,7 @@ int he_server_result(he_server *S, uint64_t id, he_ct **outs, int max_outs, int 
     S->charged -= J->charge;
     S->jobs.erase(it);
     delete J;
+    S->admit_waiting();
     return HE_OK;
 }
 
@@ -558,6 +590,7 @@ int he_server_stats(he_server *S, int kind, he_serving_stats *o) {
     r.rejected = S->rejected[kind];
     r.completed = S->completed[kind];
     r.failed = S->failed[kind];
+    r.waited = S->waited[kind];
     std::vector<double> v = S->lat[kind];
     std::sort(v.begin(), v.end());
     auto rank = [&](double q) {
@@ -590,6 +623,12 @@ int he_server_destroy(he_server *S) {
     {
         std::lock_guard<std::mutex> lk(S->m);
         S->stop = true;
+        // jobs never admitted are dropped (they hold no device memory)
+        for (Job *J : S->waiting) {
+            S->jobs.erase(J->id);
+            delete J;
+        }
+        S->waiting.clear();
     }
     S->cv_work.notify_all();
     for (auto &w : S->workers)

@@ -57,8 +57,8 @@ def poisson_arrivals(rate, duration, seed):
         out.append(t)
 
 
-def served_job_mix(rate, duration, seed, weights=(("xtx_block", 0.60), ("matmul", 0.25), ("covariance", 0.12),
-                                                  ("pca", 0.03))):
+def served_job_mix(rate, duration, seed, weights=(("xtx_block", 0.55), ("matmul", 0.25), ("covariance", 0.12),
+                                                  ("covariance_large", 0.03), ("pca", 0.05))):
     """A served workload: Poisson arrivals, each labelled with a job kind drawn
     from `weights`.  Returns [(t, kind)] in arrival order."""
     ts = poisson_arrivals(rate, duration, seed)

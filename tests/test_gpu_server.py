@@ -177,3 +177,53 @@ def test_served_pca_equals_alone(env):
             assert _same(pk, ctx, outs[l_E + m * k + jj], V[m][jj])
     for h in outs + lams + [x for v in V for x in v] + cov + v0:
         pk.he_ct_free(h)
+
+
+def test_jobs_wait_for_memory_and_are_admitted_in_order(env):
+    """A budget that holds one product's charge: later products wait
+    (HE_JOB_WAITING) and are admitted in order as results are taken; each
+    result equals the direct call.  reject_when_full turns waiting into
+    HE_ERR_ADMISSION."""
+    from paper_2305_17341_gb300.workloads import matmul_pair
+    pk, ctx, n, n1 = env
+    L = len(QBITS) - 1
+    pairs = [matmul_pair(n, 200 + i) for i in range(3)]
+    cts = [(pk.he_encrypt_matrix(ctx, A, L, 2 * i), pk.he_encrypt_matrix(ctx, B, L, 2 * i + 1))
+           for i, (A, B) in enumerate(pairs)]
+    srv = pk.he_server_create([ctx], 64e9)
+    j = pk.he_server_submit(srv, pk.HE_JOB_MATMUL, list(cts[0]), n=n, n1z=n1, n1t=n1)
+    charge = pk.he_server_stats(srv)["charged_bytes"]
+    pk.he_server_wait(srv, j, 600.0)
+    for h in pk.he_server_result(srv, j)[0]:
+        pk.he_ct_free(h)
+    pk.he_server_destroy(srv)
+    assert charge > 0
+    srv = pk.he_server_create([ctx], 1.5 * charge, max_batch=2)
+    try:
+        ids = [pk.he_server_submit(srv, pk.HE_JOB_MATMUL, list(p), n=n, n1z=n1, n1t=n1) for p in cts]
+        assert [pk.he_server_poll(srv, i)[0] for i in ids[1:]] == [pk.HE_JOB_WAITING] * 2
+        outs = []
+        for i in ids:
+            assert pk.he_server_wait(srv, i, 600.0) == pk.HE_JOB_DONE
+            outs.append(pk.he_server_result(srv, i)[0][0])     # frees the charge: the next job is admitted
+        st = pk.he_server_stats(srv)
+        assert (st["admitted"], st["waited"], st["rejected"], st["completed"]) == (3, 2, 0, 3)
+    finally:
+        pk.he_server_destroy(srv)
+    for (a, b), o in zip(cts, outs):
+        ref = pk.he_hmatmul(ctx, a, b, n, n1, n1)
+        assert _same(pk, ctx, o, ref)
+        pk.he_ct_free(ref)
+    srv = pk.he_server_create([ctx], 1.5 * charge, max_batch=2, reject_when_full=True)
+    try:
+        j1 = pk.he_server_submit(srv, pk.HE_JOB_MATMUL, list(cts[0]), n=n, n1z=n1, n1t=n1)
+        with pytest.raises(pk.HeError) as e:
+            pk.he_server_submit(srv, pk.HE_JOB_MATMUL, list(cts[1]), n=n, n1z=n1, n1t=n1)
+        assert e.value.code == pk.HE_ERR_ADMISSION
+        pk.he_server_wait(srv, j1, 600.0)
+        for h in pk.he_server_result(srv, j1)[0]:
+            pk.he_ct_free(h)
+    finally:
+        pk.he_server_destroy(srv)
+    for h in outs + [x for p in cts for x in p]:
+        pk.he_ct_free(h)
