@@ -16,7 +16,7 @@ Diagonals (Sec. 3.3, eq. 2): u_t[p] = U[p, p + t mod n^2].
 """
 import numpy as np
 
-from . import _c
+from . import _c, dcd
 from .ckks import Ct, padd, pmulconst, to_rns
 
 
@@ -74,7 +74,30 @@ def rot_slots(u, r):
 
 # ---------------------------------------------------- schedule parameters
 
-def matmul_rot_steps(n, n1z, n1t, S):
+def dcd_rot_steps(n, n1z, n1t, dcd_z, dcd_t):
+    """Matrix rotation steps of Z and T under the Diagonal Convergence
+    Decomposition (mod n^2): Z_1's left factor (babies j, giants n1z i for
+    0 < i < n2'), Z_2's left factor (giants n1z i, -n2' <= i < 0), the right
+    factors +-n'; T's left factor (babies n j, giants n n1t i, 0 < i <= n2'),
+    whose last giant is also the right factors' step n' n (Table 2 DCDmp)."""
+    n2 = n * n
+    z, t = set(), set()
+    if dcd_z:
+        n2p = dcd_z // n1z
+        z |= {j % n2 for j in range(1, n1z)}
+        z |= {(n1z * i) % n2 for i in range(-n2p, n2p) if i}
+        z |= {dcd_z % n2, (-dcd_z) % n2}
+    if dcd_t:
+        n2p = dcd_t // n1t
+        t |= {(n * j) % n2 for j in range(1, n1t)}
+        t |= {(n * n1t * i) % n2 for i in range(1, n2p + 1)}
+        t.add((n * dcd_t) % n2)
+    z.discard(0)
+    t.discard(0)
+    return sorted(z), sorted(t)
+
+
+def matmul_rot_steps(n, n1z, n1t, S, dcd_z=0, dcd_t=0):
     """Rotation steps of the hoisted JKLS schedule (Table 1 'Optimized' rows):
     replication steps -n^2 2^j (mod S), Z babies 1..n1z-1 and giants n1z*i
     (i in [-n2z, n2z) minus 0), T babies n*j and giants n*n1t*i, plus the C^k
@@ -86,15 +109,22 @@ def matmul_rot_steps(n, n1z, n1t, S):
         steps.add((-r) % S)
         r *= 2
     n2z, n2t = n // n1z, n // n1t
+    zd, td = dcd_rot_steps(n, n1z, n1t, dcd_z, dcd_t)
+    if dcd_z:
+        steps |= set(zd)
+    else:
+        for i in range(-n2z, n2z):
+            if i:
+                steps.add((n1z * i) % n2)
     for j in range(1, n1z):
-        steps.add(j % n2)
-    for i in range(-n2z, n2z):
-        if i:
-            steps.add((n1z * i) % n2)
+        steps.add(j % n2)        # Z babies, also the C^k babies
+    if dcd_t:
+        steps |= set(td)
+    else:
+        for i in range(1, n2t):
+            steps.add((n * n1t * i) % n2)
     for j in range(1, n1t):
-        steps.add((n * j) % n2)
-    for i in range(1, n2t):
-        steps.add((n * n1t * i) % n2)
+        steps.add((n * j) % n2)  # T babies, also the R^k babies
     steps.add(n1z % n2)          # C^k source chain
     steps.add((-n) % n2)         # C^k second source
     if n2t > 1:
@@ -195,6 +225,32 @@ class HMM:
         n2 = n // n1
         return self.lintrans(ct, lambda t: diag_T(n, t), n, n, n1, range(0, n2))
 
+    # --- Diagonal Convergence Decomposition (Sec. 4.2, DMatrixMult) -------
+    def _chain(self, ct, chain, n, a_left, n1, giants_left):
+        """Applies a factor chain [R_1, ..., R_{m-1}, L]: every right factor
+        (diagonals 0 and one step d) as a LinTrans with babies {0, d}; the
+        left factor by double-hoisted BSGS.  One level per factor."""
+        size = n * n
+        for f in chain[:-1]:
+            d = [k for k in dcd.diagonal_set(f, size, True) if k != 0]
+            ct = self.lintrans(ct, lambda t, f=f: dcd.diagonal(f, size, t), d[0], n, 2, range(0, 1))
+        f = chain[-1]
+        return self.lintrans(ct, lambda t: dcd.diagonal(f, size, t), a_left, n, n1, giants_left)
+
+    def sigma_dcd(self, ct, n, n1, n_prime):
+        """Z = Z_1 + Z_2, each the chain of DCDforZ with maximum diagonal n'
+        (n1 | n'); ceil((n-1)/n') levels."""
+        n2p = n_prime // n1
+        c1, c2 = dcd.dcd_Z(n, n_prime)
+        a1 = self._chain(ct, c1, n, 1, n1, range(0, n2p))
+        a2 = self._chain(ct, c2, n, 1, n1, range(-n2p, 1))
+        return self.he.add(a1, a2)
+
+    def tau_dcd(self, ct, n, n1, n_prime):
+        """T as the chain of DCDforT with maximum diagonal n' n (n1 | n')."""
+        n2p = n_prime // n1
+        return self._chain(ct, dcd.dcd_T(n, n_prime), n, n, n1, range(0, n2p + 1))
+
     def transpose(self, ct, n, n1, prescale=None):
         """G (Sec. 3.4): BSGS with a = n - 1 over the 2n-1 diagonals.
         `prescale` multiplies every diagonal by a constant (used to fold 1/s
@@ -210,22 +266,28 @@ class HMM:
             return u * prescale
         return self.lintrans(ct, d, a, n, n1, range(-n2g, n2g))
 
-    def hmatmul(self, ctA, ctB, n, n1z, n1t, relin_once=False):
+    def hmatmul(self, ctA, ctB, n, n1z, n1t, relin_once=False, dcd_z=0, dcd_t=0):
         """JKLS product (eq. 4) with the hoisting of Sec. 4.1 (DMatrixMult with
         no decomposition, reading C11).  Consumes 3 levels.
 
         relin_once: instead of DMatrixMult's relinearised Mult per k, sum the
         tensors (d0, d1, d2) of the n products (exact modular sums: decryption
         d0 + d1 s + d2 s^2 is linear) and relinearise the sum once (App. A
-        Mult applied to the sum).  Not in the paper; n - 1 fewer key switches."""
+        Mult applied to the sum).  Not in the paper; n - 1 fewer key switches.
+
+        dcd_z, dcd_t: when non-zero, Z and T are applied as their Diagonal
+        Convergence Decompositions with maximum diagonal n' = dcd_z (resp.
+        n' n, n' = dcd_t) (DMatrixMult, Sec. 4.2); the product then consumes
+        2 + max(ceil((n-1)/dcd_z), ceil((n-1)/dcd_t)) levels."""
         he, P = self.he, self.P
         n2m = n * n
         A = self.replicate(ctA, n)
         B = self.replicate(ctB, n)
         assert A.level == B.level
-        A0 = self.sigma(A, n, n1z)                 # level l-1
-        B0 = self.tau(B, n, n1t)                   # level l-1
-        l1 = A0.level
+        A0 = self.sigma_dcd(A, n, n1z, dcd_z) if dcd_z else self.sigma(A, n, n1z)   # level l-1 (or l-m)
+        B0 = self.tau_dcd(B, n, n1t, dcd_t) if dcd_t else self.tau(B, n, n1t)
+        l1 = min(A0.level, B0.level)
+        A0, B0 = he.drop(A0, l1), he.drop(B0, l1)
         qp = P.qp(l1)
         n2z, n2t = n // n1z, n // n1t
 

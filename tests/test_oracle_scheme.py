@@ -154,3 +154,33 @@ def test_hmatmul_single_relinearisation():
     _mm(P, he2, n, n1, n1, seed=1)
     assert got == (he2.cnt.MS - (n - 1), he2.cnt.Dp - (n - 1), he2.cnt.MD - (n - 1))
 
+
+
+@pytest.mark.parametrize("n_prime", [4, 8])
+def test_dcd_sigma_tau_and_product_decrypt(n_prime):
+    """Sec. 4.2 DMatrixMult: sigma and tau through their decomposition chains
+    decrypt to the index maps of eq. 5 / eq. 6 and consume ceil((n-1)/n')
+    levels; the product with both decomposed decrypts to A.B."""
+    n, n1 = 16, 4
+    P = Params(9, [60] + [40] * 6, [60])
+    he = CKKS(P, 3)
+    from oracle.hmm import HMM, matmul_rot_steps
+    for s in matmul_rot_steps(n, n1, n1, P.S, n_prime, n_prime):
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    H = HMM(he)
+    rng = np.random.default_rng(n_prime)
+    A, B = rng.uniform(-1, 1, (n, n)), rng.uniform(-1, 1, (n, n))
+    za, zb = np.zeros(P.S), np.zeros(P.S)
+    za[: n * n], zb[: n * n] = A.ravel(), B.ravel()
+    ca, cb = he.encrypt_slots(za, P.L, obj=10), he.encrypt_slots(zb, P.L, obj=11)
+    m = -(-(n - 1) // n_prime)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    s = H.sigma_dcd(H.replicate(ca, n), n, n1, n_prime)
+    t = H.tau_dcd(H.replicate(cb, n), n, n1, n_prime)
+    assert s.level == t.level == P.L - m
+    assert np.abs(he.decrypt_slots(s).real[: n * n].reshape(n, n) - A[i, (i + j) % n]).max() < 1e-6
+    assert np.abs(he.decrypt_slots(t).real[: n * n].reshape(n, n) - B[(i + j) % n, j]).max() < 1e-6
+    cc = H.hmatmul(ca, cb, n, n1, n1, dcd_z=n_prime, dcd_t=n_prime)
+    assert cc.level == P.L - m - 2
+    assert np.abs(he.decrypt_slots(cc).real[: n * n].reshape(n, n) - A @ B).max() < 1e-4

@@ -143,3 +143,66 @@ def test_table3_rotation_key_memory():
         assert round((keys + 1) * key_mib) == rtk, line
         rows += 1
     assert rows == 12
+
+
+# ---------------------------------------------------------------- DCD
+@pytest.mark.parametrize("n,n_prime", [(8, 2), (8, 4), (16, 4), (16, 8), (32, 8)])
+def test_dcd_factors_multiply_back_to_Z_and_T(n, n_prime):
+    """Sec. 4.2: the factor chains of DCDforZ / DCDforT multiply (Boolean
+    product) back to exactly the permutation matrices of eq. 5 / eq. 6; the
+    right factors have only the diagonals 0 and +-n' (Z) or n' n (T); the left
+    factor keeps diagonals inside [0, n'), (-n', 0] (Z) or {t n, t <= n'} (T);
+    each chain has ceil((n-1)/n') factors."""
+    from oracle import dcd
+    size = n * n
+    m = -(-(n - 1) // n_prime)
+    z1, z2 = dcd.dcd_Z(n, n_prime)
+    t = dcd.dcd_T(n, n_prime)
+    assert len(z1) == len(z2) == len(t) == m
+    p1, p2 = dcd.chain_product(z1), dcd.chain_product(z2)
+    assert not (p1 & p2) and (p1 | p2) == dcd.perm_entries(n, "Z")
+    assert dcd.chain_product(t) == dcd.perm_entries(n, "T")
+    # the same matrices from the closed forms of eq. 5 and eq. 6
+    for k in range(-n + 1, n):
+        u = diag_Z(n, k)
+        got = dcd.diagonal(dcd.perm_entries(n, "Z"), size, k)
+        assert np.array_equal(u, got)
+    for f in z1[:-1]:
+        assert dcd.diagonal_set(f, size, True) == [0, n_prime]
+    for f in z2[:-1]:
+        assert dcd.diagonal_set(f, size, True) == [-n_prime, 0]
+    for f in t[:-1]:
+        assert dcd.diagonal_set(f, size, False) == [0, n_prime * n]
+    assert all(0 <= k < n_prime for k in dcd.diagonal_set(z1[-1], size, True))
+    assert all(-n_prime < k <= 0 for k in dcd.diagonal_set(z2[-1], size, True))
+    assert all(k % n == 0 and k // n <= n_prime for k in dcd.diagonal_set(t[-1], size, False))
+
+
+@pytest.mark.parametrize("n,n1,n_prime", [(16, 4, 8), (32, 4, 16), (128, 8, 64), (128, 8, 32), (128, 16, 64),
+                                          (128, 16, 32)])
+def test_dcd_key_sets_match_table2(n, n1, n_prime):
+    """Table 2 DCDmp: MinRotKeys n1 + 2 n2' - 1 (Z) and n1 + n2' - 1 (T),
+    n2' = n'/n1, counted on the actual step sets of the schedule."""
+    from oracle.hmm import dcd_rot_steps
+    z, t = dcd_rot_steps(n, n1, n1, n_prime, n_prime)
+    n2p = n_prime // n1
+    assert len(z) == n1 + 2 * n2p - 1
+    assert len(t) == n1 + n2p - 1
+
+
+def test_dcd_table3_key_memory_rows():
+    """Table 3 DCDmp rows: (keys of the step sets + 1) x 45 MiB."""
+    from oracle.hmm import dcd_rot_steps
+    key_mib = 2 * 5 * 18 * (1 << 15) * 8 / (1 << 20)
+    path = os.path.join(os.path.dirname(__file__), "golden", "table3_rtk.txt")
+    seen = 0
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line or not line.startswith("DCDmp"):
+            continue
+        _, lt, n1, maxdiag, rtk = line.split()
+        z, t = dcd_rot_steps(128, int(n1), int(n1), int(maxdiag), int(maxdiag))
+        keys = len(z) if lt == "Z" else len(t)
+        assert round((keys + 1) * key_mib) == int(rtk), line
+        seen += 1
+    assert seen == 8
