@@ -824,14 +824,19 @@ def run_keyswitch(args):
 # Table 3 (dh-BSGS rows): the paper's Z and T transform times of a 128x128
 # matrix ciphertext, logN 15, 14 levels, Lattigo v4.1.0 on an AMD Ryzen 7
 # 7735HS CPU (seconds; thread count not stated)
-PAPER_TABLE3 = {("Z", 8): 2.004, ("Z", 16): 1.286, ("T", 8): 1.049, ("T", 16): 0.725}
+PAPER_TABLE3 = {("Z", 8, 0): 2.004, ("Z", 8, 64): 1.362, ("Z", 8, 32): 1.249,
+                ("Z", 16, 0): 1.286, ("Z", 16, 64): 1.094, ("Z", 16, 32): 1.179,
+                ("T", 8, 0): 1.049, ("T", 8, 64): 0.701, ("T", 8, 32): 0.652,
+                ("T", 16, 0): 0.725, ("T", 16, 64): 0.572, ("T", 16, 32): 0.613}
 
 
 def run_transforms(args):
     """The Z (sigma) and T (tau) transforms alone, as Table 3 measures them:
     one 128x128 matrix ciphertext at N = 2^15 (n^2 = slots, no replication),
-    chain 60 + 14x40 with 2x60 special primes, input at level 11 so that the
-    run ends at level 10, n1 in {8, 16}; device time per transform."""
+    chain 60 + 14x40 with 2x60 special primes, n1 in {8, 16}, undecomposed
+    (dh-BSGS) and with the Diagonal Convergence Decomposition at maximum
+    diagonal 64 and 32 (depth 2 and 4); the input level is chosen so that
+    every run ends at level 10; device time per transform."""
     import numpy as np
     import torch
 
@@ -844,38 +849,44 @@ def run_transforms(args):
     n, S = 128, 1 << 14
     steps = set()
     for n1 in (8, 16):
-        steps |= set(pk.he_rot_steps_for_matmul(n, n1, n1, S))
+        for np_ in (0, 64, 32):
+            steps |= set(pk.he_rot_steps_for_sched(n, n1, n1, S, np_, np_))
     pk.he_keygen(ctx, sorted(steps), False)
     A, _ = workloads.matmul_pair(n, 5)
-    ct = pk.he_encrypt_matrix(ctx, A, 11, 1)
     info = pk.he_ctx_info(ctx)
-    key_mb = None
     out = {}
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     for name, kind in (("Z", 0), ("T", 1)):
         for n1 in (8, 16):
-            for _ in range(max(2, args.warmup)):
-                pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1))
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(tstream)
-            for _ in range(args.steps):
-                pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1))
-            e1.record(tstream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
-            r = pk.he_linear_transform(ctx, ct, kind, n, n1)
-            d = pk.he_decrypt_matrix(ctx, r, n, n)
-            ref = A[i, (i + j) % n] if kind == 0 else A[(i + j) % n, j]
-            err = float(np.abs(d - ref).max())
-            lv = pk.he_ct_info(r)[0]
-            pk.he_ct_free(r)
-            n2 = n // n1
-            keys = (n1 + 2 * n2 - 2) if kind == 0 else (n1 + n2 - 2)
-            out["%s_n1_%d" % (name, n1)] = {"ms": ms, "end_level": lv, "max_abs_err": err,
-                                            "rotation_keys": keys,
-                                            "paper_s": PAPER_TABLE3[(name, n1)],
-                                            "speedup_vs_paper": PAPER_TABLE3[(name, n1)] * 1e3 / ms}
+            for np_ in (0, 64, 32):
+                depth = -(-(n - 1) // np_) if np_ else 1
+                ct = pk.he_encrypt_matrix(ctx, A, 10 + depth, 1)     # every run ends at level 10
+                for _ in range(max(2, args.warmup)):
+                    pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1, np_))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(tstream)
+                for _ in range(args.steps):
+                    pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1, np_))
+                e1.record(tstream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                r = pk.he_linear_transform(ctx, ct, kind, n, n1, np_)
+                d = pk.he_decrypt_matrix(ctx, r, n, n)
+                ref = A[i, (i + j) % n] if kind == 0 else A[(i + j) % n, j]
+                err = float(np.abs(d - ref).max())
+                lv = pk.he_ct_info(r)[0]
+                pk.he_ct_free(r)
+                pk.he_ct_free(ct)
+                # distinct rotation keys of the transform (Table 2): babies
+                # 1..n1-1 plus the giants (and the +-n' / n'n steps of the
+                # right factors under the decomposition)
+                n2 = (np_ if np_ else n) // n1
+                keys = (n1 + 2 * n2 - (1 if np_ else 2)) if kind == 0 else (n1 + n2 - (1 if np_ else 2))
+                out["%s_n1_%d_maxdiag_%s" % (name, n1, np_ or "n-1")] = {
+                    "ms": ms, "depth": depth, "end_level": lv, "max_abs_err": err,
+                    "rotation_keys": keys, "paper_s": PAPER_TABLE3[(name, n1, np_)],
+                    "speedup_vs_paper": PAPER_TABLE3[(name, n1, np_)] * 1e3 / ms}
     # one rotation key: dnum digits x 2 polys x (L+1+alpha) limbs x N words
     N, L, alpha, dnum = info["N"], info["L"], info["alpha"], info["dnum"]
     key_mb = dnum * 2 * (L + 1 + alpha) * N * 8 / 2 ** 20
@@ -884,8 +895,8 @@ def run_transforms(args):
                       "rotation_key_mib": key_mb,
                       "paper_hardware": "Lattigo v4.1.0, AMD Ryzen 7 7735HS (CPU), logN 15, logQP 760, 14 levels",
                       "config": {"workload": "one 128x128 matrix ciphertext, N=2^15, q 60+14x40, p 2x60 "
-                                             "(logQP 740), level 11 -> 10, n1 in {8, 16}"}}), flush=True)
-    pk.he_ct_free(ct)
+                                             "(logQP 740), ends at level 10, n1 in {8, 16}, "
+                                             "max diagonal n-1 / 64 / 32"}}), flush=True)
     pk.he_ctx_destroy(ctx)
 
 

@@ -73,6 +73,15 @@ typedef struct he_mm_sched {
     int n1_z;
     int n1_t;
     int relin_once;
+    /* Diagonal Convergence Decomposition (Sec. 4.2, DMatrixMult): 0 applies Z
+     * and T undecomposed (one level each, in parallel); n' > 0 applies Z as
+     * the factor chains of DCDforZ with maximum diagonal n' (dcd_z) and T as
+     * the chain of DCDforT with maximum diagonal n' n (dcd_t), trading
+     * ceil((n-1)/n') levels for fewer rotation keys (Table 2).  n' < n and
+     * the baby steps must divide n'.  A product consumes 2 + the longest
+     * chain (3 without decomposition). */
+    int dcd_z;
+    int dcd_t;
 } he_mm_sched;
 
 /* One product of a batch: out = A . B for n x n matrices (eq. 4). */
@@ -142,6 +151,11 @@ int he_keygen(he_ctx *ctx, const int32_t *rot_steps, int n_steps, int want_relin
 int he_rot_steps_for_matmul(int n, int n1_z, int n1_t, int slots, int32_t *out, int *count);
 
 /* Steps of the transposition G (BSGS with stride n-1, baby count n1). */
+/* The rotation steps of the product under a full schedule (baby steps and
+ * decompositions): he_rot_steps_for_matmul's set with Z's and T's steps
+ * replaced by those of their decompositions when dcd_z / dcd_t are set. */
+int he_rot_steps_for_sched(int n, const he_mm_sched *sched, int slots, int32_t *out, int *count);
+
 int he_rot_steps_for_transpose(int n, int n1, int slots, int32_t *out, int *count);
 
 /* Encode (App. A) a real slot vector z[0..nslots) (rest zero) at scale
@@ -231,13 +245,16 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
  * (Sec. 3.3.1, Table 1 "Optimized" rows): kind 0 = sigma (the Z transform
  * of eq. 5, diagonals k, -n < k < n), 1 = tau (T of eq. 6, diagonals n k,
  * 0 <= k < n), 2 = the transpose G (diagonals (n - 1) k); n1 baby steps.
- * Replicates a zero-padded input to period n^2 first; consumes one level
- * (the plaintext diagonals are encoded at scale q_l and rescaled away, so
- * the scale is kept).  Errors: HE_ERR_ARG, HE_ERR_LEVEL, HE_ERR_KEY_MISSING. */
+ * With n_prime > 0 (kinds 0 and 1) the transform runs as its Diagonal
+ * Convergence Decomposition (Sec. 4.2) with maximum diagonal n' (Z) or n' n
+ * (T): ceil((n-1)/n') factor transforms, one level each.
+ * Replicates a zero-padded input to period n^2 first; consumes one level per
+ * factor (the plaintext diagonals are encoded at scale q_l and rescaled away,
+ * so the scale is kept).  Errors: HE_ERR_ARG, HE_ERR_LEVEL, HE_ERR_KEY_MISSING. */
 #define HE_LT_SIGMA 0
 #define HE_LT_TAU 1
 #define HE_LT_TRANSPOSE 2
-int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, he_ct **out);
+int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, int n_prime, he_ct **out);
 
 /* State of the interactive modulus refresh (Sec. 7.2.3, App. C): the Philox
  * object of the next refresh is next_obj + 1; count counts refreshes. */

@@ -33,7 +33,8 @@ class he_params(ctypes.Structure):
 
 
 class he_mm_sched(ctypes.Structure):
-    _fields_ = [("n1_z", ctypes.c_int), ("n1_t", ctypes.c_int), ("relin_once", ctypes.c_int)]
+    _fields_ = [("n1_z", ctypes.c_int), ("n1_t", ctypes.c_int), ("relin_once", ctypes.c_int), ("dcd_z", ctypes.c_int),
+                ("dcd_t", ctypes.c_int)]
 
 
 class he_mm_job(ctypes.Structure):
@@ -91,6 +92,7 @@ SIGNATURES = {
     "he_keygen": [vp, i32p, ip, ip],
     "he_rot_steps_for_matmul": [ip, ip, ip, ip, i32p, P(ip)],
     "he_rot_steps_for_transpose": [ip, ip, ip, i32p, P(ip)],
+    "he_rot_steps_for_sched": [ip, P(he_mm_sched), ip, i32p, P(ip)],
     "he_encrypt_slots": [vp, dblp, ip, ip, ctypes.c_uint64, P(vp)],
     "he_encrypt_matrix": [vp, dblp, ip, ip, ip, ctypes.c_uint64, P(vp)],
     "he_decrypt_slots": [vp, vp, dblp, ip],
@@ -109,7 +111,7 @@ SIGNATURES = {
     "he_hmatmul": [vp, vp, vp, ip, P(he_mm_sched), P(vp)],
     "he_hmatmul_batch": [P(he_mm_job), ip, P(vp)],
     "he_transpose": [vp, vp, ip, ip, ctypes.c_double, P(vp)],
-    "he_linear_transform": [vp, vp, ip, ip, ip, P(vp)],
+    "he_linear_transform": [vp, vp, ip, ip, ip, ip, P(vp)],
     "he_refresh": [vp, vp, P(he_refresh_state), P(vp)],
     "he_aggregate": [vp, vp, ip, ip, P(vp)],
     "he_covariance": [vp, P(vp), ip, ip, ip, ip, ip, P(he_mm_sched), P(vp)],
@@ -243,6 +245,14 @@ def he_rot_steps_for_matmul(n, n1z, n1t, slots):
     return [int(x) for x in out[: cnt.value]]
 
 
+def he_rot_steps_for_sched(n, n1z, n1t, slots, dcd_z=0, dcd_t=0):
+    out = (ctypes.c_int32 * (8 * n + 64))()
+    cnt = ctypes.c_int()
+    s = he_mm_sched(n1z, n1t, 0, dcd_z, dcd_t)
+    check(lib().he_rot_steps_for_sched(n, ctypes.byref(s), slots, out, ctypes.byref(cnt)))
+    return list(out[:cnt.value])
+
+
 def he_rot_steps_for_transpose(n, n1, slots):
     out = np.zeros(4 * n + 64, dtype=np.int32)
     cnt = ctypes.c_int()
@@ -341,8 +351,8 @@ def he_replicate(ctx, ct, n):
     return _unary("he_replicate", ctx, ct, n)
 
 
-def he_hmatmul(ctx, A, B, n, n1z, n1t, relin_once=False):
-    s = he_mm_sched(n1z, n1t, 1 if relin_once else 0)
+def he_hmatmul(ctx, A, B, n, n1z, n1t, relin_once=False, dcd_z=0, dcd_t=0):
+    s = he_mm_sched(n1z, n1t, 1 if relin_once else 0, dcd_z, dcd_t)
     return _unary("he_hmatmul", ctx, A, B, n, ctypes.byref(s))
 
 
@@ -360,8 +370,8 @@ def he_transpose(ctx, ct, n, n1, prescale=1.0):
 HE_LT_SIGMA, HE_LT_TAU, HE_LT_TRANSPOSE = 0, 1, 2
 
 
-def he_linear_transform(ctx, ct, kind, n, n1):
-    return _unary("he_linear_transform", ctx, ct, kind, n, n1)
+def he_linear_transform(ctx, ct, kind, n, n1, n_prime=0):
+    return _unary("he_linear_transform", ctx, ct, kind, n, n1, n_prime)
 
 
 def _handles(hs):
@@ -464,14 +474,15 @@ def he_server_create(ctxs, hbm_budget_bytes, max_batch=8, reject_when_full=False
 
 
 def he_server_submit(srv, kind, inputs=(), ctx=None, n=0, n1z=1, n1t=1, n_row_blocks=0, k=0, s=0, centered=False,
-                     acc_id=0, l_E=0, l_P=0, axis=0, counts=None, B2=0.0, refresh_obj=0, relin_once=False):
+                     acc_id=0, l_E=0, l_P=0, axis=0, counts=None, B2=0.0, refresh_obj=0, relin_once=False,
+                     dcd_z=0, dcd_t=0):
     """Queues one job (see include/he.h, he_job); returns its id.  Raises
     HeError (HE_ERR_ADMISSION when over the budget)."""
     arr = _handles(list(inputs)) if len(inputs) else None
     cs = (ctypes.c_int * len(counts))(*counts) if counts else None
     j = he_job(kind, ctx.value if isinstance(ctx, vp) else ctx,
                ctypes.cast(arr, P(vp)) if arr is not None else None, len(inputs), n,
-               he_mm_sched(n1z, n1t, 1 if relin_once else 0),
+               he_mm_sched(n1z, n1t, 1 if relin_once else 0, dcd_z, dcd_t),
                n_row_blocks, k, s, 1 if centered else 0, acc_id, l_E, l_P, axis,
                ctypes.cast(cs, P(ctypes.c_int)) if cs is not None else None, B2, refresh_obj)
     jid = ctypes.c_uint64()
@@ -513,13 +524,14 @@ def he_server_destroy(srv):
 
 # ---------------------------------------------------------- graph plans
 def _mm_jobs(jobs):
-    """(A, B, n, n1z, n1t[, relin_once]) tuples -> he_mm_job array."""
+    """(A, B, n, n1z, n1t[, relin_once[, dcd_z, dcd_t]]) tuples -> he_mm_job array."""
     arr = (he_mm_job * len(jobs))()
     for i, j in enumerate(jobs):
         a, b, n, n1z, n1t = j[:5]
         once = 1 if len(j) > 5 and j[5] else 0
+        dz, dt = (j[6], j[7]) if len(j) > 7 else (0, 0)
         arr[i] = he_mm_job(a.value if isinstance(a, vp) else a, b.value if isinstance(b, vp) else b, n,
-                           he_mm_sched(n1z, n1t, once))
+                           he_mm_sched(n1z, n1t, once, dz, dt))
     return arr
 
 

@@ -71,16 +71,31 @@ static void add_mod(std::set<long> &s, long v, long m) { s.insert(((v % m) + m) 
 // Table 1 "Optimized" key set of the product: replication steps -n^2 2^j,
 // Z babies j and giants n1z*i (-n2z <= i < n2z), T babies n*j and giants
 // n*n1t*i, and the C^k / R^k source steps n1z, -n and n*n1t.
-std::vector<long> matmul_steps(int n, int n1z, int n1t, long slots) {
+std::vector<long> matmul_steps(int n, int n1z, int n1t, long slots, int dcd_z, int dcd_t) {
     long n2 = (long)n * n;
     std::set<long> st;
     for (long r = n2; r < slots; r *= 2) add_mod(st, -r, slots);
     int n2z = n / n1z, n2t = n / n1t;
-    for (int j = 1; j < n1z; j++) add_mod(st, j, n2);
-    for (int i = -n2z; i < n2z; i++)
-        if (i) add_mod(st, (long)n1z * i, n2);
-    for (int j = 1; j < n1t; j++) add_mod(st, (long)n * j, n2);
-    for (int i = 1; i < n2t; i++) add_mod(st, (long)n * n1t * i, n2);
+    for (int j = 1; j < n1z; j++) add_mod(st, j, n2);   // Z babies, also the C^k babies
+    if (dcd_z) {
+        // Z_1 left giants 0 < i < n2', Z_2 left giants -n2' <= i < 0, right factors +-n'
+        const int p2 = dcd_z / n1z;
+        for (int i = -p2; i < p2; i++)
+            if (i) add_mod(st, (long)n1z * i, n2);
+        add_mod(st, dcd_z, n2);
+        add_mod(st, -dcd_z, n2);
+    } else {
+        for (int i = -n2z; i < n2z; i++)
+            if (i) add_mod(st, (long)n1z * i, n2);
+    }
+    for (int j = 1; j < n1t; j++) add_mod(st, (long)n * j, n2);   // T babies, also the R^k babies
+    if (dcd_t) {
+        // T left giants n n1t i, 0 < i <= n2' (the last one is the right factors' step n' n)
+        const int p2 = dcd_t / n1t;
+        for (int i = 1; i <= p2; i++) add_mod(st, (long)n * n1t * i, n2);
+    } else {
+        for (int i = 1; i < n2t; i++) add_mod(st, (long)n * n1t * i, n2);
+    }
     add_mod(st, n1z, n2);
     add_mod(st, -n, n2);
     if (n2t > 1) add_mod(st, (long)n * n1t, n2);
@@ -198,6 +213,8 @@ int he_ctx_destroy(he_ctx *ctx) {
     for (auto &kv : c.rtk) cudaFree(kv.second);
     if (c.rlk) cudaFree(c.rlk);
     for (auto &kv : c.ptcache) cudaFree(kv.second);
+    for (auto &kv : c.dcd)
+        for (auto &f : kv.second.factors) cudaFree(f.dev);
     void *ptrs[] = {c.d_mod, c.d_psi, c.d_psip, c.d_ipsi, c.d_ipsip, c.d_psi2, c.d_ipsi2, c.d_ninv, c.d_dn_pinv,
                     c.d_dn_pmod,
                     c.d_dn_Pinv, c.d_Pmod, c.d_dn_hp, c.d_dn_hq, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM,
@@ -309,6 +326,19 @@ int he_rot_steps_for_matmul(int n, int n1z, int n1t, int slots, int32_t *out, in
     if (!out || !count || n < 1 || n1z < 1 || n1t < 1 || n % n1z || n % n1t || (long)n * n > slots)
         return fail(HE_ERR_ARG, "bad arguments");
     std::vector<long> st = matmul_steps(n, n1z, n1t, slots);
+    for (size_t k = 0; k < st.size(); k++) out[k] = (int32_t)st[k];
+    *count = (int)st.size();
+    return HE_OK;
+}
+
+int he_rot_steps_for_sched(int n, const he_mm_sched *sched, int slots, int32_t *out, int *count) {
+    if (!sched || !out || !count || n < 2 || sched->n1_z < 1 || sched->n1_t < 1 || n % sched->n1_z ||
+        n % sched->n1_t || (long)n * n > slots)
+        return fail(HE_ERR_ARG, "bad arguments");
+    if ((sched->dcd_z && (sched->dcd_z >= n || sched->dcd_z % sched->n1_z)) ||
+        (sched->dcd_t && (sched->dcd_t >= n || sched->dcd_t % sched->n1_t)))
+        return fail(HE_ERR_ARG, "a decomposition needs n' < n with the baby steps dividing n'");
+    std::vector<long> st = matmul_steps(n, sched->n1_z, sched->n1_t, slots, sched->dcd_z, sched->dcd_t);
     for (size_t k = 0; k < st.size(); k++) out[k] = (int32_t)st[k];
     *count = (int)st.size();
     return HE_OK;
@@ -584,13 +614,17 @@ static int check_sched(Ctx &c, int n, const he_mm_sched *s) {
     if (!pow2(n) || (long)n * n > c.S) return fail(HE_ERR_ARG, "n must be a power of two with n^2 <= slots");
     if (!pow2(s->n1_z) || !pow2(s->n1_t) || s->n1_z > n || s->n1_t > n || s->n1_z > 32 || s->n1_t > 32)
         return fail(HE_ERR_ARG, "baby-step counts must be powers of two dividing n (<= 32)");
+    if (s->dcd_z < 0 || s->dcd_t < 0 || (s->dcd_z && (s->dcd_z >= n || s->dcd_z % s->n1_z)) ||
+        (s->dcd_t && (s->dcd_t >= n || s->dcd_t % s->n1_t)))
+        return fail(HE_ERR_ARG, "a decomposition needs n' < n with the baby steps dividing n'");
     return HE_OK;
 }
 
 // Runs one group of same-shape products: gathers A's and B's, replicates,
 // aligns levels, multiplies, scatters.
 static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::vector<const he_ct *> &Bs, int n,
-                      int n1z, int n1t, int level, std::vector<he_ct *> &outs, bool relin_once) {
+                      int n1z, int n1t, int level, std::vector<he_ct *> &outs, bool relin_once, int dcd_z,
+                      int dcd_t) {
     const int Bn = (int)As.size();
     const size_t w = ct_words(&c, level);
     Buf A(&c.pool, Bn * w), B(&c.pool, Bn * w);
@@ -603,13 +637,14 @@ static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::v
     }
     if (As[0]->period != n * n) replicate(&c, A.p, Bn, level, n);
     if (Bs[0]->period != n * n) replicate(&c, B.p, Bn, level, n);
-    const size_t wo = ct_words(&c, level - 3);
+    const int depth = hmatmul_depth(n, dcd_z, dcd_t);
+    const size_t wo = ct_words(&c, level - depth);
     Buf O(&c.pool, Bn * wo);
-    hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p, relin_once);
-    double q2 = (double)c.primes[level - 2];
+    hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p, relin_once, dcd_z, dcd_t);
+    double q2 = (double)c.primes[level - depth + 1];   // the prime of the multiplication's rescale
     try {
         for (int i = 0; i < Bn; i++) {
-            he_ct *o = new_ct(&c, level - 3, (As[i]->scale * Bs[i]->scale) / q2, n * n);
+            he_ct *o = new_ct(&c, level - depth, (As[i]->scale * Bs[i]->scale) / q2, n * n);
             cudaMemcpyAsync(o->d, O.p + i * wo, wo * 8, cudaMemcpyDeviceToDevice, c.stream);
             outs[i] = o;
         }
@@ -621,7 +656,7 @@ static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::v
 
 int he_hmatmul(he_ctx *ctx, const he_ct *A, const he_ct *B, int n, const he_mm_sched *sched, he_ct **out) {
     if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
-    he_mm_job j{A, B, n, sched ? *sched : he_mm_sched{0, 0, 0}};
+    he_mm_job j{A, B, n, sched ? *sched : he_mm_sched{0, 0, 0, 0, 0}};
     if (!sched) return fail(HE_ERR_ARG, "null schedule");
     if (int rc = check_ct(ctx->c, A)) return rc;
     if (int rc = check_ct(ctx->c, B)) return rc;
@@ -633,14 +668,15 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
     for (int i = 0; i < n_jobs; i++) {
         if (!jobs[i].A || !jobs[i].B || jobs[i].A->ctx != jobs[i].B->ctx) return fail(HE_ERR_ARG, "bad job operands");
         if (int rc = check_sched(*jobs[i].A->ctx, jobs[i].n, &jobs[i].sched)) return rc;
-        if (std::min(jobs[i].A->level, jobs[i].B->level) < 3) return fail(HE_ERR_LEVEL, "a product needs 3 levels");
+        if (std::min(jobs[i].A->level, jobs[i].B->level) < hmatmul_depth(jobs[i].n, jobs[i].sched.dcd_z, jobs[i].sched.dcd_t))
+            return fail(HE_ERR_LEVEL, "not enough levels for the product");
         outs[i] = nullptr;
     }
     GUARD_BEGIN
     std::vector<ProdSpec> prods;
     for (int i = 0; i < n_jobs; i++)
         prods.push_back({jobs[i].A, jobs[i].B, jobs[i].n, jobs[i].sched.n1_z, jobs[i].sched.n1_t,
-                         jobs[i].sched.relin_once != 0});
+                         jobs[i].sched.relin_once != 0, jobs[i].sched.dcd_z, jobs[i].sched.dcd_t});
     std::vector<he_ct *> res;
     run_products(prods, res, 0);
     try {
@@ -662,13 +698,13 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
 
 namespace he {
 void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs, int max_batch) {
-    typedef std::tuple<Ctx *, int, int, int, int, int, int, int> Key;
+    typedef std::tuple<Ctx *, int, int, int, int, int, int, int, int, int> Key;
     std::map<Key, std::vector<int>> groups;
     for (size_t i = 0; i < prods.size(); i++) {
         const ProdSpec &j = prods[i];
         int lv = std::min(j.A->level, j.B->level);
         groups[Key(j.A->ctx, lv, j.n, j.n1z, j.n1t, j.A->period == j.n * j.n, j.B->period == j.n * j.n,
-                   j.relin_once)]
+                   j.relin_once, j.dcd_z, j.dcd_t)]
             .push_back((int)i);
     }
     outs.assign(prods.size(), nullptr);
@@ -687,7 +723,7 @@ void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs
                 }
                 std::vector<he_ct *> o(As.size());
                 const ProdSpec &j0 = prods[ix[s0]];
-                run_group(c, As, Bs, j0.n, j0.n1z, j0.n1t, lv, o, j0.relin_once);
+                run_group(c, As, Bs, j0.n, j0.n1z, j0.n1t, lv, o, j0.relin_once, j0.dcd_z, j0.dcd_t);
                 for (size_t t = s0; t < s1; t++) outs[ix[t]] = o[t - s0];
             }
         }
@@ -727,22 +763,26 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
     GUARD_END
 }
 
-int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, he_ct **out) {
+int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, int n_prime, he_ct **out) {
     if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
     if (kind < 0 || kind > 2) return fail(HE_ERR_ARG, "kind must be 0 (sigma), 1 (tau) or 2 (transpose)");
+    if (n_prime && kind == 2) return fail(HE_ERR_ARG, "the transpose has no decomposition");
     Ctx &c = ctx->c;
     if (int rc = check_ct(c, ct)) return rc;
-    he_mm_sched s{n1, n1, 0};
+    he_mm_sched s{n1, n1, 0, kind == 0 ? n_prime : 0, kind == 1 ? n_prime : 0};
+    if (n_prime < 0) return fail(HE_ERR_ARG, "n' must be >= 0");
     if (int rc = check_sched(c, n, &s)) return rc;
-    if (ct->level < 1) return fail(HE_ERR_LEVEL, "a linear transform needs 1 level");
+    const int m = n_prime ? dcd_levels(n, n_prime) : 1;
+    if (ct->level < m) return fail(HE_ERR_LEVEL, "not enough levels for the transform");
     GUARD_BEGIN
     he_ct *tmp = clone_ct(c, ct);
     he_ct *o = nullptr;
     try {
         if (tmp->period != n * n) replicate(&c, tmp->d, 1, tmp->level, n);
-        o = new_ct(&c, ct->level - 1, ct->scale, n * n);
+        o = new_ct(&c, ct->level - m, ct->scale, n * n);
         const int n2 = n / n1;
-        if (kind == 0) lintrans(&c, tmp->d, 1, ct->level, 0, n, 1, n1, -n2, n2, 1.0, o->d);
+        if (n_prime) zt_stage_public(&c, tmp->d, 1, ct->level, kind == 1, n, n1, n_prime, ct->level - m, o->d);
+        else if (kind == 0) lintrans(&c, tmp->d, 1, ct->level, 0, n, 1, n1, -n2, n2, 1.0, o->d);
         else if (kind == 1) lintrans(&c, tmp->d, 1, ct->level, 1, n, n, n1, 0, n2, 1.0, o->d);
         else lintrans(&c, tmp->d, 1, ct->level, 2, n, n - 1, n1, -n2, n2, 1.0, o->d);
     } catch (...) {

@@ -27,6 +27,7 @@ struct ProdSpec {
     const he_ct *A, *B;
     int n, n1z, n1t;
     bool relin_once = false;
+    int dcd_z = 0, dcd_t = 0;
 };
 
 // Runs every product of `prods`, grouping those that share (context, level,
@@ -38,7 +39,7 @@ void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs
 
 // Rotation steps (mod slots) of the product schedule and of the transpose G,
 // as he_rot_steps_for_matmul / he_rot_steps_for_transpose list them.
-std::vector<long> matmul_steps(int n, int n1z, int n1t, long slots);
+std::vector<long> matmul_steps(int n, int n1z, int n1t, long slots, int dcd_z = 0, int dcd_t = 0);
 std::vector<long> transpose_steps(int n, int n1, long slots);
 // First step of `steps` with no rotation key in c (steps >= skip_from are
 // ignored), or 0 if every key is present.

@@ -167,9 +167,11 @@ void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out) {
 // --------------------------------------------------- plaintext diagonals
 // Cached encodings (NTT, Montgomery) over Q_l P of a diagonal slot vector at
 // scale q_l.  kind/n/t/rot/value/k as in k_diag_fill.
-const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level) {
+const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level,
+                  const DcdFactor *fac) {
     std::ostringstream os;
     os << kind << ':' << n << ':' << t << ':' << rot << ':' << k << ':' << level << ':';
+    if (fac) os << fac->id << ':';
     os.precision(17);
     os << value;
     std::string key = os.str();
@@ -182,7 +184,10 @@ const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k
         throw HeError(HE_ERR_OOM, "plaintext cache allocation failed");
     }
     Buf zr(&c->pool, c->S), zi(&c->pool, c->S), m(&c->pool, N);
-    launch_diag_fill(c, (double *)zr.p, kind, n, t, rot, value, k, c->stream);
+    if (fac)
+        launch_dcd_fill(c, (double *)zr.p, fac->dev, n, t, rot, value, c->stream);
+    else
+        launch_diag_fill(c, (double *)zr.p, kind, n, t, rot, value, k, c->stream);
     cudaMemsetAsync(zi.p, 0, (size_t)c->S * 8, c->stream);
     launch_encode(c, (double *)zr.p, (double *)zi.p, (double)c->primes[level], (i64 *)m.p, c->stream);
     RowMap qp = c->map_qp(level);
@@ -219,7 +224,7 @@ static long mod_pos(long x, long m) { return ((x % m) + m) % m; }
 // rescale by q_l (plaintexts at scale q_l keep the ciphertext scale).
 // in: [B][2][l+1][N]; out: [B][2][l][N].
 void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
-              double value, u64 *out) {
+              double value, u64 *out, const DcdFactor *fac) {
     const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
     const long n2 = (long)n * n;
     const size_t qpct = (size_t)2 * rows * N;   // one item over Q_l P
@@ -244,8 +249,8 @@ void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, 
         std::vector<const u64 *> pts, Rs;
         for (int j = 0; j < n1; j++) {
             long t = a * ((long)n1 * i + j);
-            if (!diag_nonzero(kind, n, t)) continue;
-            pts.push_back(get_pt(c, kind, n, t, mod_pos(-a * n1 * i, n2), value, 0, level));
+            if (fac ? !fac->diags.count(mod_pos(t, n2)) : !diag_nonzero(kind, n, t)) continue;
+            pts.push_back(get_pt(c, kind, n, t, mod_pos(-a * n1 * i, n2), value, 0, level, fac));
             Rs.push_back(R[j].p);
         }
         if (pts.empty()) continue;
@@ -282,18 +287,65 @@ void replicate(Ctx *c, u64 *ct, int B, int level, int n) {
 
 // JKLS product (eq. 4) with the hoisting of Sec. 4.1; A, B: [Bn][2][l+1][N]
 // replicated with period n^2; out: [Bn][2][l-2][N].
+// A chain of decomposition factors (application order) on B items at
+// `level`; the output, one level per factor lower, goes to out.
+static void apply_chain(Ctx *c, const u64 *in, int B, int level, const DcdChain &ch, int n, long a_left, int n1,
+                        int gi0, int gi1, u64 *out) {
+    const size_t w = (size_t)2 * (level + 1) * c->N;
+    Buf t0(&c->pool, B * w), t1(&c->pool, B * w);
+    const u64 *cur = in;
+    int lv = level;
+    for (size_t f = 0; f + 1 < ch.factors.size(); f++) {
+        u64 *dst = (f % 2 == 0) ? t0.p : t1.p;
+        lintrans(c, cur, B, lv, 8, n, ch.factors[f].step, 2, 0, 1, 1.0, dst, &ch.factors[f]);
+        cur = dst;
+        lv--;
+    }
+    lintrans(c, cur, B, lv, 8, n, a_left, n1, gi0, gi1, 1.0, out, &ch.factors.back());
+}
+
+// sigma (Z) or tau (T) of B items at `level`, undecomposed (one level) or
+// through the decomposition chains (Sec. 4.2 DMatrixMult), then dropped to
+// level `to`.
+static void zt_stage(Ctx *c, const u64 *in, int B, int level, bool is_t, int n, int n1, int np, int to, u64 *out) {
+    const int N = c->N;
+    const int m = np ? dcd_levels(n, np) : 1, lo = level - m;
+    const size_t wlo = (size_t)2 * (lo + 1) * N;
+    Buf r(&c->pool, lo == to ? 1 : B * wlo);
+    u64 *dst = lo == to ? out : r.p;   // no copy when no level has to be dropped
+    if (!np) {
+        if (is_t) lintrans(c, in, B, level, 1, n, n, n1, 0, n / n1, 1.0, dst);
+        else lintrans(c, in, B, level, 0, n, 1, n1, -(n / n1), n / n1, 1.0, dst);
+    } else if (is_t) {
+        apply_chain(c, in, B, level, dcd_chain(c, 2, n, np), n, n, n1, 0, np / n1 + 1, dst);
+    } else {
+        Buf r2(&c->pool, B * wlo);
+        apply_chain(c, in, B, level, dcd_chain(c, 0, n, np), n, 1, n1, 0, np / n1, dst);
+        apply_chain(c, in, B, level, dcd_chain(c, 1, n, np), n, 1, n1, -(np / n1), 1, r2.p);
+        add(c, dst, r2.p, B, lo, dst);
+    }
+    if (lo != to) drop(c, r.p, B, lo, to, out);
+}
+
+void zt_stage_public(Ctx *c, const u64 *in, int B, int level, bool is_t, int n, int n1, int np, int to, u64 *out) {
+    zt_stage(c, in, B, level, is_t, n, n1, np, to, out);
+}
+
 void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
-             bool relin_once) {
-    if (level < 3) throw HeError(HE_ERR_LEVEL, "matrix product needs 3 levels");
+             bool relin_once, int dcd_z, int dcd_t) {
+    const int depth = hmatmul_depth(n, dcd_z, dcd_t);
+    if (level < depth) throw HeError(HE_ERR_LEVEL, "matrix product needs more levels");
+    if ((dcd_z && (dcd_z >= n || dcd_z % n1z)) || (dcd_t && (dcd_t >= n || dcd_t % n1t)))
+        throw HeError(HE_ERR_ARG, "a decomposition needs n' < n with n1 dividing n'");
     const int N = c->N;
     const long n2m = (long)n * n;
-    const int l1 = level - 1, l2 = level - 2;
+    const int l1 = level - (depth - 2), l2 = l1 - 1;
     const size_t ct1 = (size_t)2 * (l1 + 1) * N, ct2 = (size_t)2 * (l2 + 1) * N;
     const int rows1 = c->qp_rows(l1);
     const size_t qp1 = (size_t)2 * rows1 * N, dig1 = (size_t)c->ndig(l1) * rows1 * N;
     Buf A0(&c->pool, Bn * ct1), B0(&c->pool, Bn * ct1);
-    lintrans(c, A, Bn, level, 0, n, 1, n1z, -(n / n1z), n / n1z, 1.0, A0.p);
-    lintrans(c, Bm, Bn, level, 1, n, n, n1t, 0, n / n1t, 1.0, B0.p);
+    zt_stage(c, A, Bn, level, false, n, n1z, dcd_z, l1, A0.p);
+    zt_stage(c, Bm, Bn, level, true, n, n1t, dcd_t, l1, B0.p);
 
     // C^k sources A_g, A'_g and R^k sources B_g with their digits
     Buf Ag(&c->pool, Bn * ct1), Apg(&c->pool, Bn * ct1), Bg(&c->pool, Bn * ct1);

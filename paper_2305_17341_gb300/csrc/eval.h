@@ -31,11 +31,25 @@ void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out);
 void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out);
 void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
 void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
-const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level);
+const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level,
+                  const DcdFactor *fac = nullptr);
 void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
-              double value, u64 *out);
+              double value, u64 *out, const DcdFactor *fac = nullptr);
+// Decompositions (dcd.cu): which = 0 (Z_1), 1 (Z_2), 2 (T); levels a chain consumes.
+const DcdChain &dcd_chain(Ctx *c, int which, int n, int n_prime);
+int dcd_levels(int n, int n_prime);
+void launch_dcd_fill(Ctx *c, double *out, const int *diag, int n, long t, long rot, double value, cudaStream_t st);
+// Levels a product consumes: the Z/T stage (1, or the longer decomposition
+// chain), C^k, and the multiplication.
+// sigma (is_t false) or tau of B items through the undecomposed transform or
+// the decomposition chains, output dropped to level `to`.
+void zt_stage_public(Ctx *c, const u64 *in, int B, int level, bool is_t, int n, int n1, int np, int to, u64 *out);
+inline int hmatmul_depth(int n, int dcd_z, int dcd_t) {
+    int mz = dcd_z ? dcd_levels(n, dcd_z) : 1, mt = dcd_t ? dcd_levels(n, dcd_t) : 1;
+    return (mz > mt ? mz : mt) + 2;
+}
 void replicate(Ctx *c, u64 *ct, int B, int level, int n);
 void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
-             bool relin_once = false);
+             bool relin_once = false, int dcd_z = 0, int dcd_t = 0);
 
 }  // namespace he

@@ -22,6 +22,7 @@ struct Group {
     std::vector<int> idx;        // job indices
     int level = 0, n = 0, n1z = 0, n1t = 0;
     bool repA = false, repB = false, relin_once = false;
+    int dcd_z = 0, dcd_t = 0, depth = 3;
     u64 *O = nullptr;            // [items][2][level-2][N], plan memory
     size_t wo = 0;
 };
@@ -61,7 +62,7 @@ static void record(he_mm_plan *P) {
         }
         if (g.repA) replicate(&c, A.p, Bn, g.level, g.n);
         if (g.repB) replicate(&c, B.p, Bn, g.level, g.n);
-        hmatmul(&c, A.p, B.p, Bn, g.level, g.n, g.n1z, g.n1t, g.O, g.relin_once);
+        hmatmul(&c, A.p, B.p, Bn, g.level, g.n, g.n1z, g.n1t, g.O, g.relin_once, g.dcd_z, g.dcd_t);
     }
 }
 
@@ -80,8 +81,13 @@ int he_mm_plan_create(const he_mm_job *jobs, int n_jobs, he_mm_plan **out) {
         if (!pow2(n) || (long)n * n > c->S || !pow2(j.sched.n1_z) || !pow2(j.sched.n1_t) || j.sched.n1_z > n ||
             j.sched.n1_t > n || j.sched.n1_z > 32 || j.sched.n1_t > 32)
             return plan_fail(HE_ERR_ARG, "bad block size or schedule");
-        if (std::min(j.A->level, j.B->level) < 3) return plan_fail(HE_ERR_LEVEL, "a product needs 3 levels");
-        if (long miss = first_missing_key(c, matmul_steps(n, j.sched.n1_z, j.sched.n1_t, c->S),
+        if ((j.sched.dcd_z && (j.sched.dcd_z >= n || j.sched.dcd_z % j.sched.n1_z)) ||
+            (j.sched.dcd_t && (j.sched.dcd_t >= n || j.sched.dcd_t % j.sched.n1_t)))
+            return plan_fail(HE_ERR_ARG, "a decomposition needs n' < n with the baby steps dividing n'");
+        if (std::min(j.A->level, j.B->level) < hmatmul_depth(n, j.sched.dcd_z, j.sched.dcd_t))
+            return plan_fail(HE_ERR_LEVEL, "not enough levels for the product");
+        if (long miss = first_missing_key(c, matmul_steps(n, j.sched.n1_z, j.sched.n1_t, c->S, j.sched.dcd_z,
+                                                          j.sched.dcd_t),
                                           (j.A->period == n * n && j.B->period == n * n) ? (long)n * n : c->S))
             return plan_fail(HE_ERR_KEY_MISSING, "rotation key for step " + std::to_string(miss) + " missing");
         if (!c->rlk) return plan_fail(HE_ERR_KEY_MISSING, "relinearisation key missing");
@@ -90,18 +96,19 @@ int he_mm_plan_create(const he_mm_job *jobs, int n_jobs, he_mm_plan **out) {
     if (!P) return plan_fail(HE_ERR_OOM, "host allocation failed");
     P->c = c;
     P->jobs.assign(jobs, jobs + n_jobs);
-    typedef std::tuple<int, int, int, int, bool, bool, bool> Key;
+    typedef std::tuple<int, int, int, int, bool, bool, bool, int, int> Key;
     std::map<Key, int> gi;
     for (int i = 0; i < n_jobs; i++) {
         const he_mm_job &j = jobs[i];
         const int n = j.n, lv = std::min(j.A->level, j.B->level);
         Key k(lv, n, j.sched.n1_z, j.sched.n1_t, j.A->period != n * n, j.B->period != n * n,
-              j.sched.relin_once != 0);
+              j.sched.relin_once != 0, j.sched.dcd_z, j.sched.dcd_t);
         auto it = gi.find(k);
         if (it == gi.end()) {
             Group g;
             g.level = lv, g.n = n, g.n1z = j.sched.n1_z, g.n1t = j.sched.n1_t;
             g.repA = std::get<4>(k), g.repB = std::get<5>(k), g.relin_once = std::get<6>(k);
+            g.dcd_z = j.sched.dcd_z, g.dcd_t = j.sched.dcd_t, g.depth = hmatmul_depth(n, g.dcd_z, g.dcd_t);
             it = gi.emplace(k, (int)P->groups.size()).first;
             P->groups.push_back(g);
         }
@@ -112,7 +119,7 @@ int he_mm_plan_create(const he_mm_job *jobs, int n_jobs, he_mm_plan **out) {
     int rc = HE_OK;
     try {
         for (Group &g : P->groups) {
-            g.wo = ct_words(c, g.level - 3);
+            g.wo = ct_words(c, g.level - g.depth);
             g.O = (u64 *)P->pool.get(g.idx.size() * g.wo * 8);
         }
         // 1. recording run: fills the plan's pool and the context's caches
@@ -174,10 +181,10 @@ int he_mm_plan_run(he_mm_plan *P, he_ct **outs) {
         if (cudaGraphLaunch(P->exec, c.stream) != cudaSuccess) throw HeError(HE_ERR_CUDA, "graph launch failed");
         c.n_launch += P->launches;
         for (const Group &g : P->groups) {
-            const double q2 = (double)c.primes[g.level - 2];
+            const double q2 = (double)c.primes[g.level - g.depth + 1];
             for (size_t t = 0; t < g.idx.size(); t++) {
                 const he_mm_job &j = P->jobs[g.idx[t]];
-                he_ct *o = new_ct(&c, g.level - 3, (j.A->scale * j.B->scale) / q2, j.n * j.n);
+                he_ct *o = new_ct(&c, g.level - g.depth, (j.A->scale * j.B->scale) / q2, j.n * j.n);
                 res[g.idx[t]] = o;
                 cudaMemcpyAsync(o->d, g.O + t * g.wo, g.wo * 8, cudaMemcpyDeviceToDevice, c.stream);
             }

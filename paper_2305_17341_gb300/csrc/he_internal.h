@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstdint>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -112,6 +113,20 @@ struct LevelConsts {
     u64 *d_rs_qlmod = nullptr;       // [l]
 };
 
+// One factor of a Diagonal Convergence Decomposition (Sec. 4.2): the
+// diagonal of every row (-1 = empty row) on the device, the set of its
+// diagonals (mod n^2), the rotation step of a right factor, and a cache id.
+struct DcdFactor {
+    int *dev = nullptr;
+    std::set<long> diags;
+    std::string id;
+    long step = 0;
+};
+// Factors in application order: right factors first, the left one last.
+struct DcdChain {
+    std::vector<DcdFactor> factors;
+};
+
 struct Ctx {
     he_params prm;
     int logN, N, S, L, alpha, dnum, nprimes;
@@ -148,6 +163,7 @@ struct Ctx {
 
     // cached plaintext diagonals (NTT, Montgomery, over Q_l P), keyed by a string id
     std::map<std::string, u64 *> ptcache;
+    std::map<std::string, DcdChain> dcd;     // decompositions by (transform, n, n')
     size_t ptcache_bytes = 0;
 
     DevicePool pool;

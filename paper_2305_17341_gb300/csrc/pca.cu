@@ -671,6 +671,10 @@ int he_covariance(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, in
         set_error("the covariance circuit needs 6 levels");
         return HE_ERR_LEVEL;
     }
+    if (sched->dcd_z || sched->dcd_t) {
+        set_error("the covariance circuit uses the undecomposed Z and T");
+        return HE_ERR_ARG;
+    }
     PCA_GUARD_BEGIN
     RefreshState st{0, 0};
     PcaOps ops(&c, &st);

@@ -58,3 +58,17 @@ def test_rot_steps_match_oracle_schedule(built):
     for n, n1z, n1t, S in [(32, 8, 8, 8192), (128, 16, 16, 32768), (16, 4, 2, 512), (8, 8, 8, 64)]:
         assert _lib.he_rot_steps_for_matmul(n, n1z, n1t, S) == matmul_rot_steps(n, n1z, n1t, S)
         assert _lib.he_rot_steps_for_transpose(n, n1z, S) == transpose_rot_steps(n, n1z, S)
+
+
+def test_rot_steps_for_decomposed_schedules_match_oracle(built):
+    """The key set of a product with decomposed Z / T (Sec. 4.2) equals the
+    oracle's schedule; Table 3's 128x128 settings included."""
+    from oracle.hmm import matmul_rot_steps
+    from paper_2305_17341_gb300 import _lib
+    for n, n1z, n1t, S, dz, dt in [(16, 4, 4, 2048, 8, 8), (16, 4, 4, 2048, 4, 0), (16, 4, 2, 2048, 0, 4),
+                                    (32, 8, 8, 8192, 16, 16), (128, 8, 8, 16384, 64, 32), (128, 16, 16, 16384, 32, 64)]:
+        assert _lib.he_rot_steps_for_sched(n, n1z, n1t, S, dz, dt) == matmul_rot_steps(n, n1z, n1t, S, dz, dt)
+    assert _lib.he_rot_steps_for_sched(16, 4, 4, 2048) == _lib.he_rot_steps_for_matmul(16, 4, 4, 2048)
+    import pytest
+    with pytest.raises(_lib.HeError):
+        _lib.he_rot_steps_for_sched(16, 4, 4, 2048, 6, 0)   # n1 must divide n'
