@@ -625,25 +625,39 @@ static int check_sched(Ctx &c, int n, const he_mm_sched *s) {
 static void run_group(Ctx &c, const std::vector<const he_ct *> &As, const std::vector<const he_ct *> &Bs, int n,
                       int n1z, int n1t, int level, std::vector<he_ct *> &outs, bool relin_once, int dcd_z,
                       int dcd_t) {
-    const int Bn = (int)As.size();
-    const size_t w = ct_words(&c, level);
-    Buf A(&c.pool, Bn * w), B(&c.pool, Bn * w);
-    for (int i = 0; i < Bn; i++) {
-        // drop to the common level while gathering (keep limbs 0..level of both polys)
-        cudaMemcpy2DAsync(A.p + i * w, (size_t)(level + 1) * c.N * 8, As[i]->d, (size_t)(As[i]->level + 1) * c.N * 8,
-                          (size_t)(level + 1) * c.N * 8, 2, cudaMemcpyDeviceToDevice, c.stream);
-        cudaMemcpy2DAsync(B.p + i * w, (size_t)(level + 1) * c.N * 8, Bs[i]->d, (size_t)(Bs[i]->level + 1) * c.N * 8,
-                          (size_t)(level + 1) * c.N * 8, 2, cudaMemcpyDeviceToDevice, c.stream);
+    const int P = (int)As.size();
+    // distinct operands: a ciphertext that several products of the group
+    // take (as the left or as the right factor) is transformed once
+    std::vector<const he_ct *> uA, uB;
+    std::vector<int> ia(P), ib(P);
+    std::map<const he_ct *, int> mA, mB;
+    for (int i = 0; i < P; i++) {
+        auto a = mA.emplace(As[i], (int)uA.size());
+        if (a.second) uA.push_back(As[i]);
+        ia[i] = a.first->second;
+        auto b = mB.emplace(Bs[i], (int)uB.size());
+        if (b.second) uB.push_back(Bs[i]);
+        ib[i] = b.first->second;
     }
-    if (As[0]->period != n * n) replicate(&c, A.p, Bn, level, n);
-    if (Bs[0]->period != n * n) replicate(&c, B.p, Bn, level, n);
+    const int nA = (int)uA.size(), nB = (int)uB.size();
+    const size_t w = ct_words(&c, level);
+    Buf A(&c.pool, nA * w), B(&c.pool, nB * w);
+    // drop to the common level while gathering (keep limbs 0..level of both polys)
+    auto gather = [&](u64 *dst, const he_ct *x) {
+        cudaMemcpy2DAsync(dst, (size_t)(level + 1) * c.N * 8, x->d, (size_t)(x->level + 1) * c.N * 8,
+                          (size_t)(level + 1) * c.N * 8, 2, cudaMemcpyDeviceToDevice, c.stream);
+    };
+    for (int i = 0; i < nA; i++) gather(A.p + i * w, uA[i]);
+    for (int i = 0; i < nB; i++) gather(B.p + i * w, uB[i]);
+    if (As[0]->period != n * n) replicate(&c, A.p, nA, level, n);
+    if (Bs[0]->period != n * n) replicate(&c, B.p, nB, level, n);
     const int depth = hmatmul_depth(n, dcd_z, dcd_t);
     const size_t wo = ct_words(&c, level - depth);
-    Buf O(&c.pool, Bn * wo);
-    hmatmul(&c, A.p, B.p, Bn, level, n, n1z, n1t, O.p, relin_once, dcd_z, dcd_t);
+    Buf O(&c.pool, P * wo);
+    hmatmul_pairs(&c, A.p, nA, B.p, nB, ia.data(), ib.data(), P, level, n, n1z, n1t, O.p, relin_once, dcd_z, dcd_t);
     double q2 = (double)c.primes[level - depth + 1];   // the prime of the multiplication's rescale
     try {
-        for (int i = 0; i < Bn; i++) {
+        for (int i = 0; i < P; i++) {
             he_ct *o = new_ct(&c, level - depth, (As[i]->scale * Bs[i]->scale) / q2, n * n);
             cudaMemcpyAsync(o->d, O.p + i * wo, wo * 8, cudaMemcpyDeviceToDevice, c.stream);
             outs[i] = o;
@@ -713,9 +727,29 @@ void run_products(const std::vector<ProdSpec> &prods, std::vector<he_ct *> &outs
             Ctx &c = *std::get<0>(kv.first);
             int lv = std::get<1>(kv.first);
             const std::vector<int> &ix = kv.second;
-            const int step = max_batch > 0 ? max_batch : (int)ix.size();
-            for (size_t s0 = 0; s0 < ix.size(); s0 += step) {
-                size_t s1 = std::min(ix.size(), s0 + step);
+            const size_t step = max_batch > 0 ? (size_t)max_batch : ix.size();
+            // clusters: runs of consecutive products that share an operand
+            // with an earlier product of the run; a batch is not cut inside
+            // a cluster when an earlier cut fits
+            std::vector<char> starts(ix.size() + 1, 1);
+            {
+                std::set<const he_ct *> ops;
+                for (size_t t = 0; t < ix.size(); t++) {
+                    const ProdSpec &j = prods[ix[t]];
+                    if (t > 0 && (ops.count(j.A) || ops.count(j.B))) {
+                        starts[t] = 0;
+                    } else {
+                        ops.clear();
+                    }
+                    ops.insert(j.A);
+                    ops.insert(j.B);
+                }
+            }
+            for (size_t s0 = 0, s1; s0 < ix.size(); s0 = s1) {
+                s1 = std::min(ix.size(), s0 + step);
+                size_t cut = s1;
+                while (cut > s0 + 1 && !starts[cut]) cut--;
+                if (cut > s0 + 1 || starts[cut]) s1 = cut;
                 std::vector<const he_ct *> As, Bs;
                 for (size_t t = s0; t < s1; t++) {
                     As.push_back(prods[ix[t]].A);

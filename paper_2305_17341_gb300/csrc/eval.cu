@@ -331,8 +331,15 @@ void zt_stage_public(Ctx *c, const u64 *in, int B, int level, bool is_t, int n, 
     zt_stage(c, in, B, level, is_t, n, n1, np, to, out);
 }
 
-void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
-             bool relin_once, int dcd_z, int dcd_t) {
+// Products A[ia[p]] B[ib[p]], p < P, of nA distinct left and nB distinct
+// right operands: sigma, C^k and their hoisted rotations run once per left
+// operand, tau and R^k once per right operand, whatever the number of
+// products each takes part in (Sec. 5.2, covariance Optimizations 1 and 2:
+// C^k Z X_j^T and R^k T X_i computed once for every product that uses
+// them; the batch of products is the row segment).  Only the current k's
+// A^(k), B^(k) are held, so the memory grows with nA + nB + P, not with n.
+void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const int *ia, const int *ib, int P,
+                   int level, int n, int n1z, int n1t, u64 *out, bool relin_once, int dcd_z, int dcd_t) {
     const int depth = hmatmul_depth(n, dcd_z, dcd_t);
     if (level < depth) throw HeError(HE_ERR_LEVEL, "matrix product needs more levels");
     if ((dcd_z && (dcd_z >= n || dcd_z % n1z)) || (dcd_t && (dcd_t >= n || dcd_t % n1t)))
@@ -343,25 +350,32 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
     const size_t ct1 = (size_t)2 * (l1 + 1) * N, ct2 = (size_t)2 * (l2 + 1) * N;
     const int rows1 = c->qp_rows(l1);
     const size_t qp1 = (size_t)2 * rows1 * N, dig1 = (size_t)c->ndig(l1) * rows1 * N;
-    Buf A0(&c->pool, Bn * ct1), B0(&c->pool, Bn * ct1);
-    zt_stage(c, A, Bn, level, false, n, n1z, dcd_z, l1, A0.p);
-    zt_stage(c, Bm, Bn, level, true, n, n1t, dcd_t, l1, B0.p);
+    bool ident = nA == P && nB == P;
+    for (int p = 0; p < P && ident; p++) ident = ia[p] == p && ib[p] == p;
+    for (int p = 0; p < P; p++)
+        if (ia[p] < 0 || ia[p] >= nA || ib[p] < 0 || ib[p] >= nB) throw HeError(HE_ERR_ARG, "bad operand index");
+    Buf A0(&c->pool, nA * ct1), B0(&c->pool, nB * ct1);
+    zt_stage(c, A, nA, level, false, n, n1z, dcd_z, l1, A0.p);
+    zt_stage(c, Bm, nB, level, true, n, n1t, dcd_t, l1, B0.p);
 
     // C^k sources A_g, A'_g and R^k sources B_g with their digits
-    Buf Ag(&c->pool, Bn * ct1), Apg(&c->pool, Bn * ct1), Bg(&c->pool, Bn * ct1);
-    Buf dA(&c->pool, Bn * dig1), dAp(&c->pool, Bn * dig1), dB(&c->pool, Bn * dig1), tmp(&c->pool, Bn * ct1);
-    cudaMemcpyAsync(Ag.p, A0.p, Bn * ct1 * 8, cudaMemcpyDeviceToDevice, c->stream);
-    modup(c, Ag.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dA.p);
-    rotate_digits(c, Ag.p, Bn, l1, dA.p, galois_of_step(c, mod_pos(-n, n2m)), Apg.p);
-    modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dAp.p);
-    cudaMemcpyAsync(Bg.p, B0.p, Bn * ct1 * 8, cudaMemcpyDeviceToDevice, c->stream);
-    modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dB.p);
+    Buf Ag(&c->pool, nA * ct1), Apg(&c->pool, nA * ct1), Bg(&c->pool, nB * ct1);
+    Buf dA(&c->pool, nA * dig1), dAp(&c->pool, nA * dig1), dB(&c->pool, nB * dig1);
+    Buf tmpA(&c->pool, nA * ct1), tmpB(&c->pool, nB * ct1);
+    cudaMemcpyAsync(Ag.p, A0.p, nA * ct1 * 8, cudaMemcpyDeviceToDevice, c->stream);
+    modup(c, Ag.p + (long)(l1 + 1) * N, (long)ct1, nA, l1, dA.p);
+    rotate_digits(c, Ag.p, nA, l1, dA.p, galois_of_step(c, mod_pos(-n, n2m)), Apg.p);
+    modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, nA, l1, dAp.p);
+    cudaMemcpyAsync(Bg.p, B0.p, nB * ct1 * 8, cudaMemcpyDeviceToDevice, c->stream);
+    modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, nB, l1, dB.p);
     int gA = 0, gB = 0;
 
-    Buf acc(&c->pool, Bn * ct2), Ak(&c->pool, Bn * ct2), Bk(&c->pool, Bn * ct2), prod(&c->pool, Bn * ct2);
+    Buf acc(&c->pool, P * ct2), Ak(&c->pool, nA * ct2), Bk(&c->pool, nB * ct2), prod(&c->pool, P * ct2);
+    // the operands of every product, gathered when operands are shared
+    Buf AkP(&c->pool, ident ? 1 : P * ct2), BkP(&c->pool, ident ? 1 : P * ct2);
     // relin_once: the summed d2 of the n tensors (d0, d1 are summed in acc)
-    Buf acc2(&c->pool, relin_once ? (size_t)Bn * (l2 + 1) * N : 1);
-    Buf R1(&c->pool, Bn * qp1), R2(&c->pool, Bn * qp1), S(&c->pool, Bn * qp1), Akp(&c->pool, Bn * ct1);
+    Buf acc2(&c->pool, relin_once ? (size_t)P * (l2 + 1) * N : 1);
+    Buf R1(&c->pool, nA * qp1), R2(&c->pool, nA * qp1), S(&c->pool, nA * qp1), Akp(&c->pool, nA * ct1);
     RowMap q2 = c->map_q(l2);
 
     // The babies of a source are all its hoisted rotations at once (one
@@ -369,30 +383,30 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
     //   C^k: rotations by b of A_g and A'_g kept in Q_l P, b = 1..n1z-1;
     //   R^k: rotations by n b of B_g (ModDown'd), b = 1..n1t-1.
     const int nbA = n1z - 1, nbB = n1t - 1;
-    Buf RA(&c->pool, (size_t)std::max(1, nbA) * Bn * qp1), RAp(&c->pool, (size_t)std::max(1, nbA) * Bn * qp1);
-    Buf UB(&c->pool, (size_t)std::max(1, nbB) * Bn * qp1), BB(&c->pool, (size_t)std::max(1, nbB) * Bn * ct1);
+    Buf RA(&c->pool, (size_t)std::max(1, nbA) * nA * qp1), RAp(&c->pool, (size_t)std::max(1, nbA) * nA * qp1);
+    Buf UB(&c->pool, (size_t)std::max(1, nbB) * nB * qp1), BB(&c->pool, (size_t)std::max(1, nbB) * nB * ct1);
     auto babies_A = [&]() {
         std::vector<uint32_t> gs;
         std::vector<u64 *> o1, o2;
         for (int b = 1; b <= nbA; b++) {
             gs.push_back(galois_of_step(c, b % n2m));
-            o1.push_back(RA.p + (size_t)(b - 1) * Bn * qp1);
-            o2.push_back(RAp.p + (size_t)(b - 1) * Bn * qp1);
+            o1.push_back(RA.p + (size_t)(b - 1) * nA * qp1);
+            o2.push_back(RAp.p + (size_t)(b - 1) * nA * qp1);
         }
-        rot_qp_multi(c, Ag.p, Bn, l1, dA.p, gs.data(), nbA, o1.data());
-        rot_qp_multi(c, Apg.p, Bn, l1, dAp.p, gs.data(), nbA, o2.data());
+        rot_qp_multi(c, Ag.p, nA, l1, dA.p, gs.data(), nbA, o1.data());
+        rot_qp_multi(c, Apg.p, nA, l1, dAp.p, gs.data(), nbA, o2.data());
     };
     auto babies_B = [&]() {
         std::vector<uint32_t> gs;
         std::vector<u64 *> o;
         for (int b = 1; b <= nbB; b++) {
             gs.push_back(galois_of_step(c, ((long)n * b) % n2m));
-            o.push_back(UB.p + (size_t)(b - 1) * Bn * qp1);
+            o.push_back(UB.p + (size_t)(b - 1) * nB * qp1);
         }
-        rot_qp_multi(c, Bg.p, Bn, l1, dB.p, gs.data(), nbB, o.data());
+        rot_qp_multi(c, Bg.p, nB, l1, dB.p, gs.data(), nbB, o.data());
         if (nbB > 0) {
-            moddown(c, UB.p, 2 * Bn * nbB, l1, BB.p, (long)(l1 + 1) * N);
-            c->n_md += (long long)Bn * nbB;
+            moddown(c, UB.p, 2 * nB * nbB, l1, BB.p, (long)(l1 + 1) * N);
+            c->n_md += (long long)nB * nbB;
         }
     };
     if (nbA > 0) babies_A();
@@ -401,57 +415,74 @@ void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int 
         // ---- A^(k) = C^k A^(0) at level l2
         int g = k / n1z, b = k % n1z;
         while (gA < g) {
-            rotate_digits(c, Ag.p, Bn, l1, dA.p, galois_of_step(c, n1z % n2m), tmp.p);
-            std::swap(Ag, tmp);
-            modup(c, Ag.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dA.p);
-            rotate_digits(c, Apg.p, Bn, l1, dAp.p, galois_of_step(c, n1z % n2m), tmp.p);
-            std::swap(Apg, tmp);
-            modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dAp.p);
+            rotate_digits(c, Ag.p, nA, l1, dA.p, galois_of_step(c, n1z % n2m), tmpA.p);
+            std::swap(Ag, tmpA);
+            modup(c, Ag.p + (long)(l1 + 1) * N, (long)ct1, nA, l1, dA.p);
+            rotate_digits(c, Apg.p, nA, l1, dAp.p, galois_of_step(c, n1z % n2m), tmpA.p);
+            std::swap(Apg, tmpA);
+            modup(c, Apg.p + (long)(l1 + 1) * N, (long)ct1, nA, l1, dAp.p);
             gA++;
             if (nbA > 0) babies_A();
         }
         if (k == 0) {
-            drop(c, A0.p, Bn, l1, l2, Ak.p);
+            drop(c, A0.p, nA, l1, l2, Ak.p);
         } else {
             if (b == 0) {
-                launch_lift_P(c, R1.p, Ag.p, 2 * Bn, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
-                launch_lift_P(c, R2.p, Apg.p, 2 * Bn, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
+                launch_lift_P(c, R1.p, Ag.p, 2 * nA, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
+                launch_lift_P(c, R2.p, Apg.p, 2 * nA, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
             }
             const u64 *pts[2] = {get_pt(c, 3, n, 0, 0, 1.0, k, l1), get_pt(c, 4, n, 0, 0, 1.0, k, l1)};
-            const u64 *Rs[2] = {b == 0 ? R1.p : RA.p + (size_t)(b - 1) * Bn * qp1,
-                                b == 0 ? R2.p : RAp.p + (size_t)(b - 1) * Bn * qp1};
-            launch_pmul_acc(c, S.p, pts, Rs, 2, Bn, l1, (long)qp1, c->stream);
-            moddown(c, S.p, 2 * Bn, l1, Akp.p, (long)(l1 + 1) * N);
-            c->n_md += Bn;
-            rescale(c, Akp.p, Bn, l1, Ak.p);
+            const u64 *Rs[2] = {b == 0 ? R1.p : RA.p + (size_t)(b - 1) * nA * qp1,
+                                b == 0 ? R2.p : RAp.p + (size_t)(b - 1) * nA * qp1};
+            launch_pmul_acc(c, S.p, pts, Rs, 2, nA, l1, (long)qp1, c->stream);
+            moddown(c, S.p, 2 * nA, l1, Akp.p, (long)(l1 + 1) * N);
+            c->n_md += nA;
+            rescale(c, Akp.p, nA, l1, Ak.p);
         }
         // ---- B^(k) = R^k B^(0), dropped to l2
         int gb2 = k / n1t, bb = k % n1t;
         while (gB < gb2) {
-            rotate_digits(c, Bg.p, Bn, l1, dB.p, galois_of_step(c, ((long)n * n1t) % n2m), tmp.p);
-            std::swap(Bg, tmp);
-            modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, Bn, l1, dB.p);
+            rotate_digits(c, Bg.p, nB, l1, dB.p, galois_of_step(c, ((long)n * n1t) % n2m), tmpB.p);
+            std::swap(Bg, tmpB);
+            modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, nB, l1, dB.p);
             gB++;
             if (nbB > 0) babies_B();
         }
         if (bb == 0) {
-            drop(c, Bg.p, Bn, l1, l2, Bk.p);
+            drop(c, Bg.p, nB, l1, l2, Bk.p);
         } else {
-            drop(c, BB.p + (size_t)(bb - 1) * Bn * ct1, Bn, l1, l2, Bk.p);
+            drop(c, BB.p + (size_t)(bb - 1) * nB * ct1, nB, l1, l2, Bk.p);
         }
         // ---- product, relinearised, accumulated at level l2
+        const u64 *xa = Ak.p, *xb = Bk.p;
+        if (!ident) {
+            for (int p = 0; p < P; p++) {
+                cudaMemcpyAsync(AkP.p + (size_t)p * ct2, Ak.p + (size_t)ia[p] * ct2, ct2 * 8,
+                                cudaMemcpyDeviceToDevice, c->stream);
+                cudaMemcpyAsync(BkP.p + (size_t)p * ct2, Bk.p + (size_t)ib[p] * ct2, ct2 * 8,
+                                cudaMemcpyDeviceToDevice, c->stream);
+            }
+            xa = AkP.p, xb = BkP.p;
+        }
         if (relin_once) {
             const long cs = 2L * (l2 + 1) * N;
-            launch_tensor(c, acc.p, acc2.p, Ak.p, Bk.p, Bn, l2 + 1, cs, cs, q2, c->stream, k > 0);
+            launch_tensor(c, acc.p, acc2.p, xa, xb, P, l2 + 1, cs, cs, q2, c->stream, k > 0);
         } else if (k == 0) {
-            mult_relin(c, Ak.p, Bk.p, Bn, l2, acc.p);
+            mult_relin(c, xa, xb, P, l2, acc.p);
         } else {
-            mult_relin(c, Ak.p, Bk.p, Bn, l2, prod.p);
-            launch_add(c, acc.p, acc.p, prod.p, 2L * Bn * (l2 + 1), q2, c->stream);
+            mult_relin(c, xa, xb, P, l2, prod.p);
+            launch_add(c, acc.p, acc.p, prod.p, 2L * P * (l2 + 1), q2, c->stream);
         }
     }
-    if (relin_once) relin_into(c, acc2.p, Bn, l2, acc.p);
-    rescale(c, acc.p, Bn, l2, out);
+    if (relin_once) relin_into(c, acc2.p, P, l2, acc.p);
+    rescale(c, acc.p, P, l2, out);
+}
+
+void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
+             bool relin_once, int dcd_z, int dcd_t) {
+    std::vector<int> id(Bn);
+    for (int i = 0; i < Bn; i++) id[i] = i;
+    hmatmul_pairs(c, A, Bn, Bm, Bn, id.data(), id.data(), Bn, level, n, n1z, n1t, out, relin_once, dcd_z, dcd_t);
 }
 
 }  // namespace he

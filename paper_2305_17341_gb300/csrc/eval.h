@@ -51,5 +51,9 @@ inline int hmatmul_depth(int n, int dcd_z, int dcd_t) {
 void replicate(Ctx *c, u64 *ct, int B, int level, int n);
 void hmatmul(Ctx *c, const u64 *A, const u64 *Bm, int Bn, int level, int n, int n1z, int n1t, u64 *out,
              bool relin_once = false, int dcd_z = 0, int dcd_t = 0);
+// products A[ia[p]] B[ib[p]] of shared operands (each operand's transforms once)
+void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const int *ia, const int *ib, int P,
+                   int level, int n, int n1z, int n1t, u64 *out, bool relin_once = false, int dcd_z = 0,
+                   int dcd_t = 0);
 
 }  // namespace he

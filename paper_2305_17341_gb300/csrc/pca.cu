@@ -260,11 +260,12 @@ public:
     }
 
     // ---------------------------------------------------------- covariance
-    // HCovMtrx (Sec. 5.3) in three stages, so that a server can merge the
+    // HCovMtrx (Sec. 5.2) in three stages, so that a server can merge the
     // block products of several jobs into one batched pass:
     //   1. cov_prepare: X_j[l]^T with 1/s folded into the G diagonals, and
     //      the replicated X_j[l]; appends the products X_a[l]^T X_b[l]
-    //      (a <= b) in the order a, b, l
+    //      (a <= b) in the order l, a, b, so that the k(k+1)/2 products of
+    //      a row block, which share their operands, run in one batch
     //   2. cov_upper: C[a][b] = sum over l of those products
     //   3. cov_finish: the blocks below the diagonal as G(C[b][a]), one
     //      common level, and (not centred) minus mu_a^T mu_b
@@ -287,24 +288,24 @@ public:
                 P.XT[l * k + j] = transpose(P.blocks[l * k + j], P.n, P.n1z, inv_s);
                 P.Xr[l * k + j] = replicated(P.blocks[l * k + j], P.n);
             }
-        for (int a = 0; a < k; a++)
-            for (int b = a; b < k; b++)
-                for (int l = 0; l < P.nrb; l++)
+        for (int l = 0; l < P.nrb; l++)
+            for (int a = 0; a < k; a++)
+                for (int b = a; b < k; b++)
                     prods.push_back({P.XT[l * k + a].p, P.Xr[l * k + b].p, P.n, P.n1z, P.n1t, P.relin_once});
     }
 
     // Takes ownership of the products made from cov_prepare's list.
     std::vector<HC> cov_upper(CovPlan &P, he_ct *const *outs) {
-        const int k = P.k;
+        const int k = P.k, ppl = k * (k + 1) / 2;
         std::vector<HC> own;
-        for (int t = 0; t < k * (k + 1) / 2 * P.nrb; t++) own.emplace_back(outs[t]);
+        for (int t = 0; t < ppl * P.nrb; t++) own.emplace_back(outs[t]);
         std::vector<HC> C(k * k);
-        size_t t = 0;
+        int pr = 0;   // index of the pair (a, b) within a row block
         for (int a = 0; a < k; a++)
-            for (int b = a; b < k; b++) {
-                HC acc = std::move(own[t++]);
+            for (int b = a; b < k; b++, pr++) {
+                HC acc = std::move(own[pr]);
                 for (int l = 1; l < P.nrb; l++) {
-                    HC o = std::move(own[t++]);
+                    HC o = std::move(own[(size_t)l * ppl + pr]);
                     add(c, acc->d, o->d, 1, acc->level, acc->d);
                 }
                 C[a * k + b] = std::move(acc);
@@ -360,7 +361,8 @@ public:
         std::vector<ProdSpec> prods;
         cov_prepare(P, prods);
         std::vector<he_ct *> outs;
-        run_products(prods, outs, kCovBatch);
+        const int ppl = k * (k + 1) / 2;
+        run_products(prods, outs, std::max(1, kCovBatch / ppl) * ppl);
         return cov_finish(P, cov_upper(P, outs.data()));
     }
 

@@ -10,7 +10,7 @@ namespace he {
 
 struct CovStage;
 
-// Stage 1 of HCovMtrx (Sec. 5.3): transposes and replicas of the blocks;
+// Stage 1 of HCovMtrx (Sec. 5.2): transposes and replicas of the blocks;
 // appends the block products to `prods`.  blocks[l*k + j] must stay alive
 // until cov_finish.
 CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z, int n1t,

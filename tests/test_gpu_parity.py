@@ -198,6 +198,34 @@ def test_hmatmul_batch_equals_single(c1):
         lib.he_ct_free(h)
 
 
+def test_hmatmul_batch_shared_operands(c1):
+    """Products of one batch that share operands (Sec. 5.2, covariance
+    Optimizations 1 and 2): every product bit-exact to its single
+    he_hmatmul, and the shared sigma/tau, C^k and R^k run once per operand --
+    4 products of 2 distinct A and 2 distinct B cost the key switches of 2
+    products plus the relinearisations (one MS, Dp and MD per k) of 2 more."""
+    lib, ctx, P, he = c1
+    n, n1 = 32, 8
+    from oracle.hmm import matmul_rot_steps
+    lib.he_keygen(ctx, matmul_rot_steps(n, n1, n1, P.S), want_relin=True)
+    (A0, B0, _, _, a0, b0), (A1, B1, _, _, a1, b1) = [_matrix_pair(P, he, lib, ctx, n, 110 + i) for i in range(2)]
+    pairs = [(a0, b0, A0, B0), (a0, b1, A0, B1), (a1, b0, A1, B0), (a0, b0, A0, B0)]
+    lib.he_counters(ctx, reset=True)
+    two = lib.he_hmatmul_batch([(a0, b0, n, n1, n1), (a1, b1, n, n1, n1)])
+    c2 = lib.he_counters(ctx, reset=True)
+    shared = lib.he_hmatmul_batch([(x, y, n, n1, n1) for x, y, _, _ in pairs])
+    c4 = lib.he_counters(ctx, reset=True)
+    for key in ("MS", "Dp", "MD"):
+        assert c4[key] - c2[key] == 2 * n, (key, c2, c4)
+    for o, (x, y, X, Y) in zip(shared, pairs):
+        s = lib.he_hmatmul(ctx, x, y, n, n1, n1)
+        assert np.array_equal(lib.he_ct_export(ctx, s), lib.he_ct_export(ctx, o))
+        assert np.abs(lib.he_decrypt_matrix(ctx, o, n, n) - X @ Y).max() < TOL
+        lib.he_ct_free(s)
+    for h in two + shared + [a0, b0, a1, b1]:
+        lib.he_ct_free(h)
+
+
 def test_hmatmul_levels_and_errors(c1):
     lib, ctx, P, he = c1
     n, n1 = 32, 8
