@@ -30,6 +30,21 @@ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q) {
     return a * w - h * q;
 }
 
+// High word of the 128-bit product a b from three of its four 32 x 32
+// partial products: dropping al bl and the low halves of ah bl and al bh
+// loses less than 3 units of 2^64, so the result is the exact high word
+// minus 0, 1 or 2.
+__device__ __forceinline__ u64 mulhi64_trunc(u64 a, u64 b) {
+    const u32 al = (u32)a, ah = (u32)(a >> 32), bl = (u32)b, bh = (u32)(b >> 32);
+    return (u64)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+}
+
+// a * w mod q in [0, 4q) for any a < 2^64 and q < 2^62: Shoup's product with
+// the truncated quotient (exact quotient minus at most 2).
+__device__ __forceinline__ u64 shoup_lazy4(u64 a, u64 w, u64 wp, u64 q) {
+    return a * w - mulhi64_trunc(a, wp) * q;
+}
+
 __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 wp, u64 q) {
     u64 r = shoup_lazy(a, w, wp, q);
     return r >= q ? r - q : r;

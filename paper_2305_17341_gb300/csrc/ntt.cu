@@ -190,15 +190,16 @@ struct PassGeom {
     }
 };
 
-// Forward butterfly without the reduction of x: x' = x + t, y' = x - t + 2q
-// (t = w y mod q in [0, 2q)).  Both outputs grow by less than 2q per stage,
-// so from inputs below 4q the 16 stages of a limb stay below 36q < 2^64 for
-// every prime below 2^58 (all the 40-bit levels); larger primes use bf_fwd.
+// Forward butterfly without the reduction of x: x' = x + t, y' = x - t + 4q
+// (t = w y mod q in [0, 4q), Shoup's product with the truncated quotient).
+// Both outputs grow by less than 4q per stage, so from inputs below 4q the
+// 16 stages of a limb stay below 68q < 2^64 for every prime below 2^57 (all
+// the 40-bit levels); larger primes use bf_fwd.
 __device__ __forceinline__ void bf_fwd_nored(u64 &x, u64 &y, u64 w, u64 wp, u64 q) {
-    u64 t = shoup_lazy(y, w, wp, q);
+    u64 t = shoup_lazy4(y, w, wp, q);
     u64 a = x;
     x = a + t;
-    y = a - t + 2 * q;
+    y = a - t + 4 * q;
 }
 
 // The 8 stages of one pass (4 in registers in layout A, a shared-memory
@@ -263,11 +264,11 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[(long)(t + T * k) * stride];
-    const bool red = q >= (1ull << 58);   // uniform over the CTA
+    const bool red = q >= (1ull << 57);   // uniform over the CTA
     if (red) fwd_pass_body<LM, ROWS, true>(x, sm, w2_, G, t, w, q);
     else fwd_pass_body<LM, ROWS, false>(x, sm, w2_, G, t, w, q);
     // the row pass ends with exact residues: [0, 4q) after reducing
-    // butterflies, below 36q after the others
+    // butterflies, below 68q after the others
     const u64 wone = mods[pidx].wone;
     if (ROWS && SUBSC) {
         const long arow = ep.row0 + row;
@@ -382,21 +383,23 @@ static void inv_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st
 }
 
 // ------------------------------------------------------ integer roofline
-// Peak rate of the forward butterfly (one lazy Shoup product and two lazy
-// add/sub) with operands in registers: 16 independent chains per thread,
-// `iters` rounds, every SM filled.  The result is the denominator of the
-// NTT's "alu" roofline.
+// Peak rate of the forward butterfly that the NTT runs on the limbs of every
+// prime below 2^57 (one lazy Shoup product with the truncated quotient and
+// two lazy add/sub, bf_fwd_nored) with operands in registers: 16 independent
+// chains per thread, `iters` rounds, every SM filled.  The values wrap
+// modulo 2^64 after a few rounds; only the instruction stream matters.  The
+// result is the denominator of the NTT's "alu" roofline.
 __global__ void k_bfly_peak(u64 *sink, int iters, u64 q, u64 w, u64 wp) {
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = (threadIdx.x * 16 + k) % q;
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int k = 0; k < 16; k += 2) bf_fwd(x[k], x[k + 1], w, wp, q);
+        for (int k = 0; k < 16; k += 2) bf_fwd_nored(x[k], x[k + 1], w, wp, q);
 #pragma unroll
         for (int k = 0; k < 16; k += 4) {
-            bf_fwd(x[k], x[k + 2], w, wp, q);
-            bf_fwd(x[k + 1], x[k + 3], w, wp, q);
+            bf_fwd_nored(x[k], x[k + 2], w, wp, q);
+            bf_fwd_nored(x[k + 1], x[k + 3], w, wp, q);
         }
     }
     u64 acc = 0;
@@ -406,7 +409,7 @@ __global__ void k_bfly_peak(u64 *sink, int iters, u64 q, u64 w, u64 wp) {
 }
 
 double bfly_peak(int iters) {
-    const u64 q = 1152921504606748673ull;  // a 60-bit prime = 1 mod 2^15
+    const u64 q = 1099510054913ull;  // a 40-bit prime = 1 mod 2^17
     const u64 w = 123456789012345ull % q;
     ShoupPair sp = h_shoup(w, q);
     int nsm = 0, dev = 0;
