@@ -39,7 +39,7 @@ void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits) 
 
 // ModDown: items of [rows][N] over Q_l P (contiguous) -> out items of [l+1][N]
 // with item stride out_s.
-void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s) {
+void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s, const u64 *add, long add_s) {
     const int N = c->N, rows = c->qp_rows(level), a = c->alpha;
     Buf pc(&c->pool, (size_t)items * a * N), conv(&c->pool, (size_t)items * (level + 1) * N);
     launch_copy_rows(pc.p, (long)a * N, u + (long)(level + 1) * N, (long)rows * N, items, (long)a * N, c->stream);
@@ -50,10 +50,11 @@ void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s) {
         SubScale ep;
         ep.u = u, ep.us = (long)rows * N, ep.out = out, ep.os = out_s, ep.w = c->d_dn_Pinv;
         ep.rows_per_item = level + 1;
+        ep.add = add, ep.as = add_s;
         ntt_fwd_subscale(c, conv.p, (long)items * (level + 1), c->map_q(level), c->stream, ep);
     } else {
         ntt_fwd(c, conv.p, (long)items * (level + 1), c->map_q(level), c->stream);
-        launch_moddown_final(c, out, u, conv.p, nullptr, items, level, (long)rows * N, out_s, 0, c->stream);
+        launch_moddown_final(c, out, u, conv.p, add, items, level, (long)rows * N, out_s, add_s, c->stream);
     }
 }
 
@@ -130,34 +131,29 @@ void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out) {
 }
 
 // out (holding (d0, d1)) += KeySwitch(d2, rlk): the relinearisation of Mult.
+// The ModDown's last store adds into out in place.
 static void relin_into(Ctx *c, const u64 *d2, int B, int level, u64 *out) {
     if (!c->rlk) throw HeError(HE_ERR_KEY_MISSING, "relinearisation key missing");
     const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
     Buf dg(&c->pool, (size_t)B * c->ndig(level) * rows * N);
     modup(c, d2, (long)nq * N, B, level, dg.p);
-    Buf u(&c->pool, (size_t)B * 2 * rows * N), md(&c->pool, (size_t)B * 2 * nq * N);
+    Buf u(&c->pool, (size_t)B * 2 * rows * N);
     launch_multsum(c, u.p, dg.p, c->rlk, 1u, B, level, nullptr, 0, c->stream);
     c->n_ms += B;
-    moddown(c, u.p, 2 * B, level, md.p, (long)nq * N);
+    moddown(c, u.p, 2 * B, level, out, (long)nq * N, out, (long)nq * N);
     c->n_md += B;
-    launch_add(c, out, out, md.p, 2L * B * nq, c->map_q(level), c->stream);
 }
 
-// Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk).
-void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out) {
+// Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk);
+// with accumulate, the product is added to what out holds (the tensor adds
+// (d0, d1), the ModDown's last store adds the key switch).
+void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out, bool accumulate) {
     if (!c->rlk) throw HeError(HE_ERR_KEY_MISSING, "relinearisation key missing");
-    const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
+    const int N = c->N, nq = level + 1;
     const long cs = 2L * nq * N;
     Buf d2(&c->pool, (size_t)B * nq * N);
-    launch_tensor(c, out, d2.p, a, b, B, nq, cs, cs, c->map_q(level), c->stream);
-    Buf dg(&c->pool, (size_t)B * c->ndig(level) * rows * N);
-    modup(c, d2.p, (long)nq * N, B, level, dg.p);
-    Buf u(&c->pool, (size_t)B * 2 * rows * N), md(&c->pool, (size_t)B * 2 * nq * N);
-    launch_multsum(c, u.p, dg.p, c->rlk, 1u, B, level, nullptr, 0, c->stream);
-    c->n_ms += B;
-    moddown(c, u.p, 2 * B, level, md.p, (long)nq * N);
-    c->n_md += B;
-    launch_add(c, out, out, md.p, 2L * B * nq, c->map_q(level), c->stream);
+    launch_tensor_acc(c, out, d2.p, a, b, B, nq, cs, cs, c->map_q(level), c->stream, accumulate, false);
+    relin_into(c, d2.p, B, level, out);
 }
 
 void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out) {
@@ -370,7 +366,7 @@ void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const in
     modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, nB, l1, dB.p);
     int gA = 0, gB = 0;
 
-    Buf acc(&c->pool, P * ct2), Ak(&c->pool, nA * ct2), Bk(&c->pool, nB * ct2), prod(&c->pool, P * ct2);
+    Buf acc(&c->pool, P * ct2), Ak(&c->pool, nA * ct2), Bk(&c->pool, nB * ct2);
     // the operands of every product, gathered when operands are shared
     Buf AkP(&c->pool, ident ? 1 : P * ct2), BkP(&c->pool, ident ? 1 : P * ct2);
     // relin_once: the summed d2 of the n tensors (d0, d1 are summed in acc)
@@ -467,11 +463,8 @@ void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const in
         if (relin_once) {
             const long cs = 2L * (l2 + 1) * N;
             launch_tensor(c, acc.p, acc2.p, xa, xb, P, l2 + 1, cs, cs, q2, c->stream, k > 0);
-        } else if (k == 0) {
-            mult_relin(c, xa, xb, P, l2, acc.p);
         } else {
-            mult_relin(c, xa, xb, P, l2, prod.p);
-            launch_add(c, acc.p, acc.p, prod.p, 2L * P * (l2 + 1), q2, c->stream);
+            mult_relin(c, xa, xb, P, l2, acc.p, k > 0);
         }
     }
     if (relin_once) relin_into(c, acc2.p, P, l2, acc.p);

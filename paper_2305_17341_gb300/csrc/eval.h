@@ -21,7 +21,9 @@ const char *last_error();
 double bfly_peak(int iters);
 
 void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits);
-void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s);
+// add (may be null, item stride add_s; may equal out): out = add + ModDown(u)
+void moddown(Ctx *c, const u64 *u, int items, int level, u64 *out, long out_s, const u64 *add = nullptr,
+             long add_s = 0);
 void rot_qp(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, uint32_t g, u64 *out);
 void rot_qp_multi(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, const uint32_t *gs, int G,
                   u64 *const *outs);
@@ -29,7 +31,7 @@ void rotate_digits(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, u
 void rotate(Ctx *c, const u64 *ct, int B, int level, uint32_t g, u64 *out);
 void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out);
 void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out);
-void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
+void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out, bool accumulate = false);
 void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
 const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level,
                   const DcdFactor *fac = nullptr);

@@ -256,6 +256,8 @@ struct SubScale {
     const ShoupPair *w = nullptr;
     int rows_per_item = 1;
     long row0 = 0;   // absolute index of the launch's first row
+    const u64 *add = nullptr;   // optional addend, laid out like out (item stride as)
+    long as = 0;
 };
 void ntt_fwd_subscale(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, const SubScale &ep);
 void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st);
@@ -283,9 +285,12 @@ void launch_mulconst_rows(Ctx *c, u64 *out, const u64 *a, const ShoupPair *w, lo
 void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &rm, uint32_t g,
                       cudaStream_t st);
 // (d0, d1) -> d01 [B][2][limbs][N], d2 -> [B][limbs][N]; accumulate adds
-// the tensor to what d01 and d2 already hold.
+// the tensor to what d01 and d2 already hold (acc01 / acc2 select the two
+// outputs separately when given).
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long a_item_stride,
                    long b_item_stride, const RowMap &rm, cudaStream_t st, bool accumulate = false);
+void launch_tensor_acc(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
+                       const RowMap &rm, cudaStream_t st, bool acc01, bool acc2);
 // key switching pieces
 // own_ntt (may be null): the input in the NTT domain, item stride own_s; the
 // digit's own rows are then copied from it (and the forward NTT must skip

@@ -319,11 +319,11 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
     u64 *o = d01 + (long)it * 2 * per + off;
     u64 v0 = mulmod(a0, b0, m), v1 = redc(t1 * m.r2, mulhi64(t1, m.r2), m), v2 = mulmod(a1, b1, m);
     u64 *o2 = d2 + (long)it * per + off;
-    if (accumulate) {
+    if (accumulate & 1) {
         v0 = addmod(v0, o[0], m.q);
         v1 = addmod(v1, o[per], m.q);
-        v2 = addmod(v2, o2[0], m.q);
     }
+    if (accumulate & 2) v2 = addmod(v2, o2[0], m.q);
     o[0] = v0;
     o[per] = v1;
     o2[0] = v2;
@@ -332,7 +332,14 @@ void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B,
                    const RowMap &rm, cudaStream_t st, bool accumulate) {
     long n = (long)B * limbs * c->N;
     c->n_launch++;
-    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod, accumulate ? 1 : 0);
+    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod, accumulate ? 3 : 0);
+}
+void launch_tensor_acc(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
+                       const RowMap &rm, cudaStream_t st, bool acc01, bool acc2) {
+    long n = (long)B * limbs * c->N;
+    c->n_launch++;
+    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod,
+                                           (acc01 ? 1 : 0) | (acc2 ? 2 : 0));
 }
 
 // ------------------------------------------------------------- ModUp

@@ -278,11 +278,14 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
         const long off = (long)r * N + seq * M;
         const u64 *up = ep.u + it * ep.us + off;
         u64 *op = ep.out + it * ep.os + off;
+        const u64 *ap = ep.add ? ep.add + it * ep.as + off : nullptr;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             const u64 s = sm[G_::sidx(t + T * k, w)];
             const u64 v = red ? reduce4q(s, q) : reduce_any(s, q, wone);
-            op[t + T * k] = shoup(submod(up[t + T * k], v, q), wr.w, wr.wp, q);
+            u64 o = shoup(submod(up[t + T * k], v, q), wr.w, wr.wp, q);
+            if (ap) o = addmod(o, ap[t + T * k], q);
+            op[t + T * k] = o;
         }
         return;
     }
