@@ -440,6 +440,7 @@ def run_ours(args, rank, world, dist):
                 "d2h_bytes_per_step": B * w_out * 8},
         "clocks": ck, "gpu_launches": launches,
         "check": {"max_abs_err": err, "tol": 1e-4, "batch_equals_single_bitexact": bitexact},
+        "ntt_launch_tuning": [x for x in pk.he_autotune_log(ctx).splitlines() if x.startswith("ntt")],
     }
     if n_mat != N_MAT:
         line["note"] = "profiling case (n=%d), not the benchmark workload" % n_mat

@@ -182,10 +182,12 @@ struct Ctx {
     // launch-geometry autotuner: per (kernel, shape) the fastest variant,
     // timed on first use (variants compute identical words)
     bool autotune = true;
-    int ntt_minb = 2;        // CTAs per SM the register-blocked NTT is compiled for (2 or 3)
+    int ntt_minb = 2;        // CTAs per SM of the register-blocked forward NTT (2 or 3)
+    int ntt_minb_inv = 2;    // and of the inverse NTT
     bool ntt_tuned = false;
+    // (level, items, keys) -> (keys per launch << 8) | variant
     std::map<std::tuple<int, int, int>, int> tune_multsum;
-    std::string tune_log;   // every timed plan: "multsum level B G chunk BI stream ms"   // (level, items, keys) -> (keys per launch << 8) | variant
+    std::string tune_log;   // every timed plan, one line each
     TraceClass tr[4];                 // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv
     std::vector<cudaEvent_t> ev_free;
     cudaEvent_t ev_get();

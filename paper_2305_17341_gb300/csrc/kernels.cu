@@ -577,7 +577,7 @@ struct MultiKeys {
 // Each digit word is loaded once and multiplied into the 2G accumulators of
 // the G keys (2G independent accumulation chains per thread).
 template <int G, bool STREAM>
-__global__ void __launch_bounds__(256) k_multsum_multi(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
+__global__ void __launch_bounds__(256, G <= 2 ? 4 : G <= 5 ? 2 : 1) k_multsum_multi(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
                                                        int alpha, int L, int ndig, int nprimes, int logN,
                                                        const ModQ *mods, const u64 *c0, long c0s,
                                                        const ShoupPair *Pmod) {
@@ -595,15 +595,36 @@ __global__ void __launch_bounds__(256) k_multsum_multi(MultiKeys<G> mk, const u6
     const u64 *dp = digits + (long)b * ndig * dstride + (long)r * N + y;
     const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
     U128 a0[G], a1[G];
+    if (m.q < (1ull << 42)) {
+        // residues below 2^42 (uniform over the CTA): 96-bit accumulation
+        u32 x0[2 * G], x1[2 * G], x2[2 * G];
 #pragma unroll
-    for (int k = 0; k < G; k++) a0[k] = U128{0, 0}, a1[k] = U128{0, 0};
-    for (int d = 0; d < ndig; d++) {
-        const u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
+        for (int k = 0; k < 2 * G; k++) x0[k] = 0, x1[k] = 0, x2[k] = 0;
+        for (int d = 0; d < ndig; d++) {
+            const u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
+#pragma unroll
+            for (int k = 0; k < G; k++) {
+                const u64 *kp = mk.key[k] + (long)d * kd + koff;
+                mac96(x0[2 * k], x1[2 * k], x2[2 * k], v, __ldg(kp));
+                mac96(x0[2 * k + 1], x1[2 * k + 1], x2[2 * k + 1], v, __ldg(kp + kk));
+            }
+        }
 #pragma unroll
         for (int k = 0; k < G; k++) {
-            const u64 *kp = mk.key[k] + (long)d * kd + koff;
-            mac128(a0[k], v, __ldg(kp));
-            mac128(a1[k], v, __ldg(kp + kk));
+            a0[k] = U128{((u64)x1[2 * k] << 32) | x0[2 * k], x2[2 * k]};
+            a1[k] = U128{((u64)x1[2 * k + 1] << 32) | x0[2 * k + 1], x2[2 * k + 1]};
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k++) a0[k] = U128{0, 0}, a1[k] = U128{0, 0};
+        for (int d = 0; d < ndig; d++) {
+            const u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
+#pragma unroll
+            for (int k = 0; k < G; k++) {
+                const u64 *kp = mk.key[k] + (long)d * kd + koff;
+                mac128(a0[k], v, __ldg(kp));
+                mac128(a1[k], v, __ldg(kp + kk));
+            }
         }
     }
     u64 pc0 = 0;

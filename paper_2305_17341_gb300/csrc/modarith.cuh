@@ -84,6 +84,24 @@ __device__ __forceinline__ void mac128(U128 &acc, u64 a, u64 b) {
     acc.lo = nlo;
 }
 
+// 96-bit accumulation (w2 w1 w0) of products of residues below 2^42: each
+// product is below 2^84, so a sum of up to 2^12 of them stays below 2^96.
+// (w2 w1 w0) += a b from the four 32 x 32 partial products with the carry
+// chain of the 32-bit multiply-add (a1 b1 < 2^20 has no high word).
+__device__ __forceinline__ void mac96(u32 &w0, u32 &w1, u32 &w2, u64 a, u64 b) {
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32), b0 = (u32)b, b1 = (u32)(b >> 32);
+    asm("mad.lo.cc.u32 %0, %3, %5, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %5, %1;\n\t"
+        "addc.u32 %2, %2, 0;\n\t"
+        "mad.lo.cc.u32 %1, %3, %6, %1;\n\t"
+        "madc.hi.u32 %2, %3, %6, %2;\n\t"
+        "mad.lo.cc.u32 %1, %4, %5, %1;\n\t"
+        "madc.hi.u32 %2, %4, %5, %2;\n\t"
+        "mad.lo.u32 %2, %4, %6, %2;"
+        : "+r"(w0), "+r"(w1), "+r"(w2)
+        : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
+}
+
 // Montgomery REDC: x * 2^-64 mod q for x < q 2^64, result in [0, q).
 __device__ __forceinline__ u64 redc(u64 lo, u64 hi, const ModQ &m) {
     u64 t = lo * m.qinv;

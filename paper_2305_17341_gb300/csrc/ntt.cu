@@ -379,7 +379,7 @@ static void inv_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st
     typedef PassGeom<LM, ROWS> G_;
     dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
     const ulonglong2 *t2 = (const ulonglong2 *)ctx->d_ipsi2;
-    if (ctx->ntt_minb == 3)
+    if (ctx->ntt_minb_inv == 3)
         k_ntt_inv_fast<LM, ROWS, 3><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
     else
         k_ntt_inv_fast<LM, ROWS, 2><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
@@ -453,6 +453,10 @@ static void split(int logN, int &logN1, int &C, int &R) {
 // Picks the register budget of the register-blocked passes (2 or 3 CTAs per
 // SM) by timing a forward and an inverse transform of 256 scratch rows with
 // each; runs once per context, outside stream capture.
+// Picks the CTAs per SM (2 or 3) of the register-blocked passes, forward
+// and inverse separately: each variant transforms 1024 rows over the
+// context's whole chain (the 40-bit limbs run the non-reducing butterflies,
+// as in Decompose), 3 repetitions, fastest kept.
 static void tune_ntt(Ctx *ctx, cudaStream_t st) {
     ctx->ntt_tuned = true;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -461,38 +465,45 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
         ctx->ntt_tuned = false;
         return;
     }
-    const long R = 256;
+    const long R = 1024;
     Buf scratch(&ctx->pool, (size_t)R * ctx->N);
-    cudaMemsetAsync(scratch.p, 0, (size_t)R * ctx->N * 8, st);
+    // any words do for timing; 0x15.. keeps them below the 60-bit primes
+    cudaMemsetAsync(scratch.p, 0x15, (size_t)R * ctx->N * 8, st);
     int logN1, C, Rr;
     split(ctx->logN, logN1, C, Rr);
-    RowMap m = ctx->map_q(0);
+    RowMap m = ctx->map_qp(ctx->L);
     RowSkip none;
     cudaEvent_t a = ctx->ev_get(), b = ctx->ev_get();
-    float best = 1e30f;
-    int pick = 2;
-    for (int minb : {2, 3}) {
-        ctx->ntt_minb = minb;
-        float t = 1e30f;
-        for (int rep = 0; rep < 2; rep++) {
-            cudaEventRecord(a, st);
-            if (logN1 == 8) fwd_pass<8, false>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, false>(ctx, scratch.p, R, m, st, none);
-            if (ctx->logN - logN1 == 8) fwd_pass<8, true>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, true>(ctx, scratch.p, R, m, st, none);
-            if (ctx->logN - logN1 == 8) inv_pass<8, true>(ctx, scratch.p, R, m, st); else inv_pass<7, true>(ctx, scratch.p, R, m, st);
-            if (logN1 == 8) inv_pass<8, false>(ctx, scratch.p, R, m, st); else inv_pass<7, false>(ctx, scratch.p, R, m, st);
-            cudaEventRecord(b, st);
-            cudaEventSynchronize(b);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, a, b);
-            t = std::min(t, ms);
+    for (int dir = 0; dir < 2; dir++) {
+        float best = 1e30f;
+        int pick = 2;
+        for (int minb : {2, 3}) {
+            (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = minb;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; rep++) {
+                cudaEventRecord(a, st);
+                if (dir == 0) {
+                    if (logN1 == 8) fwd_pass<8, false>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, false>(ctx, scratch.p, R, m, st, none);
+                    if (ctx->logN - logN1 == 8) fwd_pass<8, true>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, true>(ctx, scratch.p, R, m, st, none);
+                } else {
+                    if (ctx->logN - logN1 == 8) inv_pass<8, true>(ctx, scratch.p, R, m, st); else inv_pass<7, true>(ctx, scratch.p, R, m, st);
+                    if (logN1 == 8) inv_pass<8, false>(ctx, scratch.p, R, m, st); else inv_pass<7, false>(ctx, scratch.p, R, m, st);
+                }
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                t = std::min(t, ms);
+                ctx->n_launch += 2;
+            }
+            char line[112];
+            snprintf(line, sizeof line, "ntt %s logN %d rows %ld ctas_per_sm %d ms %.4f\n", dir ? "inverse" : "forward",
+                     ctx->logN, R, minb, t);
+            ctx->tune_log += line;
+            if (t < best) best = t, pick = minb;
         }
-        ctx->n_launch += 8;
-        char line[96];
-        snprintf(line, sizeof line, "ntt logN %d rows %ld ctas_per_sm %d ms %.4f\n", ctx->logN, R, minb, t);
-        ctx->tune_log += line;
-        if (t < best) best = t, pick = minb;
+        (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = pick;
     }
-    ctx->ntt_minb = pick;
     ctx->ev_free.push_back(a);
     ctx->ev_free.push_back(b);
 }
