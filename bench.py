@@ -238,7 +238,7 @@ def run_ours(args, rank, world, dist):
     clocks = Clocks(local)
     pk.he_counters(ctx, reset=True)
     pk.he_trace_enable(ctx, True)
-    for c in range(3):
+    for c in range(5):
         pk.he_trace_read(ctx, c, reset=True)
     barrier()
     torch.cuda.synchronize()
@@ -254,7 +254,7 @@ def run_ours(args, rank, world, dist):
     barrier()
     ck = clocks.stop()
     ms_total = e0.elapsed_time(e1)
-    tr = [pk.he_trace_read(ctx, c, reset=True) for c in range(3)]
+    tr = [pk.he_trace_read(ctx, c, reset=True) for c in range(5)]
     pk.he_trace_enable(ctx, False)
     launches = pk.he_counters(ctx, reset=True)["launches"]
     t_max = max_over_ranks(ms_total, dist, "cuda")
@@ -401,6 +401,11 @@ def run_ours(args, rank, world, dist):
     roof_ni = ntt_roof(tr[2])
     totals = {"multsum": tr[0]["ms"], "ntt_fwd": tr[1]["ms"], "ntt_inv": tr[2]["ms"]}
     dominant = max(totals, key=totals.get)
+    # the two basis conversions (integer ALU with streaming stores): time and
+    # algorithmic GB/s, for attribution
+    conv = {name: {"ms": t["ms"], "launches": t["count"],
+                   "algorithmic_gbs": t["bytes"] / (t["ms"] / 1e3) / 1e9 if t["ms"] else None}
+            for name, t in (("modup_bconv", tr[3]), ("moddown_bconv", tr[4]))}
     roof = {"multsum": roof_ms, "ntt_fwd": roof_nf, "ntt_inv": roof_ni}[dominant]
     roof = dict(roof, kernel=dominant, share_of_step=totals[dominant] / ms_total)
 
@@ -432,7 +437,8 @@ def run_ours(args, rank, world, dist):
         "plain": {"value": plain, "unit": UNIT, "note": "same products, one he_hmatmul call each"},
         "batched_over_plain": value / world / plain,
         "roofline": roof, "roofline_keyswitch": roof_ms, "roofline_ntt_fwd": roof_nf, "roofline_ntt_inv": roof_ni,
-        "kernel_time_ms": totals,
+        "kernel_time_ms": dict(totals, modup_bconv=tr[3]["ms"], moddown_bconv=tr[4]["ms"]),
+        "conversions": conv,
         "graph": graph,
         "relin_once": once_line,
         "cpu_baseline": cpu,

@@ -329,7 +329,8 @@ int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long l
 
 /* Kernel tracing.  While enabled, the library records a CUDA event pair on the
  * context's stream around every launch of the traced kernel classes
- *   0 MultSum (key-switch inner product), 1 forward NTT, 2 inverse NTT
+ *   0 MultSum (key-switch inner product), 1 forward NTT, 2 inverse NTT,
+ *   3 ModUp basis conversion (Decompose), 4 ModDown basis conversion
  * and adds the launch's algorithmic bytes (words the operation must read and
  * write once).  he_trace_read synchronises the stream and returns, for one
  * class, the number of launches, their summed device time (ms) and bytes. */

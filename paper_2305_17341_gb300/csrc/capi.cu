@@ -861,7 +861,7 @@ int he_trace_enable(he_ctx *ctx, int on) {
 }
 
 int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, double *bytes, int reset) {
-    if (!ctx || cls < 0 || cls > 2) return fail(HE_ERR_ARG, "bad arguments");
+    if (!ctx || cls < 0 || cls > 4) return fail(HE_ERR_ARG, "bad arguments");
     Ctx &c = ctx->c;
     c.trace_collect();
     Ctx::TraceClass &t = c.tr[cls];

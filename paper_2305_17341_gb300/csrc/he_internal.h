@@ -188,7 +188,7 @@ struct Ctx {
     // (level, items, keys) -> (keys per launch << 8) | variant
     std::map<std::tuple<int, int, int>, int> tune_multsum;
     std::string tune_log;   // every timed plan, one line each
-    TraceClass tr[4];                 // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv
+    TraceClass tr[5];   // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv, 4 ModDown BConv
     std::vector<cudaEvent_t> ev_free;
     cudaEvent_t ev_get();
     void trace_begin(int cls, cudaEvent_t &e0);

@@ -405,8 +405,12 @@ void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cud
     const LevelConsts &L = c->lc(level);
     long n = (long)B * L.ndig * c->N;
     c->n_launch++;
+    cudaEvent_t e0;
+    c->trace_begin(3, e0);
     k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, L.ndig, c->N, c->map_qp(level),
                                                 c->d_mod, L.d_up_inv, L.d_up_mod, own_ntt, own_s);
+    // the input limbs once, every digit's extended limbs once
+    c->trace_end(3, e0, 8.0 * B * c->N * ((level + 1) + (double)L.ndig * c->qp_rows(level)));
 }
 
 // Same conversion with caller-supplied constants (layout of LevelConsts).
@@ -525,8 +529,11 @@ __global__ void __launch_bounds__(256) k_moddown_bconv(const u64 *pcoef, u64 *ou
 void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st) {
     long n = (long)items * c->N;
     c->n_launch++;
+    cudaEvent_t e0;
+    c->trace_begin(4, e0);
     k_moddown_bconv<<<nblk(n, 256), 256, 0, st>>>(pcoef, out, items, level, c->alpha, c->L, c->N, c->d_mod,
                                                   c->d_dn_pinv, c->d_dn_pmod, c->d_dn_hp, c->d_Pmod, c->d_dn_hq);
+    c->trace_end(4, e0, 8.0 * items * c->N * (c->alpha + level + 1));
 }
 
 // out_r = (u_r - conv_r) P^-1 mod q_r (+ addend_r), NTT domain, r <= level.

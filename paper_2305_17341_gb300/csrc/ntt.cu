@@ -9,6 +9,9 @@
 // psi^(2 brv(j) + 1).  Inverse: Gentleman-Sande with psi^-brv(k), bit-reversed
 // in, natural out, times N^-1.  Harvey's lazy butterflies keep values in
 // [0, 4q) (forward) / [0, 2q) (inverse) between stages; the output is in [0, q).
+// The register-blocked kernels for logN 14..16 go lazier: the forward skips
+// the per-stage reduction on primes below 2^57 and the inverse keeps values
+// in [0, 4q), both with a truncated-quotient Shoup product.
 //
 // Each limb of N = N1 * N2 coefficients is transformed in two passes: pass 1
 // runs the stages whose butterfly span is >= N2 on column tiles (elements with
@@ -37,6 +40,18 @@ __device__ __forceinline__ void bf_inv(u64 &x, u64 &y, u64 w, u64 wp, u64 q) {
     u64 d = x - y + tq;
     x = s;
     y = shoup_lazy(d, w, wp, q);
+}
+
+// Inverse butterfly on values in [0, 4q): s = x + y reduced below 4q,
+// y' = w (x - y + 4q) with the truncated-quotient Shoup product, in [0, 4q)
+// (8q < 2^64 for every prime below 2^61).
+__device__ __forceinline__ void bf_inv4(u64 &x, u64 &y, u64 w, u64 wp, u64 q) {
+    const u64 fq = 4 * q;
+    u64 s = x + y;
+    s = s >= fq ? s - fq : s;
+    const u64 d = x - y + fq;
+    x = s;
+    y = shoup_lazy4(d, w, wp, q);
 }
 
 // ---------------------------------------------------------------- forward
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_inv_fast(u64 *data, RowMap rm
         for (int k = 0; k < 16; k++)
             if (!(k & sp)) {
                 const ulonglong2 w = __ldg(w2_ + mb + k / (2 * sp));
-                bf_inv(x[k], x[k + sp], w.x, w.y, q);
+                bf_inv4(x[k], x[k + sp], w.x, w.y, q);
             }
     }
 #pragma unroll
@@ -343,7 +358,7 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_inv_fast(u64 *data, RowMap rm
         for (int k = 0; k < 16; k++)
             if (!(k & s)) {
                 const ulonglong2 w = __ldg(w2_ + mb + k / (2 * s));
-                bf_inv(x[k], x[k + s], w.x, w.y, q);
+                bf_inv4(x[k], x[k + s], w.x, w.y, q);
             }
     }
     if (!ROWS) {
