@@ -130,6 +130,15 @@ void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out) {
     launch_copy_rows(out, (long)(to + 1) * N, in, (long)(level + 1) * N, 2 * B, (long)(to + 1) * N, c->stream);
 }
 
+// out[p] = in[idx[p]] dropped from level to `to` (both polynomials).
+static void drop_gather(Ctx *c, const u64 *in, const int *idx, int P, int level, int to, u64 *out) {
+    const int N = c->N;
+    for (int p = 0; p < P; p++)
+        launch_copy_rows(out + (size_t)p * 2 * (to + 1) * N, (long)(to + 1) * N,
+                         in + (size_t)idx[p] * 2 * (level + 1) * N, (long)(level + 1) * N, 2, (long)(to + 1) * N,
+                         c->stream);
+}
+
 // out (holding (d0, d1)) += KeySwitch(d2, rlk): the relinearisation of Mult.
 // The ModDown's last store adds into out in place.
 static void relin_into(Ctx *c, const u64 *d2, int B, int level, u64 *out) {
@@ -147,12 +156,14 @@ static void relin_into(Ctx *c, const u64 *d2, int B, int level, u64 *out) {
 // Mult (App. A): tensor (d0, d1, d2), then (d0, d1) + KeySwitch(d2, rlk);
 // with accumulate, the product is added to what out holds (the tensor adds
 // (d0, d1), the ModDown's last store adds the key switch).
-void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out, bool accumulate) {
+void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out, bool accumulate, int b_level) {
     if (!c->rlk) throw HeError(HE_ERR_KEY_MISSING, "relinearisation key missing");
     const int N = c->N, nq = level + 1;
     const long cs = 2L * nq * N;
+    if (b_level < level) b_level = level;
     Buf d2(&c->pool, (size_t)B * nq * N);
-    launch_tensor_acc(c, out, d2.p, a, b, B, nq, cs, cs, c->map_q(level), c->stream, accumulate, false);
+    launch_tensor_acc(c, out, d2.p, a, b, B, nq, cs, 2L * (b_level + 1) * N, c->map_q(level), c->stream, accumulate,
+                      false, (long)(b_level + 1) * N);
     relin_into(c, d2.p, B, level, out);
 }
 
@@ -366,7 +377,7 @@ void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const in
     modup(c, Bg.p + (long)(l1 + 1) * N, (long)ct1, nB, l1, dB.p);
     int gA = 0, gB = 0;
 
-    Buf acc(&c->pool, P * ct2), Ak(&c->pool, nA * ct2), Bk(&c->pool, nB * ct2);
+    Buf acc(&c->pool, P * ct2), Ak(&c->pool, nA * ct2);
     // the operands of every product, gathered when operands are shared
     Buf AkP(&c->pool, ident ? 1 : P * ct2), BkP(&c->pool, ident ? 1 : P * ct2);
     // relin_once: the summed d2 of the n tensors (d0, d1 are summed in acc)
@@ -444,27 +455,25 @@ void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const in
             gB++;
             if (nbB > 0) babies_B();
         }
-        if (bb == 0) {
-            drop(c, Bg.p, nB, l1, l2, Bk.p);
-        } else {
-            drop(c, BB.p + (size_t)(bb - 1) * nB * ct1, nB, l1, l2, Bk.p);
-        }
+        // B^(k) stays at level l1: the tensor reads its first l2 + 1 limbs
+        const u64 *bsrc = bb == 0 ? Bg.p : BB.p + (size_t)(bb - 1) * nB * ct1;
         // ---- product, relinearised, accumulated at level l2
-        const u64 *xa = Ak.p, *xb = Bk.p;
+        const u64 *xa = Ak.p, *xb = bsrc;
+        int b_level = l1;
         if (!ident) {
             for (int p = 0; p < P; p++) {
                 cudaMemcpyAsync(AkP.p + (size_t)p * ct2, Ak.p + (size_t)ia[p] * ct2, ct2 * 8,
                                 cudaMemcpyDeviceToDevice, c->stream);
-                cudaMemcpyAsync(BkP.p + (size_t)p * ct2, Bk.p + (size_t)ib[p] * ct2, ct2 * 8,
-                                cudaMemcpyDeviceToDevice, c->stream);
             }
-            xa = AkP.p, xb = BkP.p;
+            drop_gather(c, bsrc, ib, P, l1, l2, BkP.p);
+            xa = AkP.p, xb = BkP.p, b_level = l2;
         }
         if (relin_once) {
             const long cs = 2L * (l2 + 1) * N;
-            launch_tensor(c, acc.p, acc2.p, xa, xb, P, l2 + 1, cs, cs, q2, c->stream, k > 0);
+            launch_tensor(c, acc.p, acc2.p, xa, xb, P, l2 + 1, cs, 2L * (b_level + 1) * N, q2, c->stream, k > 0,
+                          (long)(b_level + 1) * N);
         } else {
-            mult_relin(c, xa, xb, P, l2, acc.p, k > 0);
+            mult_relin(c, xa, xb, P, l2, acc.p, k > 0, b_level);
         }
     }
     if (relin_once) relin_into(c, acc2.p, P, l2, acc.p);

@@ -31,7 +31,9 @@ void rotate_digits(Ctx *c, const u64 *ct, int B, int level, const u64 *digits, u
 void rotate(Ctx *c, const u64 *ct, int B, int level, uint32_t g, u64 *out);
 void rescale(Ctx *c, const u64 *in, int B, int level, u64 *out);
 void drop(Ctx *c, const u64 *in, int B, int level, int to, u64 *out);
-void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out, bool accumulate = false);
+// b may sit at a higher level b_level (its first level + 1 limbs are used in place)
+void mult_relin(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out, bool accumulate = false,
+                int b_level = -1);
 void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
 const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level,
                   const DcdFactor *fac = nullptr);

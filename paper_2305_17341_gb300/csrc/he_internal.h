@@ -288,11 +288,13 @@ void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &
                       cudaStream_t st);
 // (d0, d1) -> d01 [B][2][limbs][N], d2 -> [B][limbs][N]; accumulate adds
 // the tensor to what d01 and d2 already hold (acc01 / acc2 select the two
-// outputs separately when given).
+// outputs separately when given).  b_poly_stride: words from b's first
+// polynomial to its second (0: limbs * N).
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long a_item_stride,
-                   long b_item_stride, const RowMap &rm, cudaStream_t st, bool accumulate = false);
+                   long b_item_stride, const RowMap &rm, cudaStream_t st, bool accumulate = false,
+                   long b_poly_stride = 0);
 void launch_tensor_acc(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
-                       const RowMap &rm, cudaStream_t st, bool acc01, bool acc2);
+                       const RowMap &rm, cudaStream_t st, bool acc01, bool acc2, long b_poly_stride = 0);
 // key switching pieces
 // own_ntt (may be null): the input in the NTT domain, item stride own_s; the
 // digit's own rows are then copied from it (and the forward NTT must skip

@@ -300,9 +300,12 @@ void launch_automorph(Ctx *c, u64 *out, const u64 *in, long rows, const RowMap &
 }
 
 // tensor product in the NTT domain: d0 = a0 b0, d1 = a0 b1 + a1 b0, d2 = a1 b1.
-// d01: [B][2][limbs][N] (d0, d1 of each item); d2: [B][limbs][N].
+// d01: [B][2][limbs][N] (d0, d1 of each item); d2: [B][limbs][N].  The
+// operands' first `limbs` limbs are used: item strides as, bs; b's second
+// polynomial starts bps words after its first (a higher-level b is read in
+// place, without a level-dropping copy).
 __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, int N,
-                         long as, long bs, RowMap rm, const ModQ *mods, int accumulate) {
+                         long as, long bs, long bps, RowMap rm, const ModQ *mods, int accumulate) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long per = (long)limbs * N;
     if (idx >= (long)B * per) return;
@@ -311,7 +314,7 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
     int limb = (int)(off / N);
     const ModQ &m = mods[rm.at(limb)];
     const u64 *pa = a + it * as, *pb = b + it * bs;
-    u64 a0 = pa[off], a1 = pa[per + off], b0 = pb[off], b1 = pb[per + off];
+    u64 a0 = pa[off], a1 = pa[per + off], b0 = pb[off], b1 = pb[bps + off];
     U128 acc = {0, 0};
     mac128(acc, a0, b1);
     mac128(acc, a1, b0);
@@ -329,17 +332,18 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
     o2[0] = v2;
 }
 void launch_tensor(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
-                   const RowMap &rm, cudaStream_t st, bool accumulate) {
+                   const RowMap &rm, cudaStream_t st, bool accumulate, long bps) {
     long n = (long)B * limbs * c->N;
     c->n_launch++;
-    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod, accumulate ? 3 : 0);
+    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, bps ? bps : (long)limbs * c->N,
+                                           rm, c->d_mod, accumulate ? 3 : 0);
 }
 void launch_tensor_acc(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, int limbs, long as, long bs,
-                       const RowMap &rm, cudaStream_t st, bool acc01, bool acc2) {
+                       const RowMap &rm, cudaStream_t st, bool acc01, bool acc2, long bps) {
     long n = (long)B * limbs * c->N;
     c->n_launch++;
-    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, rm, c->d_mod,
-                                           (acc01 ? 1 : 0) | (acc2 ? 2 : 0));
+    k_tensor<<<nblk(n, 256), 256, 0, st>>>(d01, d2, a, b, B, limbs, c->N, as, bs, bps ? bps : (long)limbs * c->N,
+                                           rm, c->d_mod, (acc01 ? 1 : 0) | (acc2 ? 2 : 0));
 }
 
 // ------------------------------------------------------------- ModUp
