@@ -543,35 +543,49 @@ def run_pca(args):
             v0s.append(pk.he_replicate(ctx3, pk.he_encrypt_matrix(ctx3, np.tile(v0[j * n:(j + 1) * n], (n, 1)), 13,
                                                                   300 + m * k + j), n))
     counts = pk.he_lazy_normalization_schedule(l_P)
-    rs = pk.he_refresh_state(1 << 20, 0)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lams, Vs, axes = pk.he_pca(ctx3, C3, k, n, l_E, v0s, 0, l_P, counts, 2.0 ** 16, rs)
-    pm_s = time.perf_counter() - t0
     Xc = X - X.mean(0)
     w, U = np.linalg.eigh(Xc.T @ Xc / s)
     w, U = w[::-1], U[:, ::-1]
-    cos, lam_he, vecs = [], [], []
-    for m in range(l_E):
-        parts = []
-        for j in range(k):
-            d = pk.he_decrypt_matrix(ctx3, Vs[m][j], n, n)
-            parts.append(d[0] if axes[m] == 0 else d[:, 0])
-        v = np.concatenate(parts)
-        vecs.append(v)
-        cos.append(float(abs(v @ U[:, m]) / np.linalg.norm(v)))
-        lam_he.append(float(pk.he_decrypt_slots(ctx3, lams[m], 1)[0] / t))
-    Vm = np.array([v / np.linalg.norm(v) * np.sign(v @ U[:, m]) for m, v in enumerate(vecs)])
-    Ut = U[:, :l_E].T
-    r2v = 1 - ((Vm - Ut) ** 2).sum() / ((Ut - Ut.mean()) ** 2).sum()
+
+    def run(compose):
+        """he_pca on the same inputs; wall time, refreshes and accuracy."""
+        pk.he_ctx_set_newton_composition(ctx3, compose)
+        rs = pk.he_refresh_state(1 << 20, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lams, Vs, axes = pk.he_pca(ctx3, C3, k, n, l_E, v0s, 0, l_P, counts, 2.0 ** 16, rs)
+        pm_s = time.perf_counter() - t0
+        cos, lam_he, vecs = [], [], []
+        for m in range(l_E):
+            parts = []
+            for j in range(k):
+                d = pk.he_decrypt_matrix(ctx3, Vs[m][j], n, n)
+                parts.append(d[0] if axes[m] == 0 else d[:, 0])
+            v = np.concatenate(parts)
+            vecs.append(v)
+            cos.append(float(abs(v @ U[:, m]) / np.linalg.norm(v)))
+            lam_he.append(float(pk.he_decrypt_slots(ctx3, lams[m], 1)[0] / t))
+        Vm = np.array([v / np.linalg.norm(v) * np.sign(v @ U[:, m]) for m, v in enumerate(vecs)])
+        Ut = U[:, :l_E].T
+        r2v = 1 - ((Vm - Ut) ** 2).sum() / ((Ut - Ut.mean()) ** 2).sum()
+        for h in lams + [x for V in Vs for x in V]:
+            pk.he_ct_free(h)
+        return pm_s, rs.count, cos, lam_he, float(r2v)
+
+    pm_s, refreshes, cos, lam_he, r2v = run(False)
+    comp = None
+    if not args.no_compose:
+        c_s, c_ref, c_cos, c_lam, c_r2 = run(True)
+        comp = {"value": c_s, "unit": "s", "refreshes": c_ref, "cosine_vs_eigh": c_cos, "lambda_he": c_lam,
+                "R2_V": c_r2, "note": "pairs of Newton steps as five-level composites (Sec. 7)"}
     print(json.dumps({"metric": "encrypted PCA time (HPowerMethod + HEigenShift, top-%d)" % l_E, "value": pm_s,
                       "unit": "s", "higher_is_better": False, "n_gpus": 1,
                       "config": {"workload": "top-%d eigenvectors of the encrypted covariance of a 256x256 low-rank "
                                              "dataset; PowerMethod at N=2^16, q 60+13x40, p 2x60; l_P=%d; Newton "
                                              "counts %s; covariance pre-scaled by d=256" % (l_E, l_P, counts)},
-                      "covariance_s": cov_s, "refreshes": rs.count, "cosine_vs_eigh": cos,
-                      "lambda_he": lam_he, "lambda_fp64": [float(x) for x in w[:l_E]], "R2_V": float(r2v),
-                      "per_pm_iteration_s": pm_s / (l_E * (l_P + 1))}), flush=True)
+                      "covariance_s": cov_s, "refreshes": refreshes, "cosine_vs_eigh": cos,
+                      "lambda_he": lam_he, "lambda_fp64": [float(x) for x in w[:l_E]], "R2_V": r2v,
+                      "per_pm_iteration_s": pm_s / (l_E * (l_P + 1)), "composed_newton": comp}), flush=True)
     pk.he_ctx_destroy(ctx3)
     pk.he_ctx_destroy(ctx2)
 
@@ -1039,6 +1053,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
     ap.add_argument("--max-batch", type=int, default=8, help="served: products per batched pass")
     ap.add_argument("--no-pca", action="store_true", help="served: leave PCA jobs out of the mix")
+    ap.add_argument("--no-compose", action="store_true", help="pca: skip the run with composite Newton steps")
     ap.add_argument("--jobs", type=int, default=96)
     ap.add_argument("--rows", type=int, default=256)
     ap.add_argument("--components", type=int, default=8)

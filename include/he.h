@@ -121,6 +121,16 @@ int he_ctx_set_stream(he_ctx *ctx, void *stream);
  * rotations per launch, 8 items per CTA, cached loads; 2 NTT CTAs per SM). */
 int he_ctx_set_autotune(he_ctx *ctx, int on);
 
+/* Newton composition for the PowerMethod's inverse square root (Sec. 7: two
+ * InvSRT iterations composited into one that spends one level less).  With
+ * on != 0, he_power_method / he_pca / PCA jobs on this context run each pair
+ * of Newton iterations as one composite of five levels instead of six
+ * (u = x y^2; y1/2 = (y/4)(3 - u); x y1^2 = (u/4)(3 - u)^2;
+ * y2 = (y1/2)(3 - x y1^2)); an odd count ends with one ordinary step.  The
+ * results are those of the same schedule in the oracle (bit-exact), not of
+ * the uncomposed circuit.  Off by default. */
+int he_ctx_set_newton_composition(he_ctx *ctx, int on);
+
 /* The autotuner's record: one line per timed launch plan (kernel, shape,
  * plan, best of two device times in ms).  Copies at most cap - 1 bytes and a
  * terminating NUL into out; *len (may be NULL) receives the full length. */

@@ -19,6 +19,12 @@ Readings (beyond those of ckks.py / hmm.py):
   * the Newton step is y <- (3y - x y^3)/2 (Newton's Method algorithm; the
     IterativInvSRTbyNewton listing has the sign of both terms flipped), in
     three levels: t1 = y y, t2 = y x, t3 = t1 t2, then (3y - t3) * 1/2;
+  * with compose_newton, pairs of Newton steps run as one composite step of
+    five levels instead of six (Sec. 7 composites two InvSRT iterations into
+    one and saves a level; the circuit is not printed): with u = x y^2,
+    y1/2 = (y/4)(3 - u), x y1^2 = (u/4)(3 - u)^2, y2 = (y1/2)(3 - x y1^2);
+    the constant 1/4 of u carries the scale that puts y2 at Delta; an odd
+    count ends with one single step;
   * HPowerMethod's j-loop multiplies by V_t[j] (the listing writes V_t[i]),
     and its "if n < l_P" reads "if t < l_P";
   * a ciphertext is refreshed (decrypted to the integer message at q_0 and
@@ -70,12 +76,13 @@ def lazy_normalization_schedule(t, S=0.5, e=1e-5, Bp=1e-3, B2=2.0 ** 16, max_ite
 # ------------------------------------------------------------------ circuits
 
 class PCA:
-    def __init__(self, ckks):
+    def __init__(self, ckks, compose_newton=False):
         self.he = ckks
         self.P = ckks.P
         self.H = HMM(ckks)
         self.refreshes = 0
         self.refresh_obj = 1 << 20
+        self.compose_newton = compose_newton
 
     # --- level management ----------------------------------------------------
     def need(self, ct, levels):
@@ -241,8 +248,34 @@ class PCA:
         t = self.mul_const(x, -0.5 * x0 ** -1.5)
         return self.add_const(t, 1.5 * x0 ** -0.5)
 
+    def newton2(self, x, y):
+        """Two Newton steps as one composite of five levels (Sec. 7):
+        u = x y^2 (2 levels), 3 - u, then (3 - u)^2, y1/2 = (y/4)(3 - u) and
+        u/4 (level 3), x y1^2 = (u/4)(3 - u)^2 (level 4), and
+        y2 = (y1/2)(3 - x y1^2) (level 5).  Returns (x, y2)."""
+        P = self.P
+        y = self.need(y, 5)
+        x = self.need(x, 5)
+        b = self.mult(y, y)
+        yq = self.mul_const(y, 0.25)
+        u = self.mult(b, x)
+        s = self.add_const(self.mul_const_int(u, -1), 3.0)
+        s2 = self.mult(s, s)
+        y1h = self.mult(yq, s)
+        lw = s2.level
+        T = P.delta * float(P.q[lw]) * float(P.q[lw - 1]) / (y1h.scale * s2.scale)
+        uq = self.mul_const(u, 0.25, target_scale=T)
+        w = self.mult(uq, s2)
+        s3 = self.add_const(self.mul_const_int(w, -1), 3.0)
+        return x, self.mult(y1h, s3)
+
     def newton(self, x, y, iters):
-        """y <- (3y - x y^3)/2, three levels per iteration."""
+        """y <- (3y - x y^3)/2, three levels per iteration (with
+        compose_newton: pairs of iterations as five-level composites)."""
+        if self.compose_newton:
+            for _ in range(iters // 2):
+                x, y = self.newton2(x, y)
+            iters %= 2
         for _ in range(iters):
             y = self.need(y, 3)
             x = self.need(x, 3)

@@ -86,6 +86,7 @@ SIGNATURES = {
     "he_ctx_set_stream": [vp, vp],
     "he_ctx_primes": [vp, u64p, u64p],
     "he_ctx_set_autotune": [vp, ip],
+    "he_ctx_set_newton_composition": [vp, ip],
     "he_autotune_log": [vp, ctypes.c_char_p, ip, P(ip)],
     "he_ctx_info": [vp, P(ip), P(ip), P(ip), P(ip), P(ip)],
     "he_sk_export": [vp, P(ctypes.c_int64)],
@@ -202,6 +203,10 @@ def he_ctx_set_stream(ctx, stream_ptr):
 
 def he_ctx_set_autotune(ctx, on=True):
     check(lib().he_ctx_set_autotune(ctx, 1 if on else 0))
+
+
+def he_ctx_set_newton_composition(ctx, on=True):
+    check(lib().he_ctx_set_newton_composition(ctx, 1 if on else 0))
 
 
 def he_autotune_log(ctx):

@@ -373,8 +373,35 @@ public:
         return add_const(std::move(t), 1.5 * std::pow(x0, -0.5));
     }
 
+    // Two Newton steps as one composite of five levels (Sec. 7 composites
+    // two InvSRT iterations into one that spends a level less): with
+    // u = x y^2, y1/2 = (y/4)(3 - u) and x y1^2 = (u/4)(3 - u)^2 at level 3
+    // and 4, y2 = (y1/2)(3 - x y1^2) at level 5; the constant 1/4 of u carries
+    // the scale that puts y2 at Delta.
+    void newton2(HC &x, HC &y) {
+        const double delta = std::ldexp(1.0, c->prm.log_delta);
+        y = need(std::move(y), 5);
+        x = need(std::move(x), 5);
+        HC b = mult(y.p, y.p);
+        HC yq = mul_const(clone(y.p), 0.25);
+        HC u = mult(b.p, x.p);
+        HC s = add_const(mul_const_int(u.p, -1), 3.0);
+        HC s2 = mult(s.p, s.p);
+        HC y1h = mult(yq.p, s.p);
+        const int lw = s2->level;
+        const double T = delta * (double)c->primes[lw] * (double)c->primes[lw - 1] / (y1h->scale * s2->scale);
+        HC uq = mul_const(std::move(u), 0.25, &T);
+        HC w = mult(std::move(uq), std::move(s2));
+        HC s3 = add_const(mul_const_int(w.p, -1), 3.0);
+        y = mult(std::move(y1h), std::move(s3));
+    }
+
     HC newton(HC x, HC y, int iters) {
         const double delta = std::ldexp(1.0, c->prm.log_delta);
+        if (c->newton_compose) {
+            for (int it = 0; it < iters / 2; it++) newton2(x, y);
+            iters %= 2;
+        }
         for (int it = 0; it < iters; it++) {
             y = need(std::move(y), 3);
             x = need(std::move(x), 3);

@@ -235,3 +235,50 @@ def test_pca_two_components_bit_exact(env):
             assert np.array_equal(pk.he_ct_export(ctx, Vs[m][j]), res(want[m][1][j]))
     for h in lams + [x for v in Vs for x in v] + Cg + V0g:
         pk.he_ct_free(h)
+
+
+def test_power_method_composed_newton_bit_exact(env):
+    """HPowerMethod with pairs of Newton steps as five-level composites
+    (Sec. 7): residues, refresh count and axis equal the oracle's same schedule."""
+    from oracle.hmm import tile
+    from oracle.pca import PCA, lazy_normalization_schedule
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk, ctx, P, he, n, n1 = env
+    k = 2
+    t = n * k
+    X = lowrank_dataset(64, t, 6)
+    Xc = X - X.mean(0)
+    Cov = Xc.T @ Xc / 64
+    Cs = Cov * (1.5 / np.linalg.eigvalsh(Cov)[-1])
+    Co, Cg = [], []
+    for a in range(k):
+        row = []
+        for b in range(k):
+            z = tile(Cs[a * n:(a + 1) * n, b * n:(b + 1) * n].ravel(), n, P.S)
+            ct = he.encrypt_slots(z, P.L, obj=600 + a * k + b, period=n * n)
+            row.append(ct)
+            Cg.append(pk.he_ct_import(ctx, res(ct), P.L, ct.scale, n * n))
+        Co.append(row)
+    v0 = np.random.default_rng(8).standard_normal(t)
+    v0 /= np.linalg.norm(v0)
+    V0o = [he.encrypt_slots(tile(np.tile(v0[j * n:(j + 1) * n], n), n, P.S), P.L, obj=950 + j, period=n * n)
+           for j in range(k)]
+    V0g = [pk.he_ct_import(ctx, res(v), P.L, v.scale, n * n) for v in V0o]
+    l_P = 2
+    counts = lazy_normalization_schedule(l_P)
+    pca = PCA(he, compose_newton=True)
+    pca.refresh_obj = 1 << 21
+    lam_o, V_o, ax_o, VT_o = pca.power_method(Co, V0o, 0, n, l_P, counts, 2.0 ** 16)
+    rs = pk.he_refresh_state(1 << 21, 0)
+    pk.he_ctx_set_newton_composition(ctx, True)
+    try:
+        lam_g, V_g, VT_g, ax_g = pk.he_power_method(ctx, Cg, k, n, V0g, 0, l_P, counts, 2.0 ** 16, rs)
+    finally:
+        pk.he_ctx_set_newton_composition(ctx, False)
+    assert ax_g == ax_o and rs.count == pca.refreshes
+    assert np.array_equal(pk.he_ct_export(ctx, lam_g), res(lam_o))
+    for j in range(k):
+        assert np.array_equal(pk.he_ct_export(ctx, V_g[j]), res(V_o[j]))
+        assert np.array_equal(pk.he_ct_export(ctx, VT_g[j]), res(VT_o[j]))
+    for h in V_g + VT_g + V0g + Cg + [lam_g]:
+        pk.he_ct_free(h)

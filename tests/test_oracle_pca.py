@@ -153,3 +153,65 @@ def test_power_method_matches_plaintext_replay():
         v = y * newton_inv_sqrt(x, taylor_inv_sqrt(x, x0), counts[it])
     assert np.abs(vec - v).max() < 1e-4
     assert abs(he.decrypt_slots(lam).real[0] - (Cs @ v) @ v) < 1e-4
+
+
+def test_composite_newton_is_two_steps_in_five_levels():
+    """The composite of Sec. 7 (two InvSRT iterations in one) decrypts to two
+    plain Newton steps, spends five levels where two steps spend six, lands at
+    scale Delta, and an odd count ends with one ordinary step."""
+    P, he = _small(14)
+    he.gen_relin_key()
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.5, 2.0, P.S)
+    y0 = 0.8 / np.sqrt(x)
+    cx = he.encrypt_slots(x, P.L, obj=1)
+    cy = he.encrypt_slots(y0, P.L, obj=2)
+    pca = PCA(he, compose_newton=True)
+    _, y2 = pca.newton2(cx, cy)
+    assert cy.level - y2.level == 5
+    assert abs(y2.scale / P.delta - 1) < 1e-9
+    want = newton_inv_sqrt(x, y0, 2)
+    assert np.abs(he.decrypt_slots(y2).real - want).max() < 1e-6
+    single = PCA(he).newton(cx, cy, 2)
+    assert cy.level - single.level == 6
+    y3 = pca.newton(cx, cy, 3)
+    assert cy.level - y3.level == 8 and pca.refreshes == 0
+    assert np.abs(he.decrypt_slots(y3).real - newton_inv_sqrt(x, y0, 3)).max() < 1e-6
+
+
+def test_power_method_with_composite_newton_matches_plaintext_replay():
+    from oracle.hmm import tile
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    P, he = _small(15)
+    n, k = 16, 2
+    t = n * k
+    _rot_keys(he, P, n, 4)
+    X = lowrank_dataset(64, t, 2)
+    Xc = X - X.mean(0)
+    Cov = Xc.T @ Xc / 64
+    Cs = Cov * (1.5 / np.linalg.eigvalsh(Cov)[-1])
+    C = [[he.encrypt_slots(tile(Cs[a * n:(a + 1) * n, b * n:(b + 1) * n].ravel(), n, P.S), P.L,
+                            obj=10 + a * k + b, period=n * n) for b in range(k)] for a in range(k)]
+    v0 = np.random.default_rng(7).standard_normal(t)
+    v0 /= np.linalg.norm(v0)
+    V0 = [he.encrypt_slots(tile(np.tile(v0[j * n:(j + 1) * n], n), n, P.S), P.L, obj=1000 + j, period=n * n)
+          for j in range(k)]
+    l_P = 3
+    counts = lazy_normalization_schedule(l_P)
+    plain, comp = PCA(he), PCA(he, compose_newton=True)
+    plain.power_method(C, V0, 0, n, l_P, counts, 2.0 ** 16)
+    lam, V, axis, VT = comp.power_method(C, V0, 0, n, l_P, counts, 2.0 ** 16)
+    assert comp.refreshes < plain.refreshes
+    vec = []
+    for j in range(k):
+        d = he.decrypt_slots(V[j]).real[: n * n].reshape(n, n)
+        vec.append(d[0] if axis == 0 else d[:, 0])
+    vec = np.concatenate(vec)
+    v = v0.copy()
+    x0 = 2.0 ** 15 + 1
+    for it in range(l_P):
+        y = Cs @ v
+        x = y @ y
+        v = y * newton_inv_sqrt(x, taylor_inv_sqrt(x, x0), counts[it])
+    assert np.abs(vec - v).max() < 1e-4
+    assert abs(he.decrypt_slots(lam).real[0] - (Cs @ v) @ v) < 1e-4
