@@ -196,9 +196,11 @@ class PCA:
         return A
 
     # --- HCovMtrx (Sec. 5.2) -----------------------------------------------------
-    def covariance(self, blocks, s, n, n1z, n1t, centered=False, relin_once=False):
+    def covariance(self, blocks, s, n, n1z, n1t, centered=False, relin_once=False, dcd_z=0, dcd_t=0):
         """blocks[l][j] = ct(X_j[l]); returns C[a][b] for a, b < k.  relin_once
-        selects the block products' relinearisation (HMM.hmatmul)."""
+        and dcd_z / dcd_t select the block products' relinearisation and
+        Diagonal Convergence Decomposition (HMM.hmatmul; Sec. 7 runs the
+        covariance's products decomposed at maximum diagonal 32)."""
         he, H = self.he, self.H
         nrb, k = len(blocks), len(blocks[0])
         inv_s = 1.0 / s
@@ -211,7 +213,7 @@ class PCA:
                 for l in range(nrb):
                     A = XT[l][a]
                     B = he.drop(Xr[l][b], A.level)
-                    p = H.hmatmul(A, B, n, n1z, n1t, relin_once=relin_once)
+                    p = H.hmatmul(A, B, n, n1z, n1t, relin_once=relin_once, dcd_z=dcd_z, dcd_t=dcd_t)
                     acc = p if acc is None else he.add(acc, p)
                 C[a][b] = acc
         for a in range(k):
@@ -234,7 +236,8 @@ class PCA:
         # mu^T mu is multiplied at the level at which the X^T X products were
         # multiplied, so both are rescaled by the same prime and their scales
         # (Delta^2 / q) agree exactly
-        pl = XT[0][0].level - 2
+        depth = 2 + max(-(-(n - 1) // dcd_z) if dcd_z else 1, -(-(n - 1) // dcd_t) if dcd_t else 1)
+        pl = XT[0][0].level - (depth - 1)
         for a in range(k):
             for b in range(k):
                 t = he.rescale(he.mult_relin(he.drop(muT[a], pl), he.drop(mu[b], pl)))

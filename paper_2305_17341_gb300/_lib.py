@@ -396,10 +396,10 @@ def he_aggregate(ctx, ct, axis, n):
     return _unary("he_aggregate", ctx, ct, axis, n)
 
 
-def he_covariance(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t, relin_once=False):
+def he_covariance(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t, relin_once=False, dcd_z=0, dcd_t=0):
     """blocks: list of handles in [l][j] order (l-major); returns k*k handles (a*k + b)."""
     out = (vp * (k * k))()
-    sc = he_mm_sched(n1z, n1t, 1 if relin_once else 0)
+    sc = he_mm_sched(n1z, n1t, 1 if relin_once else 0, dcd_z, dcd_t)
     check(lib().he_covariance(ctx, _handles(blocks), n_row_blocks, k, n, s, 1 if centered else 0,
                               ctypes.byref(sc), out))
     return [vp(o) for o in out]

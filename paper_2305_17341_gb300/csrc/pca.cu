@@ -272,6 +272,7 @@ public:
     struct CovPlan {
         int nrb = 0, k = 0, n = 0, s = 0, n1z = 0, n1t = 0;
         bool centered = true, relin_once = false;
+        int dcd_z = 0, dcd_t = 0;   // Diagonal Convergence Decomposition of the block products
         std::vector<he_ct *> blocks;
         std::vector<HC> XT, Xr;
     };
@@ -291,7 +292,8 @@ public:
         for (int l = 0; l < P.nrb; l++)
             for (int a = 0; a < k; a++)
                 for (int b = a; b < k; b++)
-                    prods.push_back({P.XT[l * k + a].p, P.Xr[l * k + b].p, P.n, P.n1z, P.n1t, P.relin_once});
+                    prods.push_back({P.XT[l * k + a].p, P.Xr[l * k + b].p, P.n, P.n1z, P.n1t, P.relin_once,
+                                     P.dcd_z, P.dcd_t});
     }
 
     // Takes ownership of the products made from cov_prepare's list.
@@ -334,7 +336,7 @@ public:
         }
         for (int j = 0; j < k; j++) muT.push_back(transpose(mu[j].p, n, P.n1z, 1.0));
         // the mean product is taken at the level of the block products' inputs minus 2
-        const int pl = P.blocks[0]->level - 3;
+        const int pl = P.blocks[0]->level - hmatmul_depth(n, P.dcd_z, P.dcd_t);
         for (int a = 0; a < k; a++)
             for (int b = 0; b < k; b++) {
                 HC x = dropto(muT[a].p, pl), y = dropto(mu[b].p, pl);
@@ -347,9 +349,11 @@ public:
     }
 
     std::vector<HC> covariance(he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z,
-                               int n1t, bool relin_once = false) {
+                               int n1t, bool relin_once = false, int dcd_z = 0, int dcd_t = 0) {
         CovPlan P;
         P.relin_once = relin_once;
+        P.dcd_z = dcd_z;
+        P.dcd_t = dcd_t;
         P.nrb = nrb;
         P.k = k;
         P.n = n;
@@ -527,7 +531,7 @@ struct CovStage {
 };
 
 CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z, int n1t,
-                    std::vector<ProdSpec> &prods, bool relin_once) {
+                    std::vector<ProdSpec> &prods, bool relin_once, int dcd_z, int dcd_t) {
     RefreshState st{0, 0};
     PcaOps ops(c, &st);
     CovStage *S = new CovStage;
@@ -540,6 +544,8 @@ CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, 
     P.n1t = n1t;
     P.centered = centered;
     P.relin_once = relin_once;
+    P.dcd_z = dcd_z;
+    P.dcd_t = dcd_t;
     P.blocks.assign(blocks, blocks + (size_t)nrb * k);
     try {
         ops.cov_prepare(P, prods);
@@ -696,19 +702,21 @@ int he_covariance(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, in
             return HE_ERR_LEVEL;
         }
     }
-    if (blocks[0]->level < 6) {
-        set_error("the covariance circuit needs 6 levels");
-        return HE_ERR_LEVEL;
-    }
-    if (sched->dcd_z || sched->dcd_t) {
-        set_error("the covariance circuit uses the undecomposed Z and T");
+    if ((sched->dcd_z && (sched->dcd_z >= n || sched->dcd_z % sched->n1_z)) ||
+        (sched->dcd_t && (sched->dcd_t >= n || sched->dcd_t % sched->n1_t))) {
+        set_error("a decomposition needs n' < n with n1 dividing n'");
         return HE_ERR_ARG;
+    }
+    // transposition, the products, the mirror transposition and the mean term
+    if (blocks[0]->level < hmatmul_depth(n, sched->dcd_z, sched->dcd_t) + 3) {
+        set_error("the covariance circuit needs the product's depth + 3 levels");
+        return HE_ERR_LEVEL;
     }
     PCA_GUARD_BEGIN
     RefreshState st{0, 0};
     PcaOps ops(&c, &st);
     std::vector<HC> C = ops.covariance(blocks, n_row_blocks, k, n, s, centered != 0, sched->n1_z, sched->n1_t,
-                                       sched->relin_once != 0);
+                                       sched->relin_once != 0, sched->dcd_z, sched->dcd_t);
     if (int rc = sync_status(c)) return rc;
     for (int i = 0; i < k * k; i++) cov[i] = C[i].release();
     return HE_OK;

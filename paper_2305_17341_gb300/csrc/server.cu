@@ -178,10 +178,10 @@ void he_server::tick(Worker *w, std::vector<Job *> &batch) {
                                  s.sched.dcd_z, s.sched.dcd_t});
             } else if (s.kind == HE_JOB_COVARIANCE) {
                 j->stage = cov_begin(c, j->in.data(), s.n_row_blocks, s.k, s.n, s.s, s.centered != 0, s.sched.n1_z,
-                                     s.sched.n1_t, prods, s.sched.relin_once != 0);
+                                     s.sched.n1_t, prods, s.sched.relin_once != 0, s.sched.dcd_z, s.sched.dcd_t);
             } else if (s.kind == HE_JOB_XTX_BLOCK) {
                 j->stage = cov_begin(c, j->in.data(), 1, s.k, s.n, s.s, true, s.sched.n1_z, s.sched.n1_t, prods,
-                                     s.sched.relin_once != 0);
+                                     s.sched.relin_once != 0, s.sched.dcd_z, s.sched.dcd_t);
             }
         });
         if (j->status == HE_JOB_FAILED) prods.resize(j->p0);
@@ -403,12 +403,14 @@ static int check_job(he_server *S, const he_job *j, Ctx **ctx_out, double *charg
         const int nrb = kind == HE_JOB_XTX_BLOCK ? 1 : j->n_row_blocks, k = j->k;
         if (nrb < 1 || k < 1 || j->s < 1 || j->n_in != nrb * k || !sched_ok())
             return reject("covariance blocks: n_in must be n_row_blocks * k with a valid schedule", HE_ERR_ARG);
-        if (j->sched.dcd_z || j->sched.dcd_t)
-            return reject("the covariance circuit uses the undecomposed Z and T", HE_ERR_ARG);
+        if ((j->sched.dcd_z && (j->sched.dcd_z >= n || j->sched.dcd_z % j->sched.n1_z)) ||
+            (j->sched.dcd_t && (j->sched.dcd_t >= n || j->sched.dcd_t % j->sched.n1_t)))
+            return reject("a decomposition needs n' < n with the baby steps dividing n'", HE_ERR_ARG);
         for (int i = 0; i < j->n_in; i++)
             if (j->in[i]->level != j->in[0]->level) return reject("blocks at different levels", HE_ERR_LEVEL);
-        if (j->in[0]->level < 6) return reject("the covariance circuit needs 6 levels", HE_ERR_LEVEL);
-        *steps = matmul_steps(n, j->sched.n1_z, j->sched.n1_t, c->S);
+        if (j->in[0]->level < hmatmul_depth(n, j->sched.dcd_z, j->sched.dcd_t) + 3)
+            return reject("the covariance circuit needs the product's depth + 3 levels", HE_ERR_LEVEL);
+        *steps = matmul_steps(n, j->sched.n1_z, j->sched.n1_t, c->S, j->sched.dcd_z, j->sched.dcd_t);
         std::vector<long> g = transpose_steps(n, j->sched.n1_z, c->S);
         steps->insert(steps->end(), g.begin(), g.end());
         if (kind == HE_JOB_COVARIANCE && !j->centered)

@@ -14,7 +14,7 @@ struct CovStage;
 // appends the block products to `prods`.  blocks[l*k + j] must stay alive
 // until cov_finish.
 CovStage *cov_begin(Ctx *c, he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z, int n1t,
-                    std::vector<ProdSpec> &prods, bool relin_once = false);
+                    std::vector<ProdSpec> &prods, bool relin_once = false, int dcd_z = 0, int dcd_t = 0);
 // Stage 2: takes ownership of the products made from stage 1's list (same
 // order); upper[a*k + b] (a <= b) = sum over row blocks, others null.
 void cov_upper(Ctx *c, CovStage *S, he_ct *const *outs, std::vector<he_ct *> &upper);

@@ -282,3 +282,27 @@ def test_power_method_composed_newton_bit_exact(env):
         assert np.array_equal(pk.he_ct_export(ctx, VT_g[j]), res(VT_o[j]))
     for h in V_g + VT_g + V0g + Cg + [lam_g]:
         pk.he_ct_free(h)
+
+
+def test_covariance_decomposed_bit_exact(env):
+    """HCovMtrx with its block products decomposed (Sec. 7 runs the
+    covariance with the Diagonal Convergence Decomposition): residues equal
+    the oracle's same schedule, decrypted blocks match FP64."""
+    from oracle.pca import PCA
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk, ctx, P, he, n, n1 = env
+    X = lowrank_dataset(32, 32, 3)
+    g, o, nrb, k = _dataset_blocks(pk, ctx, P, he, X, n)
+    C = pk.he_covariance(ctx, g, nrb, k, n, X.shape[0], False, n1, n1, dcd_z=8, dcd_t=8)
+    Co = PCA(he).covariance(o, X.shape[0], n, n1, n1, dcd_z=8, dcd_t=8)
+    Xc = X - X.mean(0)
+    ref = Xc.T @ Xc / X.shape[0]
+    for a in range(k):
+        for b in range(k):
+            assert np.array_equal(pk.he_ct_export(ctx, C[a * k + b]), res(Co[a][b])), (a, b)
+            d = pk.he_decrypt_matrix(ctx, C[a * k + b], n, n)
+            assert np.abs(d - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max() < 1e-4
+    lv_plain = PCA(he).covariance(o, X.shape[0], n, n1, n1)[0][0].level
+    assert Co[0][0].level == lv_plain - 1      # product depth 2 + ceil(15/8) = 4 instead of 3
+    for h in C + g:
+        pk.he_ct_free(h)

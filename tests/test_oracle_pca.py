@@ -93,7 +93,11 @@ def test_aggregate_axes():
     assert np.abs(r1 - M.sum(1)[:, None]).max() < 1e-5        # every column = row sums
 
 
-def test_covariance_decrypts_to_fp64():
+@pytest.mark.parametrize("dcd", [0, 8])
+def test_covariance_decrypts_to_fp64(dcd):
+    """HCovMtrx, with undecomposed block products and with the Diagonal
+    Convergence Decomposition at n' = 8 (Sec. 7 decomposes the covariance's
+    products), against FP64."""
     from paper_2305_17341_gb300.workloads import lowrank_dataset
     P, he = _small(7)
     n, n1 = 16, 4
@@ -109,7 +113,7 @@ def test_covariance_decrypts_to_fp64():
             row.append(he.encrypt_slots(z, P.L, obj=obj))
             obj += 1
         blocks.append(row)
-    C = PCA(he).covariance(blocks, 32, n, n1, n1)
+    C = PCA(he).covariance(blocks, 32, n, n1, n1, dcd_z=dcd, dcd_t=dcd)
     Xc = X - X.mean(0)
     ref = Xc.T @ Xc / 32
     for a in range(2):
