@@ -419,3 +419,29 @@ def test_linear_transform_bit_exact(c1, kind):
     assert np.abs(out - ref).max() < TOL
     for h in (ga, gb, got):
         lib.he_ct_free(h)
+
+
+@pytest.mark.parametrize("n,n1z,n1t", [(32, 1, 1), (32, 32, 32), (32, 1, 32), (32, 32, 1), (2, 1, 2), (2, 2, 1)])
+def test_hmatmul_degenerate_schedules_bit_exact(c1, n, n1z, n1t):
+    """Edge schedules of the double-hoisted BSGS (eq. 3', Table 1): n1 = 1
+    (no baby steps, n giants), n1 = n (one giant), mixed, and the smallest
+    matrix (n = 2, replicated 2048 times over the slots): residues and
+    key-switch counts equal the oracle's, the product decrypts to A.B."""
+    from oracle.hmm import HMM, matmul_rot_steps
+    lib, ctx, P, he = c1
+    steps = matmul_rot_steps(n, n1z, n1t, P.S)
+    lib.he_keygen(ctx, steps, want_relin=True)
+    for s in steps:
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    A, B, oa, ob, ga, gb = _matrix_pair(P, he, lib, ctx, n, 140 + n + n1z + 3 * n1t)
+    lib.he_counters(ctx, reset=True)
+    gc = lib.he_hmatmul(ctx, ga, gb, n, n1z, n1t)
+    cnt = lib.he_counters(ctx)
+    he.cnt.reset()
+    oc = HMM(he).hmatmul(oa, ob, n, n1z, n1t)
+    assert (cnt["MS"], cnt["Dp"], cnt["MD"]) == (he.cnt.MS, he.cnt.Dp, he.cnt.MD)
+    assert np.array_equal(lib.he_ct_export(ctx, gc), residues(he, oc))
+    assert np.abs(lib.he_decrypt_matrix(ctx, gc, n, n) - A @ B).max() < TOL
+    for h in (ga, gb, gc):
+        lib.he_ct_free(h)
