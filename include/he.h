@@ -131,6 +131,18 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * the uncomposed circuit.  Off by default. */
 int he_ctx_set_newton_composition(he_ctx *ctx, int on);
 
+/* Packed eigenvector refresh (App. C: the components of the approximate
+ * eigenvector, spread over k ciphertexts, are gathered into one ciphertext,
+ * refreshed once and spread back).  With on != 0, the PowerMethod on this
+ * context checks the vector before each covariance transformation: when a
+ * segment has fewer than 2 levels left and every segment has at least 1,
+ * segment j keeps only its row (axis 0) or column (axis 1) j, the k lines are
+ * added and refreshed as one ciphertext, and each segment is cut out and
+ * replicated again (one level and log2 n rotations each); the segments come
+ * back at level L - 1.  Results are those of the same schedule in the oracle
+ * (bit-exact).  Off by default. */
+int he_ctx_set_packed_refresh(he_ctx *ctx, int on);
+
 /* The autotuner's record: one line per timed launch plan (kernel, shape,
  * plan, best of two device times in ms).  Copies at most cap - 1 bytes and a
  * terminating NUL into out; *len (may be NULL) receives the full length. */

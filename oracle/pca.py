@@ -76,13 +76,14 @@ def lazy_normalization_schedule(t, S=0.5, e=1e-5, Bp=1e-3, B2=2.0 ** 16, max_ite
 # ------------------------------------------------------------------ circuits
 
 class PCA:
-    def __init__(self, ckks, compose_newton=False):
+    def __init__(self, ckks, compose_newton=False, pack_refresh=False):
         self.he = ckks
         self.P = ckks.P
         self.H = HMM(ckks)
         self.refreshes = 0
         self.refresh_obj = 1 << 20
         self.compose_newton = compose_newton
+        self.pack_refresh = pack_refresh
 
     # --- level management ----------------------------------------------------
     def need(self, ct, levels):
@@ -308,6 +309,58 @@ class PCA:
             out.append(self.aggregate(w, (axis + 1) % 2, n))
         return out
 
+    def line_mask(self, axis, j, n):
+        """Row j (axis 0) or column j (axis 1) of the n x n block, tiled."""
+        n2 = n * n
+        idx = np.arange(n2)
+        m = (idx // n == j) if axis == 0 else (idx % n == j)
+        return tile(m.astype(np.float64), n, self.P.S)
+
+    def packed_refresh(self, V, axis, n):
+        """App. C: the k segments of the vector (each replicated along `axis`)
+        refreshed as one ciphertext: segment j keeps only its row j (axis 0) or
+        column j (axis 1) -- one level --, the k lines are added and refreshed
+        once, then each segment is cut out again (one level) and replicated
+        (rows: rotations by n 2^i; columns: moved to column 0 by a rotation by
+        j, then rotations by -2^i)."""
+        he = self.he
+        n2 = n * n
+        packed = None
+        for j, v in enumerate(V):
+            m = self.mul_mask(self.H.replicate(v, n), self.line_mask(axis, j, n))
+            packed = m if packed is None else self.add_aligned(packed, m)
+        self.refreshes += 1
+        self.refresh_obj += 1
+        packed = he.refresh(packed, self.refresh_obj)
+        out = []
+        for j in range(len(V)):
+            u = self.mul_mask(packed, self.line_mask(axis, j, n))
+            if axis == 0:
+                i = n
+                while i < n2:
+                    u = he.add(u, he.rotate(u, i % n2))
+                    i <<= 1
+            else:
+                if j:
+                    u = he.rotate(u, j % n2)
+                i = -1
+                while i > -n:
+                    u = he.add(u, he.rotate(u, i % n2))
+                    i <<= 1
+            out.append(u)
+        return out
+
+    def refresh_vector(self, V, axis, n):
+        """With pack_refresh, before a covariance transformation (which spends
+        up to 2 levels): segments with fewer than 2 levels are refreshed
+        together by packed_refresh when every segment has a level to spend on
+        the cut, else each such segment once."""
+        if not self.pack_refresh or min(v.level for v in V) >= 2:
+            return V
+        if len(V) > 1 and min(v.level for v in V) >= 1:
+            return self.packed_refresh(V, axis, n)
+        return [self.need(v, 2) for v in V]
+
     def cov_apply(self, C, V, axis, n):
         """One covariance transformation (Sec. 6.1.1): axis-0 input -> axis-1 output and back."""
         he = self.he
@@ -330,6 +383,7 @@ class PCA:
         """HPowerMethod: l_P normalised transformations, then one more for the eigenvalue."""
         V = V0
         for t in range(l_P + 1):
+            V = self.refresh_vector(V, axis, n)
             Vn, axis_n = self.cov_apply(C, V, axis, n)
             if t < l_P:
                 acc = None

@@ -87,6 +87,7 @@ SIGNATURES = {
     "he_ctx_primes": [vp, u64p, u64p],
     "he_ctx_set_autotune": [vp, ip],
     "he_ctx_set_newton_composition": [vp, ip],
+    "he_ctx_set_packed_refresh": [vp, ip],
     "he_autotune_log": [vp, ctypes.c_char_p, ip, P(ip)],
     "he_ctx_info": [vp, P(ip), P(ip), P(ip), P(ip), P(ip)],
     "he_sk_export": [vp, P(ctypes.c_int64)],
@@ -207,6 +208,10 @@ def he_ctx_set_autotune(ctx, on=True):
 
 def he_ctx_set_newton_composition(ctx, on=True):
     check(lib().he_ctx_set_newton_composition(ctx, 1 if on else 0))
+
+
+def he_ctx_set_packed_refresh(ctx, on=True):
+    check(lib().he_ctx_set_packed_refresh(ctx, 1 if on else 0))
 
 
 def he_autotune_log(ctx):

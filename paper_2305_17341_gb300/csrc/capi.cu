@@ -260,6 +260,12 @@ int he_ctx_set_newton_composition(he_ctx *ctx, int on) {
     return HE_OK;
 }
 
+int he_ctx_set_packed_refresh(he_ctx *ctx, int on) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    ctx->c.pack_refresh = on != 0;
+    return HE_OK;
+}
+
 int he_autotune_log(const he_ctx *ctx, char *out, int cap, int *len) {
     if (!ctx || (cap > 0 && !out)) return fail(HE_ERR_ARG, "bad arguments");
     const std::string &s = ctx->c.tune_log;

@@ -185,8 +185,10 @@ struct Ctx {
     int ntt_minb = 2;        // CTAs per SM of the register-blocked forward NTT (2 or 3)
     int ntt_minb_inv = 2;    // and of the inverse NTT
     bool ntt_tuned = false;
-    // PowerMethod: pairs of Newton steps as five-level composites
+    // PowerMethod: pairs of Newton steps as five-level composites; the
+    // vector's segments refreshed as one packed ciphertext
     bool newton_compose = false;
+    bool pack_refresh = false;
     // (level, items, keys) -> (keys per launch << 8) | variant
     std::map<std::tuple<int, int, int>, int> tune_multsum;
     std::string tune_log;   // every timed plan, one line each

@@ -926,6 +926,7 @@ __global__ void k_centre_q0(const u64 *a, double *out, int N, const ModQ *mods) 
 //   kind 3  C^k mask 1 (columns j < n-k); kind 4  C^k mask 2 (j >= n-k)
 //   kind 5  all ones (constant)
 //   kind 6  first column (j == 0); kind 7  identity (i == j)
+//   kind 10 row k (i == k); kind 11 column k (j == k)
 __global__ void k_diag_fill(double *out, int S, int kind, int n, long t, long rot, double value, int k) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= S) return;
@@ -945,6 +946,8 @@ __global__ void k_diag_fill(double *out, int S, int kind, int n, long t, long ro
     case 5: one = true; break;
     case 6: one = (j == 0); break;
     case 7: one = (i == j); break;
+    case 10: one = (i == k); break;
+    case 11: one = (j == k); break;
     }
     out[p] = one ? value : 0.0;
 }

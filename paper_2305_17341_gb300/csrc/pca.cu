@@ -172,10 +172,10 @@ public:
     }
 
     // slot-vector mask (kind 6 first column, 7 identity) at scale q_l, rescale keeps the scale
-    HC mul_mask(HC a, int kind, int n) {
+    HC mul_mask(HC a, int kind, int n, int k = 0) {
         a = need(std::move(a), 1);
         int lv = a->level;
-        const u64 *pt = get_pt(c, kind, n, 0, 0, 1.0, 0, lv);
+        const u64 *pt = get_pt(c, kind, n, 0, 0, 1.0, k, lv);
         HC t = make(lv, a->scale, a->period);
         const long nq = (long)(lv + 1) * c->N;
         launch_mulM(c, t->d, a->d, pt, lv + 1, c->map_q(lv), c->stream);
@@ -424,6 +424,55 @@ public:
         return add_ct(ab.first.p, ab.second.p);
     }
 
+    // App. C: the k segments of the vector (each replicated along `axis`)
+    // refreshed as one ciphertext: segment j keeps only its row j (axis 0)
+    // or column j (axis 1) -- one level --, the k lines are added and
+    // refreshed once, then each segment is cut out again (one level) and
+    // replicated (rows: rotations by n 2^i; columns: moved to column 0 by a
+    // rotation by j, then rotations by -2^i).
+    std::vector<HC> packed_refresh(const std::vector<HC> &V, int axis, int n) {
+        const long n2 = (long)n * n;
+        const int line = axis == 0 ? 10 : 11;
+        HC packed;
+        for (size_t j = 0; j < V.size(); j++) {
+            HC m = mul_mask(replicated(V[j].p, n), line, n, (int)j);
+            packed = packed.p ? add_aligned(std::move(packed), std::move(m)) : std::move(m);
+        }
+        HC fresh = refresh(packed.p);
+        std::vector<HC> out;
+        for (size_t j = 0; j < V.size(); j++) {
+            HC u = mul_mask(clone(fresh.p), line, n, (int)j);
+            if (axis == 0) {
+                for (long i = n; i < n2; i <<= 1) {
+                    HC r = rot(u.p, i % n2);
+                    u = add_ct(u.p, r.p);
+                }
+            } else {
+                if (j) u = rot(u.p, (long)j % n2);
+                for (long i = -1; i > -n; i *= 2) {
+                    HC r = rot(u.p, ((i % n2) + n2) % n2);
+                    u = add_ct(u.p, r.p);
+                }
+            }
+            out.push_back(std::move(u));
+        }
+        return out;
+    }
+
+    // Before a covariance transformation (up to 2 levels), with packed
+    // refresh on: segments with fewer than 2 levels are refreshed together by
+    // packed_refresh when every segment has a level for the cut, else each
+    // such segment once.
+    std::vector<HC> refresh_vector(std::vector<HC> V, int axis, int n) {
+        if (!c->pack_refresh) return V;
+        int lo = V[0]->level;
+        for (auto &v : V) lo = std::min(lo, v->level);
+        if (lo >= 2) return V;
+        if (V.size() > 1 && lo >= 1) return packed_refresh(V, axis, n);
+        for (auto &v : V) v = need(std::move(v), 2);
+        return V;
+    }
+
     std::vector<HC> cov_apply(he_ct *const *C, int k, const std::vector<HC> &V, int axis, int n) {
         std::vector<HC> out;
         for (int i = 0; i < k; i++) {
@@ -452,6 +501,7 @@ public:
         std::vector<HC> V;
         for (int j = 0; j < k; j++) V.push_back(clone(V0[j]));
         for (int t = 0; t <= l_P; t++) {
+            V = refresh_vector(std::move(V), axis, n);
             std::vector<HC> Vn = cov_apply(C, k, V, axis, n);
             int axis_n = (axis + 1) % 2;
             if (t < l_P) {

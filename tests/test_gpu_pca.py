@@ -237,9 +237,11 @@ def test_pca_two_components_bit_exact(env):
         pk.he_ct_free(h)
 
 
-def test_power_method_composed_newton_bit_exact(env):
+@pytest.mark.parametrize("compose,pack", [(True, False), (False, True), (True, True)])
+def test_power_method_composed_newton_bit_exact(env, compose, pack):
     """HPowerMethod with pairs of Newton steps as five-level composites
-    (Sec. 7): residues, refresh count and axis equal the oracle's same schedule."""
+    (Sec. 7) and / or the packed eigenvector refresh (App. C): residues,
+    refresh count and axis equal the oracle's same schedule."""
     from oracle.hmm import tile
     from oracle.pca import PCA, lazy_normalization_schedule
     from paper_2305_17341_gb300.workloads import lowrank_dataset
@@ -264,17 +266,19 @@ def test_power_method_composed_newton_bit_exact(env):
     V0o = [he.encrypt_slots(tile(np.tile(v0[j * n:(j + 1) * n], n), n, P.S), P.L, obj=950 + j, period=n * n)
            for j in range(k)]
     V0g = [pk.he_ct_import(ctx, res(v), P.L, v.scale, n * n) for v in V0o]
-    l_P = 2
+    l_P = 3
     counts = lazy_normalization_schedule(l_P)
-    pca = PCA(he, compose_newton=True)
+    pca = PCA(he, compose_newton=compose, pack_refresh=pack)
     pca.refresh_obj = 1 << 21
     lam_o, V_o, ax_o, VT_o = pca.power_method(Co, V0o, 0, n, l_P, counts, 2.0 ** 16)
     rs = pk.he_refresh_state(1 << 21, 0)
-    pk.he_ctx_set_newton_composition(ctx, True)
+    pk.he_ctx_set_newton_composition(ctx, compose)
+    pk.he_ctx_set_packed_refresh(ctx, pack)
     try:
         lam_g, V_g, VT_g, ax_g = pk.he_power_method(ctx, Cg, k, n, V0g, 0, l_P, counts, 2.0 ** 16, rs)
     finally:
         pk.he_ctx_set_newton_composition(ctx, False)
+        pk.he_ctx_set_packed_refresh(ctx, False)
     assert ax_g == ax_o and rs.count == pca.refreshes
     assert np.array_equal(pk.he_ct_export(ctx, lam_g), res(lam_o))
     for j in range(k):

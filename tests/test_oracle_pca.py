@@ -219,3 +219,67 @@ def test_power_method_with_composite_newton_matches_plaintext_replay():
         v = y * newton_inv_sqrt(x, taylor_inv_sqrt(x, x0), counts[it])
     assert np.abs(vec - v).max() < 1e-4
     assert abs(he.decrypt_slots(lam).real[0] - (Cs @ v) @ v) < 1e-4
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_packed_refresh_restores_every_segment(axis):
+    """App. C: the k segments of a replicated vector refreshed as one
+    ciphertext come back replicated along the same axis with the same
+    values, at level L - 1, for one refresh instead of k."""
+    from oracle.hmm import tile
+    P, he = _small(6)
+    n, k = 16, 3
+    _rot_keys(he, P, n, 4)
+    rng = np.random.default_rng(11 + axis)
+    vs = [rng.uniform(-1, 1, n) for _ in range(k)]
+    V = []
+    for j, v in enumerate(vs):
+        blk = np.tile(v, (n, 1)) if axis == 0 else np.tile(v[:, None], (1, n))
+        ct = he.encrypt_slots(tile(blk.ravel(), n, P.S), P.L, obj=40 + j, period=n * n)
+        V.append(he.drop(ct, 1))
+    pca = PCA(he, pack_refresh=True)
+    out = pca.packed_refresh(V, axis, n)
+    assert pca.refreshes == 1
+    for j, (ct, v) in enumerate(zip(out, vs)):
+        assert ct.level == P.L - 1
+        d = he.decrypt_slots(ct).real[: n * n].reshape(n, n)
+        want = np.tile(v, (n, 1)) if axis == 0 else np.tile(v[:, None], (1, n))
+        assert np.abs(d - want).max() < 1e-6, j
+
+
+def test_power_method_with_packed_refresh_matches_plaintext_replay():
+    from oracle.hmm import tile
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    P, he = _small(13)
+    n, k = 16, 2
+    t = n * k
+    _rot_keys(he, P, n, 4)
+    X = lowrank_dataset(64, t, 2)
+    Xc = X - X.mean(0)
+    Cov = Xc.T @ Xc / 64
+    Cs = Cov * (1.5 / np.linalg.eigvalsh(Cov)[-1])
+    C = [[he.encrypt_slots(tile(Cs[a * n:(a + 1) * n, b * n:(b + 1) * n].ravel(), n, P.S), P.L,
+                            obj=10 + a * k + b, period=n * n) for b in range(k)] for a in range(k)]
+    v0 = np.random.default_rng(7).standard_normal(t)
+    v0 /= np.linalg.norm(v0)
+    V0 = [he.encrypt_slots(tile(np.tile(v0[j * n:(j + 1) * n], n), n, P.S), P.L, obj=1000 + j, period=n * n)
+          for j in range(k)]
+    l_P = 4
+    counts = lazy_normalization_schedule(l_P)
+    plain, packed = PCA(he), PCA(he, pack_refresh=True)
+    plain.power_method(C, V0, 0, n, l_P, counts, 2.0 ** 16)
+    lam, V, axis, VT = packed.power_method(C, V0, 0, n, l_P, counts, 2.0 ** 16)
+    assert packed.refreshes < plain.refreshes
+    vec = []
+    for j in range(k):
+        d = he.decrypt_slots(V[j]).real[: n * n].reshape(n, n)
+        vec.append(d[0] if axis == 0 else d[:, 0])
+    vec = np.concatenate(vec)
+    v = v0.copy()
+    x0 = 2.0 ** 15 + 1
+    for it in range(l_P):
+        y = Cs @ v
+        x = y @ y
+        v = y * newton_inv_sqrt(x, taylor_inv_sqrt(x, x0), counts[it])
+    assert np.abs(vec - v).max() < 1e-4
+    assert abs(he.decrypt_slots(lam).real[0] - (Cs @ v) @ v) < 1e-4
