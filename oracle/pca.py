@@ -29,7 +29,9 @@ Readings (beyond those of ckks.py / hmm.py):
     and its "if n < l_P" reads "if t < l_P";
   * a ciphertext is refreshed (decrypted to the integer message at q_0 and
     re-encrypted at level L) just before an operation that needs more levels
-    than it has (App. C).
+    than it has (App. C); a ciphertext that several products take (a vector
+    segment in a covariance transformation, the eigenvector segments and the
+    eigenvalue in EigenShift) is refreshed once, before the first of them.
 """
 import math
 
@@ -365,6 +367,7 @@ class PCA:
         """One covariance transformation (Sec. 6.1.1): axis-0 input -> axis-1 output and back."""
         he = self.he
         k = len(V)
+        V = [self.need(v, 1) for v in V]      # each segment enters k products
         out = []
         for i in range(k):
             acc = None
@@ -407,8 +410,9 @@ class PCA:
     def eigen_shift(self, C, lam, V, axis, VT, n):
         """HEigenShift: C[a][b] -= lambda v_a v_b^T (column-replicated v_a times row-replicated v_b)."""
         k = len(V)
-        col = V if axis == 1 else VT
-        row = VT if axis == 1 else V
+        col = [self.need(v, 1) for v in (V if axis == 1 else VT)]
+        row = [self.need(v, 1) for v in (VT if axis == 1 else V)]
+        lam = self.need(lam, 1)
         out = [[None] * k for _ in range(k)]
         for a in range(k):
             for b in range(k):

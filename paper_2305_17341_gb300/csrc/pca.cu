@@ -473,13 +473,25 @@ public:
         return V;
     }
 
-    std::vector<HC> cov_apply(he_ct *const *C, int k, const std::vector<HC> &V, int axis, int n) {
+    // a ciphertext that several products take, refreshed once (kept in hold)
+    // when it has no level left
+    const he_ct *once(const he_ct *a, std::vector<HC> &hold) {
+        if (a->level >= 1) return a;
+        hold.push_back(refresh(a));
+        return hold.back().p;
+    }
+
+    std::vector<HC> cov_apply(he_ct *const *C, int k, const std::vector<HC> &V0, int axis, int n) {
+        // each segment enters k products: refreshed once, before the first
+        std::vector<HC> hold;
+        std::vector<const he_ct *> V;
+        for (auto &v : V0) V.push_back(once(v.p, hold));
         std::vector<HC> out;
         for (int i = 0; i < k; i++) {
             HC acc;
             for (int j = 0; j < k; j++) {
                 const he_ct *blk = axis == 0 ? C[i * k + j] : C[j * k + i];
-                HC p = mult(blk, V[j].p);
+                HC p = mult(blk, V[j]);
                 acc = acc.p ? add_aligned(std::move(acc), std::move(p)) : std::move(p);
             }
             out.push_back(aggregate(acc.p, (axis + 1) % 2, n));
@@ -535,13 +547,19 @@ public:
 
     std::vector<HC> eigen_shift(he_ct *const *C, int k, const he_ct *lam, he_ct *const *V, int axis,
                                 he_ct *const *VT) {
-        he_ct *const *col = axis == 1 ? V : VT;
-        he_ct *const *row = axis == 1 ? VT : V;
+        // every segment enters k products and lambda k^2: each refreshed
+        // once, before the first
+        std::vector<HC> hold;
+        hold.reserve(2 * k + 1);
+        std::vector<const he_ct *> col, row;
+        for (int a = 0; a < k; a++) col.push_back(once(axis == 1 ? V[a] : VT[a], hold));
+        for (int b = 0; b < k; b++) row.push_back(once(axis == 1 ? VT[b] : V[b], hold));
+        const he_ct *lm = once(lam, hold);
         std::vector<HC> out;
         for (int a = 0; a < k; a++)
             for (int b = 0; b < k; b++) {
                 HC vv = mult(col[a], row[b]);
-                HC t = mult(lam, vv.p);
+                HC t = mult(lm, vv.p);
                 out.push_back(sub_matched(clone(C[a * k + b]), std::move(t)));
             }
         return out;
