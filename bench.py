@@ -873,6 +873,63 @@ PAPER_TABLE3 = {("Z", 8, 0): 2.004, ("Z", 8, 64): 1.362, ("Z", 8, 32): 1.249,
                 ("T", 16, 0): 0.725, ("T", 16, 64): 0.572, ("T", 16, 32): 0.613}
 
 
+def run_sweep(args):
+    """Batched products/s of B identical-shape 128x128 products at N=2^16,
+    level 20 (DMatrixMult), for B = 1, 2, 4, 8, 16, 32, against one
+    he_hmatmul per product: how far batching amortises the key reads."""
+    import numpy as np
+    import torch
+
+    import paper_2305_17341_gb300 as pk
+    from paper_2305_17341_gb300 import workloads
+    pk.build()
+    n, n1, level = N_MAT, 16, 20
+    ctx = pk.he_ctx_create(pk.he_params_default(2), 1000)
+    tstream = torch.cuda.Stream()
+    pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
+    pk.he_keygen(ctx, pk.he_rot_steps_for_matmul(n, n1, n1, 1 << 15), True)
+    Bmax = 32
+    mats = [workloads.matmul_pair(n, 10 * i) for i in range(Bmax)]
+    cts = [(pk.he_encrypt_matrix(ctx, A, level, 2 * i), pk.he_encrypt_matrix(ctx, Bm, level, 2 * i + 1))
+           for i, (A, Bm) in enumerate(mats)]
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(tstream)
+        for _ in range(reps):
+            fn()
+        e1.record(tstream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def plain_one():
+        pk.he_ct_free(pk.he_hmatmul(ctx, cts[0][0], cts[0][1], n, n1, n1))
+
+    plain_one()
+    plain_ms = timed(plain_one, max(1, args.steps))
+    rows = []
+    for B in (1, 2, 4, 8, 16, 32):
+        jobs = [(a, b, n, n1, n1) for a, b in cts[:B]]
+
+        def step():
+            for o in pk.he_hmatmul_batch(jobs):
+                pk.he_ct_free(o)
+
+        for _ in range(2):
+            step()
+        ms = timed(step, max(1, args.steps))
+        rows.append({"batch": B, "ms_per_step": ms, "matmul_per_s": B / (ms / 1e3),
+                     "over_plain": (B / (ms / 1e3)) / (1e3 / plain_ms)})
+    print(json.dumps({"metric": "HE 128x128 matmul/s batched vs plain (batch sweep)", "unit": "matmul/s",
+                      "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+                      "plain": {"ms_per_product": plain_ms, "matmul_per_s": 1e3 / plain_ms},
+                      "batched": rows,
+                      "config": {"workload": "B identical-shape 128x128 products, N=2^16, q 60+20x40, p 2x60, "
+                                             "level 20, n1_z=n1_t=16, DMatrixMult"}}), flush=True)
+    pk.he_ctx_destroy(ctx)
+
+
 def run_transforms(args):
     """The Z (sigma) and T (tau) transforms alone, as Table 3 measures them:
     one 128x128 matrix ciphertext at N = 2^15 (n^2 = slots, no replication),
@@ -1067,7 +1124,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served", "ntt",
-                                                           "keyswitch", "transforms"])
+                                                           "keyswitch", "transforms", "sweep"])
     ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
     ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
     ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")
@@ -1095,6 +1152,8 @@ def main():
         return run_keyswitch(args)
     if args.workload == "transforms":
         return run_transforms(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     dist = None
