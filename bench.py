@@ -46,7 +46,9 @@ TRAFFIC_RATIO = {"ntt_fwd": 1089.76 / 536.87, "multsum": 2032.15 / 2065.69}
 N1_FOR = {16: 4, 32: 8, 64: 8, 128: 16}
 LEVEL = 20
 # per-product operation counts of the hoisted schedule at n=128, n1=16
-# (Table 1 "Optimized" rows as the schedule performs them)
+# (Table 1 "Optimized" rows as the schedule performs them: Table 1 also counts
+# the trivial j = 0 baby, the i = 0 giant and two chain steps, which the
+# schedule does not perform)
 OPS = {"MS": 564, "Dp": 178, "MD": 423}
 # with one relinearisation per product instead of n = 128
 OPS_ONCE = {"MS": 564 - 127, "Dp": 178 - 127, "MD": 423 - 127}
