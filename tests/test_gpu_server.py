@@ -227,3 +227,34 @@ def test_jobs_wait_for_memory_and_are_admitted_in_order(env):
         pk.he_server_destroy(srv)
     for h in outs + [x for p in cts for x in p]:
         pk.he_ct_free(h)
+
+
+def test_served_decomposed_covariance_and_products(env):
+    """Jobs with a Diagonal Convergence Decomposition in their schedule (a
+    covariance at n' = 8, a product with Z and T decomposed) served in one
+    mix equal the same calls alone, bit for bit."""
+    from paper_2305_17341_gb300.workloads import lowrank_dataset, matmul_pair
+    pk, ctx, n, n1 = env
+    L = len(QBITS) - 1
+    A, B = matmul_pair(n, 77)
+    a, b = pk.he_encrypt_matrix(ctx, A, L, 700), pk.he_encrypt_matrix(ctx, B, L, 701)
+    X = lowrank_dataset(32, 32, 8)
+    blocks, nrb, k = _blocks(pk, ctx, X, n, L, 720)
+    want_mm = pk.he_hmatmul(ctx, a, b, n, n1, n1, dcd_z=8, dcd_t=8)
+    want_cov = pk.he_covariance(ctx, blocks, nrb, k, n, X.shape[0], False, n1, n1, dcd_z=8, dcd_t=8)
+    srv = pk.he_server_create([ctx], 64e9, max_batch=4)
+    try:
+        j_mm = pk.he_server_submit(srv, pk.HE_JOB_MATMUL, [a, b], n=n, n1z=n1, n1t=n1, dcd_z=8, dcd_t=8)
+        j_cov = pk.he_server_submit(srv, pk.HE_JOB_COVARIANCE, blocks, n=n, n1z=n1, n1t=n1, n_row_blocks=nrb, k=k,
+                                    s=X.shape[0], dcd_z=8, dcd_t=8)
+        for j in (j_mm, j_cov):
+            assert pk.he_server_wait(srv, j, 600.0) == pk.HE_JOB_DONE
+        got_mm = pk.he_server_result(srv, j_mm)[0][0]
+        got_cov = pk.he_server_result(srv, j_cov)[0]
+    finally:
+        pk.he_server_destroy(srv)
+    assert _same(pk, ctx, got_mm, want_mm)
+    for i in range(k * k):
+        assert _same(pk, ctx, got_cov[i], want_cov[i]), i
+    for h in [a, b, want_mm, got_mm] + blocks + list(want_cov) + list(got_cov):
+        pk.he_ct_free(h)
