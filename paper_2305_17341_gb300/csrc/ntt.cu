@@ -195,12 +195,16 @@ __global__ void k_ntt_inv_p1(u64 *data, RowMap rm, const ModQ *mods, const u64 *
 // span sp and local group i is psi^brv((M / 2sp) G + i), G = 1 for columns
 // and G = N/M + row for rows.  Global loads and stores are always in layout A
 // (coalesced across the W sequences for columns, along the row for rows).
+// Rows keep each sequence contiguous in shared memory with one pad word per
+// 16 (element r at r + r/16): both layouts are free of bank conflicts, and
+// every access is a compile-time offset from a per-thread base (17 t + k in
+// layout B, t + T k + k T/16 in layout A).
 template <int LM, bool ROWS>
 struct PassGeom {
     static constexpr int M = 1 << LM, T = M / 16, W = 256 / T;
-    static constexpr int SM = ROWS ? W * (M + 8) : W * M;
+    static constexpr int SM = ROWS ? W * (M + M / 16) : W * M;
     __device__ static __forceinline__ int sidx(int r, int w) {
-        if (ROWS) return w * (M + 8) + (r ^ ((r >> 4) & 15));
+        if (ROWS) return w * (M + M / 16) + r + (r >> 4);
         return r * W + w;
     }
 };
