@@ -72,3 +72,27 @@ def test_rot_steps_for_decomposed_schedules_match_oracle(built):
     import pytest
     with pytest.raises(_lib.HeError):
         _lib.he_rot_steps_for_sched(16, 4, 4, 2048, 6, 0)   # n1 must divide n'
+
+
+def test_lazy_schedule_host_matches_oracle_and_paper(built):
+    """The library's Lazy Normalization simulation (host code) equals the
+    oracle's and reproduces the printed averages 14.5 (l_P = 4) and 13.8
+    (l_P = 14) of Sec. 7."""
+    import numpy as np
+    from oracle.pca import lazy_normalization_schedule
+    from paper_2305_17341_gb300 import _lib
+    for t in (1, 4, 9, 14):
+        assert _lib.he_lazy_normalization_schedule(t) == lazy_normalization_schedule(t)
+    assert round(np.mean(_lib.he_lazy_normalization_schedule(4)), 1) == 14.5
+    assert round(np.mean(_lib.he_lazy_normalization_schedule(14)), 1) == 13.8
+    with pytest.raises(_lib.HeError):
+        _lib.he_lazy_normalization_schedule(0)
+
+
+def test_context_options_need_a_context(built):
+    """The per-context switches reject a null context without touching the GPU."""
+    from paper_2305_17341_gb300 import _lib
+    for fn in (_lib.he_ctx_set_newton_composition, _lib.he_ctx_set_packed_refresh, _lib.he_ctx_set_autotune):
+        with pytest.raises(_lib.HeError) as e:
+            fn(None, True)
+        assert e.value.code == _lib.HE_ERR_ARG

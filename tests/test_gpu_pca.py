@@ -144,16 +144,6 @@ def test_power_method_and_eigen_shift_bit_exact(env):
         pk.he_ct_free(h)
 
 
-def test_lazy_schedule_host_matches_oracle_and_paper():
-    import paper_2305_17341_gb300 as pk
-    from oracle.pca import lazy_normalization_schedule
-    pk.build()
-    for t in (1, 4, 9, 14):
-        assert pk.he_lazy_normalization_schedule(t) == lazy_normalization_schedule(t)
-    assert round(np.mean(pk.he_lazy_normalization_schedule(4)), 1) == 14.5
-    assert round(np.mean(pk.he_lazy_normalization_schedule(14)), 1) == 13.8
-
-
 def test_full_size_covariance_256():
     """Config 2: 256x256 low-rank dataset, 128x128 blocks at N=2^16, chain
     60 + 20x40, p 2x60: decrypted covariance within 1e-4 of FP64."""
