@@ -961,7 +961,7 @@ def run_transforms(args):
     for name, kind in (("Z", 0), ("T", 1)):
         for n1 in (8, 16):
             for np_ in (0, 64, 32):
-                depth = -(-(n - 1) // np_) if np_ else 1
+                depth = ((n - 1) if kind == 0 else (n - 2)) // np_ + 1 if np_ else 1
                 ct = pk.he_encrypt_matrix(ctx, A, 10 + depth, 1)     # every run ends at level 10
                 for _ in range(max(2, args.warmup)):
                     pk.he_ct_free(pk.he_linear_transform(ctx, ct, kind, n, n1, np_))

@@ -77,7 +77,8 @@ typedef struct he_mm_sched {
      * and T undecomposed (one level each, in parallel); n' > 0 applies Z as
      * the factor chains of DCDforZ with maximum diagonal n' (dcd_z) and T as
      * the chain of DCDforT with maximum diagonal n' n (dcd_t), trading
-     * ceil((n-1)/n') levels for fewer rotation keys (Table 2).  n' < n and
+     * floor((n-1)/n') + 1 levels (n/n' for n' | n) for fewer rotation keys
+     * (Table 2).  n' < n and
      * the baby steps must divide n'.  A product consumes 2 + the longest
      * chain (3 without decomposition). */
     int dcd_z;
@@ -269,7 +270,7 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
  * 0 <= k < n), 2 = the transpose G (diagonals (n - 1) k); n1 baby steps.
  * With n_prime > 0 (kinds 0 and 1) the transform runs as its Diagonal
  * Convergence Decomposition (Sec. 4.2) with maximum diagonal n' (Z) or n' n
- * (T): ceil((n-1)/n') factor transforms, one level each.
+ * (T): floor((n-1)/n') + 1 factor transforms, one level each.
  * Replicates a zero-padded input to period n^2 first; consumes one level per
  * factor (the plaintext diagonals are encoded at scale q_l and rescaled away,
  * so the scale is kept).  Errors: HE_ERR_ARG, HE_ERR_LEVEL, HE_ERR_KEY_MISSING. */

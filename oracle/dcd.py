@@ -17,8 +17,13 @@ Readings:
     "the n'-th diagonal of the left matrix", which would not add up to k);
   * T: diagonals t n with t <= n' stay (k_r = 0), the others move by n' n
     (DCDforT);
-  * ceil((n-1)/n') - 1 rounds, each applied to the previous left factor, so
-    Z_t = L R_{m-1} ... R_1 with R_1 applied first to the vector.
+  * rounds, each applied to the previous left factor, so Z_t = L R_m ...
+    R_1 with R_1 applied first to the vector: Z takes floor((n-1)/n') rounds
+    (its left factor must keep |k| < n', the range of its BSGS), T takes
+    floor((n-2)/n') (its left factor may keep t = n'); both give n/n'
+    factors for n' | n (Table 2).  With ceil((n-1)/n') - 1 rounds for Z, an
+    n' dividing n - 1 (n1 = 1 with an odd n') would leave diagonal n' in the
+    left factor, outside its BSGS range.
 """
 import numpy as np
 
@@ -62,8 +67,13 @@ def bool_product(left, right):
     return out
 
 
-def rounds(n, n_prime):
-    return -(-(n - 1) // n_prime) - 1
+def rounds(n, n_prime, which="Z"):
+    return (n - 1) // n_prime if which == "Z" else (n - 2) // n_prime
+
+
+def chain_length(n, n_prime, which="Z"):
+    """Factors (levels) of the decomposed Z or T."""
+    return rounds(n, n_prime, which) + 1
 
 
 def dcd_Z(n, n_prime):
@@ -99,7 +109,7 @@ def dcd_T(n, n_prime):
         return (k, 0) if t <= n_prime else (k - n_prime * n, n_prime * n)
 
     cur, rights = perm_entries(n, "T"), []
-    for _ in range(rounds(n, n_prime)):
+    for _ in range(rounds(n, n_prime, "T")):
         cur, r = split_step(cur, size, pick, False)
         rights.append(r)
     return rights + [cur]

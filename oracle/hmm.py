@@ -239,7 +239,7 @@ class HMM:
 
     def sigma_dcd(self, ct, n, n1, n_prime):
         """Z = Z_1 + Z_2, each the chain of DCDforZ with maximum diagonal n'
-        (n1 | n'); ceil((n-1)/n') levels."""
+        (n1 | n'); floor((n-1)/n') + 1 levels."""
         n2p = n_prime // n1
         c1, c2 = dcd.dcd_Z(n, n_prime)
         a1 = self._chain(ct, c1, n, 1, n1, range(0, n2p))
@@ -247,7 +247,8 @@ class HMM:
         return self.he.add(a1, a2)
 
     def tau_dcd(self, ct, n, n1, n_prime):
-        """T as the chain of DCDforT with maximum diagonal n' n (n1 | n')."""
+        """T as the chain of DCDforT with maximum diagonal n' n (n1 | n');
+        floor((n-2)/n') + 1 levels."""
         n2p = n_prime // n1
         return self._chain(ct, dcd.dcd_T(n, n_prime), n, n, n1, range(0, n2p + 1))
 
@@ -278,7 +279,7 @@ class HMM:
         dcd_z, dcd_t: when non-zero, Z and T are applied as their Diagonal
         Convergence Decompositions with maximum diagonal n' = dcd_z (resp.
         n' n, n' = dcd_t) (DMatrixMult, Sec. 4.2); the product then consumes
-        2 + max(ceil((n-1)/dcd_z), ceil((n-1)/dcd_t)) levels."""
+        2 + max(floor((n-1)/dcd_z) + 1, floor((n-2)/dcd_t) + 1) levels."""
         he, P = self.he, self.P
         n2m = n * n
         A = self.replicate(ctA, n)

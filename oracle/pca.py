@@ -239,7 +239,7 @@ class PCA:
         # mu^T mu is multiplied at the level at which the X^T X products were
         # multiplied, so both are rescaled by the same prime and their scales
         # (Delta^2 / q) agree exactly
-        depth = 2 + max(-(-(n - 1) // dcd_z) if dcd_z else 1, -(-(n - 1) // dcd_t) if dcd_t else 1)
+        depth = 2 + max((n - 1) // dcd_z + 1 if dcd_z else 1, (n - 2) // dcd_t + 1 if dcd_t else 1)
         pl = XT[0][0].level - (depth - 1)
         for a in range(k):
             for b in range(k):

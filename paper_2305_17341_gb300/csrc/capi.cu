@@ -818,7 +818,7 @@ int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, i
     he_mm_sched s{n1, n1, 0, kind == 0 ? n_prime : 0, kind == 1 ? n_prime : 0};
     if (n_prime < 0) return fail(HE_ERR_ARG, "n' must be >= 0");
     if (int rc = check_sched(c, n, &s)) return rc;
-    const int m = n_prime ? dcd_levels(n, n_prime) : 1;
+    const int m = dcd_levels(n, n_prime, kind == 1);
     if (ct->level < m) return fail(HE_ERR_LEVEL, "not enough levels for the transform");
     GUARD_BEGIN
     he_ct *tmp = clone_ct(c, ct);

@@ -11,7 +11,9 @@
 // middle index r + k_l = c - k_r.  Z splits into Z_1 (diagonals >= 0) and Z_2
 // (< 0); a diagonal with |k| >= n' moves by sign(k) n', the others stay on
 // the left factor.  T's diagonals t n with t > n' move by n' n.  After
-// ceil((n-1)/n') - 1 rounds, Z_t = L R_{m-1} ... R_1.
+// Z_t = L R_m ... R_1 after floor((n-1)/n') rounds for Z (its left factor
+// must keep |k| < n', the range of its BSGS) and floor((n-2)/n') for T (its
+// left factor may keep t = n'): n/n' factors for n' | n (Table 2).
 #include <set>
 #include <sstream>
 #include <stdexcept>
@@ -103,7 +105,7 @@ const DcdChain &dcd_chain(Ctx *c, int which, int n, int n_prime) {
     if (it != c->dcd.end()) return it->second;
     if (n_prime < 1 || n_prime >= n) throw HeError(HE_ERR_ARG, "the decomposition needs 1 <= n' < n");
     const long size = (long)n * n;
-    const int rounds = (int)((n - 2) / n_prime);   // ceil((n-1)/n') - 1
+    const int rounds = dcd_levels(n, n_prime, which == 2) - 1;
     // eq. 5 / eq. 6 on row-major slots: row l = i n + j
     Factor full(size);
     for (long l = 0; l < size; l++) {
@@ -148,6 +150,9 @@ const DcdChain &dcd_chain(Ctx *c, int which, int n, int n_prime) {
     return c->dcd.emplace(key, std::move(ch)).first->second;
 }
 
-int dcd_levels(int n, int n_prime) { return n_prime ? (n - 2) / n_prime + 1 : 1; }
+int dcd_levels(int n, int n_prime, bool is_t) {
+    if (!n_prime) return 1;
+    return (is_t ? (n - 2) / n_prime : (n - 1) / n_prime) + 1;
+}
 
 }  // namespace he

@@ -316,7 +316,7 @@ static void apply_chain(Ctx *c, const u64 *in, int B, int level, const DcdChain 
 // level `to`.
 static void zt_stage(Ctx *c, const u64 *in, int B, int level, bool is_t, int n, int n1, int np, int to, u64 *out) {
     const int N = c->N;
-    const int m = np ? dcd_levels(n, np) : 1, lo = level - m;
+    const int m = dcd_levels(n, np, is_t), lo = level - m;
     const size_t wlo = (size_t)2 * (lo + 1) * N;
     Buf r(&c->pool, lo == to ? 1 : B * wlo);
     u64 *dst = lo == to ? out : r.p;   // no copy when no level has to be dropped

@@ -41,7 +41,8 @@ void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, 
               double value, u64 *out, const DcdFactor *fac = nullptr);
 // Decompositions (dcd.cu): which = 0 (Z_1), 1 (Z_2), 2 (T); levels a chain consumes.
 const DcdChain &dcd_chain(Ctx *c, int which, int n, int n_prime);
-int dcd_levels(int n, int n_prime);
+// Factors (levels) of the decomposed Z (is_t false) or T; 1 without n'.
+int dcd_levels(int n, int n_prime, bool is_t);
 void launch_dcd_fill(Ctx *c, double *out, const int *diag, int n, long t, long rot, double value, cudaStream_t st);
 // Levels a product consumes: the Z/T stage (1, or the longer decomposition
 // chain), C^k, and the multiplication.
@@ -49,7 +50,7 @@ void launch_dcd_fill(Ctx *c, double *out, const int *diag, int n, long t, long r
 // the decomposition chains, output dropped to level `to`.
 void zt_stage_public(Ctx *c, const u64 *in, int B, int level, bool is_t, int n, int n1, int np, int to, u64 *out);
 inline int hmatmul_depth(int n, int dcd_z, int dcd_t) {
-    int mz = dcd_z ? dcd_levels(n, dcd_z) : 1, mt = dcd_t ? dcd_levels(n, dcd_t) : 1;
+    int mz = dcd_levels(n, dcd_z, false), mt = dcd_levels(n, dcd_t, true);
     return (mz > mt ? mz : mt) + 2;
 }
 void replicate(Ctx *c, u64 *ct, int B, int level, int n);

@@ -156,13 +156,16 @@ def test_hmatmul_single_relinearisation():
 
 
 
-@pytest.mark.parametrize("n_prime", [4, 8])
-def test_dcd_sigma_tau_and_product_decrypt(n_prime):
+@pytest.mark.parametrize("n1,n_prime", [(4, 4), (4, 8), (1, 3), (1, 5), (1, 15)])
+def test_dcd_sigma_tau_and_product_decrypt(n1, n_prime):
     """Sec. 4.2 DMatrixMult: sigma and tau through their decomposition chains
-    decrypt to the index maps of eq. 5 / eq. 6 and consume ceil((n-1)/n')
-    levels; the product with both decomposed decrypts to A.B."""
-    n, n1 = 16, 4
-    P = Params(9, [60] + [40] * 6, [60])
+    decrypt to the index maps of eq. 5 / eq. 6 and consume floor((n-1)/n') + 1
+    (Z) and floor((n-2)/n') + 1 (T) levels; the product with both decomposed
+    decrypts to A.B -- also for an n' dividing n - 1 (n1 = 1), where a chain
+    one factor shorter would leave diagonal n' outside the left factor's
+    BSGS range."""
+    n = 16
+    P = Params(9, [60] + [40] * 9, [60])
     he = CKKS(P, 3)
     from oracle.hmm import HMM, matmul_rot_steps
     for s in matmul_rot_steps(n, n1, n1, P.S, n_prime, n_prime):
@@ -174,13 +177,13 @@ def test_dcd_sigma_tau_and_product_decrypt(n_prime):
     za, zb = np.zeros(P.S), np.zeros(P.S)
     za[: n * n], zb[: n * n] = A.ravel(), B.ravel()
     ca, cb = he.encrypt_slots(za, P.L, obj=10), he.encrypt_slots(zb, P.L, obj=11)
-    m = -(-(n - 1) // n_prime)
+    mz, mt = (n - 1) // n_prime + 1, (n - 2) // n_prime + 1
     i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     s = H.sigma_dcd(H.replicate(ca, n), n, n1, n_prime)
     t = H.tau_dcd(H.replicate(cb, n), n, n1, n_prime)
-    assert s.level == t.level == P.L - m
+    assert (s.level, t.level) == (P.L - mz, P.L - mt)
     assert np.abs(he.decrypt_slots(s).real[: n * n].reshape(n, n) - A[i, (i + j) % n]).max() < 1e-6
     assert np.abs(he.decrypt_slots(t).real[: n * n].reshape(n, n) - B[(i + j) % n, j]).max() < 1e-6
     cc = H.hmatmul(ca, cb, n, n1, n1, dcd_z=n_prime, dcd_t=n_prime)
-    assert cc.level == P.L - m - 2
+    assert cc.level == P.L - max(mz, mt) - 2
     assert np.abs(he.decrypt_slots(cc).real[: n * n].reshape(n, n) - A @ B).max() < 1e-4

@@ -146,19 +146,19 @@ def test_table3_rotation_key_memory():
 
 
 # ---------------------------------------------------------------- DCD
-@pytest.mark.parametrize("n,n_prime", [(8, 2), (8, 4), (16, 4), (16, 8), (32, 8)])
+@pytest.mark.parametrize("n,n_prime", [(8, 2), (8, 4), (16, 4), (16, 8), (32, 8),
+                                       (4, 1), (8, 1), (8, 7), (16, 3), (16, 5), (16, 15)])
 def test_dcd_factors_multiply_back_to_Z_and_T(n, n_prime):
     """Sec. 4.2: the factor chains of DCDforZ / DCDforT multiply (Boolean
     product) back to exactly the permutation matrices of eq. 5 / eq. 6; the
     right factors have only the diagonals 0 and +-n' (Z) or n' n (T); the left
     factor keeps diagonals inside [0, n'), (-n', 0] (Z) or {t n, t <= n'} (T);
-    each chain has ceil((n-1)/n') factors."""
+    Z's chains have floor((n-1)/n') + 1 factors, T's floor((n-2)/n') + 1."""
     from oracle import dcd
     size = n * n
-    m = -(-(n - 1) // n_prime)
     z1, z2 = dcd.dcd_Z(n, n_prime)
     t = dcd.dcd_T(n, n_prime)
-    assert len(z1) == len(z2) == len(t) == m
+    assert len(z1) == len(z2) == (n - 1) // n_prime + 1 and len(t) == (n - 2) // n_prime + 1
     p1, p2 = dcd.chain_product(z1), dcd.chain_product(z2)
     assert not (p1 & p2) and (p1 | p2) == dcd.perm_entries(n, "Z")
     assert dcd.chain_product(t) == dcd.perm_entries(n, "T")
@@ -167,12 +167,15 @@ def test_dcd_factors_multiply_back_to_Z_and_T(n, n_prime):
         u = diag_Z(n, k)
         got = dcd.diagonal(dcd.perm_entries(n, "Z"), size, k)
         assert np.array_equal(u, got)
+    # right factors: diagonals 0 and +-n' (Z) or n' n (T) only (a late round
+    # may have moved every entry, leaving no 0 diagonal)
     for f in z1[:-1]:
-        assert dcd.diagonal_set(f, size, True) == [0, n_prime]
+        assert n_prime in dcd.diagonal_set(f, size, True) and set(dcd.diagonal_set(f, size, True)) <= {0, n_prime}
     for f in z2[:-1]:
-        assert dcd.diagonal_set(f, size, True) == [-n_prime, 0]
+        assert -n_prime in dcd.diagonal_set(f, size, True) and set(dcd.diagonal_set(f, size, True)) <= {-n_prime, 0}
     for f in t[:-1]:
-        assert dcd.diagonal_set(f, size, False) == [0, n_prime * n]
+        assert n_prime * n in dcd.diagonal_set(f, size, False)
+        assert set(dcd.diagonal_set(f, size, False)) <= {0, n_prime * n}
     assert all(0 <= k < n_prime for k in dcd.diagonal_set(z1[-1], size, True))
     assert all(-n_prime < k <= 0 for k in dcd.diagonal_set(z2[-1], size, True))
     assert all(k % n == 0 and k // n <= n_prime for k in dcd.diagonal_set(t[-1], size, False))
