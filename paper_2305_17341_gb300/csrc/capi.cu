@@ -787,7 +787,7 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
     if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
     Ctx &c = ctx->c;
     if (int rc = check_ct(c, ct)) return rc;
-    he_mm_sched s{n1, n1};
+    he_mm_sched s{n1, n1, 0, 0, 0};
     if (int rc = check_sched(c, n, &s)) return rc;
     if (ct->level < 1) return fail(HE_ERR_LEVEL, "transpose needs 1 level");
     GUARD_BEGIN

@@ -9,8 +9,6 @@
 
 namespace he {
 
-static const size_t W = 1;  // words helper
-
 // ------------------------------------------------------------ key switch
 // Decompose (Sec. 3.3): poly of every item (stride item_s) -> digits
 // [B][ndig][l+1+alpha][N] in the NTT domain.
