@@ -283,3 +283,31 @@ def test_power_method_with_packed_refresh_matches_plaintext_replay():
         v = y * newton_inv_sqrt(x, taylor_inv_sqrt(x, x0), counts[it])
     assert np.abs(vec - v).max() < 1e-4
     assert abs(he.decrypt_slots(lam).real[0] - (Cs @ v) @ v) < 1e-4
+
+
+def test_covariance_three_column_blocks_decrypts_to_fp64():
+    """HCovMtrx with k = 3 column blocks (t = 3n features, ragged rows):
+    six block products per row block, three mirrored by G, against FP64."""
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    P, he = _small(7)
+    n, n1 = 16, 4
+    _rot_keys(he, P, n, n1)
+    X = lowrank_dataset(20, 48, 6)           # 2 row blocks, the second zero-padded
+    k, nrb = 3, 2
+    Xp = np.zeros((nrb * n, k * n))
+    Xp[:20] = X
+    blocks = []
+    for l in range(nrb):
+        row = []
+        for j in range(k):
+            z = np.zeros(P.S)
+            z[: n * n] = Xp[l * n:(l + 1) * n, j * n:(j + 1) * n].ravel()
+            row.append(he.encrypt_slots(z, P.L, obj=200 + l * k + j))
+        blocks.append(row)
+    C = PCA(he).covariance(blocks, 20, n, n1, n1)
+    Xc = X - X.mean(0)
+    ref = Xc.T @ Xc / 20
+    for a in range(k):
+        for b in range(k):
+            d = he.decrypt_slots(C[a][b]).real[: n * n].reshape(n, n)
+            assert np.abs(d - ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max() < 1e-4, (a, b)

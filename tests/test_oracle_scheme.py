@@ -187,3 +187,24 @@ def test_dcd_sigma_tau_and_product_decrypt(n1, n_prime):
     cc = H.hmatmul(ca, cb, n, n1, n1, dcd_z=n_prime, dcd_t=n_prime)
     assert cc.level == P.L - max(mz, mt) - 2
     assert np.abs(he.decrypt_slots(cc).real[: n * n].reshape(n, n) - A @ B).max() < 1e-4
+
+
+def test_relin_once_with_decomposed_transforms_decrypts():
+    """One relinearisation per product combined with decomposed Z and T
+    (both schedule options together) still decrypts to A.B."""
+    n, n1, n_prime = 16, 4, 8
+    P = Params(9, [60] + [40] * 6, [60])
+    he = CKKS(P, 5)
+    from oracle.hmm import HMM, matmul_rot_steps
+    for s in matmul_rot_steps(n, n1, n1, P.S, n_prime, n_prime):
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    rng = np.random.default_rng(21)
+    A, B = rng.uniform(-1, 1, (n, n)), rng.uniform(-1, 1, (n, n))
+    za, zb = np.zeros(P.S), np.zeros(P.S)
+    za[: n * n], zb[: n * n] = A.ravel(), B.ravel()
+    ca, cb = he.encrypt_slots(za, P.L, obj=12), he.encrypt_slots(zb, P.L, obj=13)
+    he.cnt.reset()
+    cc = HMM(he).hmatmul(ca, cb, n, n1, n1, relin_once=True, dcd_z=n_prime, dcd_t=n_prime)
+    assert cc.level == P.L - ((n - 1) // n_prime + 1) - 2
+    assert np.abs(he.decrypt_slots(cc).real[: n * n].reshape(n, n) - A @ B).max() < 1e-4
