@@ -220,10 +220,15 @@ int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out);
  *     device memory when it is loaded (each device that loads the library
  *     holds it until the process exits); no call allocates.  The first call
  *     on a device looks up the array's device address.
+ *   Stream: the work runs on the context's stream, which is not ordered
+ *     after the caller's streams.  The caller must have finished every write
+ *     to in_dev and out_dev (e.g. synchronised the stream that made them)
+ *     before the call; the call waits for its own work before returning.
  *   Returns HE_ERR_ARG when the ring degree and level need more than 32 MiB
- *     of temporaries (e.g. N = 2^16 above level 3), HE_ERR_KEY_MISSING without
- *     the rotation key.  The call waits for its work to finish.
- *   All calls share the array: calls whose work overlaps on the GPU race. */
+ *     of temporaries (at N = 2^16: above level 4 with two special primes,
+ *     above level 3 with one), HE_ERR_KEY_MISSING without the rotation key.
+ *   All calls share the array: calls whose work overlaps on the GPU race,
+ *     and a call must not overlap any other call on the same context. */
 int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level, int step, uint64_t *out_dev);
 
 /* Add (App. A Addition module): same level and scale. */

@@ -13,8 +13,10 @@ a = r + k_l = c - k_r (Theorem 2).
 
 Readings:
   * a diagonal with |k| >= n' (Z) goes to k_r = sign(k) n'; the others keep
-    k_l = k, k_r = 0 (the DCDforZ listing; its prose says "greater than" and
-    "the n'-th diagonal of the left matrix", which would not add up to k);
+    k_l = k, k_r = 0 (DCDforZ, Sec. 4.2).  The prose of that section uses a
+    strict comparison and names diagonal n' of the left factor as the target,
+    and a left part n' with a right part sign(k) n' would not add up to k, so
+    the algorithm's own steps are taken;
   * T: diagonals t n with t <= n' stay (k_r = 0), the others move by n' n
     (DCDforT);
   * rounds, each applied to the previous left factor, so Z_t = L R_m ...

@@ -205,7 +205,10 @@ void or_sample_ternary(u64 seed, u32 obj, u32 tag, int N, i64 *out) {
 
 /* Cumulative table of the discrete Gaussian truncated to |x| <= 19 (App. A,
  * chi_e with standard deviation sigma).  T[k] = floor(2^63 * P(|x| <= k)),
- * T[19] = 2^63.  Evaluated in the fixed order stated in the design notes. */
+ * T[19] = 2^63.  Evaluated in one fixed order: rho[v] = exp(-v^2 / (2 sigma^2))
+ * for v = 0..19, total = rho[0] + 2 rho[1] + ... + 2 rho[19] added in
+ * increasing v, and the cumulative sums in increasing k (the CUDA side runs
+ * the same sequence of IEEE operations). */
 void or_gauss_table(double sigma, u64 *T) {
     double denom = (2.0 * sigma) * sigma;
     double rho[20];
@@ -466,7 +469,7 @@ void or_moddown_round(int N, int nq, const u64 *qs, const u64 *uQ, int np, const
  * Canonical embedding (App. A Encode/Decode): slot j holds m(zeta^(5^j)),
  * zeta = exp(i pi / N), S = N/2 slots.  The inverse map, written as
  *   u_i = (1/S) sum_j z_j zeta^(-i 5^j),  m_i = Re u_i,  m_(i+S) = Im u_i,
- * is evaluated in the order fixed by the design notes:
+ * is evaluated in this fixed order:
  *   1. x[t] = z[j] with t = (5^j mod 2N - 1)/4   (5^j = 1 + 4t runs over all
  *      residues = 1 mod 4 exactly once),
  *   2. bit-reversal permutation of x over log2(S) bits,

@@ -15,8 +15,14 @@
 // nothing has to start at zero.  Calls whose work overlaps on the GPU (two
 // host threads, or several contexts on one device) race on the array and
 // must be serialised by the caller.
+//
+// The work runs on the context's stream, which is not ordered after any
+// stream of the caller: the caller finishes its own writes to the input and
+// output buffers (for instance by synchronising the stream that made them)
+// before the call, and the call returns only when its work is done.
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "eval.h"
 
@@ -66,7 +72,40 @@ static int noalloc_scratch(int dev, u64 **out) {
     return HE_OK;
 }
 
+// Turns the context's tracing and launch tuner off for the duration of a
+// call (both would create CUDA events) and restores them on every exit path.
+struct QuietCtx {
+    Ctx &c;
+    bool tr, at;
+    explicit QuietCtx(Ctx &cc) : c(cc), tr(cc.trace), at(cc.autotune) {
+        c.trace = false;
+        c.autotune = false;
+    }
+    ~QuietCtx() {
+        c.trace = tr;
+        c.autotune = at;
+    }
+};
+
+static int rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level, int step, uint64_t *out_dev);
+
 extern "C" int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level, int step, uint64_t *out_dev) {
+    // nothing may cross the C boundary as a C++ exception
+    try {
+        return rotate_noalloc(ctx, in_dev, level, step, out_dev);
+    } catch (const HeError &e) {
+        set_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return HE_ERR_OOM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return HE_ERR_ARG;
+    }
+}
+
+static int rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level, int step, uint64_t *out_dev) {
     if (!ctx || !in_dev || !out_dev) {
         set_error("null argument");
         return HE_ERR_ARG;
@@ -122,9 +161,7 @@ extern "C" int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level,
         }
     }
     cudaStream_t st = c.stream;
-    const bool tr = c.trace, at = c.autotune;
-    c.trace = false;     // tracing would create CUDA events
-    c.autotune = false;  // so would the launch tuner
+    QuietCtx quiet(c);
     cudaMemcpyAsync(d_inv, h_inv, sizeof(ShoupPair) * (nd * a + (size_t)nd * a * rows), cudaMemcpyHostToDevice, st);
     // Decompose c1 (the input is in coefficient form already), extend, NTT
     const u64 *in = (const u64 *)in_dev;
@@ -142,8 +179,6 @@ extern "C" int he_rotate_noalloc(he_ctx *ctx, const uint64_t *in_dev, int level,
     launch_moddown_final(&c, S_ct, S_u, S_conv, nullptr, 2, level, (long)rows * N, (long)nq * N, 0, st);
     ntt_inv(&c, S_ct, 2L * nq, c.map_q(level), st);
     cudaMemcpyAsync(out_dev, S_ct, wct * 8, cudaMemcpyDeviceToDevice, st);
-    c.trace = tr;
-    c.autotune = at;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
