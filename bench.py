@@ -205,6 +205,8 @@ def run_ours(args, rank, world, dist):
     pk.build()
     L = _lib.lib()
     ctx = pk.he_ctx_create(pk.he_params_default(args.preset), 1000 + rank)
+    if args.ms_variant is not None:
+        pk.he_ctx_set_multsum_variant(ctx, args.ms_variant)
     # the library launches on this stream; every CUDA event below is recorded on it
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
@@ -817,6 +819,8 @@ def run_keyswitch(args):
     import paper_2305_17341_gb300 as pk
     pk.build()
     ctx = pk.he_ctx_create(pk.he_params_default(2), 11)
+    if args.ms_variant is not None:
+        pk.he_ctx_set_multsum_variant(ctx, args.ms_variant)
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
     R, B = args.rot_steps, args.batch
@@ -858,7 +862,8 @@ def run_keyswitch(args):
                                              "frac": ach / hbm, "launches": t["count"], "avg_us": avg * 1e6,
                                              "algorithmic_bytes_per_launch": t["bytes"] / t["count"]},
                       "kernel_time_ms": {"multsum": tr[0]["ms"], "ntt_fwd": tr[1]["ms"], "ntt_inv": tr[2]["ms"]},
-                      "config": {"workload": "%d ciphertexts x %d rotation steps, one Decompose per ciphertext" % (B, R)},
+                      "config": {"workload": "%d ciphertexts x %d rotation steps, one Decompose per ciphertext" % (B, R),
+                                 "multsum_variant": args.ms_variant},
                       "autotune": pk.he_autotune_log(ctx).splitlines()}),
           flush=True)
     for h in cts:
@@ -1129,6 +1134,8 @@ def main():
                                                            "keyswitch", "transforms", "sweep"])
     ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
     ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
+    ap.add_argument("--ms-variant", type=int, default=None,
+                    help="matmul / keyswitch: pin every MultSum launch to one variant (default: the tuner)")
     ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")

@@ -122,6 +122,16 @@ int he_ctx_set_stream(he_ctx *ctx, void *stream);
  * rotations per launch, 8 items per CTA, cached loads; 2 NTT CTAs per SM). */
 int he_ctx_set_autotune(he_ctx *ctx, int on);
 
+/* Pins every MultSum launch of the context to one launch variant, with up to
+ * 8 hoisted rotations per launch and no tuning (-1 returns to the tuner /
+ * defaults).  Variants compute identical words; this is for tests and
+ * measurement.  0..7: one thread per (item, coefficient, row), digit and key
+ * words loaded by the threads (bits 0-1: 8/4/2/1 items per CTA, bit 2:
+ * streaming digit loads); 8, 9: persistent CTAs fed by bulk asynchronous
+ * global->shared copies of 64-coefficient digit and key segments with 4 or
+ * 6 stages in flight.  Errors: HE_ERR_ARG outside -1..9. */
+int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
+
 /* Newton composition for the PowerMethod's inverse square root (Sec. 7: two
  * InvSRT iterations composited into one that spends one level less).  With
  * on != 0, he_power_method / he_pca / PCA jobs on this context run each pair

@@ -86,6 +86,7 @@ SIGNATURES = {
     "he_ctx_set_stream": [vp, vp],
     "he_ctx_primes": [vp, u64p, u64p],
     "he_ctx_set_autotune": [vp, ip],
+    "he_ctx_set_multsum_variant": [vp, ip],
     "he_ctx_set_newton_composition": [vp, ip],
     "he_ctx_set_packed_refresh": [vp, ip],
     "he_autotune_log": [vp, ctypes.c_char_p, ip, P(ip)],
@@ -204,6 +205,11 @@ def he_ctx_set_stream(ctx, stream_ptr):
 
 def he_ctx_set_autotune(ctx, on=True):
     check(lib().he_ctx_set_autotune(ctx, 1 if on else 0))
+
+
+def he_ctx_set_multsum_variant(ctx, variant=-1):
+    """Pins every MultSum launch to one variant (-1: tuner / defaults)."""
+    check(lib().he_ctx_set_multsum_variant(ctx, int(variant)))
 
 
 def he_ctx_set_newton_composition(ctx, on=True):

@@ -189,6 +189,15 @@ int he_ctx_create(const he_params *prm, uint64_t seed, he_ctx **out) {
         return fail(HE_ERR_CUDA, "stream creation failed");
     }
     c.own_stream = true;
+    if (cudaHostAlloc((void **)&c.h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c.d_err, c.h_err, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (c.h_err) cudaFreeHost(c.h_err);
+        cudaStreamDestroy(c.stream);
+        delete h;
+        return fail(HE_ERR_CUDA, "mapped host flag allocation failed");
+    }
+    *c.h_err = 0;
     build_tables(&c);
     create_keys(&c);
     if (cudaStreamSynchronize(c.stream) != cudaSuccess) {
@@ -228,6 +237,7 @@ int he_ctx_destroy(he_ctx *ctx) {
         if (l.d_rs_qlmod) cudaFree(l.d_rs_qlmod);
     }
     c.pool.release_all();
+    if (c.h_err) cudaFreeHost(c.h_err);
     if (c.own_stream) cudaStreamDestroy(c.stream);
     delete ctx;
     return HE_OK;
@@ -251,6 +261,13 @@ int he_ctx_set_stream(he_ctx *ctx, void *stream) {
 int he_ctx_set_autotune(he_ctx *ctx, int on) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
     ctx->c.autotune = on != 0;
+    return HE_OK;
+}
+
+int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    if (variant < -1 || variant > 9) return fail(HE_ERR_ARG, "MultSum variant in -1..9");
+    ctx->c.force_multsum = variant;
     return HE_OK;
 }
 
@@ -311,6 +328,7 @@ int he_sk_export(const he_ctx *ctx, int64_t *s_out) {
     std::vector<u64> h(c.N);
     HE_CUDA_CHECK(cudaMemcpyAsync(h.data(), t.p, (size_t)c.N * 8, cudaMemcpyDeviceToHost, c.stream));
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     u64 q = c.primes[0];
     for (int i = 0; i < c.N; i++) s_out[i] = h[i] > q / 2 ? -(int64_t)(q - h[i]) : (int64_t)h[i];
     return HE_OK;
@@ -330,6 +348,7 @@ int he_keygen(he_ctx *ctx, const int32_t *rot_steps, int n_steps, int want_relin
     }
     if (want_relin && !c.rlk) c.rlk = gen_relin_key(&c);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     return cuda_status(&c);
     GUARD_END
 }
@@ -380,6 +399,7 @@ int he_encrypt_slots(he_ctx *ctx, const double *z, int nslots, int level, uint64
     he_ct *ct = new_ct(&c, level, delta, c.S);
     encrypt_poly(&c, m.p, level, (uint32_t)enc_counter, false, ct->d);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     int rc = cuda_status(&c);
     if (rc) {
         free_ct(ct);
@@ -413,6 +433,7 @@ int he_decrypt_slots(he_ctx *ctx, const he_ct *ct, double *z, int nslots) {
     std::vector<double> host(c.S);
     HE_CUDA_CHECK(cudaMemcpyAsync(host.data(), zr.p, sizeof(double) * c.S, cudaMemcpyDeviceToHost, c.stream));
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     if (nslots) std::memcpy(z, host.data(), sizeof(double) * nslots);
     return cuda_status(&c);
     GUARD_END
@@ -442,6 +463,7 @@ int he_ct_export(const he_ct *ct, uint64_t *residues) {
     ntt_inv(&c, t.p, 2L * (ct->level + 1), c.map_q(ct->level), c.stream);
     HE_CUDA_CHECK(cudaMemcpyAsync(residues, t.p, w * 8, cudaMemcpyDeviceToHost, c.stream));
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     return cuda_status(&c);
     GUARD_END
 }
@@ -456,6 +478,7 @@ int he_ct_import(he_ctx *ctx, const uint64_t *residues, int level, double scale,
     HE_CUDA_CHECK(cudaMemcpyAsync(ct->d, residues, w * 8, cudaMemcpyHostToDevice, c.stream));
     ntt_fwd(&c, ct->d, 2L * (level + 1), c.map_q(level), c.stream);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     *out = ct;
     return cuda_status(&c);
     GUARD_END
@@ -485,6 +508,7 @@ int he_rotate(he_ctx *ctx, const he_ct *ct, int step, he_ct **out) {
         throw;
     }
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     *out = o;
     return cuda_status(&c);
     GUARD_END
@@ -532,6 +556,7 @@ int he_rotate_hoisted(he_ctx *ctx, const he_ct *const *cts, int n_cts, const int
                 }
         }
         HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+        if (int rc_dev = device_status(&c)) return rc_dev;
         if (int rc = cuda_status(&c)) throw HeError(rc, last_error());
     } catch (...) {
         for (he_ct *o : res) free_ct(o);
@@ -553,6 +578,7 @@ int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out) {
     he_ct *o = new_ct(&c, a->level, a->scale, std::min(a->period, b->period));
     add(&c, a->d, b->d, 1, a->level, o->d);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     *out = o;
     return cuda_status(&c);
     GUARD_END
@@ -573,6 +599,7 @@ int he_mult(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct **out) {
         throw;
     }
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     *out = o;
     return cuda_status(&c);
     GUARD_END
@@ -587,6 +614,7 @@ int he_rescale(he_ctx *ctx, const he_ct *a, he_ct **out) {
     he_ct *o = new_ct(&c, a->level - 1, a->scale / (double)c.primes[a->level], a->period);
     rescale(&c, a->d, 1, a->level, o->d);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     *out = o;
     return cuda_status(&c);
     GUARD_END
@@ -615,6 +643,7 @@ int he_replicate(he_ctx *ctx, const he_ct *ct, int n, he_ct **out) {
         o->period = n * n;
     }
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     *out = o;
     return cuda_status(&c);
     GUARD_END
@@ -709,8 +738,10 @@ int he_hmatmul_batch(const he_mm_job *jobs, int n_jobs, he_ct **outs) {
         std::set<Ctx *> ctxs;
         for (auto &p : prods) ctxs.insert(p.A->ctx);
         for (Ctx *c : ctxs) HE_CUDA_CHECK(cudaStreamSynchronize(c->stream));
-        for (Ctx *c : ctxs)
+        for (Ctx *c : ctxs) {
             if (int rc = cuda_status(c)) throw HeError(rc, last_error());
+            if (int rc = device_status(c)) throw HeError(rc, last_error());
+        }
     } catch (...) {
         for (he_ct *o : res) free_ct(o);
         throw;
@@ -803,6 +834,7 @@ int he_transpose(he_ctx *ctx, const he_ct *ct, int n, int n1, double prescale, h
         throw;
     }
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     free_ct(tmp);
     *out = o;
     return cuda_status(&c);
@@ -837,6 +869,7 @@ int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, i
         throw;
     }
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     free_ct(tmp);
     *out = o;
     return cuda_status(&c);
@@ -853,6 +886,7 @@ int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inv
     else
         ntt_fwd(&c, (u64 *)rows_dev, n_rows, c.map_qp(level), c.stream);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
     return cuda_status(&c);
     GUARD_END
 }

@@ -9,6 +9,15 @@ namespace he {
 // -------------------------------------------------------------- errors
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
+
+int device_status(const Ctx *c) {
+    if (c && c->h_err && *(volatile int *)c->h_err) {
+        *(volatile int *)c->h_err = 0;
+        set_error("a device-side wait ran out of its iteration limit (kernel stopped early; outputs invalid)");
+        return HE_ERR_TIMEOUT;
+    }
+    return HE_OK;
+}
 const char *last_error() { return g_err.c_str(); }
 
 // --------------------------------------------------------- number theory

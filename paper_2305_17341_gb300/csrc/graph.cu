@@ -192,6 +192,7 @@ int he_mm_plan_run(he_mm_plan *P, he_ct **outs) {
         cudaError_t e = cudaStreamSynchronize(c.stream);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) throw HeError(HE_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(e));
+        if (device_status(&c)) throw HeError(HE_ERR_TIMEOUT, last_error());
     } catch (const HeError &e) {
         for (he_ct *o : res) free_ct(o);
         set_error(e.what());

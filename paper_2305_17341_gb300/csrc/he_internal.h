@@ -169,6 +169,10 @@ struct Ctx {
     DevicePool pool;
     std::mutex mu;
 
+    // Flag that kernels with bounded waits set when a wait runs out: host
+    // memory mapped into the device, read by the host after a synchronise.
+    int *h_err = nullptr, *d_err = nullptr;
+
     // instrumentation
     std::atomic<long long> n_ms{0}, n_dp{0}, n_md{0}, n_launch{0};
     // per-kernel-class tracing: CUDA events on the context stream around each
@@ -189,6 +193,8 @@ struct Ctx {
     // vector's segments refreshed as one packed ciphertext
     bool newton_compose = false;
     bool pack_refresh = false;
+    // >= 0: every MultSum launch uses this variant (keys per launch 8), no tuning
+    int force_multsum = -1;
     // (level, items, keys) -> (keys per launch << 8) | variant
     std::map<std::tuple<int, int, int>, int> tune_multsum;
     std::string tune_log;   // every timed plan, one line each
@@ -232,6 +238,9 @@ struct Ct {
 
 // error handling
 void set_error(const std::string &msg);
+// HE_OK, or HE_ERR_TIMEOUT if a kernel's bounded wait ran out since the last
+// check (the flag is cleared).  Call after synchronising the context's stream.
+int device_status(const Ctx *c);
 #define HE_CUDA_CHECK(expr)                                                          \
     do {                                                                             \
         cudaError_t e__ = (expr);                                                    \

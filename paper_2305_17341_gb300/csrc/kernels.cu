@@ -670,6 +670,34 @@ void launch_permute_key(Ctx *c, u64 *out, const u64 *in, long rows, uint32_t g, 
     k_permute_key<<<nblk(n, 256), 256, 0, st>>>(out, in, rows, c->logN, g);
 }
 
+#include "multsum_tma.cuh"
+
+// Launch of the bulk-copy MultSum (variants 8 and 9: 4 or 6 stages in
+// flight per CTA), persistent: as many CTAs as fit on the GPU at once.
+template <int G, int S>
+static void multsum_tma_launch(Ctx *c, const MultiKeys<G> &mk, const u64 *digits, int B, int level, const u64 *c0,
+                               long c0s, cudaStream_t st) {
+    static int occ[64];   // resident CTAs per SM, per device
+    const size_t smem = (size_t)S * (MST_BI + 2 * G) * MST_TW * 8;
+    const int dev = c->device & 63;
+    if (!occ[dev]) {
+        cudaFuncSetAttribute(k_multsum_tma<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_multsum_tma<G, S>, MST_THREADS, smem);
+        occ[dev] = nb > 0 ? nb : 1;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    MstGeom g;
+    g.N = c->N, g.logN = c->logN, g.rows = level + 1 + c->alpha, g.level = level, g.L = c->L;
+    g.ndig = c->ndig(level), g.nprimes = c->nprimes, g.ntx = c->N / MST_TW, g.nig = (B + MST_BI - 1) / MST_BI;
+    g.B = B;
+    g.ntiles = (long)g.ntx * g.rows * g.nig;
+    const long grid = std::min<long>(g.ntiles, (long)nsm * occ[dev]);
+    k_multsum_tma<G, S><<<(unsigned)grid, MST_THREADS, smem, st>>>(mk, digits, g, c->d_mod, c0, c0s, c->d_Pmod,
+                                                                    c->d_err);
+}
+
 // MultSum launch variants: items per CTA (BI), streaming digit loads.
 static void multsum_variant(int v, int B, int &BI, bool &stream) {
     static const int bis[4] = {8, 4, 2, 1};
@@ -690,6 +718,12 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         u32 g = gs[k], inv = g;
         for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
         mk.ginv[k] = inv & (M - 1);
+    }
+    if (v >= 8) {
+        if (v == 8) multsum_tma_launch<G, 4>(c, mk, digits, B, level, c0, c0s, st);
+        else multsum_tma_launch<G, 6>(c, mk, digits, B, level, c0, c0s, st);
+        c->n_launch++;
+        return;
     }
     int BI;
     bool stream;
@@ -743,7 +777,9 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
         }
     };
     int chunk = std::min(G, kMultSumMaxKeys), v = 0;  // default: 8 keys, 8 items per CTA, cached loads
-    if (c->autotune) {
+    if (c->force_multsum >= 0) {
+        v = c->force_multsum;
+    } else if (c->autotune) {
         auto key3 = std::make_tuple(level, B, G);
         auto it = c->tune_multsum.find(key3);
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -758,10 +794,11 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand = 0; cand < 8; cand++) {
+                for (int cand = 0; cand < 10; cand++) {
                     int BI;
                     bool stream;
                     multsum_variant(cand, B, BI, stream);
+                    if (cand >= 8) BI = 100 + cand;   // the bulk-copy kernel: its own entries
                     if (!seen.insert(std::make_tuple(cc, BI, stream)).second) continue;
                     float t = 1e30f;
                     for (int rep = 0; rep < 2; rep++) {

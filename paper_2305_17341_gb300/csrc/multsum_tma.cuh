@@ -1,0 +1,253 @@
+// multsum_tma.cuh -- MultSum + Permute (Sec. 3.3.1) fed by bulk asynchronous
+// copies.  Included by kernels.cu, after MultiKeys and auto_index.
+//
+// The inner product of the hoisted key switch reads every digit word once
+// and every key word once per launch; the work per byte is a few 32-bit
+// multiply-adds, so the kernel lives on memory throughput.  Here each CTA is
+// persistent and walks a sequence of (tile, digit) stages: a tile is TW
+// coefficients of one row of Q_l P for up to BI items, a stage the digit-d
+// words of those items plus the digit-d words of the G keys (2 polynomials
+// each).  One thread issues every segment of a stage as a `cp.async.bulk`
+// global->shared copy (contiguous TW words) that completes on the stage's
+// mbarrier; S stages are in flight while the 256 threads multiply-accumulate
+// the oldest, so the copies run back to back across digits and tiles and no
+// register holds a load in flight.  Each thread owns one coefficient of two
+// items and the 2G accumulators of each: the key words it reads from shared
+// memory serve both items, the digit words all G keys.
+//
+// Waits are bounded: a stage that does not complete within the iteration
+// limit sets *err (a flag the host checks after synchronising) and the CTA
+// stops, after a bounded wait for the copies it still has in flight.
+#pragma once
+
+constexpr int MST_TW = 64;        // coefficients per tile (512-byte segments)
+constexpr int MST_BI = 8;         // items per tile
+constexpr int MST_THREADS = 256;  // MST_TW * MST_BI / 2 items per thread
+constexpr int MST_WAIT_LIMIT = 1 << 22;
+
+__device__ __forceinline__ u32 mst_smem(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mst_bar_init(u64 *bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mst_smem(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mst_expect_tx(u64 *bar, u32 bytes) {
+    u64 state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(mst_smem(bar)), "r"(bytes)
+                 : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ bool mst_try_wait(u64 *bar, u32 parity) {
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mst_smem(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.
+__device__ __forceinline__ bool mst_wait(u64 *bar, u32 parity) {
+    for (int it = 0; it < MST_WAIT_LIMIT; it++)
+        if (mst_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// bytes (a multiple of 16) from global src to shared dst (both 16-byte
+// aligned), completing on bar's transaction count.
+__device__ __forceinline__ void mst_bulk(void *dst, const void *src, u32 bytes, u64 *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            mst_smem(dst)),
+        "l"(src), "r"(bytes), "r"(mst_smem(bar))
+        : "memory");
+}
+
+struct MstGeom {
+    int N, logN, rows, level, L, ndig, nprimes, ntx, nig, B;
+    long ntiles;
+    __device__ __forceinline__ void tile(long t, int &ig, int &xt, int &r) const {
+        ig = (int)(t % nig);
+        const long rest = t / nig;
+        xt = (int)(rest % ntx);
+        r = (int)(rest / ntx);
+    }
+    __device__ __forceinline__ int prime_of_row(int r) const { return r <= level ? r : L + 1 + (r - level - 1); }
+};
+
+// Issues the copies of stage jj of this CTA's sequence (tile jj / ndig of
+// the CTA, digit jj % ndig) into buffer jj % S; false past the last tile.
+template <int G, int S>
+__device__ __forceinline__ bool mst_issue(const MstGeom &g, const MultiKeys<G> &mk, const u64 *digits, u64 *stage,
+                                          u64 *bar, long jj) {
+    constexpr int SEG = MST_BI + 2 * G;
+    const long ti = jj / g.ndig;
+    const int d = (int)(jj - ti * g.ndig);
+    const long t = (long)blockIdx.x + ti * (long)gridDim.x;
+    if (t >= g.ntiles) return false;
+    int ig, xt, r;
+    g.tile(t, ig, xt, r);
+    const int kr = g.prime_of_row(r);
+    const int s = (int)(jj % S);
+    const int b0 = ig * MST_BI, nb = min(MST_BI, g.B - b0);
+    u64 *dst = stage + (long)s * SEG * MST_TW;
+    const long y0 = (long)xt * MST_TW, N = g.N;
+    // the stage's previous contents were read through the generic proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mst_expect_tx(&bar[s], (u32)((nb + 2 * G) * MST_TW * 8));
+    const long dstride = (long)g.rows * N;
+    for (int b = 0; b < nb; b++)
+        mst_bulk(dst + b * MST_TW, digits + ((long)(b0 + b) * g.ndig + d) * dstride + (long)r * N + y0, MST_TW * 8,
+                 &bar[s]);
+    const long kd = 2L * g.nprimes * N, kk = (long)g.nprimes * N;
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        const u64 *kp = mk.key[k] + (long)d * kd + (long)kr * N + y0;
+        mst_bulk(dst + (MST_BI + 2 * k) * MST_TW, kp, MST_TW * 8, &bar[s]);
+        mst_bulk(dst + (MST_BI + 2 * k + 1) * MST_TW, kp + kk, MST_TW * 8, &bar[s]);
+    }
+    return true;
+}
+
+// Accumulators of one thread: per (item, key, polynomial) 96 bits (three
+// 32-bit words) for rows below 2^42, 128 bits for the 60-bit rows.
+template <int G, bool W96>
+struct MstAcc;
+template <int G>
+struct MstAcc<G, true> {
+    u32 x0[2][2 * G], x1[2][2 * G], x2[2][2 * G];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) x0[i][k] = 0, x1[i][k] = 0, x2[i][k] = 0;
+    }
+    __device__ __forceinline__ void mac(int i, int k, u64 v, u64 key) { mac96(x0[i][k], x1[i][k], x2[i][k], v, key); }
+    __device__ __forceinline__ u64 out(int i, int k, const ModQ &m) const {
+        return redc(((u64)x1[i][k] << 32) | x0[i][k], x2[i][k], m);
+    }
+};
+template <int G>
+struct MstAcc<G, false> {
+    U128 w[2][2 * G];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) w[i][k] = U128{0, 0};
+    }
+    __device__ __forceinline__ void mac(int i, int k, u64 v, u64 key) { mac128(w[i][k], v, key); }
+    __device__ __forceinline__ u64 out(int i, int k, const ModQ &m) const { return redc(w[i][k].lo, w[i][k].hi, m); }
+};
+
+// One tile: its ndig stages (waiting, accumulating, releasing each buffer
+// and refilling it S stages ahead), then the epilogue.  Returns false when
+// a wait ran out (the caller drains).  jj counts this CTA's stages.
+template <int G, int S, bool W96>
+__device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digits, const MstGeom &geo, u64 *stage,
+                                         u64 *bar, volatile int &abort_flag, int *err, long &jj, int r, int y,
+                                         int b0, const ModQ &m, const u64 *c0, long c0s, const ShoupPair *Pmod) {
+    constexpr int SEG = MST_BI + 2 * G;
+    const int tid = threadIdx.x, c = tid % MST_TW, ip = tid / MST_TW;
+    MstAcc<G, W96> acc;
+    acc.zero();
+    for (int d = 0; d < geo.ndig; d++, jj++) {
+        const int s = (int)(jj % S);
+        if (!mst_wait(&bar[s], (u32)((jj / S) & 1))) {
+            abort_flag = 1;
+            atomicExch(err, 1);
+        } else {
+            const u64 *sg = stage + (long)s * SEG * MST_TW;
+            u64 kv[2 * G];
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) kv[k] = sg[(MST_BI + k) * MST_TW + c];
+            const u64 v0 = sg[(2 * ip) * MST_TW + c], v1 = sg[(2 * ip + 1) * MST_TW + c];
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) {
+                acc.mac(0, k, v0, kv[k]);
+                acc.mac(1, k, v1, kv[k]);
+            }
+        }
+        __syncthreads();
+        if (abort_flag) return false;
+        if (tid == 0) mst_issue<G, S>(geo, mk, digits, stage, bar, jj + S);
+    }
+    // epilogue: one Montgomery reduction per output word, P c0 on the Q rows
+    // of polynomial 0, store at the permuted position
+    const int N = geo.N, rows = geo.rows;
+    const bool with_c0 = c0 && r <= geo.level;
+    const ShoupPair wP = with_c0 ? Pmod[r] : ShoupPair{0, 0};
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int b = b0 + i;
+        if (b >= geo.B) continue;
+        u64 pc0 = 0;
+        if (with_c0) pc0 = shoup(c0[(long)b * c0s + (long)r * N + y], wP.w, wP.wp, m.q);
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            u64 o0 = acc.out(i, 2 * k, m);
+            const u64 o1 = acc.out(i, 2 * k + 1, m);
+            if (with_c0) o0 = addmod(o0, pc0, m.q);
+            const int x = mk.ginv[k] == 1u ? y : auto_index(y, mk.ginv[k], geo.logN);
+            u64 *ob = mk.out[k] + (long)b * 2 * rows * N;
+            ob[(long)r * N + x] = o0;
+            ob[(long)(rows + r) * N + x] = o1;
+        }
+    }
+    return true;
+}
+
+template <int G, int S>
+__global__ void __launch_bounds__(MST_THREADS, G <= 4 ? 2 : 1)
+    k_multsum_tma(MultiKeys<G> mk, const u64 *digits, MstGeom geo, const ModQ *mods, const u64 *c0, long c0s,
+                  const ShoupPair *Pmod, int *err) {
+    extern __shared__ __align__(128) u64 mst_stage[];
+    __shared__ __align__(8) u64 bar[S];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < S; s++) mst_bar_init(&bar[s], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const int c = tid % MST_TW, ip = tid / MST_TW;   // coefficient; item pair
+    long jj = 0;
+    if (tid == 0)
+        for (int k = 0; k < S; k++) mst_issue<G, S>(geo, mk, digits, mst_stage, bar, k);
+    for (long ti = 0;; ti++) {
+        const long t = (long)blockIdx.x + ti * (long)gridDim.x;
+        if (t >= geo.ntiles) break;
+        int ig, xt, r;
+        geo.tile(t, ig, xt, r);
+        const ModQ m = mods[geo.prime_of_row(r)];
+        const int y = xt * MST_TW + c, b0 = ig * MST_BI + 2 * ip;
+        // 96-bit accumulation on the rows below 2^42 (uniform over the tile)
+        const bool ok = m.q < (1ull << 42)
+                            ? mst_tile<G, S, true>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r, y, b0, m,
+                                                   c0, c0s, Pmod)
+                            : mst_tile<G, S, false>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r, y, b0,
+                                                    m, c0, c0s, Pmod);
+        if (!ok) {
+            // a stage timed out: wait (bounded) for every copy this CTA
+            // still has in flight before its shared memory is given back
+            if (tid == 0) {
+                for (int k = 0; k < S; k++) {
+                    const long jk = jj + k;
+                    const long tk = (long)blockIdx.x + (jk / geo.ndig) * (long)gridDim.x;
+                    if (tk >= geo.ntiles) break;
+                    mst_wait(&bar[jk % S], (u32)((jk / S) & 1));
+                }
+            }
+            __syncthreads();
+            return;
+        }
+    }
+}

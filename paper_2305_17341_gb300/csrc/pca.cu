@@ -708,7 +708,7 @@ static int sync_status(Ctx &c) {
         set_error(std::string("CUDA error: ") + cudaGetErrorString(e));
         return HE_ERR_CUDA;
     }
-    return HE_OK;
+    return device_status(&c);
 }
 
 static bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }

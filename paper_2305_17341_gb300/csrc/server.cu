@@ -292,10 +292,12 @@ void he_server::tick(Worker *w, std::vector<Job *> &batch) {
     // 4. the stream decides whether anything of the tick failed on the device
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
+    const int dev_rc = e == cudaSuccess ? device_status(c) : HE_OK;
     std::lock_guard<std::mutex> lk(m);
     const double t = now();
     for (Job *j : batch) {
         if (e != cudaSuccess) fail_job(j, HE_ERR_CUDA, std::string("CUDA error: ") + cudaGetErrorString(e));
+        else if (dev_rc) fail_job(j, dev_rc, "a device-side wait ran out of its iteration limit");
         if (j->status != HE_JOB_FAILED) j->status = HE_JOB_DONE;
         j->t_done = t;
         const int kd = j->spec.kind;
