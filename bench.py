@@ -592,9 +592,40 @@ def run_pca(args):
         r2v = 1 - ((Vm - Ut) ** 2).sum() / ((Ut - Ut.mean()) ** 2).sum()
         for h in lams + [x for V in Vs for x in V]:
             pk.he_ct_free(h)
+        # agreement with the FP64 run of the same schedule: the CKKS error alone
+        run.vs_fp64 = [float(abs(v @ f) / (np.linalg.norm(v) * np.linalg.norm(f))) for v, f in zip(vecs, f_vec)]
         return pm_s, rs.count, cos, lam_he, float(r2v)
 
+    # The same method in FP64 on the exact covariance (pre-scaled by d like
+    # the encrypted one): the same start vectors, PowerMethod iterations,
+    # TaylorInit + Newton counts of Lazy Normalization (Sec. 6.1.2) and
+    # EigenShift deflation (Sec. 6.2).  Its cosines against eigh are the
+    # method's own convergence; the encrypted run adds the CKKS error.
+    def fp64_same_schedule():
+        Cs = (Xc.T @ Xc / s) * t
+        x0 = 2.0 ** 15 + 1.0
+        rs_ = np.random.default_rng(3)
+        out_cos, out_lam, out_vec = [], [], []
+        for m in range(l_E):
+            v = rs_.standard_normal(t)
+            v /= np.linalg.norm(v)
+            for it in range(l_P):
+                yv = Cs @ v
+                x = yv @ yv
+                inv = x0 ** -0.5 * (1.5 - x / (2.0 * x0))
+                for _ in range(counts[it]):
+                    inv = 0.5 * inv * (3.0 - x * inv * inv)
+                v = yv * inv
+            lam = (Cs @ v) @ v
+            out_cos.append(float(abs(v @ U[:, m]) / np.linalg.norm(v)))
+            out_lam.append(float(lam / t))
+            out_vec.append(v)
+            Cs = Cs - lam * np.outer(v, v)
+        return out_cos, out_lam, out_vec
+
+    f_cos, f_lam, f_vec = fp64_same_schedule()
     pm_s, refreshes, cos, lam_he, r2v = run(False)
+    run_vs_fp64 = run.vs_fp64
     comp = packed = None
     if not args.no_compose:
         c_s, c_ref, c_cos, c_lam, c_r2 = run(True)
@@ -610,6 +641,12 @@ def run_pca(args):
                                              "counts %s; covariance pre-scaled by d=256" % (l_E, l_P, counts)},
                       "covariance_s": cov_s, "refreshes": refreshes, "cosine_vs_eigh": cos,
                       "lambda_he": lam_he, "lambda_fp64": [float(x) for x in w[:l_E]], "R2_V": r2v,
+                      "fp64_same_schedule": {"cosine_vs_eigh": f_cos, "lambda": f_lam,
+                                             "note": "the PowerMethod of the encrypted run (same start vectors, "
+                                                     "l_P, Newton counts, deflation) in FP64 on the exact "
+                                                     "covariance"},
+                      "cosine_he_vs_fp64_same_schedule": run_vs_fp64,
+                      "eigen_gaps": [float(w[m + 1] / w[m]) for m in range(l_E)],
                       "per_pm_iteration_s": pm_s / (l_E * (l_P + 1)), "composed_newton": comp,
                       "composed_newton_packed_refresh": packed}), flush=True)
     pk.he_ctx_destroy(ctx3)

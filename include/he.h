@@ -127,9 +127,10 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * defaults).  Variants compute identical words; this is for tests and
  * measurement.  0..7: one thread per (item, coefficient, row), digit and key
  * words loaded by the threads (bits 0-1: 8/4/2/1 items per CTA, bit 2:
- * streaming digit loads); 8, 9: persistent CTAs fed by bulk asynchronous
- * global->shared copies of 64-coefficient digit and key segments with 4 or
- * 6 stages in flight.  Errors: HE_ERR_ARG outside -1..9. */
+ * streaming digit loads); 8, 9, 10: persistent CTAs fed by bulk
+ * asynchronous global->shared copies of digit and key segments, 4 stages in
+ * flight, tiles of 64 coefficients x 8 items, 128 x 4 and 256 x 2.
+ * Errors: HE_ERR_ARG outside -1..10. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Newton composition for the PowerMethod's inverse square root (Sec. 7: two

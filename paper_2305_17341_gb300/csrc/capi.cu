@@ -266,7 +266,7 @@ int he_ctx_set_autotune(he_ctx *ctx, int on) {
 
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
-    if (variant < -1 || variant > 9) return fail(HE_ERR_ARG, "MultSum variant in -1..9");
+    if (variant < -1 || variant > 10) return fail(HE_ERR_ARG, "MultSum variant in -1..10");
     ctx->c.force_multsum = variant;
     return HE_OK;
 }

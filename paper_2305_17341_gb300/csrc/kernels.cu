@@ -672,30 +672,32 @@ void launch_permute_key(Ctx *c, u64 *out, const u64 *in, long rows, uint32_t g, 
 
 #include "multsum_tma.cuh"
 
-// Launch of the bulk-copy MultSum (variants 8 and 9: 4 or 6 stages in
-// flight per CTA), persistent: as many CTAs as fit on the GPU at once.
-template <int G, int S>
+// Launch of the bulk-copy MultSum, persistent: as many CTAs as fit on the
+// GPU at once.  Variants: 8: 64-coefficient segments of 8 items, 9: 128 of
+// 4, 10: 256 of 2 (4 stages in flight each).
+template <int G, int S, int TW, int BI>
 static void multsum_tma_launch(Ctx *c, const MultiKeys<G> &mk, const u64 *digits, int B, int level, const u64 *c0,
                                long c0s, cudaStream_t st) {
+    static_assert(TW * BI == 2 * MST_THREADS, "two items per thread");
     static int occ[64];   // resident CTAs per SM, per device
-    const size_t smem = (size_t)S * (MST_BI + 2 * G) * MST_TW * 8;
+    const size_t smem = (size_t)S * (BI + 2 * G) * TW * 8;
     const int dev = c->device & 63;
     if (!occ[dev]) {
-        cudaFuncSetAttribute(k_multsum_tma<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_multsum_tma<G, S, TW, BI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_multsum_tma<G, S>, MST_THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_multsum_tma<G, S, TW, BI>, MST_THREADS, smem);
         occ[dev] = nb > 0 ? nb : 1;
     }
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     MstGeom g;
     g.N = c->N, g.logN = c->logN, g.rows = level + 1 + c->alpha, g.level = level, g.L = c->L;
-    g.ndig = c->ndig(level), g.nprimes = c->nprimes, g.ntx = c->N / MST_TW, g.nig = (B + MST_BI - 1) / MST_BI;
+    g.ndig = c->ndig(level), g.nprimes = c->nprimes, g.ntx = c->N / TW, g.nig = (B + BI - 1) / BI;
     g.B = B;
     g.ntiles = (long)g.ntx * g.rows * g.nig;
     const long grid = std::min<long>(g.ntiles, (long)nsm * occ[dev]);
-    k_multsum_tma<G, S><<<(unsigned)grid, MST_THREADS, smem, st>>>(mk, digits, g, c->d_mod, c0, c0s, c->d_Pmod,
-                                                                    c->d_err);
+    k_multsum_tma<G, S, TW, BI><<<(unsigned)grid, MST_THREADS, smem, st>>>(mk, digits, g, c->d_mod, c0, c0s,
+                                                                            c->d_Pmod, c->d_err);
 }
 
 // MultSum launch variants: items per CTA (BI), streaming digit loads.
@@ -720,8 +722,9 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         mk.ginv[k] = inv & (M - 1);
     }
     if (v >= 8) {
-        if (v == 8) multsum_tma_launch<G, 4>(c, mk, digits, B, level, c0, c0s, st);
-        else multsum_tma_launch<G, 6>(c, mk, digits, B, level, c0, c0s, st);
+        if (v == 8) multsum_tma_launch<G, 4, 64, 8>(c, mk, digits, B, level, c0, c0s, st);
+        else if (v == 9) multsum_tma_launch<G, 4, 128, 4>(c, mk, digits, B, level, c0, c0s, st);
+        else multsum_tma_launch<G, 4, 256, 2>(c, mk, digits, B, level, c0, c0s, st);
         c->n_launch++;
         return;
     }
@@ -794,7 +797,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand = 0; cand < 10; cand++) {
+                for (int cand = 0; cand < 11; cand++) {
                     int BI;
                     bool stream;
                     multsum_variant(cand, B, BI, stream);

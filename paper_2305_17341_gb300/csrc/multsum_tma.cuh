@@ -15,14 +15,18 @@
 // items and the 2G accumulators of each: the key words it reads from shared
 // memory serve both items, the digit words all G keys.
 //
+// Segments of 8 TW bytes: the copy engine's cost per request, not the bytes,
+// limits small segments, so wider tiles with fewer items (keys then come
+// from L2 for the other item groups of a tile) are launch variants.
+//
 // Waits are bounded: a stage that does not complete within the iteration
 // limit sets *err (a flag the host checks after synchronising) and the CTA
 // stops, after a bounded wait for the copies it still has in flight.
 #pragma once
 
-constexpr int MST_TW = 64;        // coefficients per tile (512-byte segments)
-constexpr int MST_BI = 8;         // items per tile
-constexpr int MST_THREADS = 256;  // MST_TW * MST_BI / 2 items per thread
+// A tile is TW coefficients (segments of 8 TW bytes) of BI items; 256
+// threads, each with one coefficient of two items: TW * BI = 512.
+constexpr int MST_THREADS = 256;
 constexpr int MST_WAIT_LIMIT = 1 << 22;
 
 __device__ __forceinline__ u32 mst_smem(const void *p) { return (u32)__cvta_generic_to_shared(p); }
@@ -70,7 +74,7 @@ __device__ __forceinline__ void mst_bulk(void *dst, const void *src, u32 bytes, 
 }
 
 struct MstGeom {
-    int N, logN, rows, level, L, ndig, nprimes, ntx, nig, B;
+    int N, logN, rows, level, L, ndig, nprimes, ntx, nig, B;   // ntx = N / TW, nig = ceil(B / BI)
     long ntiles;
     __device__ __forceinline__ void tile(long t, int &ig, int &xt, int &r) const {
         ig = (int)(t % nig);
@@ -83,10 +87,10 @@ struct MstGeom {
 
 // Issues the copies of stage jj of this CTA's sequence (tile jj / ndig of
 // the CTA, digit jj % ndig) into buffer jj % S; false past the last tile.
-template <int G, int S>
+template <int G, int S, int TW, int BI>
 __device__ __forceinline__ bool mst_issue(const MstGeom &g, const MultiKeys<G> &mk, const u64 *digits, u64 *stage,
                                           u64 *bar, long jj) {
-    constexpr int SEG = MST_BI + 2 * G;
+    constexpr int SEG = BI + 2 * G;
     const long ti = jj / g.ndig;
     const int d = (int)(jj - ti * g.ndig);
     const long t = (long)blockIdx.x + ti * (long)gridDim.x;
@@ -95,22 +99,21 @@ __device__ __forceinline__ bool mst_issue(const MstGeom &g, const MultiKeys<G> &
     g.tile(t, ig, xt, r);
     const int kr = g.prime_of_row(r);
     const int s = (int)(jj % S);
-    const int b0 = ig * MST_BI, nb = min(MST_BI, g.B - b0);
-    u64 *dst = stage + (long)s * SEG * MST_TW;
-    const long y0 = (long)xt * MST_TW, N = g.N;
+    const int b0 = ig * BI, nb = min(BI, g.B - b0);
+    u64 *dst = stage + (long)s * SEG * TW;
+    const long y0 = (long)xt * TW, N = g.N;
     // the stage's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mst_expect_tx(&bar[s], (u32)((nb + 2 * G) * MST_TW * 8));
+    mst_expect_tx(&bar[s], (u32)((nb + 2 * G) * TW * 8));
     const long dstride = (long)g.rows * N;
     for (int b = 0; b < nb; b++)
-        mst_bulk(dst + b * MST_TW, digits + ((long)(b0 + b) * g.ndig + d) * dstride + (long)r * N + y0, MST_TW * 8,
-                 &bar[s]);
+        mst_bulk(dst + b * TW, digits + ((long)(b0 + b) * g.ndig + d) * dstride + (long)r * N + y0, TW * 8, &bar[s]);
     const long kd = 2L * g.nprimes * N, kk = (long)g.nprimes * N;
 #pragma unroll
     for (int k = 0; k < G; k++) {
         const u64 *kp = mk.key[k] + (long)d * kd + (long)kr * N + y0;
-        mst_bulk(dst + (MST_BI + 2 * k) * MST_TW, kp, MST_TW * 8, &bar[s]);
-        mst_bulk(dst + (MST_BI + 2 * k + 1) * MST_TW, kp + kk, MST_TW * 8, &bar[s]);
+        mst_bulk(dst + (BI + 2 * k) * TW, kp, TW * 8, &bar[s]);
+        mst_bulk(dst + (BI + 2 * k + 1) * TW, kp + kk, TW * 8, &bar[s]);
     }
     return true;
 }
@@ -149,12 +152,12 @@ struct MstAcc<G, false> {
 // One tile: its ndig stages (waiting, accumulating, releasing each buffer
 // and refilling it S stages ahead), then the epilogue.  Returns false when
 // a wait ran out (the caller drains).  jj counts this CTA's stages.
-template <int G, int S, bool W96>
+template <int G, int S, int TW, int BI, bool W96>
 __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digits, const MstGeom &geo, u64 *stage,
                                          u64 *bar, volatile int &abort_flag, int *err, long &jj, int r, int y,
                                          int b0, const ModQ &m, const u64 *c0, long c0s, const ShoupPair *Pmod) {
-    constexpr int SEG = MST_BI + 2 * G;
-    const int tid = threadIdx.x, c = tid % MST_TW, ip = tid / MST_TW;
+    constexpr int SEG = BI + 2 * G;
+    const int tid = threadIdx.x, c = tid % TW, ip = tid / TW;
     MstAcc<G, W96> acc;
     acc.zero();
     for (int d = 0; d < geo.ndig; d++, jj++) {
@@ -163,11 +166,11 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digi
             abort_flag = 1;
             atomicExch(err, 1);
         } else {
-            const u64 *sg = stage + (long)s * SEG * MST_TW;
+            const u64 *sg = stage + (long)s * SEG * TW;
             u64 kv[2 * G];
 #pragma unroll
-            for (int k = 0; k < 2 * G; k++) kv[k] = sg[(MST_BI + k) * MST_TW + c];
-            const u64 v0 = sg[(2 * ip) * MST_TW + c], v1 = sg[(2 * ip + 1) * MST_TW + c];
+            for (int k = 0; k < 2 * G; k++) kv[k] = sg[(BI + k) * TW + c];
+            const u64 v0 = sg[(2 * ip) * TW + c], v1 = sg[(2 * ip + 1) * TW + c];
 #pragma unroll
             for (int k = 0; k < 2 * G; k++) {
                 acc.mac(0, k, v0, kv[k]);
@@ -176,7 +179,7 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digi
         }
         __syncthreads();
         if (abort_flag) return false;
-        if (tid == 0) mst_issue<G, S>(geo, mk, digits, stage, bar, jj + S);
+        if (tid == 0) mst_issue<G, S, TW, BI>(geo, mk, digits, stage, bar, jj + S);
     }
     // epilogue: one Montgomery reduction per output word, P c0 on the Q rows
     // of polynomial 0, store at the permuted position
@@ -203,7 +206,7 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digi
     return true;
 }
 
-template <int G, int S>
+template <int G, int S, int TW, int BI>
 __global__ void __launch_bounds__(MST_THREADS, G <= 4 ? 2 : 1)
     k_multsum_tma(MultiKeys<G> mk, const u64 *digits, MstGeom geo, const ModQ *mods, const u64 *c0, long c0s,
                   const ShoupPair *Pmod, int *err) {
@@ -218,23 +221,23 @@ __global__ void __launch_bounds__(MST_THREADS, G <= 4 ? 2 : 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    const int c = tid % MST_TW, ip = tid / MST_TW;   // coefficient; item pair
+    const int c = tid % TW, ip = tid / TW;   // coefficient; item pair
     long jj = 0;
     if (tid == 0)
-        for (int k = 0; k < S; k++) mst_issue<G, S>(geo, mk, digits, mst_stage, bar, k);
+        for (int k = 0; k < S; k++) mst_issue<G, S, TW, BI>(geo, mk, digits, mst_stage, bar, k);
     for (long ti = 0;; ti++) {
         const long t = (long)blockIdx.x + ti * (long)gridDim.x;
         if (t >= geo.ntiles) break;
         int ig, xt, r;
         geo.tile(t, ig, xt, r);
         const ModQ m = mods[geo.prime_of_row(r)];
-        const int y = xt * MST_TW + c, b0 = ig * MST_BI + 2 * ip;
+        const int y = xt * TW + c, b0 = ig * BI + 2 * ip;
         // 96-bit accumulation on the rows below 2^42 (uniform over the tile)
         const bool ok = m.q < (1ull << 42)
-                            ? mst_tile<G, S, true>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r, y, b0, m,
-                                                   c0, c0s, Pmod)
-                            : mst_tile<G, S, false>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r, y, b0,
-                                                    m, c0, c0s, Pmod);
+                            ? mst_tile<G, S, TW, BI, true>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r, y,
+                                                           b0, m, c0, c0s, Pmod)
+                            : mst_tile<G, S, TW, BI, false>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r,
+                                                            y, b0, m, c0, c0s, Pmod);
         if (!ok) {
             // a stage timed out: wait (bounded) for every copy this CTA
             // still has in flight before its shared memory is given back

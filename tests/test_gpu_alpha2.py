@@ -19,8 +19,8 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-4
 LOGN, QBITS, PBITS = 14, [60] + [40] * 12, [60, 60]
 # MultSum launch variants: -1 the tuner's pick, 0 the thread-per-word
-# kernel, 8 and 9 the bulk-copy kernel with 4 and 6 stages in flight
-VARIANTS = (-1, 0, 8, 9)
+# kernel, 8, 9, 10 the bulk-copy kernel with three tile shapes
+VARIANTS = (-1, 0, 8, 9, 10)
 
 
 def res(ct):
