@@ -128,8 +128,9 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * measurement.  0..7: one thread per (item, coefficient, row), digit and key
  * words loaded by the threads (bits 0-1: 8/4/2/1 items per CTA, bit 2:
  * streaming digit loads); 8, 9, 10: persistent CTAs fed by bulk
- * asynchronous global->shared copies of digit and key segments, 4 stages in
- * flight, tiles of 64 coefficients x 8 items, 128 x 4 and 256 x 2.
+ * asynchronous global->shared copies of digit and key segments issued by a
+ * producer warp, tiles of 64 coefficients x 8 items (8 stages), 128 x 4 (6)
+ * and 256 x 2 (4).
  * Errors: HE_ERR_ARG outside -1..10. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 

@@ -673,12 +673,12 @@ void launch_permute_key(Ctx *c, u64 *out, const u64 *in, long rows, uint32_t g, 
 #include "multsum_tma.cuh"
 
 // Launch of the bulk-copy MultSum, persistent: as many CTAs as fit on the
-// GPU at once.  Variants: 8: 64-coefficient segments of 8 items, 9: 128 of
-// 4, 10: 256 of 2 (4 stages in flight each).
+// GPU at once.  Variants: 8: 64-coefficient segments of 8 items, 8 stages;
+// 9: 128 of 4, 6 stages; 10: 256 of 2, 4 stages.
 template <int G, int S, int TW, int BI>
 static void multsum_tma_launch(Ctx *c, const MultiKeys<G> &mk, const u64 *digits, int B, int level, const u64 *c0,
                                long c0s, cudaStream_t st) {
-    static_assert(TW * BI == 2 * MST_THREADS, "two items per thread");
+    static_assert(TW * BI == 2 * MST_CONSUMERS, "two items per consumer thread");
     static int occ[64];   // resident CTAs per SM, per device
     const size_t smem = (size_t)S * (BI + 2 * G) * TW * 8;
     const int dev = c->device & 63;
@@ -722,8 +722,8 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         mk.ginv[k] = inv & (M - 1);
     }
     if (v >= 8) {
-        if (v == 8) multsum_tma_launch<G, 4, 64, 8>(c, mk, digits, B, level, c0, c0s, st);
-        else if (v == 9) multsum_tma_launch<G, 4, 128, 4>(c, mk, digits, B, level, c0, c0s, st);
+        if (v == 8) multsum_tma_launch<G, 8, 64, 8>(c, mk, digits, B, level, c0, c0s, st);
+        else if (v == 9) multsum_tma_launch<G, 6, 128, 4>(c, mk, digits, B, level, c0, c0s, st);
         else multsum_tma_launch<G, 4, 256, 2>(c, mk, digits, B, level, c0, c0s, st);
         c->n_launch++;
         return;

@@ -9,30 +9,42 @@
 // words of those items plus the digit-d words of the G keys (2 polynomials
 // each).  One thread issues every segment of a stage as a `cp.async.bulk`
 // global->shared copy (contiguous TW words) that completes on the stage's
-// mbarrier; S stages are in flight while the 256 threads multiply-accumulate
-// the oldest, so the copies run back to back across digits and tiles and no
-// register holds a load in flight.  Each thread owns one coefficient of two
-// items and the 2G accumulators of each: the key words it reads from shared
-// memory serve both items, the digit words all G keys.
+// "full" mbarrier.  The copies are issued by a producer warp of its own,
+// which refills a buffer as soon as the eight consumer warps have released
+// it on the buffer's "empty" mbarrier, so S stages stay in flight while the
+// consumers multiply-accumulate the oldest: the copies run back to back
+// across digits and tiles, no register holds a load in flight and no
+// CTA-wide barrier is taken in the loop.  Each consumer thread owns one
+// coefficient of two items and the 2G accumulators of each: the key words
+// it reads from shared memory serve both items, the digit words all G keys.
 //
 // Segments of 8 TW bytes: the copy engine's cost per request, not the bytes,
 // limits small segments, so wider tiles with fewer items (keys then come
 // from L2 for the other item groups of a tile) are launch variants.
 //
-// Waits are bounded: a stage that does not complete within the iteration
-// limit sets *err (a flag the host checks after synchronising) and the CTA
-// stops, after a bounded wait for the copies it still has in flight.
+// Waits are bounded: a wait that does not complete within the iteration
+// limit sets *err (a flag the host checks after synchronising) and a shared
+// stop flag; every thread then leaves its loop, and the producer waits (again
+// bounded) for the copies it still has in flight before the CTA exits.
 #pragma once
 
 // A tile is TW coefficients (segments of 8 TW bytes) of BI items; 256
-// threads, each with one coefficient of two items: TW * BI = 512.
-constexpr int MST_THREADS = 256;
+// consumer threads, each with one coefficient of two items (TW * BI = 512),
+// and one producer warp.
+constexpr int MST_CONSUMERS = 256;
+constexpr int MST_THREADS = MST_CONSUMERS + 32;
 constexpr int MST_WAIT_LIMIT = 1 << 22;
 
 __device__ __forceinline__ u32 mst_smem(const void *p) { return (u32)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mst_bar_init(u64 *bar, u32 count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mst_smem(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mst_arrive(u64 *bar) {
+    u64 state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(mst_smem(bar)) : "memory");
+    (void)state;
 }
 
 __device__ __forceinline__ void mst_expect_tx(u64 *bar, u32 bytes) {
@@ -89,7 +101,7 @@ struct MstGeom {
 // the CTA, digit jj % ndig) into buffer jj % S; false past the last tile.
 template <int G, int S, int TW, int BI>
 __device__ __forceinline__ bool mst_issue(const MstGeom &g, const MultiKeys<G> &mk, const u64 *digits, u64 *stage,
-                                          u64 *bar, long jj) {
+                                          u64 *full, long jj) {
     constexpr int SEG = BI + 2 * G;
     const long ti = jj / g.ndig;
     const int d = (int)(jj - ti * g.ndig);
@@ -104,6 +116,7 @@ __device__ __forceinline__ bool mst_issue(const MstGeom &g, const MultiKeys<G> &
     const long y0 = (long)xt * TW, N = g.N;
     // the stage's previous contents were read through the generic proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    u64 *bar = full;
     mst_expect_tx(&bar[s], (u32)((nb + 2 * G) * TW * 8));
     const long dstride = (long)g.rows * N;
     for (int b = 0; b < nb; b++)
@@ -149,37 +162,38 @@ struct MstAcc<G, false> {
     __device__ __forceinline__ u64 out(int i, int k, const ModQ &m) const { return redc(w[i][k].lo, w[i][k].hi, m); }
 };
 
-// One tile: its ndig stages (waiting, accumulating, releasing each buffer
-// and refilling it S stages ahead), then the epilogue.  Returns false when
-// a wait ran out (the caller drains).  jj counts this CTA's stages.
+// One tile on a consumer thread: its ndig stages (wait until the buffer is
+// full, accumulate, release it to the producer), then the epilogue.
+// Returns false when a wait ran out or another thread stopped the CTA.
 template <int G, int S, int TW, int BI, bool W96>
-__device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digits, const MstGeom &geo, u64 *stage,
-                                         u64 *bar, volatile int &abort_flag, int *err, long &jj, int r, int y,
-                                         int b0, const ModQ &m, const u64 *c0, long c0s, const ShoupPair *Pmod) {
+__device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const MstGeom &geo, const u64 *stage, u64 *full,
+                                         u64 *empty, volatile int &stop, int *err, long &jj, int r, int y, int b0,
+                                         const ModQ &m, const u64 *c0, long c0s, const ShoupPair *Pmod) {
     constexpr int SEG = BI + 2 * G;
-    const int tid = threadIdx.x, c = tid % TW, ip = tid / TW;
+    const int tid = threadIdx.x, c = tid % TW, ip = tid / TW, lane = tid & 31;
     MstAcc<G, W96> acc;
     acc.zero();
     for (int d = 0; d < geo.ndig; d++, jj++) {
         const int s = (int)(jj % S);
-        if (!mst_wait(&bar[s], (u32)((jj / S) & 1))) {
-            abort_flag = 1;
+        if (stop) return false;
+        if (!mst_wait(&full[s], (u32)((jj / S) & 1))) {
+            stop = 1;
             atomicExch(err, 1);
-        } else {
-            const u64 *sg = stage + (long)s * SEG * TW;
-            u64 kv[2 * G];
-#pragma unroll
-            for (int k = 0; k < 2 * G; k++) kv[k] = sg[(BI + k) * TW + c];
-            const u64 v0 = sg[(2 * ip) * TW + c], v1 = sg[(2 * ip + 1) * TW + c];
-#pragma unroll
-            for (int k = 0; k < 2 * G; k++) {
-                acc.mac(0, k, v0, kv[k]);
-                acc.mac(1, k, v1, kv[k]);
-            }
+            return false;
         }
-        __syncthreads();
-        if (abort_flag) return false;
-        if (tid == 0) mst_issue<G, S, TW, BI>(geo, mk, digits, stage, bar, jj + S);
+        const u64 *sg = stage + (long)s * SEG * TW;
+        u64 kv[2 * G];
+#pragma unroll
+        for (int k = 0; k < 2 * G; k++) kv[k] = sg[(BI + k) * TW + c];
+        const u64 v0 = sg[(2 * ip) * TW + c], v1 = sg[(2 * ip + 1) * TW + c];
+        // every word of the buffer this warp needs is in registers: release it
+        __syncwarp();
+        if (lane == 0) mst_arrive(&empty[s]);
+#pragma unroll
+        for (int k = 0; k < 2 * G; k++) {
+            acc.mac(0, k, v0, kv[k]);
+            acc.mac(1, k, v1, kv[k]);
+        }
     }
     // epilogue: one Montgomery reduction per output word, P c0 on the Q rows
     // of polynomial 0, store at the permuted position
@@ -207,50 +221,60 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const u64 *digi
 }
 
 template <int G, int S, int TW, int BI>
-__global__ void __launch_bounds__(MST_THREADS, G <= 4 ? 2 : 1)
+__global__ void __launch_bounds__(MST_THREADS, 1)
     k_multsum_tma(MultiKeys<G> mk, const u64 *digits, MstGeom geo, const ModQ *mods, const u64 *c0, long c0s,
                   const ShoupPair *Pmod, int *err) {
     extern __shared__ __align__(128) u64 mst_stage[];
-    __shared__ __align__(8) u64 bar[S];
-    __shared__ volatile int abort_flag;
+    __shared__ __align__(8) u64 full[S], empty[S];
+    __shared__ volatile int stop;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        for (int s = 0; s < S; s++) mst_bar_init(&bar[s], 1);
-        abort_flag = 0;
+        for (int s = 0; s < S; s++) {
+            mst_bar_init(&full[s], 1);
+            mst_bar_init(&empty[s], MST_CONSUMERS / 32);
+        }
+        stop = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    const long per_cta = geo.ntiles > blockIdx.x ? (geo.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long nstages = per_cta * geo.ndig;
+    if (tid >= MST_CONSUMERS) {
+        // producer warp: one lane refills each buffer once the consumers
+        // have released it
+        if (tid != MST_CONSUMERS) return;
+        long jj = 0;
+        for (; jj < nstages; jj++) {
+            const int s = (int)(jj % S);
+            if (jj >= S && !mst_wait(&empty[s], (u32)(((jj / S) - 1) & 1))) {
+                stop = 1;
+                atomicExch(err, 1);
+                break;
+            }
+            if (stop) break;
+            mst_issue<G, S, TW, BI>(geo, mk, digits, mst_stage, full, jj);
+        }
+        // copies still in flight land before the CTA's shared memory is
+        // given back: wait (bounded) for every issued stage that no consumer
+        // consumed, or simply the last S of them
+        for (long k = (jj > S ? jj - S : 0); k < jj; k++) mst_wait(&full[k % S], (u32)((k / S) & 1));
+        return;
+    }
     const int c = tid % TW, ip = tid / TW;   // coefficient; item pair
     long jj = 0;
-    if (tid == 0)
-        for (int k = 0; k < S; k++) mst_issue<G, S, TW, BI>(geo, mk, digits, mst_stage, bar, k);
-    for (long ti = 0;; ti++) {
+    for (long ti = 0; ti < per_cta; ti++) {
         const long t = (long)blockIdx.x + ti * (long)gridDim.x;
-        if (t >= geo.ntiles) break;
         int ig, xt, r;
         geo.tile(t, ig, xt, r);
         const ModQ m = mods[geo.prime_of_row(r)];
         const int y = xt * TW + c, b0 = ig * BI + 2 * ip;
         // 96-bit accumulation on the rows below 2^42 (uniform over the tile)
         const bool ok = m.q < (1ull << 42)
-                            ? mst_tile<G, S, TW, BI, true>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r, y,
-                                                           b0, m, c0, c0s, Pmod)
-                            : mst_tile<G, S, TW, BI, false>(mk, digits, geo, mst_stage, bar, abort_flag, err, jj, r,
-                                                            y, b0, m, c0, c0s, Pmod);
-        if (!ok) {
-            // a stage timed out: wait (bounded) for every copy this CTA
-            // still has in flight before its shared memory is given back
-            if (tid == 0) {
-                for (int k = 0; k < S; k++) {
-                    const long jk = jj + k;
-                    const long tk = (long)blockIdx.x + (jk / geo.ndig) * (long)gridDim.x;
-                    if (tk >= geo.ntiles) break;
-                    mst_wait(&bar[jk % S], (u32)((jk / S) & 1));
-                }
-            }
-            __syncthreads();
-            return;
-        }
+                            ? mst_tile<G, S, TW, BI, true>(mk, geo, mst_stage, full, empty, stop, err, jj, r, y, b0,
+                                                           m, c0, c0s, Pmod)
+                            : mst_tile<G, S, TW, BI, false>(mk, geo, mst_stage, full, empty, stop, err, jj, r, y, b0,
+                                                            m, c0, c0s, Pmod);
+        if (!ok) return;
     }
 }
