@@ -134,6 +134,15 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * Errors: HE_ERR_ARG outside -1..10. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
+/* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without
+ * tuning (-1 returns to the tuner, which times them at the next transform).
+ * Variants compute identical words; this is for tests and measurement.
+ * 2, 3: one 8-stage tile per CTA, 2 or 3 CTAs per SM (forward and inverse);
+ * 4: forward passes on persistent CTAs whose tiles arrive through bulk
+ * asynchronous copies (a producer warp, two buffers), inverse as 3.
+ * Errors: HE_ERR_ARG for other values. */
+int he_ctx_set_ntt_variant(he_ctx *ctx, int variant);
+
 /* Newton composition for the PowerMethod's inverse square root (Sec. 7: two
  * InvSRT iterations composited into one that spends one level less).  With
  * on != 0, he_power_method / he_pca / PCA jobs on this context run each pair

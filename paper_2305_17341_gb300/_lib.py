@@ -87,6 +87,7 @@ SIGNATURES = {
     "he_ctx_primes": [vp, u64p, u64p],
     "he_ctx_set_autotune": [vp, ip],
     "he_ctx_set_multsum_variant": [vp, ip],
+    "he_ctx_set_ntt_variant": [vp, ip],
     "he_ctx_set_newton_composition": [vp, ip],
     "he_ctx_set_packed_refresh": [vp, ip],
     "he_autotune_log": [vp, ctypes.c_char_p, ip, P(ip)],
@@ -210,6 +211,11 @@ def he_ctx_set_autotune(ctx, on=True):
 def he_ctx_set_multsum_variant(ctx, variant=-1):
     """Pins every MultSum launch to one variant (-1: tuner / defaults)."""
     check(lib().he_ctx_set_multsum_variant(ctx, int(variant)))
+
+
+def he_ctx_set_ntt_variant(ctx, variant=-1):
+    """Pins the NTT passes to one variant (-1: tuner)."""
+    check(lib().he_ctx_set_ntt_variant(ctx, int(variant)))
 
 
 def he_ctx_set_newton_composition(ctx, on=True):

@@ -271,6 +271,22 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
     return HE_OK;
 }
 
+int he_ctx_set_ntt_variant(he_ctx *ctx, int variant) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    if (variant != -1 && (variant < 2 || variant > 4)) return fail(HE_ERR_ARG, "NTT variant -1, 2, 3 or 4");
+    Ctx &c = ctx->c;
+    cudaStreamSynchronize(c.stream);
+    if (variant < 0) {
+        c.ntt_tuned = false;   // the tuner picks again at the next transform
+        c.ntt_minb = c.ntt_minb_inv = 2;
+    } else {
+        c.ntt_tuned = true;
+        c.ntt_minb = variant;
+        c.ntt_minb_inv = variant == 4 ? 3 : variant;
+    }
+    return HE_OK;
+}
+
 int he_ctx_set_newton_composition(he_ctx *ctx, int on) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
     ctx->c.newton_compose = on != 0;

@@ -9,6 +9,7 @@
 #include <set>
 #include <stdexcept>
 
+#include "bulkcopy.cuh"
 #include "he_internal.h"
 
 namespace he {

@@ -27,63 +27,13 @@
 // stop flag; every thread then leaves its loop, and the producer waits (again
 // bounded) for the copies it still has in flight before the CTA exits.
 #pragma once
+// (bulkcopy.cuh is included by the including file, outside its namespace)
 
 // A tile is TW coefficients (segments of 8 TW bytes) of BI items; 256
 // consumer threads, each with one coefficient of two items (TW * BI = 512),
 // and one producer warp.
 constexpr int MST_CONSUMERS = 256;
 constexpr int MST_THREADS = MST_CONSUMERS + 32;
-constexpr int MST_WAIT_LIMIT = 1 << 22;
-
-__device__ __forceinline__ u32 mst_smem(const void *p) { return (u32)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mst_bar_init(u64 *bar, u32 count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mst_smem(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mst_arrive(u64 *bar) {
-    u64 state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(mst_smem(bar)) : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ void mst_expect_tx(u64 *bar, u32 bytes) {
-    u64 state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(mst_smem(bar)), "r"(bytes)
-                 : "memory");
-    (void)state;
-}
-
-__device__ __forceinline__ bool mst_try_wait(u64 *bar, u32 parity) {
-    u32 ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(mst_smem(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of `parity` to complete.
-__device__ __forceinline__ bool mst_wait(u64 *bar, u32 parity) {
-    for (int it = 0; it < MST_WAIT_LIMIT; it++)
-        if (mst_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// bytes (a multiple of 16) from global src to shared dst (both 16-byte
-// aligned), completing on bar's transaction count.
-__device__ __forceinline__ void mst_bulk(void *dst, const void *src, u32 bytes, u64 *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            mst_smem(dst)),
-        "l"(src), "r"(bytes), "r"(mst_smem(bar))
-        : "memory");
-}
 
 struct MstGeom {
     int N, logN, rows, level, L, ndig, nprimes, ntx, nig, B;   // ntx = N / TW, nig = ceil(B / BI)
@@ -114,19 +64,20 @@ __device__ __forceinline__ bool mst_issue(const MstGeom &g, const MultiKeys<G> &
     const int b0 = ig * BI, nb = min(BI, g.B - b0);
     u64 *dst = stage + (long)s * SEG * TW;
     const long y0 = (long)xt * TW, N = g.N;
-    // the stage's previous contents were read through the generic proxy
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // the buffer's previous contents were read by the consumers before they
+    // arrived on its "empty" barrier, which the producer waited on: that
+    // ordering covers the copy engine's writes (no proxy fence per stage)
     u64 *bar = full;
-    mst_expect_tx(&bar[s], (u32)((nb + 2 * G) * TW * 8));
+    bc_expect_tx(&bar[s], (u32)((nb + 2 * G) * TW * 8));
     const long dstride = (long)g.rows * N;
     for (int b = 0; b < nb; b++)
-        mst_bulk(dst + b * TW, digits + ((long)(b0 + b) * g.ndig + d) * dstride + (long)r * N + y0, TW * 8, &bar[s]);
+        bc_bulk(dst + b * TW, digits + ((long)(b0 + b) * g.ndig + d) * dstride + (long)r * N + y0, TW * 8, &bar[s]);
     const long kd = 2L * g.nprimes * N, kk = (long)g.nprimes * N;
 #pragma unroll
     for (int k = 0; k < G; k++) {
         const u64 *kp = mk.key[k] + (long)d * kd + (long)kr * N + y0;
-        mst_bulk(dst + (BI + 2 * k) * TW, kp, TW * 8, &bar[s]);
-        mst_bulk(dst + (BI + 2 * k + 1) * TW, kp + kk, TW * 8, &bar[s]);
+        bc_bulk(dst + (BI + 2 * k) * TW, kp, TW * 8, &bar[s]);
+        bc_bulk(dst + (BI + 2 * k + 1) * TW, kp + kk, TW * 8, &bar[s]);
     }
     return true;
 }
@@ -176,7 +127,7 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const MstGeom &
     for (int d = 0; d < geo.ndig; d++, jj++) {
         const int s = (int)(jj % S);
         if (stop) return false;
-        if (!mst_wait(&full[s], (u32)((jj / S) & 1))) {
+        if (!bc_wait(&full[s], (u32)((jj / S) & 1))) {
             stop = 1;
             atomicExch(err, 1);
             return false;
@@ -188,7 +139,7 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const MstGeom &
         const u64 v0 = sg[(2 * ip) * TW + c], v1 = sg[(2 * ip + 1) * TW + c];
         // every word of the buffer this warp needs is in registers: release it
         __syncwarp();
-        if (lane == 0) mst_arrive(&empty[s]);
+        if (lane == 0) bc_arrive(&empty[s]);
 #pragma unroll
         for (int k = 0; k < 2 * G; k++) {
             acc.mac(0, k, v0, kv[k]);
@@ -230,12 +181,11 @@ __global__ void __launch_bounds__(MST_THREADS, 1)
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int s = 0; s < S; s++) {
-            mst_bar_init(&full[s], 1);
-            mst_bar_init(&empty[s], MST_CONSUMERS / 32);
+            bc_bar_init(&full[s], 1);
+            bc_bar_init(&empty[s], MST_CONSUMERS / 32);
         }
         stop = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bc_init_fence();
     }
     __syncthreads();
     const long per_cta = geo.ntiles > blockIdx.x ? (geo.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -247,7 +197,7 @@ __global__ void __launch_bounds__(MST_THREADS, 1)
         long jj = 0;
         for (; jj < nstages; jj++) {
             const int s = (int)(jj % S);
-            if (jj >= S && !mst_wait(&empty[s], (u32)(((jj / S) - 1) & 1))) {
+            if (jj >= S && !bc_wait(&empty[s], (u32)(((jj / S) - 1) & 1))) {
                 stop = 1;
                 atomicExch(err, 1);
                 break;
@@ -258,7 +208,7 @@ __global__ void __launch_bounds__(MST_THREADS, 1)
         // copies still in flight land before the CTA's shared memory is
         // given back: wait (bounded) for every issued stage that no consumer
         // consumed, or simply the last S of them
-        for (long k = (jj > S ? jj - S : 0); k < jj; k++) mst_wait(&full[k % S], (u32)((k / S) & 1));
+        for (long k = (jj > S ? jj - S : 0); k < jj; k++) bc_wait(&full[k % S], (u32)((k / S) & 1));
         return;
     }
     const int c = tid % TW, ip = tid / TW;   // coefficient; item pair

@@ -19,8 +19,11 @@
 // the remaining log2(N2) stages on rows of N2 contiguous coefficients.  Both
 // passes read and write HBM once.
 #include <cstdio>
+#include <cstring>
+#include <algorithm>
 #include <stdexcept>
 
+#include "bulkcopy.cuh"
 #include "he_internal.h"
 
 namespace he {
@@ -221,9 +224,17 @@ __device__ __forceinline__ void bf_fwd_nored(u64 &x, u64 &y, u64 w, u64 wp, u64 
     y = a - t + 4 * q;
 }
 
+// Barrier of the threads that run the butterflies: the whole CTA, or the
+// 256 consumer threads (named barrier 1) of a CTA that also has a producer warp.
+template <bool CONS>
+__device__ __forceinline__ void pass_sync() {
+    if (CONS) asm volatile("bar.sync 1, 256;" ::: "memory");
+    else __syncthreads();
+}
+
 // The 8 stages of one pass (4 in registers in layout A, a shared-memory
 // transpose, 4 in layout B), leaving the result in shared memory (layout B).
-template <int LM, bool ROWS, bool RED>
+template <int LM, bool ROWS, bool RED, bool CONS = false>
 __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulonglong2 *w2_, long G, int t, int w,
                                               u64 q) {
     typedef PassGeom<LM, ROWS> G_;
@@ -241,7 +252,7 @@ __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulong
     }
 #pragma unroll
     for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = x[k];
-    __syncthreads();
+    pass_sync<CONS>();
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = sm[G_::sidx(16 * t + k, w)];
 #pragma unroll
@@ -257,7 +268,7 @@ __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulong
     }
 #pragma unroll
     for (int k = 0; k < 16; k++) sm[G_::sidx(16 * t + k, w)] = x[k];
-    __syncthreads();
+    pass_sync<CONS>();
 }
 
 template <int LM, bool ROWS, int MINB, bool SUBSC>
@@ -374,6 +385,240 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_inv_fast(u64 *data, RowMap rm
     for (int k = 0; k < 16; k++) p[(long)(t + T * k) * stride] = x[k];
 }
 
+// ------------------------------------------ persistent passes, bulk copies
+// The same passes (butterflies, stages and lazy reductions as k_ntt_fwd_fast,
+// so the same words) on persistent CTAs whose input tiles arrive through the
+// copy engine: a producer warp loads tile i + 1 (a 32 KiB contiguous run of
+// W sequences for the row pass; a W-column x M-row box of a 2-D tensor map
+// for the column pass) into one of two shared buffers while the 256 consumer
+// threads transform tile i, so the load latency that stalls the one-tile
+// CTAs is off the critical path.  Rows that a RowSkip excludes are not in the
+// tile sequence at all.  Waits are bounded (see bulkcopy.cuh); a wait that
+// runs out sets *err, and the consumers stop together after a vote taken on
+// their own barrier, so no consumer is left at a barrier.
+constexpr int NTC_CONS = 256, NTC_THREADS = NTC_CONS + 32, NTC_STAGES = 2, NTC_TILE = 4096;
+
+// The tiles of a launch: every transformed row, in order, tpr tiles each.
+struct NttTiles {
+    long rows = 0;   // rows transformed (those a RowSkip keeps)
+    int tpr = 0;     // tiles per row
+    RowSkip sk;      // rows_per_digit == 0: no row is skipped
+    // Absolute row (within the launch) of the ridx-th transformed row: in
+    // Decompose output [item][digit][rows_per_digit], digit d skips its own
+    // rows [d alpha, min(d alpha + alpha, nq)).
+    __device__ __forceinline__ long row_of(long ridx) const {
+        if (!sk.rows_per_digit) return ridx;
+        const int rpd = sk.rows_per_digit, nd = sk.ndig, a = sk.alpha;
+        const long per_item = (long)nd * rpd - sk.nq;
+        const long item = ridx / per_item;
+        const long rem = ridx - item * per_item, first = (long)(nd - 1) * (rpd - a);
+        int d;
+        long j;
+        if (rem < first) {
+            d = (int)(rem / (rpd - a));
+            j = rem - (long)d * (rpd - a);
+        } else {
+            d = nd - 1;
+            j = rem - first;
+        }
+        const int i0 = d * a, kd = d < nd - 1 ? a : sk.nq - i0;
+        return (item * nd + d) * rpd + (j < i0 ? j : j + kd);
+    }
+};
+
+template <int LM, bool ROWS, bool SUBSC>
+__global__ void __launch_bounds__(NTC_THREADS, 2)
+    k_ntt_fwd_tma(u64 *data, const __grid_constant__ CUtensorMap tmap, RowMap rm, const ModQ *mods,
+                  const ulonglong2 *tw2, int logN, NttTiles tl, SubScale ep, int *err) {
+    typedef PassGeom<LM, ROWS> G_;
+    constexpr int M = G_::M, T = G_::T, W = G_::W;
+    static_assert(W * M == NTC_TILE, "a tile is 4096 words");
+    extern __shared__ __align__(128) u64 ntc_dyn[];
+    u64 *stage = ntc_dyn;                       // [NTC_STAGES][NTC_TILE], dense
+    u64 *sm = ntc_dyn + NTC_STAGES * NTC_TILE;  // transpose scratch, G_::SM words
+    __shared__ __align__(8) u64 full[NTC_STAGES], empty[NTC_STAGES];
+    __shared__ volatile int stop, cons_fail;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < NTC_STAGES; s++) {
+            bc_bar_init(&full[s], 1);
+            bc_bar_init(&empty[s], NTC_CONS / 32);
+        }
+        stop = 0;
+        cons_fail = 0;
+        bc_init_fence();
+    }
+    __syncthreads();
+    const int N = 1 << logN;
+    const long ntiles = tl.rows * tl.tpr;
+    const long per_cta = ntiles > (long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (tid >= NTC_CONS) {
+        // producer warp: one lane loads each tile once its buffer is free
+        if (tid != NTC_CONS) return;
+        long jj = 0;
+        for (; jj < per_cta; jj++) {
+            const int s = (int)(jj % NTC_STAGES);
+            if (jj >= NTC_STAGES && !bc_wait(&empty[s], (u32)(((jj / NTC_STAGES) - 1) & 1))) {
+                stop = 1;
+                atomicExch(err, 1);
+                break;
+            }
+            if (stop) break;
+            const long u = (long)blockIdx.x + jj * (long)gridDim.x;
+            const long row = tl.row_of(u / tl.tpr);
+            const int tr = (int)(u % tl.tpr);
+            u64 *dst = stage + (long)s * NTC_TILE;
+            bc_expect_tx(&full[s], NTC_TILE * 8);
+            if (ROWS) {
+                const u64 *src = data + row * (long)N + (long)tr * NTC_TILE;
+#pragma unroll
+                for (int k = 0; k < 4; k++) bc_bulk(dst + k * 1024, src + k * 1024, 8192, &full[s]);
+            } else {
+                bc_tensor2d(dst, &tmap, tr * W, (int)(row * M), &full[s]);
+            }
+        }
+        // copies still in flight land before the CTA's shared memory goes
+        for (long k = (jj > NTC_STAGES ? jj - NTC_STAGES : 0); k < jj; k++)
+            bc_wait(&full[k % NTC_STAGES], (u32)((k / NTC_STAGES) & 1));
+        return;
+    }
+    int t, w;
+    if (ROWS) {
+        w = tid / T;
+        t = tid % T;
+    } else {
+        t = tid / W;
+        w = tid % W;
+    }
+    const long stride = ROWS ? 1 : (N >> LM);
+    for (long jj = 0; jj < per_cta; jj++) {
+        const int s = (int)(jj % NTC_STAGES);
+        if (!bc_wait(&full[s], (u32)((jj / NTC_STAGES) & 1))) {
+            cons_fail = 1;
+            atomicExch(err, 1);
+        }
+        if (stop) cons_fail = 1;
+        // every consumer reads the vote after the barrier: a uniform exit
+        pass_sync<true>();
+        if (cons_fail) return;
+        const long u = (long)blockIdx.x + jj * (long)gridDim.x;
+        const long row = tl.row_of(u / tl.tpr);
+        const int tr = (int)(u % tl.tpr);
+        const u64 *sg = stage + (long)s * NTC_TILE;
+        u64 x[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) x[k] = ROWS ? sg[w * M + t + T * k] : sg[(t + T * k) * W + w];
+        __syncwarp();
+        if ((tid & 31) == 0) bc_arrive(&empty[s]);
+        const int pidx = rm.at(row);
+        const u64 q = mods[pidx].q;
+        const ulonglong2 *w2_ = tw2 + (long)pidx * N;
+        const long seq = (long)tr * W + w;
+        u64 *p = data + row * (long)N + (ROWS ? seq * M : seq);
+        const long G = ROWS ? ((long)(N >> LM) + seq) : 1;
+        const bool red = q >= (1ull << 57);   // uniform over the CTA
+        if (red) fwd_pass_body<LM, ROWS, true, true>(x, sm, w2_, G, t, w, q);
+        else fwd_pass_body<LM, ROWS, false, true>(x, sm, w2_, G, t, w, q);
+        const u64 wone = mods[pidx].wone;
+        if (ROWS && SUBSC) {
+            const long arow = ep.row0 + row;
+            const long it = arow / ep.rows_per_item;
+            const int r = (int)(arow - it * ep.rows_per_item);
+            const ShoupPair wr = ep.w[r];
+            const long off = (long)r * N + seq * M;
+            const u64 *up = ep.u + it * ep.us + off;
+            u64 *op = ep.out + it * ep.os + off;
+            const u64 *ap = ep.add ? ep.add + it * ep.as + off : nullptr;
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const u64 sv = sm[G_::sidx(t + T * k, w)];
+                const u64 v = red ? reduce4q(sv, q) : reduce_any(sv, q, wone);
+                u64 o = shoup(submod(up[t + T * k], v, q), wr.w, wr.wp, q);
+                if (ap) o = addmod(o, ap[t + T * k], q);
+                op[t + T * k] = o;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                u64 v = sm[G_::sidx(t + T * k, w)];
+                if (ROWS) v = red ? reduce4q(v, q) : reduce_any(v, q, wone);
+                p[(long)(t + T * k) * stride] = v;
+            }
+        }
+        // the scratch is rewritten by the next tile
+        pass_sync<true>();
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            throw std::runtime_error("cuTensorMapEncodeTiled is not available");
+        fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// One pass over all `nr` rows of `d` (no 65535-row split: the grid is
+// persistent).  skip: rows left out; ep: the row pass's fused epilogue.
+template <int LM, bool ROWS>
+static void fwd_pass_tma(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk,
+                         const SubScale *ep) {
+    typedef PassGeom<LM, ROWS> G_;
+    const int N = ctx->N;
+    NttTiles tl;
+    tl.sk = sk;
+    tl.sk.row0 = 0;
+    tl.tpr = (N >> LM) / G_::W;
+    tl.rows = nr;
+    if (sk.rows_per_digit) {
+        const long per_item = (long)sk.ndig * sk.rows_per_digit;
+        tl.rows = (nr / per_item) * (per_item - sk.nq);
+    }
+    if (tl.rows <= 0) return;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof map);
+    if (!ROWS) {
+        // the rows as a (N / M) x (M nr) matrix; a box is W columns x M rows
+        const cuuint64_t dims[2] = {(cuuint64_t)(N >> LM), (cuuint64_t)G_::M * (cuuint64_t)nr};
+        const cuuint64_t strides[1] = {(cuuint64_t)(N >> LM) * 8};
+        const cuuint32_t box[2] = {(cuuint32_t)G_::W, (cuuint32_t)G_::M}, es[2] = {1, 1};
+        if (encode_tiled()(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, d, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            throw std::runtime_error("tensor map encoding failed");
+    }
+    const size_t smem = ((size_t)NTC_STAGES * NTC_TILE + G_::SM) * 8;
+    const SubScale e = ep ? *ep : SubScale();
+    auto launch = [&](auto kern) {
+        static int occ[64];
+        const int dev = ctx->device & 63;
+        if (!occ[dev]) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTC_THREADS, smem);
+            occ[dev] = nb > 0 ? nb : 1;
+        }
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        const long grid = std::min<long>(tl.rows * tl.tpr, (long)nsm * occ[dev]);
+        kern<<<(unsigned)grid, NTC_THREADS, smem, st>>>(d, map, m, ctx->d_mod, (const ulonglong2 *)ctx->d_psi2,
+                                                        ctx->logN, tl, e, ctx->d_err);
+    };
+    if (ROWS && ep) launch(k_ntt_fwd_tma<LM, ROWS, true>);
+    else launch(k_ntt_fwd_tma<LM, ROWS, false>);
+}
+
 template <int LM, bool ROWS>
 static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk,
                      const SubScale *ep = nullptr) {
@@ -469,6 +714,26 @@ static void split(int logN, int &logN1, int &C, int &R) {
     if (R > N1) R = N1;
 }
 
+// Both forward passes over nr rows (at most 65535 for the one-tile CTAs;
+// any number for the persistent ones), with the variant the context picked:
+// ntt_minb 2 or 3 CTAs per SM of one-tile CTAs, 4 the persistent passes fed
+// by bulk copies.
+static void fwd_both(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk,
+                     const SubScale *ep) {
+    int logN1, C, R;
+    split(ctx->logN, logN1, C, R);
+    const bool rows8 = ctx->logN - logN1 == 8;
+    if (ctx->ntt_minb == 4) {
+        if (logN1 == 8) fwd_pass_tma<8, false>(ctx, d, nr, m, st, sk, nullptr);
+        else fwd_pass_tma<7, false>(ctx, d, nr, m, st, sk, nullptr);
+        if (rows8) fwd_pass_tma<8, true>(ctx, d, nr, m, st, sk, ep);
+        else fwd_pass_tma<7, true>(ctx, d, nr, m, st, sk, ep);
+        return;
+    }
+    if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st, sk); else fwd_pass<7, false>(ctx, d, nr, m, st, sk);
+    if (rows8) fwd_pass<8, true>(ctx, d, nr, m, st, sk, ep); else fwd_pass<7, true>(ctx, d, nr, m, st, sk, ep);
+}
+
 // Picks the register budget of the register-blocked passes (2 or 3 CTAs per
 // SM) by timing a forward and an inverse transform of 256 scratch rows with
 // each; runs once per context, outside stream capture.
@@ -496,14 +761,14 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
     for (int dir = 0; dir < 2; dir++) {
         float best = 1e30f;
         int pick = 2;
-        for (int minb : {2, 3}) {
+        for (int minb : {2, 3, 4}) {
+            if (dir == 1 && minb == 4) continue;   // 4: the forward passes fed by bulk copies
             (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = minb;
             float t = 1e30f;
             for (int rep = 0; rep < 3; rep++) {
                 cudaEventRecord(a, st);
                 if (dir == 0) {
-                    if (logN1 == 8) fwd_pass<8, false>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, false>(ctx, scratch.p, R, m, st, none);
-                    if (ctx->logN - logN1 == 8) fwd_pass<8, true>(ctx, scratch.p, R, m, st, none); else fwd_pass<7, true>(ctx, scratch.p, R, m, st, none);
+                    fwd_both(ctx, scratch.p, R, m, st, none, nullptr);
                 } else {
                     if (ctx->logN - logN1 == 8) inv_pass<8, true>(ctx, scratch.p, R, m, st); else inv_pass<7, true>(ctx, scratch.p, R, m, st);
                     if (logN1 == 8) inv_pass<8, false>(ctx, scratch.p, R, m, st); else inv_pass<7, false>(ctx, scratch.p, R, m, st);
@@ -516,8 +781,9 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
                 ctx->n_launch += 2;
             }
             char line[112];
-            snprintf(line, sizeof line, "ntt %s logN %d rows %ld ctas_per_sm %d ms %.4f\n", dir ? "inverse" : "forward",
-                     ctx->logN, R, minb, t);
+            snprintf(line, sizeof line, "ntt %s logN %d rows %ld %s %d ms %.4f\n", dir ? "inverse" : "forward",
+                     ctx->logN, R, minb == 4 ? "bulk-copy persistent, ctas_per_sm" : "ctas_per_sm", minb == 4 ? 2 : minb,
+                     t);
             ctx->tune_log += line;
             if (t < best) best = t, pick = minb;
         }
@@ -533,6 +799,23 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, 
     int logN = ctx->logN, logN1, C, R;
     split(logN, logN1, C, R);
     int N1 = 1 << logN1, N2 = 1 << (logN - logN1);
+    if (logN >= 14 && logN <= 16 && ctx->ntt_minb == 4) {
+        // persistent passes: one launch each over every row
+        RowSkip sk;
+        long done = rows;
+        if (skip) {
+            sk = *skip;
+            sk.row0 = 0;
+            const long per_item = (long)sk.ndig * sk.rows_per_digit;
+            done = (rows / per_item) * (per_item - sk.nq);
+        }
+        ctx->n_launch += 2;
+        cudaEvent_t e0;
+        ctx->trace_begin(1, e0);
+        fwd_both(ctx, data, rows, rm, st, sk, nullptr);
+        ctx->trace_end(1, e0, 2.0 * done * ctx->N * 8.0);
+        return;
+    }
     for (long r0 = 0; r0 < rows; r0 += 65535) {
         long nr = rows - r0 < 65535 ? rows - r0 : 65535;
         u64 *d = data + r0 * (long)ctx->N;
@@ -570,6 +853,15 @@ void ntt_fwd_subscale(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStre
     int logN = ctx->logN, logN1, C, R;
     split(logN, logN1, C, R);
     if (logN < 14 || logN > 16) throw std::logic_error("the fused NTT epilogue needs the register-blocked NTT");
+    if (ctx->ntt_minb == 4) {
+        ctx->n_launch += 2;
+        cudaEvent_t e0;
+        ctx->trace_begin(1, e0);
+        RowSkip none;
+        fwd_both(ctx, data, rows, rm, st, none, &ep);
+        ctx->trace_end(1, e0, 2.0 * rows * ctx->N * 8.0);
+        return;
+    }
     for (long r0 = 0; r0 < rows; r0 += 65535) {
         long nr = rows - r0 < 65535 ? rows - r0 : 65535;
         u64 *d = data + r0 * (long)ctx->N;

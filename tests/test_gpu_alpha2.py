@@ -21,6 +21,8 @@ LOGN, QBITS, PBITS = 14, [60] + [40] * 12, [60, 60]
 # MultSum launch variants: -1 the tuner's pick, 0 the thread-per-word
 # kernel, 8, 9, 10 the bulk-copy kernel with three tile shapes
 VARIANTS = (-1, 0, 8, 9, 10)
+# NTT variants: one-tile CTAs (2 or 3 per SM), persistent bulk-copy passes
+NTT_VARIANTS = (2, 3, 4)
 
 
 def res(ct):
@@ -80,7 +82,8 @@ def test_alpha2_primes_and_key_switch_shape(a2):
 def test_alpha2_product_bit_exact_every_multsum_variant(a2, sched):
     """16 x 16 product at level 12 (digits {q0,q1} .. {q12}): residues and
     MultSum / Decompose / ModDown counts equal the oracle's under every
-    MultSum launch variant; the product decrypts to A.B."""
+    MultSum launch variant and every NTT variant; the product decrypts to
+    A.B."""
     from oracle.hmm import HMM
     pk, ctx, P, he, n, n1 = a2
     kw = {"dmatrixmult": {}, "relin_once": {"relin_once": True}, "dcd8": {"dcd_z": 8, "dcd_t": 8}}[sched]
@@ -89,20 +92,23 @@ def test_alpha2_product_bit_exact_every_multsum_variant(a2, sched):
     oc = HMM(he).hmatmul(oa, ob, n, n1, n1, **kw)
     want = res(oc)
     try:
-        for v in VARIANTS:
+        for v, nv in [(v, -1) for v in VARIANTS] + [(-1, nv) for nv in NTT_VARIANTS]:
             pk.he_ctx_set_multsum_variant(ctx, v)
+            pk.he_ctx_set_ntt_variant(ctx, nv)
             pk.he_counters(ctx, reset=True)
             gc = pk.he_hmatmul(ctx, ga, gb, n, n1, n1, **kw)
             cnt = pk.he_counters(ctx)
             assert (cnt["MS"], cnt["Dp"], cnt["MD"]) == (he.cnt.MS, he.cnt.Dp, he.cnt.MD), v
             got = pk.he_ct_export(ctx, gc)
-            assert np.array_equal(got, want), "variant %d: %d of %d words differ" % (v, (got != want).sum(), got.size)
+            assert np.array_equal(got, want), "variants %d/%d: %d of %d words differ" % (
+                v, nv, (got != want).sum(), got.size)
             lv, sc, per = pk.he_ct_info(gc)
             assert (lv, per) == (oc.level, n * n) and sc == oc.scale
             assert np.abs(pk.he_decrypt_matrix(ctx, gc, n, n) - A @ B).max() < TOL
             pk.he_ct_free(gc)
     finally:
         pk.he_ctx_set_multsum_variant(ctx, -1)
+        pk.he_ctx_set_ntt_variant(ctx, -1)
     for h in (ga, gb):
         pk.he_ct_free(h)
 

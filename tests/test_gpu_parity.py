@@ -445,3 +445,35 @@ def test_hmatmul_degenerate_schedules_bit_exact(c1, n, n1z, n1t):
     assert np.abs(lib.he_decrypt_matrix(ctx, gc, n, n) - A @ B).max() < TOL
     for h in (ga, gb, gc):
         lib.he_ct_free(h)
+
+
+@pytest.mark.parametrize("logN", [14, 15, 16])
+def test_ntt_variants_compute_the_same_words(lib, logN):
+    """Every NTT variant (one-tile CTAs at 2 or 3 per SM; persistent passes
+    fed by bulk copies: row tiles as contiguous copies, column tiles as 2-D
+    tensor-map boxes) gives the same forward words on a ragged number of
+    rows cycling through q_0..q_L, p_0, p_1 (the 60-bit rows take the
+    reducing butterflies), and the inverse returns the input."""
+    import torch
+    ctx = lib.he_ctx_create(lib.make_params(logN, [60] + [40] * 6, [60, 60]), 6)
+    try:
+        q, p = lib.he_ctx_primes(ctx)
+        primes = list(q) + list(p)
+        N, R, level = 1 << logN, 37, 6
+        rng = np.random.default_rng(logN + 100)
+        a = np.stack([rng.integers(0, primes[r % len(primes)], N, dtype=np.uint64) for r in range(R)])
+        outs = {}
+        for v in (2, 3, 4):
+            lib.he_ctx_set_ntt_variant(ctx, v)
+            d = torch.from_numpy(a.view(np.int64).copy()).cuda()
+            torch.cuda.synchronize()
+            lib.he_ntt(ctx, d.data_ptr(), R, level)
+            outs[v] = d.cpu().numpy().view(np.uint64).copy()
+            lib.he_ntt(ctx, d.data_ptr(), R, level, inverse=True)
+            assert np.array_equal(d.cpu().numpy().view(np.uint64), a), v
+        assert np.array_equal(outs[2], outs[3]) and np.array_equal(outs[2], outs[4])
+        for r in range(R):
+            assert int(outs[4][r].max()) < primes[r % len(primes)]
+    finally:
+        lib.he_ctx_set_ntt_variant(ctx, -1)
+        lib.he_ctx_destroy(ctx)
