@@ -163,9 +163,70 @@ def oracle_sample(ops_per_step=1, ops=None):
     return 1.0 / per, time.time() - t_all, threads, {k: statistics.mean(v) for k, v in t.items()}
 
 
+def oracle_full_product(logN, qbits, pbits, n, n1, sample_level):
+    """The oracle on one whole encrypted n x n product (key generation
+    excluded) next to the per-op extrapolation that cpu_baseline uses, at the
+    same parameters: Decompose, MultSum and ModDown timed once each at
+    `sample_level` and scaled by the product's own operation counts.  Returns
+    a dict with both times and their ratio."""
+    import numpy as np
+
+    from oracle.ckks import CKKS, Params
+    from oracle.hmm import HMM, matmul_rot_steps
+    P = Params(logN, qbits, pbits)
+    he = CKKS(P, 77)
+    t0 = time.time()
+    steps = matmul_rot_steps(n, n1, n1, P.S)
+    for s in steps:
+        he.gen_rotation_key(s)
+    he.gen_relin_key()
+    keygen = time.time() - t0
+    rng = np.random.default_rng(2)
+    z = [np.zeros(P.S), np.zeros(P.S)]
+    for zz in z:
+        zz[: n * n] = rng.uniform(-1, 1, n * n)
+    a, b = he.encrypt_slots(z[0], P.L, obj=2), he.encrypt_slots(z[1], P.L, obj=3)
+    he.cnt.reset()
+    t0 = time.time()
+    HMM(he).hmatmul(a, b, n, n1, n1)
+    full = time.time() - t0
+    cnt = {"MS": he.cnt.MS, "Dp": he.cnt.Dp, "MD": he.cnt.MD}
+    ct = he.drop(a, sample_level)
+    t0 = time.time()
+    dg = he.modup(ct.c1, sample_level)
+    t1 = time.time()
+    u0, u1 = he.multsum(dg, he.rtk[P.galois(steps[0])], sample_level)
+    t2 = time.time()
+    he.moddown2(u0, u1, sample_level)
+    t3 = time.time()
+    per = {"Dp": t1 - t0, "MS": t2 - t1, "MD": t3 - t2}
+    extra = sum(cnt[k] * per[k] for k in cnt)
+    return {"workload": "%dx%d product, N=2^%d, %d q + %d p primes, level %d" % (n, n, logN, len(qbits), len(pbits),
+                                                                             P.L),
+            "measured_s": full, "extrapolated_s": extra, "ratio_measured_over_extrapolated": full / extra,
+            "keygen_s": keygen, "counts": cnt, "per_op_s": per}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
+        return
+    if args.oracle_full:
+        # the oracle on one whole 128x128 product at the bench's parameters
+        # (minutes on the host cores), with the extrapolation beside it
+        chk = oracle_full_product(16, [60] + [40] * 20, [60, 60], N_MAT, 16, 19)
+        threads = env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
+        value = 1.0 / chk["measured_s"]
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1,
+                "warmup": 0, "ms_per_step": 1000 * chk["measured_s"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "one 128x128 encrypted matmul, N=2^16, q 60+20x40, p 2x60, level 20 "
+                                       "(whole product, not extrapolated)"},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                 "sample": "one whole product"},
+                "extrapolation_check": chk,
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     vals = []
     for _ in range(args.warmup):
@@ -177,7 +238,8 @@ def run_reference(args, rank, world):
     dt = time.time() - t0
     value = statistics.mean(vals)
     sample = ("per step: oracle Decompose + MultSum + ModDown once each at logN 16, level 19 (23 primes), "
-              "scaled by the product's counts MS 564, Dp 178, MD 423")
+              "scaled by the product's counts MS 564, Dp 178, MD 423 (an extrapolation: --oracle-full times one "
+              "whole product)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -207,6 +269,8 @@ def run_ours(args, rank, world, dist):
     ctx = pk.he_ctx_create(pk.he_params_default(args.preset), 1000 + rank)
     if args.ms_variant is not None:
         pk.he_ctx_set_multsum_variant(ctx, args.ms_variant)
+    if args.ntt_variant is not None:
+        pk.he_ctx_set_ntt_variant(ctx, args.ntt_variant)
     # the library launches on this stream; every CUDA event below is recorded on it
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
@@ -421,10 +485,14 @@ def run_ours(args, rank, world, dist):
         ops = OPS_ONCE if once else OPS
         v, spent, threads, per = oracle_sample(ops=ops)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "oracle Decompose + MultSum + ModDown once each at logN 16, level 19, 23 primes "
-                         "(%.1f s incl. key generation), scaled by the product's counts MS %d, Dp %d, MD %d"
+               "sample": "extrapolated: oracle Decompose + MultSum + ModDown once each at logN 16, level 19, 23 "
+                         "primes (%.1f s incl. key generation), scaled by the product's counts MS %d, Dp %d, MD %d"
                          % (spent, ops["MS"], ops["Dp"], ops["MD"]),
                "per_op_s": per}
+        if not once:
+            # the same extrapolation checked against a whole product where
+            # the oracle finishes one in seconds (config 1: 32x32, N = 2^14)
+            cpu["extrapolation_check_m1"] = oracle_full_product(14, [60, 40, 40, 40], [60], 32, 8, 2)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -858,6 +926,8 @@ def run_keyswitch(args):
     ctx = pk.he_ctx_create(pk.he_params_default(2), 11)
     if args.ms_variant is not None:
         pk.he_ctx_set_multsum_variant(ctx, args.ms_variant)
+    if args.ntt_variant is not None:
+        pk.he_ctx_set_ntt_variant(ctx, args.ntt_variant)
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
     R, B = args.rot_steps, args.batch
@@ -1056,6 +1126,8 @@ def run_ntt(args):
     import paper_2305_17341_gb300 as pk
     pk.build()
     ctx = pk.he_ctx_create(pk.he_params_default(2), 9)
+    if args.ntt_variant is not None:
+        pk.he_ctx_set_ntt_variant(ctx, args.ntt_variant)
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
     q, p = pk.he_ctx_primes(ctx)
@@ -1093,7 +1165,7 @@ def run_ntt(args):
                       "peak_gbfly_s": peak, "peak_source": "measured lazy-Shoup butterfly microbenchmark",
                       "forward": out["forward"], "inverse": out["inverse"],
                       "config": {"workload": "%d rows x 2^16 words, primes of q 60+20x40 and p 2x60 cycled"
-                                             % R}}), flush=True)
+                                             % R, "ntt_variant": args.ntt_variant}}), flush=True)
     pk.he_ctx_destroy(ctx)
 
 
@@ -1167,10 +1239,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="--impl reference: time the oracle on one whole 128x128 product (minutes)")
     ap.add_argument("--workload", default="matmul", choices=["matmul", "covariance", "pca", "mixed", "served", "ntt",
                                                            "keyswitch", "transforms", "sweep"])
     ap.add_argument("--ntt-rows", type=int, default=2024, help="ntt: rows transformed per launch")
     ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
+    ap.add_argument("--ntt-variant", type=int, default=None,
+                    help="matmul / keyswitch / ntt: pin the NTT passes to one variant (default: the tuner)")
     ap.add_argument("--ms-variant", type=int, default=None,
                     help="matmul / keyswitch: pin every MultSum launch to one variant (default: the tuner)")
     ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")

@@ -569,6 +569,28 @@ static EncodeTiledFn encode_tiled() {
     return fn;
 }
 
+// Launch of one persistent pass kernel: its shared-memory attribute and
+// occupancy are set up once per device for this very instantiation.
+template <int LM, bool ROWS, bool SUBSC>
+static void ntt_tma_launch(Ctx *ctx, u64 *d, const CUtensorMap &map, const RowMap &m, cudaStream_t st,
+                           const NttTiles &tl, const SubScale &e) {
+    typedef PassGeom<LM, ROWS> G_;
+    const size_t smem = ((size_t)NTC_STAGES * NTC_TILE + G_::SM) * 8;
+    static int occ[64];
+    const int dev = ctx->device & 63;
+    if (!occ[dev]) {
+        cudaFuncSetAttribute(k_ntt_fwd_tma<LM, ROWS, SUBSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ntt_fwd_tma<LM, ROWS, SUBSC>, NTC_THREADS, smem);
+        occ[dev] = nb > 0 ? nb : 1;
+    }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    const long grid = std::min<long>(tl.rows * tl.tpr, (long)nsm * occ[dev]);
+    k_ntt_fwd_tma<LM, ROWS, SUBSC><<<(unsigned)grid, NTC_THREADS, smem, st>>>(
+        d, map, m, ctx->d_mod, (const ulonglong2 *)ctx->d_psi2, ctx->logN, tl, e, ctx->d_err);
+}
+
 // One pass over all `nr` rows of `d` (no 65535-row split: the grid is
 // persistent).  skip: rows left out; ep: the row pass's fused epilogue.
 template <int LM, bool ROWS>
@@ -598,25 +620,9 @@ static void fwd_pass_tma(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             throw std::runtime_error("tensor map encoding failed");
     }
-    const size_t smem = ((size_t)NTC_STAGES * NTC_TILE + G_::SM) * 8;
     const SubScale e = ep ? *ep : SubScale();
-    auto launch = [&](auto kern) {
-        static int occ[64];
-        const int dev = ctx->device & 63;
-        if (!occ[dev]) {
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            int nb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTC_THREADS, smem);
-            occ[dev] = nb > 0 ? nb : 1;
-        }
-        int nsm = 0;
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        const long grid = std::min<long>(tl.rows * tl.tpr, (long)nsm * occ[dev]);
-        kern<<<(unsigned)grid, NTC_THREADS, smem, st>>>(d, map, m, ctx->d_mod, (const ulonglong2 *)ctx->d_psi2,
-                                                        ctx->logN, tl, e, ctx->d_err);
-    };
-    if (ROWS && ep) launch(k_ntt_fwd_tma<LM, ROWS, true>);
-    else launch(k_ntt_fwd_tma<LM, ROWS, false>);
+    if (ROWS && ep) ntt_tma_launch<LM, ROWS, true>(ctx, d, map, m, st, tl, e);
+    else ntt_tma_launch<LM, ROWS, false>(ctx, d, map, m, st, tl, e);
 }
 
 template <int LM, bool ROWS>
