@@ -137,9 +137,9 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without
  * tuning (-1 returns to the tuner, which times them at the next transform).
  * Variants compute identical words; this is for tests and measurement.
- * 2, 3: one 8-stage tile per CTA, 2 or 3 CTAs per SM (forward and inverse);
- * 4: forward passes on persistent CTAs whose tiles arrive through bulk
- * asynchronous copies (a producer warp, two buffers), inverse as 3.
+ * 2, 3, 5: one 8-stage tile per CTA, 2, 3 or 4 CTAs per SM (forward and
+ * inverse); 4: forward passes on persistent CTAs whose tiles arrive through
+ * bulk asynchronous copies (a producer warp, two buffers), inverse as 3.
  * Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_ntt_variant(he_ctx *ctx, int variant);
 
@@ -331,6 +331,24 @@ int he_aggregate(he_ctx *ctx, const he_ct *ct, int axis, int n, he_ct **out);
  * the transposition of X, mu from Aggregate.  Consumes 5 levels. */
 int he_covariance(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, int n, int s, int centered,
                   const he_mm_sched *sched, he_ct **cov);
+
+/* HCovMtrx over row blocks spread across devices (Sec. 5.2: the block
+ * products of different row blocks are independent, so each device takes a
+ * share of the rows).  he_covariance_partial runs on one device's row blocks
+ * (blocks as in he_covariance, n_row_blocks of them; s is the TOTAL row
+ * count of the dataset): upper[u] receives, for the pairs (a, b) with a <= b
+ * in row-major order (u = 0 .. k(k+1)/2 - 1), the sum over these row blocks
+ * of X_a[l]^T X_b[l] / s, and, unless centered, colsum[j] the sum over these
+ * row blocks of X_j[l] (level of the blocks).  The parts of all devices are
+ * added residue by residue modulo each prime (an all-reduce of the
+ * exported residues; they are linear in the ciphertexts), imported, and
+ * he_covariance_finish turns the sums into the k*k covariance blocks:
+ * exactly the words he_covariance gives on all row blocks at once.
+ * block_level is the level of the input blocks.  Errors as he_covariance. */
+int he_covariance_partial(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, int n, int s, int centered,
+                          const he_mm_sched *sched, he_ct **upper, he_ct **colsum);
+int he_covariance_finish(he_ctx *ctx, he_ct *const *upper, he_ct *const *colsum, int k, int n, int s, int centered,
+                         const he_mm_sched *sched, int block_level, he_ct **cov);
 
 /* Newton-iteration counts of Lazy Normalization (Sec. 6.1.2): the PowerMethod
  * simulation with contraction coefficient S, error bound e, precision bound

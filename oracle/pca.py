@@ -204,12 +204,21 @@ class PCA:
         and dcd_z / dcd_t select the block products' relinearisation and
         Diagonal Convergence Decomposition (HMM.hmatmul; Sec. 7 runs the
         covariance's products decomposed at maximum diagonal 32)."""
+        upper, sums = self.covariance_partial(blocks, s, n, n1z, n1t, centered, relin_once, dcd_z, dcd_t)
+        return self.covariance_finish(upper, sums, s, n, n1z, blocks[0][0].level, centered, dcd_z, dcd_t)
+
+    def covariance_partial(self, blocks, s, n, n1z, n1t, centered=False, relin_once=False, dcd_z=0, dcd_t=0):
+        """The sums over the given row blocks that HCovMtrx needs (Sec. 5.2):
+        upper[(a, b)] = sum_l X_a[l]^T X_b[l] / s for a <= b (1/s folded into
+        the transposition of X_a[l]), and unless centred sums[j] = sum_l
+        X_j[l].  Both are plain sums over the row blocks, so the parts of
+        disjoint sets of row blocks add up (mod q) to those of their union."""
         he, H = self.he, self.H
         nrb, k = len(blocks), len(blocks[0])
         inv_s = 1.0 / s
         XT = [[H.transpose(blocks[l][j], n, n1z, prescale=inv_s) for j in range(k)] for l in range(nrb)]
         Xr = [[H.replicate(blocks[l][j], n) for j in range(k)] for l in range(nrb)]
-        C = [[None] * k for _ in range(k)]
+        upper = {}
         for a in range(k):
             for b in range(a, k):
                 acc = None
@@ -218,7 +227,26 @@ class PCA:
                     B = he.drop(Xr[l][b], A.level)
                     p = H.hmatmul(A, B, n, n1z, n1t, relin_once=relin_once, dcd_z=dcd_z, dcd_t=dcd_t)
                     acc = p if acc is None else he.add(acc, p)
-                C[a][b] = acc
+                upper[(a, b)] = acc
+        sums = []
+        if not centered:
+            for j in range(k):
+                acc = blocks[0][j]
+                for l in range(1, nrb):
+                    acc = he.add(acc, blocks[l][j])
+                sums.append(acc)
+        return upper, sums
+
+    def covariance_finish(self, upper, sums, s, n, n1z, block_level, centered=False, dcd_z=0, dcd_t=0):
+        """HCovMtrx from the row-block sums: blocks a > b as G of block (b, a),
+        one common level, and (not centred) minus mu_a^T mu_b with
+        mu_j = (1/s) Aggregate_0(sums[j]); block_level = the input blocks' level."""
+        he, H = self.he, self.H
+        k = len(sums) if sums else int(round((np.sqrt(8 * len(upper) + 1) - 1) / 2))
+        inv_s = 1.0 / s
+        C = [[None] * k for _ in range(k)]
+        for (a, b), ct in upper.items():
+            C[a][b] = ct
         for a in range(k):
             for b in range(a):
                 C[a][b] = H.transpose(C[b][a], n, n1z)
@@ -230,17 +258,14 @@ class PCA:
             return C
         mu = []
         for j in range(k):
-            acc = blocks[0][j]
-            for l in range(1, nrb):
-                acc = he.add(acc, blocks[l][j])
-            m = self.aggregate(acc, 0, n)
+            m = self.aggregate(sums[j], 0, n)
             mu.append(self.mul_const(m, inv_s))
         muT = [H.transpose(m, n, n1z) for m in mu]
         # mu^T mu is multiplied at the level at which the X^T X products were
         # multiplied, so both are rescaled by the same prime and their scales
         # (Delta^2 / q) agree exactly
         depth = 2 + max((n - 1) // dcd_z + 1 if dcd_z else 1, (n - 2) // dcd_t + 1 if dcd_t else 1)
-        pl = XT[0][0].level - (depth - 1)
+        pl = (block_level - 1) - (depth - 1)
         for a in range(k):
             for b in range(k):
                 t = he.rescale(he.mult_relin(he.drop(muT[a], pl), he.drop(mu[b], pl)))

@@ -119,6 +119,8 @@ SIGNATURES = {
     "he_refresh": [vp, vp, P(he_refresh_state), P(vp)],
     "he_aggregate": [vp, vp, ip, ip, P(vp)],
     "he_covariance": [vp, P(vp), ip, ip, ip, ip, ip, P(he_mm_sched), P(vp)],
+    "he_covariance_partial": [vp, P(vp), ip, ip, ip, ip, ip, P(he_mm_sched), P(vp), P(vp)],
+    "he_covariance_finish": [vp, P(vp), P(vp), ip, ip, ip, ip, P(he_mm_sched), ip, P(vp)],
     "he_lazy_normalization_schedule": [ip, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip,
                                        P(ip)],
     "he_power_method": [vp, P(vp), ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp), P(vp),
@@ -411,6 +413,30 @@ def he_refresh(ctx, ct, rs):
 
 def he_aggregate(ctx, ct, axis, n):
     return _unary("he_aggregate", ctx, ct, axis, n)
+
+
+def he_covariance_partial(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t, relin_once=False, dcd_z=0,
+                          dcd_t=0):
+    """One device's part of HCovMtrx over its row blocks ([l][j] order, l-major):
+    returns (upper, colsum), upper the k(k+1)/2 sums X_a^T X_b / s (a <= b,
+    row-major), colsum the k column sums ([] if centered)."""
+    up = (vp * (k * (k + 1) // 2))()
+    cs = (vp * k)()
+    sc = he_mm_sched(n1z, n1t, 1 if relin_once else 0, dcd_z, dcd_t)
+    check(lib().he_covariance_partial(ctx, _handles(blocks), n_row_blocks, k, n, s, 1 if centered else 0,
+                                      ctypes.byref(sc), up, cs))
+    return [vp(o) for o in up], ([] if centered else [vp(o) for o in cs])
+
+
+def he_covariance_finish(ctx, upper, colsum, k, n, s, centered, n1z, n1t, block_level, relin_once=False, dcd_z=0,
+                         dcd_t=0):
+    """The k*k covariance blocks from summed parts (he_covariance_partial's outputs)."""
+    out = (vp * (k * k))()
+    sc = he_mm_sched(n1z, n1t, 1 if relin_once else 0, dcd_z, dcd_t)
+    cs = _handles(colsum) if colsum else None
+    check(lib().he_covariance_finish(ctx, _handles(upper), cs, k, n, s, 1 if centered else 0, ctypes.byref(sc),
+                                     block_level, out))
+    return [vp(o) for o in out]
 
 
 def he_covariance(ctx, blocks, n_row_blocks, k, n, s, centered, n1z, n1t, relin_once=False, dcd_z=0, dcd_t=0):

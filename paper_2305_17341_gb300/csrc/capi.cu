@@ -273,7 +273,7 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
 
 int he_ctx_set_ntt_variant(he_ctx *ctx, int variant) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
-    if (variant != -1 && (variant < 2 || variant > 4)) return fail(HE_ERR_ARG, "NTT variant -1, 2, 3 or 4");
+    if (variant != -1 && (variant < 2 || variant > 5)) return fail(HE_ERR_ARG, "NTT variant -1, 2, 3, 4 or 5");
     Ctx &c = ctx->c;
     cudaStreamSynchronize(c.stream);
     if (variant < 0) {
@@ -282,7 +282,7 @@ int he_ctx_set_ntt_variant(he_ctx *ctx, int variant) {
     } else {
         c.ntt_tuned = true;
         c.ntt_minb = variant;
-        c.ntt_minb_inv = variant == 4 ? 3 : variant;
+        c.ntt_minb_inv = variant == 4 ? 3 : variant;   // the inverse has no bulk-copy variant
     }
     return HE_OK;
 }

@@ -632,13 +632,18 @@ static void fwd_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st
     dim3 grid((unsigned)((ctx->N >> LM) / G_::W), (unsigned)nr);
     const ulonglong2 *t2 = (const ulonglong2 *)ctx->d_psi2;
     const SubScale e = ep ? *ep : SubScale();
+    // ntt_minb: 2 or 3 CTAs per SM; 5: 4 CTAs per SM
     if (ROWS && ep) {
         if (ctx->ntt_minb == 3)
             k_ntt_fwd_fast<LM, ROWS, 3, true><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
+        else if (ctx->ntt_minb == 5)
+            k_ntt_fwd_fast<LM, ROWS, 4, true><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
         else
             k_ntt_fwd_fast<LM, ROWS, 2, true><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
     } else if (ctx->ntt_minb == 3) {
         k_ntt_fwd_fast<LM, ROWS, 3, false><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
+    } else if (ctx->ntt_minb == 5) {
+        k_ntt_fwd_fast<LM, ROWS, 4, false><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
     } else {
         k_ntt_fwd_fast<LM, ROWS, 2, false><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->logN, sk, e);
     }
@@ -651,6 +656,8 @@ static void inv_pass(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st
     const ulonglong2 *t2 = (const ulonglong2 *)ctx->d_ipsi2;
     if (ctx->ntt_minb_inv == 3)
         k_ntt_inv_fast<LM, ROWS, 3><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
+    else if (ctx->ntt_minb_inv == 5)
+        k_ntt_inv_fast<LM, ROWS, 4><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
     else
         k_ntt_inv_fast<LM, ROWS, 2><<<grid, 256, 0, st>>>(d, m, ctx->d_mod, t2, ctx->d_ninv, ctx->logN);
 }
@@ -767,7 +774,7 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
     for (int dir = 0; dir < 2; dir++) {
         float best = 1e30f;
         int pick = 2;
-        for (int minb : {2, 3, 4}) {
+        for (int minb : {2, 3, 5, 4}) {
             if (dir == 1 && minb == 4) continue;   // 4: the forward passes fed by bulk copies
             (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = minb;
             float t = 1e30f;
@@ -788,7 +795,8 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
             }
             char line[112];
             snprintf(line, sizeof line, "ntt %s logN %d rows %ld %s %d ms %.4f\n", dir ? "inverse" : "forward",
-                     ctx->logN, R, minb == 4 ? "bulk-copy persistent, ctas_per_sm" : "ctas_per_sm", minb == 4 ? 2 : minb,
+                     ctx->logN, R, minb == 4 ? "bulk-copy persistent, ctas_per_sm" : "ctas_per_sm",
+                     minb == 4 ? 2 : minb == 5 ? 4 : minb,
                      t);
             ctx->tune_log += line;
             if (t < best) best = t, pick = minb;

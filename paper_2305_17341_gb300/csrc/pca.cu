@@ -318,25 +318,40 @@ public:
     }
 
     std::vector<HC> cov_finish(const CovPlan &P, std::vector<HC> C) {
-        const int k = P.k, n = P.n, nrb = P.nrb;
+        const int k = P.k, nrb = P.nrb;
+        std::vector<HC> sums;
+        if (!P.centered)
+            for (int j = 0; j < k; j++) {
+                HC acc = clone(P.blocks[j]);
+                for (int l = 1; l < nrb; l++) acc = add_ct(acc.p, P.blocks[l * k + j]);
+                sums.push_back(std::move(acc));
+            }
+        return cov_finish_sums(k, P.n, P.s, P.centered, P.n1z, P.dcd_z, P.dcd_t, P.blocks[0]->level, std::move(C),
+                               std::move(sums));
+    }
+
+    // The last stage from the upper blocks C[a][b] (a <= b) and, when not
+    // centred, the column sums sum_l X_j[l] of the input blocks (level
+    // block_level): whether they cover all row blocks or were summed from
+    // the parts of several devices makes no difference to the words.
+    std::vector<HC> cov_finish_sums(int k, int n, int s, bool centered, int n1z, int dcd_z, int dcd_t,
+                                    int block_level, std::vector<HC> C, std::vector<HC> sums) {
         for (int a = 0; a < k; a++)
-            for (int b = 0; b < a; b++) C[a * k + b] = transpose(C[b * k + a].p, n, P.n1z, 1.0);
+            for (int b = 0; b < a; b++) C[a * k + b] = transpose(C[b * k + a].p, n, n1z, 1.0);
         int lv = C[0]->level;
         for (auto &x : C) lv = std::min(lv, x->level);
         for (auto &x : C)
             if (x->level != lv) x = dropto(x.p, lv);
-        if (P.centered) return C;
-        const double inv_s = 1.0 / P.s;
+        if (centered) return C;
+        const double inv_s = 1.0 / s;
         std::vector<HC> mu, muT;
         for (int j = 0; j < k; j++) {
-            HC acc = clone(P.blocks[j]);
-            for (int l = 1; l < nrb; l++) acc = add_ct(acc.p, P.blocks[l * k + j]);
-            HC m = aggregate(acc.p, 0, n);
+            HC m = aggregate(sums[j].p, 0, n);
             mu.push_back(mul_const(std::move(m), inv_s));
         }
-        for (int j = 0; j < k; j++) muT.push_back(transpose(mu[j].p, n, P.n1z, 1.0));
+        for (int j = 0; j < k; j++) muT.push_back(transpose(mu[j].p, n, n1z, 1.0));
         // the mean product is taken at the level of the block products' inputs minus 2
-        const int pl = P.blocks[0]->level - hmatmul_depth(n, P.dcd_z, P.dcd_t);
+        const int pl = block_level - hmatmul_depth(n, dcd_z, dcd_t);
         for (int a = 0; a < k; a++)
             for (int b = 0; b < k; b++) {
                 HC x = dropto(muT[a].p, pl), y = dropto(mu[b].p, pl);
@@ -346,6 +361,44 @@ public:
                 C[a * k + b] = sub_matched(std::move(C[a * k + b]), std::move(tr));
             }
         return C;
+    }
+
+    // The part of HCovMtrx that a device computes on its own row blocks
+    // when the rows are spread over several devices (Sec. 5.2: the block
+    // products of different row blocks are independent): the upper blocks of
+    // X^T X / s summed over these row blocks, and (not centred) the column
+    // sums of the blocks.  Sums of these parts over the devices, residue by
+    // residue mod q, are what cov_finish_sums takes.
+    void covariance_partial(he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z, int n1t,
+                            bool relin_once, int dcd_z, int dcd_t, std::vector<HC> &upper, std::vector<HC> &sums) {
+        CovPlan P;
+        P.relin_once = relin_once;
+        P.dcd_z = dcd_z;
+        P.dcd_t = dcd_t;
+        P.nrb = nrb;
+        P.k = k;
+        P.n = n;
+        P.s = s;
+        P.n1z = n1z;
+        P.n1t = n1t;
+        P.centered = centered;
+        P.blocks.assign(blocks, blocks + (size_t)nrb * k);
+        std::vector<ProdSpec> prods;
+        cov_prepare(P, prods);
+        std::vector<he_ct *> outs;
+        const int ppl = k * (k + 1) / 2;
+        run_products(prods, outs, std::max(1, kCovBatch / ppl) * ppl);
+        std::vector<HC> C = cov_upper(P, outs.data());
+        upper.clear();
+        for (int a = 0; a < k; a++)
+            for (int b = a; b < k; b++) upper.push_back(std::move(C[a * k + b]));
+        sums.clear();
+        if (!centered)
+            for (int j = 0; j < k; j++) {
+                HC acc = clone(P.blocks[j]);
+                for (int l = 1; l < nrb; l++) acc = add_ct(acc.p, P.blocks[l * k + j]);
+                sums.push_back(std::move(acc));
+            }
     }
 
     std::vector<HC> covariance(he_ct *const *blocks, int nrb, int k, int n, int s, bool centered, int n1z,
@@ -785,6 +838,97 @@ int he_covariance(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, in
     PcaOps ops(&c, &st);
     std::vector<HC> C = ops.covariance(blocks, n_row_blocks, k, n, s, centered != 0, sched->n1_z, sched->n1_t,
                                        sched->relin_once != 0, sched->dcd_z, sched->dcd_t);
+    if (int rc = sync_status(c)) return rc;
+    for (int i = 0; i < k * k; i++) cov[i] = C[i].release();
+    return HE_OK;
+    PCA_GUARD_END
+}
+
+// Arguments shared by the covariance entry points.
+static int check_cov_args(he_ctx *ctx, int k, int n, int s, const he_mm_sched *sched) {
+    if (!ctx || !sched || k < 1 || s < 1 || !pow2(n) || (long)n * n > ctx->c.S || !pow2(sched->n1_z) ||
+        !pow2(sched->n1_t) || sched->n1_z > n || sched->n1_t > n) {
+        set_error("bad arguments");
+        return HE_ERR_ARG;
+    }
+    if ((sched->dcd_z && (sched->dcd_z >= n || sched->dcd_z % sched->n1_z)) ||
+        (sched->dcd_t && (sched->dcd_t >= n || sched->dcd_t % sched->n1_t))) {
+        set_error("a decomposition needs n' < n with n1 dividing n'");
+        return HE_ERR_ARG;
+    }
+    return HE_OK;
+}
+
+int he_covariance_partial(he_ctx *ctx, he_ct *const *blocks, int n_row_blocks, int k, int n, int s, int centered,
+                          const he_mm_sched *sched, he_ct **upper, he_ct **colsum) {
+    if (int rc = check_cov_args(ctx, k, n, s, sched)) return rc;
+    if (!blocks || !upper || n_row_blocks < 1 || (!centered && !colsum)) {
+        set_error("bad arguments");
+        return HE_ERR_ARG;
+    }
+    Ctx &c = ctx->c;
+    for (int i = 0; i < n_row_blocks * k; i++) {
+        if (!blocks[i] || blocks[i]->ctx != &c) {
+            set_error("bad block");
+            return HE_ERR_ARG;
+        }
+        if (blocks[i]->level != blocks[0]->level) {
+            set_error("blocks at different levels");
+            return HE_ERR_LEVEL;
+        }
+    }
+    if (blocks[0]->level < hmatmul_depth(n, sched->dcd_z, sched->dcd_t) + 3) {
+        set_error("the covariance circuit needs the product's depth + 3 levels");
+        return HE_ERR_LEVEL;
+    }
+    PCA_GUARD_BEGIN
+    RefreshState st{0, 0};
+    PcaOps ops(&c, &st);
+    std::vector<HC> up, sums;
+    ops.covariance_partial(blocks, n_row_blocks, k, n, s, centered != 0, sched->n1_z, sched->n1_t,
+                           sched->relin_once != 0, sched->dcd_z, sched->dcd_t, up, sums);
+    if (int rc = sync_status(c)) return rc;
+    for (size_t i = 0; i < up.size(); i++) upper[i] = up[i].release();
+    for (size_t j = 0; j < sums.size(); j++) colsum[j] = sums[j].release();
+    return HE_OK;
+    PCA_GUARD_END
+}
+
+int he_covariance_finish(he_ctx *ctx, he_ct *const *upper, he_ct *const *colsum, int k, int n, int s, int centered,
+                         const he_mm_sched *sched, int block_level, he_ct **cov) {
+    if (int rc = check_cov_args(ctx, k, n, s, sched)) return rc;
+    if (!upper || !cov || (!centered && !colsum)) {
+        set_error("bad arguments");
+        return HE_ERR_ARG;
+    }
+    Ctx &c = ctx->c;
+    const int nu = k * (k + 1) / 2;
+    for (int i = 0; i < nu; i++)
+        if (!upper[i] || upper[i]->ctx != &c || upper[i]->level != upper[0]->level || upper[i]->period != n * n) {
+            set_error("bad upper block");
+            return HE_ERR_ARG;
+        }
+    if (!centered)
+        for (int j = 0; j < k; j++)
+            if (!colsum[j] || colsum[j]->ctx != &c || colsum[j]->level != block_level) {
+                set_error("bad column sum");
+                return HE_ERR_ARG;
+            }
+    if (upper[0]->level < 1 || block_level < hmatmul_depth(n, sched->dcd_z, sched->dcd_t) + 3) {
+        set_error("the covariance circuit needs the product's depth + 3 levels");
+        return HE_ERR_LEVEL;
+    }
+    PCA_GUARD_BEGIN
+    RefreshState st{0, 0};
+    PcaOps ops(&c, &st);
+    std::vector<HC> C(k * k), sums;
+    int u = 0;
+    for (int a = 0; a < k; a++)
+        for (int b = a; b < k; b++) C[a * k + b] = ops.clone(upper[u++]);
+    if (!centered)
+        for (int j = 0; j < k; j++) sums.push_back(ops.clone(colsum[j]));
+    C = ops.cov_finish_sums(k, n, s, centered != 0, sched->n1_z, sched->dcd_z, sched->dcd_t, block_level,
+                            std::move(C), std::move(sums));
     if (int rc = sync_status(c)) return rc;
     for (int i = 0; i < k * k; i++) cov[i] = C[i].release();
     return HE_OK;

@@ -373,3 +373,52 @@ def test_pca_cosine_vs_eigh_with_clear_eigen_gap(env):
         C64 = C64 - lam64 * np.outer(f, f)
     for h in lams + [x for vv in Vs for x in vv] + Cg + V0g:
         pk.he_ct_free(h)
+
+
+def test_covariance_parts_over_row_block_shares_equal_whole(env):
+    """he_covariance_partial on two shares of the row blocks (2 + 1 of a
+    ragged 40 x 32 dataset), the parts added residue by residue mod q (what
+    the all-reduce of the sharded covariance does), imported, and
+    he_covariance_finish: the covariance blocks equal he_covariance's word
+    for word.  The sharding module run on a one-rank process group gives the
+    same words."""
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2305_17341_gb300 import sharding
+    from paper_2305_17341_gb300.workloads import lowrank_dataset
+    pk, ctx, P, he, n, n1 = env
+    X = lowrank_dataset(40, 32, 2)
+    g, _, nrb, k = _dataset_blocks(pk, ctx, P, he, X, n)
+    s = X.shape[0]
+    whole = pk.he_covariance(ctx, g, nrb, k, n, s, False, n1, n1)
+    want = [pk.he_ct_export(ctx, h) for h in whole]
+    q, _ = pk.he_ctx_primes(ctx)
+    parts = [pk.he_covariance_partial(ctx, g[lo * k:hi * k], hi - lo, k, n, s, False, n1, n1)
+             for lo, hi in ((0, 2), (2, 3))]
+
+    def add(hs):
+        lv, sc, per = pk.he_ct_info(hs[0])
+        r = sum(pk.he_ct_export(ctx, h).astype(object) for h in hs)
+        r = np.array(r % np.array(q[: lv + 1], dtype=object)[:, None], dtype=np.uint64)
+        return pk.he_ct_import(ctx, r, lv, sc, per)
+
+    upper = [add([p[0][u] for p in parts]) for u in range(k * (k + 1) // 2)]
+    colsum = [add([p[1][j] for p in parts]) for j in range(k)]
+    C = pk.he_covariance_finish(ctx, upper, colsum, k, n, s, False, n1, n1, pk.he_ct_info(g[0])[0])
+    for i in range(k * k):
+        assert np.array_equal(pk.he_ct_export(ctx, C[i]), want[i]), i
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    try:
+        C1 = sharding.covariance_sharded(ctx, g, nrb, k, n, s, False, n1, n1)
+    finally:
+        dist.destroy_process_group()
+    for i in range(k * k):
+        assert np.array_equal(pk.he_ct_export(ctx, C1[i]), want[i]), i
+    for h in C + C1 + whole + upper + colsum + g + [x for p in parts for hs in p for x in hs]:
+        pk.he_ct_free(h)
