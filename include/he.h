@@ -409,19 +409,23 @@ int he_trace_enable(he_ctx *ctx, int on);
 int he_bench_butterfly(int iters, double *bfly_per_s);
 int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, double *bytes, int reset);
 
-/* Captured batched products.  he_mm_plan_create runs the jobs once (as
- * he_hmatmul_batch would, grouping equal shapes) and records every launch of
- * that batched step -- gathers, replication, the hoisted product passes --
- * as one CUDA graph on the context's stream; he_mm_plan_run replays it and
- * returns fresh output ciphertexts, bit-identical to he_hmatmul_batch on the
- * inputs' contents at the time of the run.  The plan keeps the device
- * addresses of the jobs' input ciphertexts: those handles must stay alive
- * (contents may change between runs) until he_mm_plan_destroy.  The graph's
- * temporaries and the product outputs live in memory the plan owns (the
- * working set of the whole batch, held until destroy).  All jobs must belong
- * to one context; runs of one plan, and anything else on that context, must
- * not overlap.  The paper runs its products as parallel CPU threads
- * (Sec. 4.1.2); the graph is this library's form of that parallel step.
+/* Captured batched products.  he_mm_plan_create runs the jobs once (grouped
+ * as he_hmatmul_batch groups them: context, level, block size, schedule) and
+ * records every launch of that batched step -- gathers, replication, the
+ * hoisted product passes -- as one CUDA graph in which every group is a
+ * branch of its own (forked from and joined to the plan's stream), so the
+ * groups run concurrently at replay; he_mm_plan_run replays it and returns
+ * fresh output ciphertexts, bit-identical to he_hmatmul_batch on the inputs'
+ * contents at the time of the run.  Jobs may come from several contexts of
+ * one device (different ring degrees, levels, block sizes).  The plan keeps
+ * the device addresses of the jobs' input ciphertexts: those handles must
+ * stay alive (contents may change between runs) until he_mm_plan_destroy.
+ * Each branch's temporaries live in memory of its own that the plan owns
+ * (the working set of the whole batch, held until destroy).  A run waits for
+ * work queued on the jobs' contexts before it starts; runs of one plan, and
+ * anything else on those contexts, must not overlap a run.  The paper runs
+ * its products as parallel CPU threads (Sec. 4.1.2); the concurrent branches
+ * are this library's form of that parallel step.
  * Errors as he_hmatmul_batch, plus HE_ERR_KEY_MISSING at creation. */
 typedef struct he_mm_plan he_mm_plan;
 int he_mm_plan_create(const he_mm_job *jobs, int n_jobs, he_mm_plan **out);
