@@ -68,6 +68,12 @@ __device__ __forceinline__ void bc_bulk(void *dst, const void *src, u32 bytes, u
         : "memory");
 }
 
+// Asks the copy engine to bring `bytes` (a multiple of 16, 16-byte aligned)
+// of global memory into L2; nothing waits for it.
+__device__ __forceinline__ void bc_prefetch_l2(const void *src, u32 bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // One box of a 2-D tensor map (coordinates x innermost, y) into shared `dst`.
 __device__ __forceinline__ void bc_tensor2d(void *dst, const CUtensorMap *map, int x, int y, u64 *bar) {
     asm volatile(

@@ -291,6 +291,15 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
     const long seq = (long)blockIdx.x * W + w;
     u64 *p = data + row * (long)N + (ROWS ? seq * M : seq);
     const long G = ROWS ? ((long)(N >> LM) + seq) : 1;
+    if (ROWS && SUBSC && threadIdx.x == 0) {
+        // the epilogue's operands (this CTA's W sequences of u, and of the
+        // addend) are contiguous: have the copy engine bring them into L2
+        // while the butterflies run, so the epilogue does not wait on DRAM
+        const long arow = ep.row0 + row, it = arow / ep.rows_per_item;
+        const long off = (arow - it * ep.rows_per_item) * (long)N + (long)blockIdx.x * W * M;
+        bc_prefetch_l2(ep.u + it * ep.us + off, W * M * 8);
+        if (ep.add) bc_prefetch_l2(ep.add + it * ep.as + off, W * M * 8);
+    }
     u64 x[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) x[k] = p[(long)(t + T * k) * stride];
