@@ -266,7 +266,8 @@ int he_ctx_set_autotune(he_ctx *ctx, int on) {
 
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
-    if (variant < -1 || variant > 10) return fail(HE_ERR_ARG, "MultSum variant in -1..10");
+    if (variant < -1 || (variant > 10 && variant != 16 && variant != 20))
+        return fail(HE_ERR_ARG, "MultSum variant -1..10, 16 or 20");
     ctx->c.force_multsum = variant;
     return HE_OK;
 }

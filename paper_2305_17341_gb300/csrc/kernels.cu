@@ -588,7 +588,12 @@ struct MultiKeys {
 
 // Each digit word is loaded once and multiplied into the 2G accumulators of
 // the G keys (2G independent accumulation chains per thread).
-template <int G, bool STREAM>
+// With PF > 0 every thread also asks L2 for its digit word PF digits ahead,
+// and the threads of the first item for their key words, so that more DRAM
+// requests are in flight than the loads themselves keep (no registers held).
+__device__ __forceinline__ void l2_prefetch(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+template <int G, bool STREAM, int PF = 0>
 __global__ void __launch_bounds__(256, G <= 2 ? 4 : G <= 5 ? 2 : 1) k_multsum_multi(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
                                                        int alpha, int L, int ndig, int nprimes, int logN,
                                                        const ModQ *mods, const u64 *c0, long c0s,
@@ -613,6 +618,15 @@ __global__ void __launch_bounds__(256, G <= 2 ? 4 : G <= 5 ? 2 : 1) k_multsum_mu
 #pragma unroll
         for (int k = 0; k < 2 * G; k++) x0[k] = 0, x1[k] = 0, x2[k] = 0;
         for (int d = 0; d < ndig; d++) {
+            if (PF && d + PF < ndig) {
+                l2_prefetch(dp + (long)(d + PF) * dstride);
+                if (ti == 0)
+#pragma unroll
+                    for (int k = 0; k < G; k++) {
+                        l2_prefetch(mk.key[k] + (long)(d + PF) * kd + koff);
+                        l2_prefetch(mk.key[k] + (long)(d + PF) * kd + koff + kk);
+                    }
+            }
             const u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
 #pragma unroll
             for (int k = 0; k < G; k++) {
@@ -630,6 +644,15 @@ __global__ void __launch_bounds__(256, G <= 2 ? 4 : G <= 5 ? 2 : 1) k_multsum_mu
 #pragma unroll
         for (int k = 0; k < G; k++) a0[k] = U128{0, 0}, a1[k] = U128{0, 0};
         for (int d = 0; d < ndig; d++) {
+            if (PF && d + PF < ndig) {
+                l2_prefetch(dp + (long)(d + PF) * dstride);
+                if (ti == 0)
+#pragma unroll
+                    for (int k = 0; k < G; k++) {
+                        l2_prefetch(mk.key[k] + (long)(d + PF) * kd + koff);
+                        l2_prefetch(mk.key[k] + (long)(d + PF) * kd + koff + kk);
+                    }
+            }
             const u64 v = STREAM ? __ldcs(dp + (long)d * dstride) : __ldg(dp + (long)d * dstride);
 #pragma unroll
             for (int k = 0; k < G; k++) {
@@ -731,15 +754,19 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
     }
     int BI;
     bool stream;
-    multsum_variant(v, B, BI, stream);
+    multsum_variant(v & 15, B, BI, stream);
+    const bool pf = (v & 16) != 0;
     const int rows = level + 1 + c->alpha, XW = 256 / BI;
     dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
-    if (stream)
-        k_multsum_multi<G, true><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L, c->ndig(level),
-                                                       c->nprimes, c->logN, c->d_mod, c0, c0s, c->d_Pmod);
-    else
-        k_multsum_multi<G, false><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L, c->ndig(level),
-                                                        c->nprimes, c->logN, c->d_mod, c0, c0s, c->d_Pmod);
+#define MS_LAUNCH(STR, PFD)                                                                                   \
+    k_multsum_multi<G, STR, PFD><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L, c->ndig(level), \
+                                                       c->nprimes, c->logN, c->d_mod, c0, c0s, c->d_Pmod)
+    if (stream) {
+        if (pf) MS_LAUNCH(true, 2); else MS_LAUNCH(true, 0);
+    } else {
+        if (pf) MS_LAUNCH(false, 2); else MS_LAUNCH(false, 0);
+    }
+#undef MS_LAUNCH
     c->n_launch++;
 }
 
@@ -798,11 +825,11 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand = 0; cand < 11; cand++) {
+                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 8, 9, 10}) {
                     int BI;
                     bool stream;
-                    multsum_variant(cand, B, BI, stream);
-                    if (cand >= 8) BI = 100 + cand;   // the bulk-copy kernel: its own entries
+                    multsum_variant(cand & 15, B, BI, stream);
+                    if (cand >= 8) BI = 100 + cand;   // the bulk-copy and prefetching kernels: their own entries
                     if (!seen.insert(std::make_tuple(cc, BI, stream)).second) continue;
                     float t = 1e30f;
                     for (int rep = 0; rep < 2; rep++) {

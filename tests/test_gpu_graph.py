@@ -54,7 +54,10 @@ def test_plan_replays_equal_batch(env):
         pk.he_ct_free(h)
 
 
-def test_plan_refuses_missing_keys_and_mixed_contexts(env):
+def test_plan_refuses_missing_keys_and_operands_of_two_contexts(env):
+    """A plan may hold jobs of several contexts (each group a branch), but
+    not a job whose operands belong to two contexts, nor a job of a context
+    without the product's rotation keys."""
     pk, ctx, n, n1 = env
     L = len(QBITS) - 1
     a = pk.he_encrypt_matrix(ctx, np.eye(n), L, 1)
@@ -65,8 +68,11 @@ def test_plan_refuses_missing_keys_and_mixed_contexts(env):
     try:
         b = pk.he_encrypt_matrix(other, np.eye(n), L, 1)
         with pytest.raises(pk.HeError) as e:
-            pk.he_mm_plan_create([(a, a, n, n1, n1), (b, b, n, n1, n1)])
+            pk.he_mm_plan_create([(a, b, n, n1, n1)])
         assert e.value.code == pk.HE_ERR_ARG
+        with pytest.raises(pk.HeError) as e:
+            pk.he_mm_plan_create([(a, a, n, n1, n1), (b, b, n, n1, n1)])
+        assert e.value.code == pk.HE_ERR_KEY_MISSING
         pk.he_ct_free(b)
     finally:
         pk.he_ctx_destroy(other)
