@@ -754,12 +754,27 @@ def run_served(args):
     from paper_2305_17341_gb300 import workloads
     pk.build()
     n, n1, k, t = 128, 16, 2, 256
-    mix = workloads.served_job_mix(args.rate, args.duration, 5)
+    if args.served_rows:
+        # the streamed dataset: served_rows x 256 as ceil(rows / 128) row blocks
+        blocks_total = -(-args.served_rows // n)
+        mix = workloads.served_job_mix(args.rate, args.duration, 5, workloads.SERVED_STREAM_WEIGHTS, blocks_total)
+        s_rows = args.served_rows
+    else:
+        mix = workloads.served_job_mix(args.rate, args.duration, 5)
+        s_rows = None
     ctx2 = pk.he_ctx_create(pk.he_params_default(2), 52)
     _cov_keys(pk, ctx2, n, n1, 1 << 15)
     # client side, before the timed region: encrypt every input
     n_blk = max(1, sum(1 for _, kd in mix if kd == "xtx_block"))
-    Xs = workloads.lowrank_dataset(n * n_blk, t, 6)
+    if s_rows:
+        # every arriving block of the dataset; the total row count s is the
+        # dataset's (the accumulator divides by it), the last block zero-padded
+        Xfull = workloads.lowrank_dataset(s_rows, t, 6)
+        Xs = np.zeros((n * max(n_blk, -(-s_rows // n)), t))
+        Xs[:s_rows] = Xfull
+    else:
+        s_rows = n * n_blk
+        Xs = workloads.lowrank_dataset(n * n_blk, t, 6)
     stream = [[pk.he_encrypt_matrix(ctx2, Xs[l * n:(l + 1) * n, j * n:(j + 1) * n], 20, 10000 + 2 * l + j)
                for j in range(k)] for l in range(n_blk)]
     pairs = [workloads.matmul_pair(n, 70 + i) for i in range(4)]
@@ -795,7 +810,7 @@ def run_served(args):
     def submit(kind, idx, acc_id=1):
         if kind == "xtx_block":
             return pk.he_server_submit(srv, pk.HE_JOB_XTX_BLOCK, stream[idx], n=n, n1z=n1, n1t=n1, k=k,
-                                       s=n * n_blk, acc_id=acc_id)
+                                       s=s_rows, acc_id=acc_id)
         if kind == "matmul":
             a, b = mm[idx % len(mm)]
             return pk.he_server_submit(srv, pk.HE_JOB_MATMUL, [a, b], n=n, n1z=n1, n1t=n1)
@@ -866,7 +881,7 @@ def run_served(args):
     xtx = res[fin][1]
     if not isinstance(xtx, Exception):
         Xb = Xs[:n * nb]
-        ref = Xb.T @ Xb / (n * n_blk)
+        ref = Xb.T @ Xb / s_rows
         check["xtx_max_abs_err"] = max(float(np.abs(pk.he_decrypt_matrix(ctx2, xtx[a * k + b], n, n) -
                                                     ref[a * n:(a + 1) * n, b * n:(b + 1) * n]).max())
                                        for a in range(k) for b in range(k))
@@ -900,10 +915,17 @@ def run_served(args):
         "ticks": st["ticks"], "products": st["products"],
         "products_per_tick": st["products"] / max(1, st["ticks"]), "max_products_per_tick": st["max_products_per_tick"],
         "key_bytes": st["key_bytes"], "wall_s": wall, "clocks": ck,
-        "config": {"workload": "Poisson arrivals at %.2f jobs/s for %.0f s: X^T X row blocks (128x256 each, one "
-                               "accumulator, %d blocks), 128x128 products, 256x256 and 4096x256 covariances, "
-                               "top-%d PCA; N=2^16, covariance chain 60+20x40 / PowerMethod chain 60+13x40, p 2x60"
-                               % (args.rate, args.duration, nb, args.components),
+        # the arrival rate against what the server completes: when it cannot
+        # keep up, the queue grows and drains after the last arrival
+        "backlog": {"arrivals_per_s": len(mix) / args.duration, "completed_per_s": st["jobs_per_s"],
+                    "keeps_up": st["jobs_per_s"] >= len(mix) / args.duration,
+                    "drain_s_after_last_arrival": wall - (mix[-1][0] if mix else 0.0)},
+        "config": {"workload": "Poisson arrivals at %.2f jobs/s for %.0f s: X^T X row blocks of a %dx256 dataset "
+                               "(128x256 each, one accumulator, %d of %d blocks arrived), 256x256 and 4096x256 "
+                               "covariances, top-%d PCA%s; N=2^16, covariance chain 60+20x40 / PowerMethod chain "
+                               "60+13x40, p 2x60"
+                               % (args.rate, args.duration, s_rows, nb, -(-s_rows // n), args.components,
+                                  "" if args.served_rows else ", 128x128 products"),
                    "budget_gb": args.budget_gb, "max_batch": args.max_batch, "jobs": len(mix)},
         "check": dict(check, tol=1e-4)}), flush=True)
     for h in [x for blk in stream for x in blk] + [x for p in mm for x in p] + cov_in + cov_big + pca_in:
@@ -1274,7 +1296,9 @@ def main():
     ap.add_argument("--ms-variant", type=int, default=None,
                     help="matmul / keyswitch: pin every MultSum launch to one variant (default: the tuner)")
     ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")
-    ap.add_argument("--duration", type=float, default=20.0, help="served: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=120.0, help="served: seconds of arrivals")
+    ap.add_argument("--served-rows", type=int, default=60000,
+                    help="served: rows of the dataset streamed as 128-row blocks (0: the older mix with products)")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
     ap.add_argument("--max-batch", type=int, default=8, help="served: products per batched pass")
     ap.add_argument("--no-pca", action="store_true", help="served: leave PCA jobs out of the mix")

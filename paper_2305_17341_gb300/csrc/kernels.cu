@@ -745,7 +745,7 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
         mk.ginv[k] = inv & (M - 1);
     }
-    if (v >= 8) {
+    if (v >= 8 && v <= 10) {
         if (v == 8) multsum_tma_launch<G, 8, 64, 8>(c, mk, digits, B, level, c0, c0s, st);
         else if (v == 9) multsum_tma_launch<G, 6, 128, 4>(c, mk, digits, B, level, c0, c0s, st);
         else multsum_tma_launch<G, 4, 256, 2>(c, mk, digits, B, level, c0, c0s, st);

@@ -58,12 +58,31 @@ def poisson_arrivals(rate, duration, seed):
 
 
 def served_job_mix(rate, duration, seed, weights=(("xtx_block", 0.55), ("matmul", 0.25), ("covariance", 0.12),
-                                                  ("covariance_large", 0.03), ("pca", 0.05))):
+                                                  ("covariance_large", 0.03), ("pca", 0.05)), max_xtx=None):
     """A served workload: Poisson arrivals, each labelled with a job kind drawn
-    from `weights`.  Returns [(t, kind)] in arrival order."""
+    from `weights`.  With max_xtx, at most that many arrivals are row blocks
+    ("xtx_block") of the streamed dataset; later draws of that kind become
+    "covariance".  Returns [(t, kind)] in arrival order."""
     ts = poisson_arrivals(rate, duration, seed)
     rng = np.random.default_rng(seed + 1)
     kinds = [k for k, _ in weights]
     p = np.array([w for _, w in weights], dtype=float)
     p /= p.sum()
-    return [(t, kinds[int(rng.choice(len(kinds), p=p))]) for t in ts]
+    out, nx = [], 0
+    for t in ts:
+        kind = kinds[int(rng.choice(len(kinds), p=p))]
+        if kind == "xtx_block" and max_xtx is not None:
+            if nx >= max_xtx:
+                kind = "covariance"
+            else:
+                nx += 1
+        out.append((t, kind))
+    return out
+
+
+# The served configuration's mix: one 60000 x 256 dataset streamed as its
+# 469 row blocks of 128 x 256 (the last zero-padded), 256 x 256 and
+# 4096 x 256 covariances and top-k PCA jobs; at 4 jobs/s over 120 s the
+# expected number of row-block arrivals (0.97 x 480) is about the dataset's
+# 469 blocks.
+SERVED_STREAM_WEIGHTS = (("xtx_block", 0.97), ("covariance", 0.015), ("covariance_large", 0.005), ("pca", 0.01))
