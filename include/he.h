@@ -132,7 +132,8 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * producer warp, tiles of 64 coefficients x 8 items (8 stages), 128 x 4 (6)
  * and 256 x 2 (4).
  * 16, 20: variants 0 and 4 with an L2 prefetch of the digit and key words
- * two digits ahead.  Errors: HE_ERR_ARG for other values. */
+ * two digits ahead; 32, 36: variants 0 and 4 compiled for more resident CTAs
+ * per SM (fewer registers).  Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without

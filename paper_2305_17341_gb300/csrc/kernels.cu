@@ -593,8 +593,9 @@ struct MultiKeys {
 // requests are in flight than the loads themselves keep (no registers held).
 __device__ __forceinline__ void l2_prefetch(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-template <int G, bool STREAM, int PF = 0>
-__global__ void __launch_bounds__(256, G <= 2 ? 4 : G <= 5 ? 2 : 1) k_multsum_multi(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
+// OCC: resident CTAs per SM the launch bound asks for (0: by G).
+template <int G, bool STREAM, int PF = 0, int OCC = 0>
+__global__ void __launch_bounds__(256, OCC ? OCC : G <= 2 ? 4 : G <= 5 ? 2 : 1) k_multsum_multi(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
                                                        int alpha, int L, int ndig, int nprimes, int logN,
                                                        const ModQ *mods, const u64 *c0, long c0s,
                                                        const ShoupPair *Pmod) {
@@ -758,13 +759,19 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
     const bool pf = (v & 16) != 0;
     const int rows = level + 1 + c->alpha, XW = 256 / BI;
     dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
-#define MS_LAUNCH(STR, PFD)                                                                                   \
-    k_multsum_multi<G, STR, PFD><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L, c->ndig(level), \
-                                                       c->nprimes, c->logN, c->d_mod, c0, c0s, c->d_Pmod)
-    if (stream) {
-        if (pf) MS_LAUNCH(true, 2); else MS_LAUNCH(true, 0);
+    // bit 5: the launch bound asks for more resident CTAs (fewer registers)
+    constexpr int OCC_HI = G <= 1 ? 8 : G <= 2 ? 6 : G <= 4 ? 4 : 3;
+    const bool hi = (v & 32) != 0;
+#define MS_LAUNCH(STR, PFD, OCC)                                                                           \
+    k_multsum_multi<G, STR, PFD, OCC><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L,          \
+                                                            c->ndig(level), c->nprimes, c->logN, c->d_mod, c0, c0s, \
+                                                            c->d_Pmod)
+    if (hi) {
+        if (stream) MS_LAUNCH(true, 0, OCC_HI); else MS_LAUNCH(false, 0, OCC_HI);
+    } else if (stream) {
+        if (pf) MS_LAUNCH(true, 2, 0); else MS_LAUNCH(true, 0, 0);
     } else {
-        if (pf) MS_LAUNCH(false, 2); else MS_LAUNCH(false, 0);
+        if (pf) MS_LAUNCH(false, 2, 0); else MS_LAUNCH(false, 0, 0);
     }
 #undef MS_LAUNCH
     c->n_launch++;
@@ -825,7 +832,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 8, 9, 10}) {
+                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 8, 9, 10}) {
                     int BI;
                     bool stream;
                     multsum_variant(cand & 15, B, BI, stream);
