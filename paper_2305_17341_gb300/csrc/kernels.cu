@@ -680,6 +680,82 @@ __global__ void __launch_bounds__(256, OCC ? OCC : G <= 2 ? 4 : G <= 5 ? 2 : 1) 
     }
 }
 
+// The same MultSum with the G keys split over the CTA's warps: 8 warps =
+// (G / KG) key groups x BI = 8 KG / G items, 32 coefficients of one row per
+// CTA; each thread accumulates KG keys of one item, so its state (2 KG
+// accumulators) does not grow with G and more CTAs fit on an SM.  A digit
+// word is loaded by the warps of every key group (one DRAM read, L1 for the
+// others), a key word by the warps of every item; every output word is
+// still the sum over the digits of the same products, reduced once.
+template <int G, int KG, int OCC>
+__global__ void __launch_bounds__(256, OCC) k_multsum_split(const __grid_constant__ MultiKeys<G> mk, const u64 *digits, int B, int level,
+                                                            int alpha, int L, int ndig, int nprimes, int logN,
+                                                            const ModQ *mods, const u64 *c0, long c0s,
+                                                            const ShoupPair *Pmod) {
+    constexpr int NGRP = G / KG, BI = 8 / NGRP;
+    const int N = 1 << logN;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int kg0 = (wid / BI) * KG, bi = wid % BI;
+    const int y = blockIdx.x * 32 + lane;
+    const int r = blockIdx.y;
+    const int b = blockIdx.z * BI + bi;
+    if (b >= B || y >= N) return;
+    const int rows = level + 1 + alpha;
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ m = mods[kr];
+    const long dstride = (long)rows * N;
+    const u64 *dp = digits + (long)b * ndig * dstride + (long)r * N + y;
+    const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    U128 a0[KG], a1[KG];
+    if (m.q < (1ull << 42)) {
+        u32 x0[2 * KG], x1[2 * KG], x2[2 * KG];
+#pragma unroll
+        for (int k = 0; k < 2 * KG; k++) x0[k] = 0, x1[k] = 0, x2[k] = 0;
+        for (int d = 0; d < ndig; d++) {
+            const u64 v = __ldg(dp + (long)d * dstride);
+#pragma unroll
+            for (int k = 0; k < KG; k++) {
+                const u64 *kp = mk.key[kg0 + k] + (long)d * kd + koff;
+                mac96(x0[2 * k], x1[2 * k], x2[2 * k], v, __ldg(kp));
+                mac96(x0[2 * k + 1], x1[2 * k + 1], x2[2 * k + 1], v, __ldg(kp + kk));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KG; k++) {
+            a0[k] = U128{((u64)x1[2 * k] << 32) | x0[2 * k], x2[2 * k]};
+            a1[k] = U128{((u64)x1[2 * k + 1] << 32) | x0[2 * k + 1], x2[2 * k + 1]};
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KG; k++) a0[k] = U128{0, 0}, a1[k] = U128{0, 0};
+        for (int d = 0; d < ndig; d++) {
+            const u64 v = __ldg(dp + (long)d * dstride);
+#pragma unroll
+            for (int k = 0; k < KG; k++) {
+                const u64 *kp = mk.key[kg0 + k] + (long)d * kd + koff;
+                mac128(a0[k], v, __ldg(kp));
+                mac128(a1[k], v, __ldg(kp + kk));
+            }
+        }
+    }
+    u64 pc0 = 0;
+    const bool with_c0 = c0 && r <= level;
+    if (with_c0) {
+        ShoupPair w = Pmod[r];
+        pc0 = shoup(c0[b * c0s + (long)r * N + y], w.w, w.wp, m.q);
+    }
+#pragma unroll
+    for (int k = 0; k < KG; k++) {
+        u64 o0 = redc(a0[k].lo, a0[k].hi, m), o1 = redc(a1[k].lo, a1[k].hi, m);
+        if (with_c0) o0 = addmod(o0, pc0, m.q);
+        const u32 gi = mk.ginv[kg0 + k];
+        const int x = gi == 1u ? y : auto_index(y, gi, logN);
+        u64 *ob = mk.out[kg0 + k] + (long)b * 2 * rows * N;
+        ob[(long)r * N + x] = o0;
+        ob[(long)(rows + r) * N + x] = o1;
+    }
+}
+
 // Permutes key rows into the layout above: out[row][pi_g(x)] = in[row][x].
 __global__ void k_permute_key(u64 *out, const u64 *in, long rows, int logN, u32 g) {
     const int N = 1 << logN;
@@ -745,6 +821,30 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         u32 g = gs[k], inv = g;
         for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
         mk.ginv[k] = inv & (M - 1);
+    }
+    if (v == 64 || v == 65) {
+        // keys split over warps: KG = 1 (64) or 2 (65, G even)
+        const int rows = level + 1 + c->alpha;
+        auto go = [&](auto kern, int bi) {
+            dim3 grid((unsigned)((c->N + 31) / 32), (unsigned)rows, (unsigned)((B + bi - 1) / bi));
+            kern<<<grid, 256, 0, st>>>(mk, digits, B, level, c->alpha, c->L, c->ndig(level), c->nprimes, c->logN,
+                                       c->d_mod, c0, c0s, c->d_Pmod);
+        };
+        if (v == 65 && G % 2 == 0 && G >= 2) {
+            constexpr int KG2 = (G % 2 == 0 && G >= 2) ? 2 : 1;
+            constexpr int NG2 = G / KG2;
+            if constexpr (8 % NG2 == 0) {
+                go(k_multsum_split<G, KG2, 4>, 8 / NG2);
+                c->n_launch++;
+                return;
+            }
+        }
+        if constexpr (8 % G == 0) {
+            go(k_multsum_split<G, 1, 6>, 8 / G);
+            c->n_launch++;
+            return;
+        }
+        v = 32;   // G does not divide the warps: the high-occupancy thread-per-word kernel
     }
     if (v >= 8 && v <= 10) {
         if (v == 8) multsum_tma_launch<G, 8, 64, 8>(c, mk, digits, B, level, c0, c0s, st);
@@ -832,7 +932,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 8, 9, 10}) {
+                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 64, 65, 8, 9, 10}) {
                     int BI;
                     bool stream;
                     multsum_variant(cand & 15, B, BI, stream);
