@@ -133,10 +133,11 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * and 256 x 2 (4).
  * 16, 20: variants 0 and 4 with an L2 prefetch of the digit and key words
  * two digits ahead; 32, 36: variants 0 and 4 compiled for more resident CTAs
- * per SM (fewer registers); 64, 65: the rotations of a launch split over the
- * CTA's warps, 1 or 2 per thread (a thread's state no longer grows with the
- * number of rotations; where that number does not divide the 8 warps, as
- * 32).  Errors: HE_ERR_ARG for other values. */
+ * per SM (fewer registers), 48 the same with the prefetch of 16; 64, 65:
+ * the rotations of a launch split over the CTA's warps, 1 or 2 per thread (a
+ * thread's state no longer grows with the number of rotations; where that
+ * number does not divide the 8 warps, as 32).  Errors: HE_ERR_ARG for other
+ * values. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without

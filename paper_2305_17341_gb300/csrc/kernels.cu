@@ -867,7 +867,9 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
                                                             c->ndig(level), c->nprimes, c->logN, c->d_mod, c0, c0s, \
                                                             c->d_Pmod)
     if (hi) {
-        if (stream) MS_LAUNCH(true, 0, OCC_HI); else MS_LAUNCH(false, 0, OCC_HI);
+        if (pf) MS_LAUNCH(false, 2, OCC_HI);
+        else if (stream) MS_LAUNCH(true, 0, OCC_HI);
+        else MS_LAUNCH(false, 0, OCC_HI);
     } else if (stream) {
         if (pf) MS_LAUNCH(true, 2, 0); else MS_LAUNCH(true, 0, 0);
     } else {
@@ -932,7 +934,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 64, 65, 8, 9, 10}) {
+                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 48, 64, 65, 8, 9, 10}) {
                     int BI;
                     bool stream;
                     multsum_variant(cand & 15, B, BI, stream);

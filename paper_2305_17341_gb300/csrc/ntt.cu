@@ -291,16 +291,6 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
     const long seq = (long)blockIdx.x * W + w;
     u64 *p = data + row * (long)N + (ROWS ? seq * M : seq);
     const long G = ROWS ? ((long)(N >> LM) + seq) : 1;
-    if (ROWS && threadIdx.x == 0) {
-        // a row tile is 32 KiB of contiguous words: ask L2 for the tile of
-        // the CTA one resident wave later (MINB CTAs on every SM), so that
-        // it finds its input in L2 instead of waiting on DRAM
-        u32 nsm;
-        asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
-        const long lin = (long)blockIdx.y * gridDim.x + blockIdx.x + (long)MINB * nsm;
-        const long ty = lin / gridDim.x, tx = lin - ty * gridDim.x;
-        if (ty < gridDim.y && !skip.skip(ty)) bc_prefetch_l2(data + ty * (long)N + tx * (long)(W * M), W * M * 8);
-    }
     if (ROWS && SUBSC && threadIdx.x == 0) {
         // the epilogue's operands (this CTA's W sequences of u, and of the
         // addend) are contiguous: have the copy engine bring them into L2
