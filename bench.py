@@ -527,8 +527,13 @@ def run_ours(args, rank, world, dist):
     pk.he_ctx_destroy(ctx)
 
 
-def _cov_keys(pk, ctx, n, n1, S):
+def _cov_keys(pk, ctx, n, n1, S, dcd=0):
+    """Rotation keys of HCovMtrx with n x n blocks: the block products (with
+    the decomposition at maximum diagonal dcd if given), transpositions,
+    Aggregate sums and replication; and the relinearisation key."""
     steps = set(pk.he_rot_steps_for_matmul(n, n1, n1, S)) | set(pk.he_rot_steps_for_transpose(n, n1, S))
+    if dcd:
+        steps |= set(pk.he_rot_steps_for_sched(n, n1, n1, S, dcd, dcd))
     i = 1
     while i < n * n:
         steps |= {i % (n * n), (-i) % (n * n)}
@@ -763,7 +768,10 @@ def run_served(args):
         mix = workloads.served_job_mix(args.rate, args.duration, 5)
         s_rows = None
     ctx2 = pk.he_ctx_create(pk.he_params_default(2), 52)
-    _cov_keys(pk, ctx2, n, n1, 1 << 15)
+    _cov_keys(pk, ctx2, n, n1, 1 << 15, args.served_dcd)
+    # the covariance jobs' block products: decomposed at maximum diagonal
+    # served_dcd (Sec. 7 runs the covariance with n' = 32), or undecomposed
+    dk = dict(dcd_z=args.served_dcd, dcd_t=args.served_dcd)
     # client side, before the timed region: encrypt every input
     n_blk = max(1, sum(1 for _, kd in mix if kd == "xtx_block"))
     if s_rows:
@@ -810,16 +818,16 @@ def run_served(args):
     def submit(kind, idx, acc_id=1):
         if kind == "xtx_block":
             return pk.he_server_submit(srv, pk.HE_JOB_XTX_BLOCK, stream[idx], n=n, n1z=n1, n1t=n1, k=k,
-                                       s=s_rows, acc_id=acc_id)
+                                       s=s_rows, acc_id=acc_id, **dk)
         if kind == "matmul":
             a, b = mm[idx % len(mm)]
             return pk.he_server_submit(srv, pk.HE_JOB_MATMUL, [a, b], n=n, n1z=n1, n1t=n1)
         if kind == "covariance":
             return pk.he_server_submit(srv, pk.HE_JOB_COVARIANCE, cov_in, n=n, n1z=n1, n1t=n1, n_row_blocks=2, k=k,
-                                       s=256)
+                                       s=256, **dk)
         if kind == "covariance_large":
             return pk.he_server_submit(srv, pk.HE_JOB_COVARIANCE, cov_big, n=n, n1z=n1, n1t=n1,
-                                       n_row_blocks=big_rows // n, k=k, s=big_rows)
+                                       n_row_blocks=big_rows // n, k=k, s=big_rows, **dk)
         return pk.he_server_submit(srv, pk.HE_JOB_PCA, pca_in, n=n, k=k, l_E=args.components, l_P=args.pm_iters,
                                    axis=0, counts=counts, B2=2.0 ** 16, refresh_obj=(1 << 20) + (idx << 16))
 
@@ -836,8 +844,8 @@ def run_served(args):
     # warm-up (plaintext-diagonal caches of every shape and level), untimed
     warm = [(submit("matmul", 0), "matmul"), (submit("covariance", 0), "covariance"),
             (submit("xtx_block", 0, acc_id=0), "xtx_block")]
-    warm.append((pk.he_server_submit(srv, pk.HE_JOB_XTX_FINAL, [], ctx=ctx2, n=n, n1z=n1, n1t=n1, k=k, acc_id=0),
-                 "final"))
+    warm.append((pk.he_server_submit(srv, pk.HE_JOB_XTX_FINAL, [], ctx=ctx2, n=n, n1z=n1, n1t=n1, k=k, acc_id=0,
+                                     **dk), "final"))
     for kind, res in drain(warm).values():
         if not isinstance(res, Exception):
             for h in res:
@@ -862,7 +870,7 @@ def run_served(args):
         except pk.HeError as e:
             if e.code != pk.HE_ERR_ADMISSION:     # counted by the server's statistics
                 raise
-    fin = pk.he_server_submit(srv, pk.HE_JOB_XTX_FINAL, [], ctx=ctx2, n=n, n1z=n1, n1t=n1, k=k, acc_id=1)
+    fin = pk.he_server_submit(srv, pk.HE_JOB_XTX_FINAL, [], ctx=ctx2, n=n, n1z=n1, n1t=n1, k=k, acc_id=1, **dk)
     ids.append((fin, "final"))
     res = drain(ids)
     wall = time.perf_counter() - t0
@@ -926,7 +934,9 @@ def run_served(args):
                                "60+13x40, p 2x60"
                                % (args.rate, args.duration, s_rows, nb, -(-s_rows // n), args.components,
                                   "" if args.served_rows else ", 128x128 products"),
-                   "budget_gb": args.budget_gb, "max_batch": args.max_batch, "jobs": len(mix)},
+                   "budget_gb": args.budget_gb, "max_batch": args.max_batch, "jobs": len(mix),
+                   "covariance_products": "decomposed, n' = %d (Sec. 7)" % args.served_dcd if args.served_dcd
+                   else "undecomposed"},
         "check": dict(check, tol=1e-4)}), flush=True)
     for h in [x for blk in stream for x in blk] + [x for p in mm for x in p] + cov_in + cov_big + pca_in:
         pk.he_ct_free(h)
@@ -1297,6 +1307,8 @@ def main():
                     help="matmul / keyswitch: pin every MultSum launch to one variant (default: the tuner)")
     ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=120.0, help="served: seconds of arrivals")
+    ap.add_argument("--served-dcd", type=int, default=32,
+                    help="served: maximum diagonal of the covariance products' decomposition (0: undecomposed)")
     ap.add_argument("--served-rows", type=int, default=60000,
                     help="served: rows of the dataset streamed as 128-row blocks (0: the older mix with products)")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="served: device-memory budget of admitted jobs")
