@@ -149,6 +149,15 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
  * Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_ntt_variant(he_ctx *ctx, int variant);
 
+/* Rows per launch pair of the two-pass NTTs (both directions): with rows > 0
+ * a transform of many rows runs as chunks of that many rows, pass 0 then
+ * pass 1 per chunk, so that pass 1 finds pass 0's output in L2 when a
+ * chunk's rows fit there (0: every row in one pair of launches).  The tuner
+ * sets it per direction (all, 96 MiB or 48 MiB chunks) when it tunes the
+ * NTT; this call overrides it until the next tuning.  Words are identical.
+ * Errors: HE_ERR_ARG for a negative count. */
+int he_ctx_set_ntt_chunk(he_ctx *ctx, int rows);
+
 /* Newton composition for the PowerMethod's inverse square root (Sec. 7: two
  * InvSRT iterations composited into one that spends one level less).  With
  * on != 0, he_power_method / he_pca / PCA jobs on this context run each pair

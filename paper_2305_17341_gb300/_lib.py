@@ -88,6 +88,7 @@ SIGNATURES = {
     "he_ctx_set_autotune": [vp, ip],
     "he_ctx_set_multsum_variant": [vp, ip],
     "he_ctx_set_ntt_variant": [vp, ip],
+    "he_ctx_set_ntt_chunk": [vp, ip],
     "he_ctx_set_newton_composition": [vp, ip],
     "he_ctx_set_packed_refresh": [vp, ip],
     "he_autotune_log": [vp, ctypes.c_char_p, ip, P(ip)],
@@ -218,6 +219,11 @@ def he_ctx_set_multsum_variant(ctx, variant=-1):
 def he_ctx_set_ntt_variant(ctx, variant=-1):
     """Pins the NTT passes to one variant (-1: tuner)."""
     check(lib().he_ctx_set_ntt_variant(ctx, int(variant)))
+
+
+def he_ctx_set_ntt_chunk(ctx, rows=0):
+    """Rows per launch pair of the two-pass NTTs (0: all rows at once)."""
+    check(lib().he_ctx_set_ntt_chunk(ctx, int(rows)))
 
 
 def he_ctx_set_newton_composition(ctx, on=True):

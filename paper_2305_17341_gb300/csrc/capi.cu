@@ -290,6 +290,15 @@ int he_ctx_set_ntt_variant(he_ctx *ctx, int variant) {
     return HE_OK;
 }
 
+int he_ctx_set_ntt_chunk(he_ctx *ctx, int rows) {
+    if (!ctx) return fail(HE_ERR_ARG, "null context");
+    if (rows < 0) return fail(HE_ERR_ARG, "rows per launch must be >= 0");
+    Ctx &c = ctx->c;
+    cudaStreamSynchronize(c.stream);
+    c.ntt_chunk = c.ntt_chunk_inv = rows;
+    return HE_OK;
+}
+
 int he_ctx_set_newton_composition(he_ctx *ctx, int on) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
     ctx->c.newton_compose = on != 0;

@@ -189,6 +189,9 @@ struct Ctx {
     int ntt_minb = 2;        // CTAs per SM of the register-blocked forward NTT (2 or 3)
     int ntt_minb_inv = 2;    // and of the inverse NTT
     bool ntt_tuned = false;
+    // rows per launch pair of the two-pass NTTs (0: as many as the grid
+    // takes): chunks small enough that pass 1 reads pass 0's output from L2
+    int ntt_chunk = 0, ntt_chunk_inv = 0;
     // PowerMethod: pairs of Newton steps as five-level composites; the
     // vector's segments refreshed as one packed ciphertext
     bool newton_compose = false;

@@ -811,6 +811,43 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
             if (t < best) best = t, pick = minb;
         }
         (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = pick;
+        if (pick == 4) continue;   // the persistent passes take every row in one launch
+        // then the rows per launch pair: all, or chunks of 96 or 48 MiB
+        // whose pass-0 output pass 1 still finds in L2
+        int &chunk = dir == 0 ? ctx->ntt_chunk : ctx->ntt_chunk_inv;
+        int cpick = 0;
+        for (long mb : {0L, 96L, 48L}) {
+            const int c = mb ? (int)std::max(1L, (mb << 20) / (8L * ctx->N)) : 0;
+            if (c >= R) continue;
+            chunk = c;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; rep++) {
+                cudaEventRecord(a, st);
+                const long step = c ? c : R;
+                for (long r0 = 0; r0 < R; r0 += step) {
+                    const long nr = std::min(step, R - r0);
+                    u64 *d = scratch.p + r0 * (long)ctx->N;
+                    RowMap mm = m.shifted(r0);
+                    if (dir == 0) {
+                        fwd_both(ctx, d, nr, mm, st, none, nullptr);
+                    } else {
+                        if (ctx->logN - logN1 == 8) inv_pass<8, true>(ctx, d, nr, mm, st); else inv_pass<7, true>(ctx, d, nr, mm, st);
+                        if (logN1 == 8) inv_pass<8, false>(ctx, d, nr, mm, st); else inv_pass<7, false>(ctx, d, nr, mm, st);
+                    }
+                }
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                t = std::min(t, ms);
+            }
+            char line[112];
+            snprintf(line, sizeof line, "ntt %s logN %d rows %ld rows_per_launch %d ms %.4f\n",
+                     dir ? "inverse" : "forward", ctx->logN, R, c ? c : (int)R, t);
+            ctx->tune_log += line;
+            if (mb == 0 || t < best) best = t, cpick = c;
+        }
+        chunk = cpick;
     }
     ctx->ev_free.push_back(a);
     ctx->ev_free.push_back(b);
@@ -839,8 +876,9 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, 
         ctx->trace_end(1, e0, 2.0 * done * ctx->N * 8.0);
         return;
     }
-    for (long r0 = 0; r0 < rows; r0 += 65535) {
-        long nr = rows - r0 < 65535 ? rows - r0 : 65535;
+    const long chunk = ctx->ntt_chunk > 0 && ctx->ntt_chunk < 65535 ? ctx->ntt_chunk : 65535;
+    for (long r0 = 0; r0 < rows; r0 += chunk) {
+        long nr = rows - r0 < chunk ? rows - r0 : chunk;
         u64 *d = data + r0 * (long)ctx->N;
         RowMap m = rm.shifted(r0);
         ctx->n_launch += 2;
@@ -885,8 +923,9 @@ void ntt_fwd_subscale(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStre
         ctx->trace_end(1, e0, 2.0 * rows * ctx->N * 8.0);
         return;
     }
-    for (long r0 = 0; r0 < rows; r0 += 65535) {
-        long nr = rows - r0 < 65535 ? rows - r0 : 65535;
+    const long chunk = ctx->ntt_chunk > 0 && ctx->ntt_chunk < 65535 ? ctx->ntt_chunk : 65535;
+    for (long r0 = 0; r0 < rows; r0 += chunk) {
+        long nr = rows - r0 < chunk ? rows - r0 : chunk;
         u64 *d = data + r0 * (long)ctx->N;
         RowMap m = rm.shifted(r0);
         SubScale e = ep;
@@ -910,8 +949,9 @@ void ntt_inv(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st) 
     int logN = ctx->logN, logN1, C, R;
     split(logN, logN1, C, R);
     int N1 = 1 << logN1, N2 = 1 << (logN - logN1);
-    for (long r0 = 0; r0 < rows; r0 += 65535) {
-        long nr = rows - r0 < 65535 ? rows - r0 : 65535;
+    const long chunk = ctx->ntt_chunk_inv > 0 && ctx->ntt_chunk_inv < 65535 ? ctx->ntt_chunk_inv : 65535;
+    for (long r0 = 0; r0 < rows; r0 += chunk) {
+        long nr = rows - r0 < chunk ? rows - r0 : chunk;
         u64 *d = data + r0 * (long)ctx->N;
         RowMap m = rm.shifted(r0);
         ctx->n_launch += 2;

@@ -96,7 +96,7 @@ def test_context_options_need_a_context(built):
         with pytest.raises(_lib.HeError) as e:
             fn(None, True)
         assert e.value.code == _lib.HE_ERR_ARG
-    for fn in (_lib.he_ctx_set_multsum_variant, _lib.he_ctx_set_ntt_variant):
+    for fn in (_lib.he_ctx_set_multsum_variant, _lib.he_ctx_set_ntt_variant, _lib.he_ctx_set_ntt_chunk):
         with pytest.raises(_lib.HeError) as e:
             fn(None, 4)
         assert e.value.code == _lib.HE_ERR_ARG

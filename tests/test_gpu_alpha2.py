@@ -94,9 +94,12 @@ def test_alpha2_product_bit_exact_every_multsum_variant(a2, sched):
     oc = HMM(he).hmatmul(oa, ob, n, n1, n1, **kw)
     want = res(oc)
     try:
-        for v, nv in [(v, -1) for v in VARIANTS] + [(-1, nv) for nv in NTT_VARIANTS]:
+        for v, nv, chunk in ([(v, -1, None) for v in VARIANTS] + [(-1, nv, 0) for nv in NTT_VARIANTS] +
+                             [(-1, 3, 5)]):
             pk.he_ctx_set_multsum_variant(ctx, v)
             pk.he_ctx_set_ntt_variant(ctx, nv)
+            if chunk is not None:
+                pk.he_ctx_set_ntt_chunk(ctx, chunk)
             pk.he_counters(ctx, reset=True)
             gc = pk.he_hmatmul(ctx, ga, gb, n, n1, n1, **kw)
             cnt = pk.he_counters(ctx)
@@ -111,6 +114,7 @@ def test_alpha2_product_bit_exact_every_multsum_variant(a2, sched):
     finally:
         pk.he_ctx_set_multsum_variant(ctx, -1)
         pk.he_ctx_set_ntt_variant(ctx, -1)
+        pk.he_ctx_set_ntt_chunk(ctx, 0)
     for h in (ga, gb):
         pk.he_ct_free(h)
 

@@ -449,9 +449,10 @@ def test_hmatmul_degenerate_schedules_bit_exact(c1, n, n1z, n1t):
 
 @pytest.mark.parametrize("logN", [14, 15, 16])
 def test_ntt_variants_compute_the_same_words(lib, logN):
-    """Every NTT variant (one-tile CTAs at 2 or 3 per SM; persistent passes
-    fed by bulk copies: row tiles as contiguous copies, column tiles as 2-D
-    tensor-map boxes) gives the same forward words on a ragged number of
+    """Every NTT variant (one-tile CTAs at 2, 3 or 4 per SM, all rows at once
+    or in chunks of rows; persistent passes fed by bulk copies: row tiles as
+    contiguous copies, column tiles as 2-D tensor-map boxes) gives the same
+    forward words on a ragged number of
     rows cycling through q_0..q_L, p_0, p_1 (the 60-bit rows take the
     reducing butterflies), and the inverse returns the input."""
     import torch
@@ -463,17 +464,21 @@ def test_ntt_variants_compute_the_same_words(lib, logN):
         rng = np.random.default_rng(logN + 100)
         a = np.stack([rng.integers(0, primes[r % len(primes)], N, dtype=np.uint64) for r in range(R)])
         outs = {}
-        for v in (2, 3, 4):
+        # (variant, rows per launch pair): 7-row chunks leave a ragged last chunk of 2
+        for v, chunk in ((2, 0), (3, 0), (5, 0), (4, 0), (3, 7), (5, 7)):
             lib.he_ctx_set_ntt_variant(ctx, v)
+            lib.he_ctx_set_ntt_chunk(ctx, chunk)
             d = torch.from_numpy(a.view(np.int64).copy()).cuda()
             torch.cuda.synchronize()
             lib.he_ntt(ctx, d.data_ptr(), R, level)
-            outs[v] = d.cpu().numpy().view(np.uint64).copy()
+            outs[(v, chunk)] = d.cpu().numpy().view(np.uint64).copy()
             lib.he_ntt(ctx, d.data_ptr(), R, level, inverse=True)
-            assert np.array_equal(d.cpu().numpy().view(np.uint64), a), v
-        assert np.array_equal(outs[2], outs[3]) and np.array_equal(outs[2], outs[4])
+            assert np.array_equal(d.cpu().numpy().view(np.uint64), a), (v, chunk)
+        for key, o in outs.items():
+            assert np.array_equal(o, outs[(2, 0)]), key
         for r in range(R):
-            assert int(outs[4][r].max()) < primes[r % len(primes)]
+            assert int(outs[(4, 0)][r].max()) < primes[r % len(primes)]
     finally:
+        lib.he_ctx_set_ntt_chunk(ctx, 0)
         lib.he_ctx_set_ntt_variant(ctx, -1)
         lib.he_ctx_destroy(ctx)
