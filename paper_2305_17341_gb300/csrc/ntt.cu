@@ -811,7 +811,10 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
             if (t < best) best = t, pick = minb;
         }
         (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = pick;
-        if (pick == 4) continue;   // the persistent passes take every row in one launch
+        if (pick == 4) {   // the persistent passes take every row in one launch
+            ctx->ntt_chunk = 0;
+            continue;
+        }
         // then the rows per launch pair: all, or chunks of 96 or 48 MiB
         // whose pass-0 output pass 1 still finds in L2
         int &chunk = dir == 0 ? ctx->ntt_chunk : ctx->ntt_chunk_inv;
