@@ -960,6 +960,8 @@ def run_keyswitch(args):
         pk.he_ctx_set_multsum_variant(ctx, args.ms_variant)
     if args.ntt_variant is not None:
         pk.he_ctx_set_ntt_variant(ctx, args.ntt_variant)
+    if args.ntt_chunk is not None:
+        pk.he_ctx_set_ntt_chunk(ctx, args.ntt_chunk)
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
     R, B = args.rot_steps, args.batch
@@ -1160,6 +1162,8 @@ def run_ntt(args):
     ctx = pk.he_ctx_create(pk.he_params_default(2), 9)
     if args.ntt_variant is not None:
         pk.he_ctx_set_ntt_variant(ctx, args.ntt_variant)
+    if args.ntt_chunk is not None:
+        pk.he_ctx_set_ntt_chunk(ctx, args.ntt_chunk)
     tstream = torch.cuda.Stream()
     pk.he_ctx_set_stream(ctx, tstream.cuda_stream)
     q, p = pk.he_ctx_primes(ctx)
@@ -1197,7 +1201,8 @@ def run_ntt(args):
                       "peak_gbfly_s": peak, "peak_source": "measured lazy-Shoup butterfly microbenchmark",
                       "forward": out["forward"], "inverse": out["inverse"],
                       "config": {"workload": "%d rows x 2^16 words, primes of q 60+20x40 and p 2x60 cycled"
-                                             % R, "ntt_variant": args.ntt_variant}}), flush=True)
+                                             % R, "ntt_variant": args.ntt_variant, "ntt_chunk": args.ntt_chunk},
+                      "traffic_note": "DRAM bytes per transform from ncu on the same command"}), flush=True)
     pk.he_ctx_destroy(ctx)
 
 
@@ -1303,6 +1308,8 @@ def main():
     ap.add_argument("--rot-steps", type=int, default=8, help="keyswitch: rotation steps per ciphertext")
     ap.add_argument("--ntt-variant", type=int, default=None,
                     help="matmul / keyswitch / ntt: pin the NTT passes to one variant (default: the tuner)")
+    ap.add_argument("--ntt-chunk", type=int, default=None,
+                    help="ntt: rows per launch pair of the two-pass NTT (default: the tuner's)")
     ap.add_argument("--ms-variant", type=int, default=None,
                     help="matmul / keyswitch: pin every MultSum launch to one variant (default: the tuner)")
     ap.add_argument("--rate", type=float, default=4.0, help="served: arrivals per second")
