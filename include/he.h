@@ -136,8 +136,10 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * per SM (fewer registers), 48 the same with the prefetch of 16; 64, 65:
  * the rotations of a launch split over the CTA's warps, 1 or 2 per thread (a
  * thread's state no longer grows with the number of rotations; where that
- * number does not divide the 8 warps, as 32).  Errors: HE_ERR_ARG for other
- * values. */
+ * number does not divide the 8 warps, as 32); 80, 84: two adjacent
+ * coefficients per thread with 16-byte digit and key loads (cached /
+ * streaming digit loads), more CTAs per SM, for at most two rotations per
+ * launch (more: as 32 / 36).  Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without

@@ -680,6 +680,88 @@ __global__ void __launch_bounds__(256, OCC ? OCC : G <= 2 ? 4 : G <= 5 ? 2 : 1) 
     }
 }
 
+// The thread-per-word MultSum with two adjacent coefficients per thread:
+// every digit and key load is 16 bytes (ulonglong2), so twice the bytes are
+// in flight per load at the same number of resident warps.  For launches of
+// at most two rotations (the per-thread accumulators double).
+template <int G, bool STREAM, int OCC>
+__global__ void __launch_bounds__(256, OCC) k_multsum_vec(MultiKeys<G> mk, const u64 *digits, int B, int BI, int level,
+                                                          int alpha, int L, int ndig, int nprimes, int logN,
+                                                          const ModQ *mods, const u64 *c0, long c0s,
+                                                          const ShoupPair *Pmod) {
+    const int N = 1 << logN;
+    const int XW = 256 / BI;
+    const int tx = threadIdx.x % XW, ti = threadIdx.x / XW;
+    const int y = 2 * (blockIdx.x * XW + tx);
+    const int r = blockIdx.y;
+    const int b = blockIdx.z * BI + ti;
+    if (b >= B || y >= N) return;
+    const int rows = level + 1 + alpha;
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ m = mods[kr];
+    const long dstride = (long)rows * N;
+    const ulonglong2 *dp = (const ulonglong2 *)(digits + (long)b * ndig * dstride + (long)r * N + y);
+    const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    U128 acc[2][2 * G];   // [coefficient][key, polynomial]
+    if (m.q < (1ull << 42)) {
+        u32 x0[2][2 * G], x1[2][2 * G], x2[2][2 * G];
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) x0[c][k] = 0, x1[c][k] = 0, x2[c][k] = 0;
+        for (int d = 0; d < ndig; d++) {
+            const ulonglong2 v = STREAM ? __ldcs(dp + (long)d * dstride / 2) : __ldg(dp + (long)d * dstride / 2);
+#pragma unroll
+            for (int k = 0; k < G; k++) {
+                const ulonglong2 *kp = (const ulonglong2 *)(mk.key[k] + (long)d * kd + koff);
+                const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
+                mac96(x0[0][2 * k], x1[0][2 * k], x2[0][2 * k], v.x, k0.x);
+                mac96(x0[1][2 * k], x1[1][2 * k], x2[1][2 * k], v.y, k0.y);
+                mac96(x0[0][2 * k + 1], x1[0][2 * k + 1], x2[0][2 * k + 1], v.x, k1.x);
+                mac96(x0[1][2 * k + 1], x1[1][2 * k + 1], x2[1][2 * k + 1], v.y, k1.y);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) acc[c][k] = U128{((u64)x1[c][k] << 32) | x0[c][k], x2[c][k]};
+    } else {
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int k = 0; k < 2 * G; k++) acc[c][k] = U128{0, 0};
+        for (int d = 0; d < ndig; d++) {
+            const ulonglong2 v = STREAM ? __ldcs(dp + (long)d * dstride / 2) : __ldg(dp + (long)d * dstride / 2);
+#pragma unroll
+            for (int k = 0; k < G; k++) {
+                const ulonglong2 *kp = (const ulonglong2 *)(mk.key[k] + (long)d * kd + koff);
+                const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
+                mac128(acc[0][2 * k], v.x, k0.x);
+                mac128(acc[1][2 * k], v.y, k0.y);
+                mac128(acc[0][2 * k + 1], v.x, k1.x);
+                mac128(acc[1][2 * k + 1], v.y, k1.y);
+            }
+        }
+    }
+    const bool with_c0 = c0 && r <= level;
+    const ShoupPair w = with_c0 ? Pmod[r] : ShoupPair{0, 0};
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const int yc = y + c;
+        u64 pc0 = 0;
+        if (with_c0) pc0 = shoup(c0[b * c0s + (long)r * N + yc], w.w, w.wp, m.q);
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            u64 o0 = redc(acc[c][2 * k].lo, acc[c][2 * k].hi, m), o1 = redc(acc[c][2 * k + 1].lo, acc[c][2 * k + 1].hi, m);
+            if (with_c0) o0 = addmod(o0, pc0, m.q);
+            const int x = mk.ginv[k] == 1u ? yc : auto_index(yc, mk.ginv[k], logN);
+            u64 *ob = mk.out[k] + (long)b * 2 * rows * N;
+            ob[(long)r * N + x] = o0;
+            ob[(long)(rows + r) * N + x] = o1;
+        }
+    }
+}
+
 // The same MultSum with the G keys split over the CTA's warps: 8 warps =
 // (G / KG) key groups x BI = 8 KG / G items, 32 coefficients of one row per
 // CTA; each thread accumulates KG keys of one item, so its state (2 KG
@@ -822,6 +904,29 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
         mk.ginv[k] = inv & (M - 1);
     }
+    if ((v == 80 || v == 84) && G <= 2) {
+        // two coefficients per thread, 16-byte loads, more resident CTAs
+        if constexpr (G <= 2) {
+            constexpr int OCCV = G == 1 ? 5 : 3;
+            int BI;
+            bool stream;
+            multsum_variant(0, B, BI, stream);
+            stream = v == 84;
+            const int rows = level + 1 + c->alpha, XW = 256 / BI;
+            dim3 grid((unsigned)((c->N / 2 + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
+            if (stream)
+                k_multsum_vec<G, true, OCCV><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L,
+                                                                   c->ndig(level), c->nprimes, c->logN, c->d_mod, c0,
+                                                                   c0s, c->d_Pmod);
+            else
+                k_multsum_vec<G, false, OCCV><<<grid, 256, 0, st>>>(mk, digits, B, BI, level, c->alpha, c->L,
+                                                                    c->ndig(level), c->nprimes, c->logN, c->d_mod, c0,
+                                                                    c0s, c->d_Pmod);
+            c->n_launch++;
+            return;
+        }
+    }
+    if (v == 80 || v == 84) v = v == 80 ? 32 : 36;   // more than two rotations: the one-coefficient kernel
     if (v == 64 || v == 65) {
         // keys split over warps: KG = 1 (64) or 2 (65, G even)
         const int rows = level + 1 + c->alpha;
@@ -934,7 +1039,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 48, 64, 65, 8, 9, 10}) {
+                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 48, 64, 65, 80, 84, 8, 9, 10}) {
                     int BI;
                     bool stream;
                     multsum_variant(cand & 15, B, BI, stream);
