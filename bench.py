@@ -1191,11 +1191,14 @@ def run_ntt(args):
     out = {}
     for c, name in ((1, "forward"), (2, "inverse")):
         t = tr[c]
-        avg = t["ms"] / t["count"] / 1e3
+        # per transform of all R rows (a transform may run as several
+        # launch pairs when the rows are chunked)
+        avg = t["ms"] / args.steps / 1e3
         bfly = R * (N // 2) * 16 / avg / 1e9
         out[name] = {"avg_us": avg * 1e6, "gbfly_s": bfly, "frac_of_measured_peak": bfly / peak,
-                     "algorithmic_gbs": t["bytes"] / t["count"] / avg / 1e9,
-                     "hbm_frac_of_measured": t["bytes"] / t["count"] / avg / 1e9 / hbm}
+                     "launch_pairs_per_transform": t["count"] / args.steps,
+                     "algorithmic_gbs": t["bytes"] / args.steps / avg / 1e9,
+                     "hbm_frac_of_measured": t["bytes"] / args.steps / avg / 1e9 / hbm}
     print(json.dumps({"metric": "NTT butterflies/s (N=2^16, %d rows)" % R, "value": out["forward"]["gbfly_s"],
                       "unit": "Gbutterfly/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
                       "peak_gbfly_s": peak, "peak_source": "measured lazy-Shoup butterfly microbenchmark",
