@@ -147,7 +147,10 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
  * Variants compute identical words; this is for tests and measurement.
  * 2, 3, 5: one 8-stage tile per CTA, 2, 3 or 4 CTAs per SM (forward and
  * inverse); 4: forward passes on persistent CTAs whose tiles arrive through
- * bulk asynchronous copies (a producer warp, two buffers), inverse as 3.
+ * bulk asynchronous copies (a producer warp, two buffers), inverse as 3;
+ * 6 (N = 2^16; otherwise as 3): the forward transform of a limb in one pass
+ * by a cluster of 8 CTAs exchanging through distributed shared memory (one
+ * read and one write of every word), inverse as 3.
  * Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_ntt_variant(he_ctx *ctx, int variant);
 

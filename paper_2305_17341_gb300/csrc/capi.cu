@@ -276,7 +276,7 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
 
 int he_ctx_set_ntt_variant(he_ctx *ctx, int variant) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
-    if (variant != -1 && (variant < 2 || variant > 5)) return fail(HE_ERR_ARG, "NTT variant -1, 2, 3, 4 or 5");
+    if (variant != -1 && (variant < 2 || variant > 6)) return fail(HE_ERR_ARG, "NTT variant -1 or 2..6");
     Ctx &c = ctx->c;
     cudaStreamSynchronize(c.stream);
     if (variant < 0) {
@@ -284,8 +284,8 @@ int he_ctx_set_ntt_variant(he_ctx *ctx, int variant) {
         c.ntt_minb = c.ntt_minb_inv = 2;
     } else {
         c.ntt_tuned = true;
-        c.ntt_minb = variant;
-        c.ntt_minb_inv = variant == 4 ? 3 : variant;   // the inverse has no bulk-copy variant
+        c.ntt_minb = variant == 6 && c.logN != 16 ? 3 : variant;   // the cluster pass is for N = 2^16
+        c.ntt_minb_inv = variant == 4 || variant == 6 ? 3 : variant;   // forward-only variants
     }
     return HE_OK;
 }

@@ -559,6 +559,230 @@ __global__ void __launch_bounds__(NTC_THREADS, 2)
     }
 }
 
+// ---------------------------------------- one pass per limb, 8-CTA clusters
+// N = 2^16: the 8 CTAs of a cluster transform one limb with a single read
+// and a single write of it.  CTA c loads, from each eighth e of the limb,
+// the 1024 words [e 8192 + 1024 c, + 1024) (8 bulk copies of 8 KiB) and
+// runs the first three stages (spans N/2, N/4, N/8: the eighths of one
+// position) in registers; element (e, p) then belongs to eighth e and is
+// stored straight into CTA e's shared memory (distributed shared memory)
+// at index 1024 c + p.  After a cluster barrier CTA r holds eighth r and runs
+// its 13 remaining stages: 5 in registers on elements t + 256 k, 5 on
+// a + 8 k + 256 b, 3 on 32 t + i, each round a shared-memory transpose;
+// eighth r's stage-s group g uses twiddle psi^brv(2^s (8 + r) + g).  The
+// words are those of the two-pass kernels (same butterflies in the same
+// stage order, same lazy bounds: 16 stages from inputs below 4q).  Shared
+// rows hold one pad word per 32.  Every CTA passes both cluster barriers on
+// every path (a bounded load wait that runs out only flags the error).
+constexpr int NCL = 8, NCL_EIGHTH = 8192, NCL_SMEM_WORDS = NCL_EIGHTH + NCL_EIGHTH / 32;
+
+__device__ __forceinline__ int ncl_pad(int l) { return l + (l >> 5); }
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ u32 cluster_rank() {
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of `local` (a shared address of this CTA) in CTA `rank`'s shared memory.
+__device__ __forceinline__ u32 cluster_map(u32 local, u32 rank) {
+    u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_u64(u32 addr, u64 v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+template <bool RED>
+__device__ __forceinline__ void ncl_bf(u64 &x, u64 &y, const ulonglong2 w, u64 q) {
+    if (RED) bf_fwd(x, y, w.x, w.y, q);
+    else bf_fwd_nored(x, y, w.x, w.y, q);
+}
+
+template <bool RED>
+__device__ __forceinline__ void ncl_local(u64 *buf, const ulonglong2 *w2_, int r, int t, u64 q) {
+    u64 x[32];
+    // round A: l = t + 256 k, spans 4096 .. 256 (stages s = 0 .. 4 of the eighth)
+#pragma unroll
+    for (int k = 0; k < 32; k++) x[k] = buf[ncl_pad(t + 256 * k)];
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int h = 16 >> s;
+#pragma unroll
+        for (int k = 0; k < 32; k++)
+            if (!(k & h)) ncl_bf<RED>(x[k], x[k + h], __ldg(w2_ + ((8 + r) << s) + (k >> (5 - s))), q);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; k++) buf[ncl_pad(t + 256 * k)] = x[k];
+    __syncthreads();
+    // round B: l = a + 8 k + 256 b, spans 128 .. 8 (stages 5 .. 9)
+    const int a = t & 7, b = t >> 3;
+#pragma unroll
+    for (int k = 0; k < 32; k++) x[k] = buf[ncl_pad(a + 8 * k + 256 * b)];
+#pragma unroll
+    for (int sp = 0; sp < 5; sp++) {
+        const int h = 16 >> sp;
+        const long base = ((long)(8 + r) << (5 + sp)) + ((long)b << sp);
+#pragma unroll
+        for (int k = 0; k < 32; k++)
+            if (!(k & h)) ncl_bf<RED>(x[k], x[k + h], __ldg(w2_ + base + (k >> (5 - sp))), q);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; k++) buf[ncl_pad(a + 8 * k + 256 * b)] = x[k];
+    __syncthreads();
+    // round C: l = 32 t + i, spans 4, 2, 1 (stages 10 .. 12)
+#pragma unroll
+    for (int i = 0; i < 32; i++) x[i] = buf[ncl_pad(32 * t + i)];
+#pragma unroll
+    for (int s = 10; s < 13; s++) {
+        const int span = 1 << (12 - s);
+        const long base = (long)(8 + r) << s;
+#pragma unroll
+        for (int i = 0; i < 32; i++)
+            if (!(i & span)) ncl_bf<RED>(x[i], x[i + span], __ldg(w2_ + base + ((32 * t + i) >> (13 - s))), q);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; i++) buf[ncl_pad(32 * t + i)] = x[i];
+    __syncthreads();
+}
+
+template <bool SUBSC>
+__global__ void __launch_bounds__(256, 2) k_ntt_fwd_cluster(u64 *data, RowMap rm, const ModQ *mods,
+                                                            const ulonglong2 *tw2, RowSkip skip, SubScale ep,
+                                                            int *err) {
+    constexpr int N = 1 << 16;
+    extern __shared__ __align__(128) u64 ncl_buf[];   // NCL_SMEM_WORDS
+    __shared__ __align__(8) u64 full;
+    const long row = blockIdx.y;
+    if (skip.skip(row)) return;   // uniform over the cluster: no cluster barrier is taken
+    const int t = threadIdx.x;
+    const u32 c = cluster_rank();
+    const int pidx = rm.at(row);
+    const u64 q = mods[pidx].q, wone = mods[pidx].wone;
+    const ulonglong2 *w2_ = tw2 + (long)pidx * N;
+    u64 *rowp = data + row * (long)N;
+    if (t == 0) {
+        bc_bar_init(&full, 1);
+        bc_init_fence();
+    }
+    __syncthreads();
+    if (t == 0) {
+        bc_expect_tx(&full, 8 * 1024 * 8);
+        for (int e = 0; e < 8; e++) bc_bulk(ncl_buf + e * 1024, rowp + e * NCL_EIGHTH + c * 1024, 8192, &full);
+    }
+    const bool loaded = bc_wait(&full, 0);
+    if (!loaded) atomicExch(err, 1);   // the words are garbage then; every barrier is still taken
+    const bool red = q >= (1ull << 57);   // uniform over the cluster
+    // stages 1-3 on the eighths of positions p = t + 256 j
+    u64 x[4][8];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int e = 0; e < 8; e++) x[j][e] = ncl_buf[e * 1024 + t + 256 * j];
+    const ulonglong2 w1 = __ldg(w2_ + 1), w2 = __ldg(w2_ + 2), w3 = __ldg(w2_ + 3), w4 = __ldg(w2_ + 4),
+                     w5 = __ldg(w2_ + 5), w6 = __ldg(w2_ + 6), w7 = __ldg(w2_ + 7);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        if (red) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) ncl_bf<true>(x[j][e], x[j][e + 4], w1, q);
+            ncl_bf<true>(x[j][0], x[j][2], w2, q), ncl_bf<true>(x[j][1], x[j][3], w2, q);
+            ncl_bf<true>(x[j][4], x[j][6], w3, q), ncl_bf<true>(x[j][5], x[j][7], w3, q);
+            ncl_bf<true>(x[j][0], x[j][1], w4, q), ncl_bf<true>(x[j][2], x[j][3], w5, q);
+            ncl_bf<true>(x[j][4], x[j][5], w6, q), ncl_bf<true>(x[j][6], x[j][7], w7, q);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) ncl_bf<false>(x[j][e], x[j][e + 4], w1, q);
+            ncl_bf<false>(x[j][0], x[j][2], w2, q), ncl_bf<false>(x[j][1], x[j][3], w2, q);
+            ncl_bf<false>(x[j][4], x[j][6], w3, q), ncl_bf<false>(x[j][5], x[j][7], w3, q);
+            ncl_bf<false>(x[j][0], x[j][1], w4, q), ncl_bf<false>(x[j][2], x[j][3], w5, q);
+            ncl_bf<false>(x[j][4], x[j][5], w6, q), ncl_bf<false>(x[j][6], x[j][7], w7, q);
+        }
+    }
+    // every CTA has its words in registers before anyone writes into its buffer
+    cluster_sync_all();
+    const u32 base = bc_smem(ncl_buf);
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const u32 rb = cluster_map(base, (u32)e);
+#pragma unroll
+        for (int j = 0; j < 4; j++) st_cluster_u64(rb + 8u * (u32)ncl_pad((int)c * 1024 + t + 256 * j), x[j][e]);
+    }
+    // every CTA's eighth has arrived
+    cluster_sync_all();
+    if (red) ncl_local<true>(ncl_buf, w2_, (int)c, t, q);
+    else ncl_local<false>(ncl_buf, w2_, (int)c, t, q);
+    // exact residues, coalesced stores of eighth c (or the fused epilogue)
+    const long off0 = (long)c * NCL_EIGHTH;
+    if (SUBSC) {
+        const long arow = ep.row0 + row;
+        const long it = arow / ep.rows_per_item;
+        const int rr = (int)(arow - it * ep.rows_per_item);
+        const ShoupPair wr = ep.w[rr];
+        const long off = (long)rr * N + off0;
+        const u64 *up = ep.u + it * ep.us + off;
+        u64 *op = ep.out + it * ep.os + off;
+        const u64 *ap = ep.add ? ep.add + it * ep.as + off : nullptr;
+#pragma unroll 8
+        for (int k = 0; k < 32; k++) {
+            const int l = t + 256 * k;
+            const u64 sv = ncl_buf[ncl_pad(l)];
+            const u64 v = red ? reduce4q(sv, q) : reduce_any(sv, q, wone);
+            u64 o = shoup(submod(up[l], v, q), wr.w, wr.wp, q);
+            if (ap) o = addmod(o, ap[l], q);
+            op[l] = o;
+        }
+    } else {
+#pragma unroll 8
+        for (int k = 0; k < 32; k++) {
+            const int l = t + 256 * k;
+            const u64 sv = ncl_buf[ncl_pad(l)];
+            rowp[off0 + l] = red ? reduce4q(sv, q) : reduce_any(sv, q, wone);
+        }
+    }
+    // a load that ran out of its wait may still land: wait for it (bounded)
+    // before this CTA's shared memory is given back
+    if (!loaded && t == 0) bc_wait(&full, 0);
+}
+
+// Launches the cluster kernel over nr rows (nr <= 65535); false if no
+// cluster of 8 such CTAs fits on the device.
+template <bool SUBSC>
+static bool ntt_cluster_launch(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk,
+                               const SubScale &e) {
+    static int ok[64];   // 0 unknown, 1 fits, -1 does not
+    const int dev = ctx->device & 63;
+    const size_t smem = (size_t)NCL_SMEM_WORDS * 8;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NCL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(NCL, (unsigned)nr, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (!ok[dev]) {
+        cudaFuncSetAttribute(k_ntt_fwd_cluster<SUBSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_ntt_fwd_cluster<SUBSC>, &cfg) != cudaSuccess) cudaGetLastError();
+        ok[dev] = nc > 0 ? 1 : -1;
+    }
+    if (ok[dev] < 0) return false;
+    cudaLaunchKernelEx(&cfg, k_ntt_fwd_cluster<SUBSC>, d, m, (const ModQ *)ctx->d_mod,
+                       (const ulonglong2 *)ctx->d_psi2, sk, e, ctx->d_err);
+    return true;
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -736,14 +960,23 @@ static void split(int logN, int &logN1, int &C, int &R) {
     if (R > N1) R = N1;
 }
 
-// Both forward passes over nr rows (at most 65535 for the one-tile CTAs;
-// any number for the persistent ones), with the variant the context picked:
-// ntt_minb 2 or 3 CTAs per SM of one-tile CTAs, 4 the persistent passes fed
-// by bulk copies.
+// Both forward passes over nr rows (at most 65535 for the one-tile CTAs
+// and the clusters; any number for the persistent ones), with the variant
+// the context picked: ntt_minb 2, 3 or 5 (4 CTAs per SM) for one-tile CTAs,
+// 4 the persistent passes fed by bulk copies, 6 one pass per limb over
+// 8-CTA clusters (N = 2^16).
 static void fwd_both(Ctx *ctx, u64 *d, long nr, const RowMap &m, cudaStream_t st, const RowSkip &sk,
                      const SubScale *ep) {
     int logN1, C, R;
     split(ctx->logN, logN1, C, R);
+    if (ctx->ntt_minb == 6 && ctx->logN == 16) {
+        // one pass per limb over 8-CTA clusters (N = 2^16)
+        const SubScale e = ep ? *ep : SubScale();
+        const bool done = ep ? ntt_cluster_launch<true>(ctx, d, nr, m, st, sk, e)
+                             : ntt_cluster_launch<false>(ctx, d, nr, m, st, sk, e);
+        if (done) return;
+        ctx->ntt_minb = 3;   // no cluster fits: the one-tile passes from now on
+    }
     const bool rows8 = ctx->logN - logN1 == 8;
     if (ctx->ntt_minb == 4) {
         if (logN1 == 8) fwd_pass_tma<8, false>(ctx, d, nr, m, st, sk, nullptr);
@@ -783,8 +1016,9 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
     for (int dir = 0; dir < 2; dir++) {
         float best = 1e30f;
         int pick = 2;
-        for (int minb : {2, 3, 5, 4}) {
-            if (dir == 1 && minb == 4) continue;   // 4: the forward passes fed by bulk copies
+        for (int minb : {2, 3, 5, 4, 6}) {
+            if (dir == 1 && (minb == 4 || minb == 6)) continue;   // 4, 6: forward only
+            if (minb == 6 && ctx->logN != 16) continue;            // the cluster pass is for N = 2^16
             (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = minb;
             float t = 1e30f;
             for (int rep = 0; rep < 3; rep++) {
@@ -804,14 +1038,15 @@ static void tune_ntt(Ctx *ctx, cudaStream_t st) {
             }
             char line[112];
             snprintf(line, sizeof line, "ntt %s logN %d rows %ld %s %d ms %.4f\n", dir ? "inverse" : "forward",
-                     ctx->logN, R, minb == 4 ? "bulk-copy persistent, ctas_per_sm" : "ctas_per_sm",
-                     minb == 4 ? 2 : minb == 5 ? 4 : minb,
-                     t);
+                     ctx->logN, R,
+                     minb == 4 ? "bulk-copy persistent, ctas_per_sm"
+                               : minb == 6 ? "one pass, 8-CTA clusters, ctas_per_sm" : "ctas_per_sm",
+                     minb == 4 ? 2 : minb == 5 ? 4 : minb == 6 ? 2 : minb, t);
             ctx->tune_log += line;
             if (t < best) best = t, pick = minb;
         }
         (dir == 0 ? ctx->ntt_minb : ctx->ntt_minb_inv) = pick;
-        if (pick == 4) {   // the persistent passes take every row in one launch
+        if (pick == 4 || pick == 6) {   // these take every row in one launch (no chunks)
             ctx->ntt_chunk = 0;
             continue;
         }
@@ -896,8 +1131,7 @@ void ntt_fwd(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStream_t st, 
                 done = 0;
                 for (long r = 0; r < nr; r++) done += !sk.skip(r);
             }
-            if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st, sk); else fwd_pass<7, false>(ctx, d, nr, m, st, sk);
-            if (logN - logN1 == 8) fwd_pass<8, true>(ctx, d, nr, m, st, sk); else fwd_pass<7, true>(ctx, d, nr, m, st, sk);
+            fwd_both(ctx, d, nr, m, st, sk, nullptr);
             // algorithmic bytes: every transformed word read and written once
             // (the two passes move twice that)
             ctx->trace_end(1, e0, 2.0 * done * ctx->N * 8.0);
@@ -937,8 +1171,7 @@ void ntt_fwd_subscale(Ctx *ctx, u64 *data, long rows, const RowMap &rm, cudaStre
         cudaEvent_t e0;
         ctx->trace_begin(1, e0);
         RowSkip none;
-        if (logN1 == 8) fwd_pass<8, false>(ctx, d, nr, m, st, none); else fwd_pass<7, false>(ctx, d, nr, m, st, none);
-        if (logN - logN1 == 8) fwd_pass<8, true>(ctx, d, nr, m, st, none, &e); else fwd_pass<7, true>(ctx, d, nr, m, st, none, &e);
+        fwd_both(ctx, d, nr, m, st, none, &e);
         // algorithmic bytes of the transform: every word read and written once
         // (the fused epilogue's read of u is not counted, so butterflies per
         // traced byte stay those of a plain transform)

@@ -451,7 +451,8 @@ def test_hmatmul_degenerate_schedules_bit_exact(c1, n, n1z, n1t):
 def test_ntt_variants_compute_the_same_words(lib, logN):
     """Every NTT variant (one-tile CTAs at 2, 3 or 4 per SM, all rows at once
     or in chunks of rows; persistent passes fed by bulk copies: row tiles as
-    contiguous copies, column tiles as 2-D tensor-map boxes) gives the same
+    contiguous copies, column tiles as 2-D tensor-map boxes; one pass per
+    limb by an 8-CTA cluster at N = 2^16, as 3 below) gives the same
     forward words on a ragged number of
     rows cycling through q_0..q_L, p_0, p_1 (the 60-bit rows take the
     reducing butterflies), and the inverse returns the input."""
@@ -465,7 +466,7 @@ def test_ntt_variants_compute_the_same_words(lib, logN):
         a = np.stack([rng.integers(0, primes[r % len(primes)], N, dtype=np.uint64) for r in range(R)])
         outs = {}
         # (variant, rows per launch pair): 7-row chunks leave a ragged last chunk of 2
-        for v, chunk in ((2, 0), (3, 0), (5, 0), (4, 0), (3, 7), (5, 7)):
+        for v, chunk in ((2, 0), (3, 0), (5, 0), (4, 0), (6, 0), (3, 7), (5, 7), (6, 7)):
             lib.he_ctx_set_ntt_variant(ctx, v)
             lib.he_ctx_set_ntt_chunk(ctx, chunk)
             d = torch.from_numpy(a.view(np.int64).copy()).cuda()
@@ -478,7 +479,37 @@ def test_ntt_variants_compute_the_same_words(lib, logN):
             assert np.array_equal(o, outs[(2, 0)]), key
         for r in range(R):
             assert int(outs[(4, 0)][r].max()) < primes[r % len(primes)]
+            assert int(outs[(6, 0)][r].max()) < primes[r % len(primes)]
     finally:
         lib.he_ctx_set_ntt_chunk(ctx, 0)
         lib.he_ctx_set_ntt_variant(ctx, -1)
         lib.he_ctx_destroy(ctx)
+
+
+def test_full_size_product_same_words_under_every_ntt_variant(c2):
+    """The benchmarked shape (128x128, N = 2^16, level 20, two special
+    primes): the product's residues are the same whether the forward NTTs
+    run as two passes of one-tile CTAs, as persistent bulk-copy passes or in
+    one pass per limb by 8-CTA clusters exchanging through distributed
+    shared memory (Decompose with its skipped rows, the fused ModDown and
+    Rescale epilogues)."""
+    lib, ctx = c2
+    n, n1 = 128, 16
+    lib.he_keygen(ctx, lib.he_rot_steps_for_matmul(n, n1, n1, 1 << 15), want_relin=True)
+    rng = np.random.default_rng(19)
+    A, B = rng.uniform(-1, 1, (n, n)), rng.uniform(-1, 1, (n, n))
+    a, b = lib.he_encrypt_matrix(ctx, A, 20, 90), lib.he_encrypt_matrix(ctx, B, 20, 91)
+    outs = {}
+    try:
+        for v in (3, 6, 4):
+            lib.he_ctx_set_ntt_variant(ctx, v)
+            o = lib.he_hmatmul(ctx, a, b, n, n1, n1)
+            outs[v] = lib.he_ct_export(ctx, o)
+            if v == 6:
+                assert np.abs(lib.he_decrypt_matrix(ctx, o, n, n) - A @ B).max() < TOL
+            lib.he_ct_free(o)
+    finally:
+        lib.he_ctx_set_ntt_variant(ctx, -1)
+    assert np.array_equal(outs[6], outs[3]) and np.array_equal(outs[4], outs[3])
+    lib.he_ct_free(a)
+    lib.he_ct_free(b)
