@@ -139,7 +139,8 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * number does not divide the 8 warps, as 32); 80, 84: two adjacent
  * coefficients per thread with 16-byte digit and key loads (cached /
  * streaming digit loads), more CTAs per SM, for at most two rotations per
- * launch (more: as 32 / 36).  Errors: HE_ERR_ARG for other values. */
+ * launch (more: as 32 / 36); 96, 97: as 64, 65 with two coefficients per
+ * thread and 16-byte loads.  Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without

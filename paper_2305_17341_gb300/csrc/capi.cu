@@ -268,8 +268,8 @@ int he_ctx_set_multsum_variant(he_ctx *ctx, int variant) {
     if (!ctx) return fail(HE_ERR_ARG, "null context");
     if (variant < -1 ||
         (variant > 10 && variant != 16 && variant != 20 && variant != 32 && variant != 36 && variant != 48 &&
-         variant != 64 && variant != 65 && variant != 80 && variant != 84))
-        return fail(HE_ERR_ARG, "MultSum variant -1..10, 16, 20, 32, 36, 48, 64, 65, 80 or 84");
+         variant != 64 && variant != 65 && variant != 80 && variant != 84 && variant != 96 && variant != 97))
+        return fail(HE_ERR_ARG, "MultSum variant -1..10, 16, 20, 32, 36, 48, 64, 65, 80, 84, 96 or 97");
     ctx->c.force_multsum = variant;
     return HE_OK;
 }

@@ -838,6 +838,88 @@ __global__ void __launch_bounds__(256, OCC) k_multsum_split(const __grid_constan
     }
 }
 
+// The key-split MultSum with two adjacent coefficients per thread and
+// 16-byte digit and key loads (each warp covers 64 coefficients).
+template <int G, int KG, int OCC>
+__global__ void __launch_bounds__(256, OCC) k_multsum_splitv(const __grid_constant__ MultiKeys<G> mk,
+                                                             const u64 *digits, int B, int level, int alpha, int L,
+                                                             int ndig, int nprimes, int logN, const ModQ *mods,
+                                                             const u64 *c0, long c0s, const ShoupPair *Pmod) {
+    constexpr int NGRP = G / KG, BI = 8 / NGRP;
+    const int N = 1 << logN;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int kg0 = (wid / BI) * KG, bi = wid % BI;
+    const int y = 2 * (blockIdx.x * 32 + lane);
+    const int r = blockIdx.y;
+    const int b = blockIdx.z * BI + bi;
+    if (b >= B || y >= N) return;
+    const int rows = level + 1 + alpha;
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ m = mods[kr];
+    const long dstride = (long)rows * N;
+    const ulonglong2 *dp = (const ulonglong2 *)(digits + (long)b * ndig * dstride + (long)r * N + y);
+    const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    U128 acc[2][2 * KG];
+    if (m.q < (1ull << 42)) {
+        u32 x0[2][2 * KG], x1[2][2 * KG], x2[2][2 * KG];
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int k = 0; k < 2 * KG; k++) x0[c][k] = 0, x1[c][k] = 0, x2[c][k] = 0;
+        for (int d = 0; d < ndig; d++) {
+            const ulonglong2 v = __ldg(dp + (long)d * dstride / 2);
+#pragma unroll
+            for (int k = 0; k < KG; k++) {
+                const ulonglong2 *kp = (const ulonglong2 *)(mk.key[kg0 + k] + (long)d * kd + koff);
+                const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
+                mac96(x0[0][2 * k], x1[0][2 * k], x2[0][2 * k], v.x, k0.x);
+                mac96(x0[1][2 * k], x1[1][2 * k], x2[1][2 * k], v.y, k0.y);
+                mac96(x0[0][2 * k + 1], x1[0][2 * k + 1], x2[0][2 * k + 1], v.x, k1.x);
+                mac96(x0[1][2 * k + 1], x1[1][2 * k + 1], x2[1][2 * k + 1], v.y, k1.y);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int k = 0; k < 2 * KG; k++) acc[c][k] = U128{((u64)x1[c][k] << 32) | x0[c][k], x2[c][k]};
+    } else {
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int k = 0; k < 2 * KG; k++) acc[c][k] = U128{0, 0};
+        for (int d = 0; d < ndig; d++) {
+            const ulonglong2 v = __ldg(dp + (long)d * dstride / 2);
+#pragma unroll
+            for (int k = 0; k < KG; k++) {
+                const ulonglong2 *kp = (const ulonglong2 *)(mk.key[kg0 + k] + (long)d * kd + koff);
+                const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
+                mac128(acc[0][2 * k], v.x, k0.x);
+                mac128(acc[1][2 * k], v.y, k0.y);
+                mac128(acc[0][2 * k + 1], v.x, k1.x);
+                mac128(acc[1][2 * k + 1], v.y, k1.y);
+            }
+        }
+    }
+    const bool with_c0 = c0 && r <= level;
+    const ShoupPair w = with_c0 ? Pmod[r] : ShoupPair{0, 0};
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const int yc = y + c;
+        u64 pc0 = 0;
+        if (with_c0) pc0 = shoup(c0[b * c0s + (long)r * N + yc], w.w, w.wp, m.q);
+#pragma unroll
+        for (int k = 0; k < KG; k++) {
+            u64 o0 = redc(acc[c][2 * k].lo, acc[c][2 * k].hi, m), o1 = redc(acc[c][2 * k + 1].lo, acc[c][2 * k + 1].hi, m);
+            if (with_c0) o0 = addmod(o0, pc0, m.q);
+            const u32 gi = mk.ginv[kg0 + k];
+            const int x = gi == 1u ? yc : auto_index(yc, gi, logN);
+            u64 *ob = mk.out[kg0 + k] + (long)b * 2 * rows * N;
+            ob[(long)r * N + x] = o0;
+            ob[(long)(rows + r) * N + x] = o1;
+        }
+    }
+}
+
 // Permutes key rows into the layout above: out[row][pi_g(x)] = in[row][x].
 __global__ void k_permute_key(u64 *out, const u64 *in, long rows, int logN, u32 g) {
     const int N = 1 << logN;
@@ -927,6 +1009,31 @@ static void multsum_launch_g(Ctx *c, int v, u64 *const *outs, const u64 *digits,
         }
     }
     if (v == 80 || v == 84) v = v == 80 ? 32 : 36;   // more than two rotations: the one-coefficient kernel
+    if (v == 96 || v == 97) {
+        // rotations split over warps (1 or 2 per thread), two coefficients per thread
+        const int rows = level + 1 + c->alpha;
+        auto go = [&](auto kern, int bi) {
+            dim3 grid((unsigned)((c->N / 2 + 31) / 32), (unsigned)rows, (unsigned)((B + bi - 1) / bi));
+            kern<<<grid, 256, 0, st>>>(mk, digits, B, level, c->alpha, c->L, c->ndig(level), c->nprimes, c->logN,
+                                       c->d_mod, c0, c0s, c->d_Pmod);
+        };
+        if (v == 97 && G % 2 == 0 && G >= 2) {
+            constexpr int KG2 = (G % 2 == 0 && G >= 2) ? 2 : 1;
+            constexpr int NG2 = G / KG2;
+            if constexpr (8 % NG2 == 0) {
+                go(k_multsum_splitv<G, KG2, 3>, 8 / NG2);
+                c->n_launch++;
+                return;
+            }
+        }
+        if constexpr (8 % G == 0) {
+            go(k_multsum_splitv<G, 1, 5>, 8 / G);
+            c->n_launch++;
+            return;
+        }
+        v = 80;   // G does not divide the warps
+    }
+    if ((v == 80 || v == 84) && G > 2) v = v == 80 ? 32 : 36;
     if (v == 64 || v == 65) {
         // keys split over warps: KG = 1 (64) or 2 (65, G even)
         const int rows = level + 1 + c->alpha;
@@ -1039,7 +1146,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
             std::set<std::tuple<int, int, bool>> seen;
             for (int ch : {8, 4, 2, 1}) {
                 const int cc = std::min(ch, G);
-                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 48, 64, 65, 80, 84, 8, 9, 10}) {
+                for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 16, 20, 32, 36, 48, 64, 65, 80, 84, 96, 97, 8, 9, 10}) {
                     int BI;
                     bool stream;
                     multsum_variant(cand & 15, B, BI, stream);

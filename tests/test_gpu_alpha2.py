@@ -20,9 +20,9 @@ TOL = 1e-4
 LOGN, QBITS, PBITS = 14, [60] + [40] * 12, [60, 60]
 # MultSum launch variants: -1 the tuner's pick, 0 the thread-per-word
 # kernel (16, 20: with L2 prefetch; 32, 36, 48: more CTAs per SM; 64, 65: the
-# rotations split over warps; 80, 84: two coefficients per thread), 8, 9, 10
-# the bulk-copy kernel with three tile shapes
-VARIANTS = (-1, 0, 16, 20, 32, 36, 48, 64, 65, 80, 84, 8, 9, 10)
+# rotations split over warps; 80, 84, 96, 97: two coefficients per thread),
+# 8, 9, 10 the bulk-copy kernel with three tile shapes
+VARIANTS = (-1, 0, 16, 20, 32, 36, 48, 64, 65, 80, 84, 96, 97, 8, 9, 10)
 # NTT variants: one-tile CTAs (2, 3 or, as 5, 4 per SM), persistent bulk-copy passes (4),
 # one pass per limb by 8-CTA clusters (6; N = 2^16 only, here as 3)
 NTT_VARIANTS = (2, 3, 5, 4, 6)
