@@ -37,11 +37,11 @@ N_MAT = 128
 # the traced class counts): the forward NTT's two passes each read and write
 # the rows once, plus the row pass's twiddle misses (512-row capture: 1050.20
 # MB against 536.87 MB); MultSum reads the keys, the digits and c0 once and
-# writes its outputs once (8 items x 2 hoisted rotations at level 20: 2032.15
-# MB against 2065.69 MB).  Traffic grows
-# with the rows / items of a launch, so per launch it is this ratio times the
-# launch's algorithmic bytes.
-TRAFFIC_RATIO = {"ntt_fwd": 1050.20 / 536.87, "multsum": 2032.15 / 2065.69}
+# writes its outputs once (8 items x 4 hoisted rotations at level 20, the
+# step's largest MultSum launches, compiled for 4 CTAs per SM: 2964.69 MB
+# against 2982.15 MB).  Traffic grows with the rows / items of a launch, so
+# per launch it is this ratio times the launch's algorithmic bytes.
+TRAFFIC_RATIO = {"ntt_fwd": 1050.20 / 536.87, "multsum": 2964.69 / 2982.15}
 # baby-step count n1 used for each matrix dimension
 N1_FOR = {16: 4, 32: 8, 64: 8, 128: 16}
 LEVEL = 20
