@@ -407,17 +407,47 @@ void or_bconv(int N, int ns, const u64 *sq, const u64 *src, int nd, const u64 *d
 }
 
 /*
+ * Unsigned integers of BN_LIMBS little-endian 32-bit limbs: enough for a
+ * product of up to 8 primes below 2^62 times 8 (the ModDown overflow sums).
+ */
+#define BN_LIMBS 17
+static void bn_from_u64(u32 *a, u64 v) {
+    memset(a, 0, BN_LIMBS * sizeof(u32));
+    a[0] = (u32)v;
+    a[1] = (u32)(v >> 32);
+}
+static void bn_mul_u64(u32 *a, u64 m) {    /* a <- a m */
+    u128 carry = 0;
+    for (int i = 0; i < BN_LIMBS; i++) {
+        u128 t = (u128)a[i] * m + carry;
+        a[i] = (u32)t;
+        carry = t >> 32;
+    }
+}
+static void bn_add(u32 *a, const u32 *b) {   /* a <- a + b */
+    u64 carry = 0;
+    for (int i = 0; i < BN_LIMBS; i++) {
+        u64 t = (u64)a[i] + b[i] + carry;
+        a[i] = (u32)t;
+        carry = t >> 32;
+    }
+}
+static int bn_less(const u32 *a, const u32 *b) {
+    for (int i = BN_LIMBS - 1; i >= 0; i--)
+        if (a[i] != b[i]) return a[i] < b[i];
+    return 0;
+}
+
+/*
  * ModDown with rounding (App. A KeySwitch: round(P^-1 <a, swk>) mod Q_l).
  * Input: an element X of Q_l P given by residues uQ [nq][N] and uP [np][N].
  * With h = (P-1)/2 and Y = X + h, the result is floor(Y / P) = round(X / P):
  *   v_j   = (uP_j + h) mod p_j
  *   y_j   = [v_j (P/p_j)^-1]_{p_j}
- *   e     = floor(sum_j y_j / p_j)          (FP64, j ascending, one division
- *                                             and one addition per term)
+ *   e     = floor(sum_j y_j (P/p_j) / P)    (exact, big integers)
  *   Y mod P = sum_j y_j (P/p_j) - e P       (reduced mod each q_i)
  *   out_i = ((uQ_i + h) - (Y mod P)) P^-1 mod q_i.
- * e counts the overflow of the sum of the y_j (P/p_j) past P; its FP64
- * estimate is wrong only when sum_j y_j/p_j lies within ~1e-15 of an integer.
+ * e counts how often the sum of the y_j (P/p_j), each below P, passes P.
  */
 void or_moddown_round(int N, int nq, const u64 *qs, const u64 *uQ, int np, const u64 *ps, const u64 *uP, u64 *out) {
     u64 hp[8], phat_inv[8], hq[64], Pq[64], Pinv[64], phat_q[8][64];
@@ -444,16 +474,35 @@ void or_moddown_round(int N, int nq, const u64 *qs, const u64 *uQ, int np, const
         Pinv[i] = invmod(Pm, q);
         hq[i] = mulmod(submod(Pm, 1, q), invmod(2, q), q);
     }
+    /* P and P/p_j as big integers */
+    u32 Pbig[BN_LIMBS], phat[8][BN_LIMBS];
+    bn_from_u64(Pbig, 1);
+    for (int k = 0; k < np; k++) bn_mul_u64(Pbig, ps[k]);
+    for (int j = 0; j < np; j++) {
+        bn_from_u64(phat[j], 1);
+        for (int k = 0; k < np; k++)
+            if (k != j) bn_mul_u64(phat[j], ps[k]);
+    }
 #pragma omp parallel for
     for (int x = 0; x < N; x++) {
         u64 y[8];
-        double e_f = 0.0;
         for (int j = 0; j < np; j++) {
             u64 v = addmod(uP[(size_t)j * N + x], hp[j], ps[j]);
             y[j] = mulmod(v, phat_inv[j], ps[j]);
-            e_f = e_f + (double)y[j] / (double)ps[j];
         }
-        u64 e = (u64)floor(e_f);
+        u32 S[BN_LIMBS], term[BN_LIMBS], bound[BN_LIMBS];
+        bn_from_u64(S, 0);
+        for (int j = 0; j < np; j++) {
+            memcpy(term, phat[j], sizeof term);
+            bn_mul_u64(term, y[j]);
+            bn_add(S, term);
+        }
+        u64 e = 0;   /* the largest e with e P <= S */
+        memcpy(bound, Pbig, sizeof bound);
+        while (!bn_less(S, bound)) {
+            e++;
+            bn_add(bound, Pbig);
+        }
         for (int i = 0; i < nq; i++) {
             u64 q = qs[i];
             u64 conv = 0;

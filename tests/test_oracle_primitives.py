@@ -195,6 +195,59 @@ def test_moddown_is_rounding(pbits):
         assert Y == ((2 * X + P.P) // (2 * P.P)) % Q
 
 
+def overflow_boundary_residues(ps, ks):
+    """P-residues uP of coefficients whose fast-conversion sum
+    S = sum_j y_j (P/p_j) is congruent to -k mod P (k in ks): S sits k units
+    below a multiple of P, so sum_j y_j / p_j lies within k/P of an integer.
+    y_j = -k (P/p_j)^-1 mod p_j; v_j = y_j (P/p_j); uP_j = v_j - (P-1)/2."""
+    P = 1
+    for p in ps:
+        P *= p
+    h = (P - 1) // 2
+    uP = np.zeros((len(ps), len(ks)), dtype=np.uint64)
+    ys = []
+    for c, k in enumerate(ks):
+        yc = []
+        for j, p in enumerate(ps):
+            ph = P // p
+            y = (-k * pow(ph, -1, p)) % p
+            yc.append(y)
+            uP[j, c] = ((y * ph) - h) % p
+        ys.append(yc)
+    return uP, ys, P
+
+
+@pytest.mark.parametrize("pbits", [[60], [60, 60], [60, 50, 45], [60, 60, 60, 60]])
+def test_moddown_rounds_at_the_overflow_boundary(pbits):
+    # App. A KeySwitch rounds P^-1 x exactly.  Where sum_j y_j / p_j is just
+    # below an integer, its FP64 evaluation rounds up to that integer and
+    # would subtract P once too often; ModDown must still be round(X / P).
+    from oracle.ckks import CKKS
+    P = Params(8, [60, 40, 40], pbits)
+    he = CKKS(P, 9)
+    lv = 2
+    qp = P.qp(lv)
+    ks = list(range(1, 65))
+    uP, ys, Pbig = overflow_boundary_residues(P.p, ks)
+    rng = np.random.default_rng(3)
+    u = np.stack([rng.integers(0, q, P.N, dtype=np.uint64) for q in qp])
+    u[lv + 1:, : len(ks)] = uP
+    out = he.moddown(u, lv)
+    Qs = P.qs(lv)
+    fp64_wrong = 0
+    for c in range(len(ks)):
+        X, _ = _crt(u[:, c], qp)
+        Y, Q = _crt(out[:, c], Qs)
+        assert Y == ((2 * X + Pbig) // (2 * Pbig)) % Q, c
+        exact = sum(y * (Pbig // p) for y, p in zip(ys[c], P.p)) // Pbig
+        est = 0.0
+        for y, p in zip(ys[c], P.p):
+            est = est + float(y) / float(p)
+        fp64_wrong += int(np.floor(est)) != exact
+    # the cases do reach past what an FP64 overflow estimate resolves
+    assert fp64_wrong > 0
+
+
 def test_keyswitch_noise_is_centred():
     # The rounding ModDown leaves no systematic offset in the key-switch
     # noise: Dec(Rot(ct)) - kappa(Dec(ct)) has mean ~0 (a floor-type ModDown
