@@ -520,11 +520,31 @@ def run_ours(args, rank, world, dist):
         "clocks": ck, "gpu_launches": launches,
         "check": {"max_abs_err": err, "tol": 1e-4, "batch_equals_single_bitexact": bitexact},
         "ntt_launch_tuning": [x for x in pk.he_autotune_log(ctx).splitlines() if x.startswith("ntt")],
+        "multsum_launch_picks": multsum_picks(pk.he_autotune_log(ctx)),
     }
     if n_mat != N_MAT:
         line["note"] = "profiling case (n=%d), not the benchmark workload" % n_mat
     print(json.dumps(line), flush=True)
     pk.he_ctx_destroy(ctx)
+
+
+def multsum_picks(log):
+    """The MultSum launch plan the tuner kept for each (level, items, rotations):
+    the fastest of its timed candidates (log lines "multsum level L B b G g
+    chunk c BI v stream s ms t"; BI above 100 names launch variant BI - 100)."""
+    best = {}
+    for ln in log.splitlines():
+        f = ln.split()
+        if len(f) != 15 or f[0] != "multsum":
+            continue
+        key = (int(f[2]), int(f[4]), int(f[6]))
+        t = float(f[14])
+        if key not in best or t < best[key][0]:
+            best[key] = (t, int(f[8]), int(f[10]), int(f[12]))
+    return ["level %d B %d G %d: %d keys per launch, %s, %.4f ms" %
+            (k + (v[1], ("variant %d" % (v[2] - 100)) if v[2] > 100 else "%d items per CTA%s" %
+                  (v[2], ", streaming" if v[3] else ""), v[0]))
+            for k, v in sorted(best.items())]
 
 
 def _cov_keys(pk, ctx, n, n1, S, dcd=0):
@@ -978,7 +998,7 @@ def run_keyswitch(args):
     for _ in range(max(3, args.warmup)):
         step()
     pk.he_trace_enable(ctx, True)
-    for c in range(3):
+    for c in range(5):
         pk.he_trace_read(ctx, c, reset=True)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -990,7 +1010,7 @@ def run_keyswitch(args):
     e1.record(tstream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    tr = [pk.he_trace_read(ctx, c, reset=True) for c in range(3)]
+    tr = [pk.he_trace_read(ctx, c, reset=True) for c in range(5)]
     pk.he_trace_enable(ctx, False)
     hbm = peaks().get("hbm_gbs") or 6800.0
     t = tr[0]
@@ -1002,7 +1022,11 @@ def run_keyswitch(args):
                       "roofline_keyswitch": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                                              "frac": ach / hbm, "launches": t["count"], "avg_us": avg * 1e6,
                                              "algorithmic_bytes_per_launch": t["bytes"] / t["count"]},
-                      "kernel_time_ms": {"multsum": tr[0]["ms"], "ntt_fwd": tr[1]["ms"], "ntt_inv": tr[2]["ms"]},
+                      "kernel_time_ms": {"multsum": tr[0]["ms"], "ntt_fwd": tr[1]["ms"], "ntt_inv": tr[2]["ms"],
+                                         "modup_bconv": tr[3]["ms"], "moddown_bconv": tr[4]["ms"]},
+                      "conversions": {name: {"ms": t["ms"], "launches": t["count"],
+                                             "algorithmic_gbs": t["bytes"] / (t["ms"] / 1e3) / 1e9 if t["ms"] else None}
+                                      for name, t in (("modup_bconv", tr[3]), ("moddown_bconv", tr[4]))},
                       "config": {"workload": "%d ciphertexts x %d rotation steps, one Decompose per ciphertext" % (B, R),
                                  "multsum_variant": args.ms_variant},
                       "autotune": pk.he_autotune_log(ctx).splitlines()}),

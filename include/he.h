@@ -411,6 +411,28 @@ int he_pca(he_ctx *ctx, he_ct *const *cov, int k, int n, int l_E, he_ct *const *
  * 0..L), HE_ERR_CUDA. */
 int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inverse);
 
+/* Decompose alone (Sec. 3.3, "Dp"; App. A KeySwitch): the digits of
+ * polynomials over Q_level, each extended to Q_level P by the fast basis
+ * conversion.  poly_dev: n_items polynomials of level+1 rows of N words in
+ * the NTT domain (item stride (level+1) N).  digits_dev: n_items x dnum'
+ * digits of level+1+alpha rows, NTT domain, laid out
+ * [item][digit][row][N], rows q_0..q_level then p_0..p_{alpha-1}; dnum' =
+ * ceil((level+1)/alpha).  Both device buffers are caller-owned, 16-byte
+ * aligned and disjoint.  Runs on the context's stream and returns when it is
+ * done.  Errors: HE_ERR_ARG (null, misaligned or negative sizes, more than
+ * 2^20 items), HE_ERR_LEVEL, HE_ERR_OOM, HE_ERR_CUDA. */
+int he_decompose(he_ctx *ctx, const uint64_t *poly_dev, long long n_items, int level, uint64_t *digits_dev);
+
+/* ModDown alone (Sec. 3.3, "MD"; App. A KeySwitch): round(X / P) over
+ * Q_level for elements X of Q_level P.  in_dev: n_items elements of
+ * level+1+alpha rows (q_0..q_level, then p_0..p_{alpha-1}) of N words in
+ * the NTT domain; out_dev: n_items polynomials of level+1 rows, NTT domain.
+ * The overflow of the fast conversion is counted exactly, so the result is
+ * round(X / P) for every coefficient.  Both device buffers are
+ * caller-owned, 16-byte aligned and disjoint.  Runs on the context's stream
+ * and returns when it is done.  Errors: as he_decompose. */
+int he_moddown(he_ctx *ctx, const uint64_t *in_dev, long long n_items, int level, uint64_t *out_dev);
+
 /* Counters of the key-switch phases since the last reset: MultSum, Decompose,
  * ModDown (Table 1 caption), and kernel launches.  Any pointer may be NULL. */
 int he_counters(he_ctx *ctx, long long *ms, long long *dp, long long *md, long long *launches, int reset);

@@ -130,6 +130,8 @@ SIGNATURES = {
     "he_pca": [vp, P(vp), ip, ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp),
                P(ip)],
     "he_ntt": [vp, vp, ctypes.c_longlong, ip, ip],
+    "he_decompose": [vp, vp, ctypes.c_longlong, ip, vp],
+    "he_moddown": [vp, vp, ctypes.c_longlong, ip, vp],
     "he_counters": [vp, llp, llp, llp, llp, ip],
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
@@ -495,6 +497,16 @@ TRACE_MULTSUM, TRACE_NTT_FWD, TRACE_NTT_INV = 0, 1, 2
 def he_ntt(ctx, rows_dev_ptr, n_rows, level, inverse=False):
     """In-place NTT (or inverse) of n_rows device rows (see include/he.h)."""
     check(lib().he_ntt(ctx, rows_dev_ptr, n_rows, level, 1 if inverse else 0))
+
+
+def he_decompose(ctx, poly_dev_ptr, n_items, level, digits_dev_ptr):
+    """Decompose of n_items device polynomials into their extended digits (see include/he.h)."""
+    check(lib().he_decompose(ctx, poly_dev_ptr, n_items, level, digits_dev_ptr))
+
+
+def he_moddown(ctx, in_dev_ptr, n_items, level, out_dev_ptr):
+    """Rounding ModDown of n_items device elements of Q_level P (see include/he.h)."""
+    check(lib().he_moddown(ctx, in_dev_ptr, n_items, level, out_dev_ptr))
 
 
 def he_trace_enable(ctx, on=True):

@@ -226,7 +226,7 @@ int he_ctx_destroy(he_ctx *ctx) {
         for (auto &f : kv.second.factors) cudaFree(f.dev);
     void *ptrs[] = {c.d_mod, c.d_psi, c.d_psip, c.d_ipsi, c.d_ipsip, c.d_psi2, c.d_ipsi2, c.d_ninv, c.d_dn_pinv,
                     c.d_dn_pmod,
-                    c.d_dn_Pinv, c.d_Pmod, c.d_dn_hp, c.d_dn_hq, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM,
+                    c.d_dn_Pinv, c.d_Pmod, c.d_dn_E, c.d_zeta, c.d_slot_t, c.d_sk, c.d_skM,
                     c.d_pkM};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -913,6 +913,35 @@ int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inv
         ntt_inv(&c, (u64 *)rows_dev, n_rows, c.map_qp(level), c.stream);
     else
         ntt_fwd(&c, (u64 *)rows_dev, n_rows, c.map_qp(level), c.stream);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_decompose(he_ctx *ctx, const uint64_t *poly_dev, long long n_items, int level, uint64_t *digits_dev) {
+    if (!ctx || n_items < 0 || n_items > (1 << 20) || (n_items > 0 && (!poly_dev || !digits_dev)))
+        return fail(HE_ERR_ARG, "bad arguments");
+    if (((uintptr_t)poly_dev | (uintptr_t)digits_dev) & 15) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    Ctx &c = ctx->c;
+    if (level < 0 || level > c.L) return fail(HE_ERR_LEVEL, "level out of range");
+    GUARD_BEGIN
+    if (n_items > 0) modup(&c, (const u64 *)poly_dev, (long)(level + 1) * c.N, (int)n_items, level, (u64 *)digits_dev);
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
+    return cuda_status(&c);
+    GUARD_END
+}
+
+int he_moddown(he_ctx *ctx, const uint64_t *in_dev, long long n_items, int level, uint64_t *out_dev) {
+    if (!ctx || n_items < 0 || n_items > (1 << 20) || (n_items > 0 && (!in_dev || !out_dev)))
+        return fail(HE_ERR_ARG, "bad arguments");
+    if (((uintptr_t)in_dev | (uintptr_t)out_dev) & 15) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    Ctx &c = ctx->c;
+    if (level < 0 || level > c.L) return fail(HE_ERR_LEVEL, "level out of range");
+    GUARD_BEGIN
+    if (n_items > 0)
+        moddown(&c, (const u64 *)in_dev, (int)n_items, level, (u64 *)out_dev, (long)(level + 1) * c.N, nullptr, 0);
     HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
     if (int rc_dev = device_status(&c)) return rc_dev;
     return cuda_status(&c);

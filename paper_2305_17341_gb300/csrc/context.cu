@@ -381,18 +381,46 @@ void build_tables(Ctx *c) {
     c->d_dn_Pinv = upload(Pinv);
     c->d_Pmod = upload(Pmod);
     // h = (P-1)/2 reduced mod every prime: 2h = P - 1 exactly (P odd)
-    std::vector<u64> hp(a), hq(L + 1);
+    MdExact &mk = c->md_exact;
+    mk = MdExact();
     for (int j = 0; j < a; j++) {
         u64 pj = c->primes[L + 1 + j], Pm = 1;
         for (int t = 0; t < a; t++) Pm = h_mulmod(Pm, c->primes[L + 1 + t] % pj, pj);
-        hp[j] = h_mulmod((Pm + pj - 1) % pj, h_invmod(2, pj), pj);
+        mk.p[j] = pj;
+        mk.hp[j] = h_mulmod((Pm + pj - 1) % pj, h_invmod(2, pj), pj);
+        mk.pinv[j] = pinv[j];
     }
+    // P/p_j and k P as 64-bit limbs (P < 2^(62 alpha))
+    auto limb_mul = [](u64 *x, int n, u64 m) {
+        unsigned __int128 carry = 0;
+        for (int i = 0; i < n; i++) {
+            unsigned __int128 t = (unsigned __int128)x[i] * m + carry;
+            x[i] = (u64)t;
+            carry = t >> 64;
+        }
+    };
+    u64 P4[4] = {1, 0, 0, 0};
+    for (int t = 0; t < a; t++) limb_mul(P4, 4, c->primes[L + 1 + t]);
+    for (int j = 0; j < a; j++) {
+        u64 ph[4] = {1, 0, 0, 0};
+        for (int t = 0; t < a; t++)
+            if (t != j) limb_mul(ph, 4, c->primes[L + 1 + t]);
+        for (int i = 0; i < 3; i++) mk.phat[j][i] = ph[i];
+    }
+    for (int m = 0; m + 1 < a; m++) {
+        for (int i = 0; i < 4; i++) mk.kP[m][i] = P4[i];
+        limb_mul(mk.kP[m], 4, (u64)(m + 1));
+    }
+    std::vector<u64> E((size_t)a * (L + 1));
     for (int r = 0; r <= L; r++) {
         u64 qr = c->primes[r];
-        hq[r] = h_mulmod((Pmod[r].w + qr - 1) % qr, h_invmod(2, qr), qr);
+        const u64 hq = h_mulmod((Pmod[r].w + qr - 1) % qr, h_invmod(2, qr), qr);
+        for (int e = 0; e < a; e++) {
+            const u64 t = (h_mulmod((u64)e, Pmod[r].w, qr) + hq) % qr;
+            E[(size_t)e * (L + 1) + r] = t ? qr - t : 0;
+        }
     }
-    c->d_dn_hp = upload(hp);
-    c->d_dn_hq = upload(hq);
+    c->d_dn_E = upload(E);
     c->lvl.assign(L + 1, LevelConsts());
 
     // encoder: zeta^e = (cos, sin)((pi e) / N); slot j -> t = (5^j mod 2N - 1)/4

@@ -388,18 +388,26 @@ void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const in
     //   C^k: rotations by b of A_g and A'_g kept in Q_l P, b = 1..n1z-1;
     //   R^k: rotations by n b of B_g (ModDown'd), b = 1..n1t-1.
     const int nbA = n1z - 1, nbB = n1t - 1;
-    Buf RA(&c->pool, (size_t)std::max(1, nbA) * nA * qp1), RAp(&c->pool, (size_t)std::max(1, nbA) * nA * qp1);
+    Buf SA(&c->pool, (size_t)std::max(1, nbA) * nA * qp1);
     Buf UB(&c->pool, (size_t)std::max(1, nbB) * nB * qp1), BB(&c->pool, (size_t)std::max(1, nbB) * nB * ct1);
+    // the babies of giant g, masked and summed in one pass:
+    // SA_b = m_k (.) rot_qp(A_g; b) + m'_k (.) rot_qp(A'_g; b), k = n1z g + b
     auto babies_A = [&]() {
         std::vector<uint32_t> gs;
-        std::vector<u64 *> o1, o2;
+        std::vector<u64 *> o;
+        std::vector<const u64 *> m1, m2;
         for (int b = 1; b <= nbA; b++) {
+            const int k = n1z * gA + b;
             gs.push_back(galois_of_step(c, b % n2m));
-            o1.push_back(RA.p + (size_t)(b - 1) * nA * qp1);
-            o2.push_back(RAp.p + (size_t)(b - 1) * nA * qp1);
+            o.push_back(SA.p + (size_t)(b - 1) * nA * qp1);
+            m1.push_back(get_pt(c, 3, n, 0, 0, 1.0, k, l1));
+            m2.push_back(get_pt(c, 4, n, 0, 0, 1.0, k, l1));
         }
-        rot_qp_multi(c, Ag.p, nA, l1, dA.p, gs.data(), nbA, o1.data());
-        rot_qp_multi(c, Apg.p, nA, l1, dAp.p, gs.data(), nbA, o2.data());
+        std::vector<const u64 *> keys(nbA);
+        for (int i = 0; i < nbA; i++) keys[i] = need_key(c, gs[i]);
+        launch_multsum_ck(c, o.data(), dA.p, dAp.p, keys.data(), gs.data(), m1.data(), m2.data(), nbA, nA, l1,
+                          Ag.p, Apg.p, (long)ct1, c->stream);
+        c->n_ms += 2LL * nA * nbA;
     };
     auto babies_B = [&]() {
         std::vector<uint32_t> gs;
@@ -432,15 +440,18 @@ void hmatmul_pairs(Ctx *c, const u64 *A, int nA, const u64 *Bm, int nB, const in
         if (k == 0) {
             drop(c, A0.p, nA, l1, l2, Ak.p);
         } else {
-            if (b == 0) {
+            const u64 *Sk = S.p;
+            if (b > 0) {
+                Sk = SA.p + (size_t)(b - 1) * nA * qp1;
+            } else {
+                // the giant's own sources, lifted to Q_l P, masked and summed
                 launch_lift_P(c, R1.p, Ag.p, 2 * nA, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
                 launch_lift_P(c, R2.p, Apg.p, 2 * nA, l1, (long)(l1 + 1) * N, (long)rows1 * N, c->stream);
+                const u64 *pts[2] = {get_pt(c, 3, n, 0, 0, 1.0, k, l1), get_pt(c, 4, n, 0, 0, 1.0, k, l1)};
+                const u64 *Rs[2] = {R1.p, R2.p};
+                launch_pmul_acc(c, S.p, pts, Rs, 2, nA, l1, (long)qp1, c->stream);
             }
-            const u64 *pts[2] = {get_pt(c, 3, n, 0, 0, 1.0, k, l1), get_pt(c, 4, n, 0, 0, 1.0, k, l1)};
-            const u64 *Rs[2] = {b == 0 ? R1.p : RA.p + (size_t)(b - 1) * nA * qp1,
-                                b == 0 ? R2.p : RAp.p + (size_t)(b - 1) * nA * qp1};
-            launch_pmul_acc(c, S.p, pts, Rs, 2, nA, l1, (long)qp1, c->stream);
-            moddown(c, S.p, 2 * nA, l1, Akp.p, (long)(l1 + 1) * N);
+            moddown(c, Sk, 2 * nA, l1, Akp.p, (long)(l1 + 1) * N);
             c->n_md += nA;
             rescale(c, Akp.p, nA, l1, Ak.p);
         }

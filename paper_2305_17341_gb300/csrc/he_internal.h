@@ -101,6 +101,15 @@ struct ShoupPair {
     u64 w, wp;
 };
 
+// Constants of the exact overflow count of the rounding ModDown, alpha <= 4
+// special primes below 2^62 (kernel parameter).
+struct MdExact {
+    u64 p[4], hp[4];          // p_j, (P-1)/2 mod p_j
+    ShoupPair pinv[4];        // (P/p_j)^-1 mod p_j
+    u64 phat[4][3];           // P/p_j, little-endian 64-bit limbs (alpha-1 used)
+    u64 kP[3][4];             // k P for k = 1..alpha-1 (alpha limbs used)
+};
+
 // Constants of one level l (limbs q_0..q_l, then p's).
 struct LevelConsts {
     int level = -1;
@@ -146,8 +155,8 @@ struct Ctx {
     ShoupPair *d_dn_pmod = nullptr;  // [alpha][L+1] (P/p_j) mod q_r
     ShoupPair *d_dn_Pinv = nullptr;  // [L+1]     P^-1 mod q_r
     ShoupPair *d_Pmod = nullptr;     // [L+1]     P mod q_r
-    u64 *d_dn_hp = nullptr;          // [alpha]   (P-1)/2 mod p_j
-    u64 *d_dn_hq = nullptr;          // [L+1]     (P-1)/2 mod q_r
+    u64 *d_dn_E = nullptr;           // [alpha][L+1] -(e P + (P-1)/2) mod q_r, e < alpha
+    MdExact md_exact;
     std::vector<LevelConsts> lvl;
 
     // encoder tables
@@ -200,6 +209,7 @@ struct Ctx {
     int force_multsum = -1;
     // (level, items, keys) -> (keys per launch << 8) | variant
     std::map<std::tuple<int, int, int>, int> tune_multsum;
+    std::map<std::tuple<int, int, int>, int> tune_ck;   // fused C^k babies: (keys per launch << 8) | items per CTA
     std::string tune_log;   // every timed plan, one line each
     TraceClass tr[5];   // 0 MultSum, 1 NTT forward, 2 NTT inverse, 3 ModUp BConv, 4 ModDown BConv
     std::vector<cudaEvent_t> ev_free;
@@ -328,6 +338,11 @@ void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_
 constexpr int kMultSumMaxKeys = 8;
 void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64 *const *keys, const uint32_t *gs,
                           int G, int B, int level, const u64 *c0_for_P, long c0s, cudaStream_t st);
+// G hoisted rotations of two sources with the same keys, each output the
+// masked sum m1_k (.) rot(source 1) + m2_k (.) rot(source 2) over Q_l P.
+void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig2, const u64 *const *keys,
+                       const uint32_t *gs, const u64 *const *m1, const u64 *const *m2, int G, int B, int level,
+                       const u64 *c01, const u64 *c02, long c0s, cudaStream_t st);
 void launch_permute_key(Ctx *c, u64 *out, const u64 *in, long rows, uint32_t g, cudaStream_t st);
 void launch_pmul_acc(Ctx *c, u64 *out, const u64 *const *pts, const u64 *const *R, int nterms, int B,
                      int level, long R_item_stride, cudaStream_t st);

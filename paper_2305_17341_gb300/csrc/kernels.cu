@@ -320,8 +320,8 @@ __global__ void k_tensor(u64 *d01, u64 *d2, const u64 *a, const u64 *b, int B, i
     mac128(acc, a0, b1);
     mac128(acc, a1, b0);
     u64 t1 = redc(acc.lo, acc.hi, m);
-    u64 *o = d01 + (long)it * 2 * per + off;
     u64 v0 = mulmod(a0, b0, m), v1 = redc(t1 * m.r2, mulhi64(t1, m.r2), m), v2 = mulmod(a1, b1, m);
+    u64 *o = d01 + (long)it * 2 * per + off;
     u64 *o2 = d2 + (long)it * per + off;
     if (accumulate & 1) {
         v0 = addmod(v0, o[0], m.q);
@@ -352,68 +352,108 @@ void launch_tensor_acc(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, in
 // target row r of Q_l P gets sum_i y_i (Q_d/q_i mod r) mod r, except the
 // digit's own rows, which keep c_r.  In/out in coefficient form.
 // coef: [B][l+1][N]; out: [B][ndig][l+1+alpha][N].
-__global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int alpha,
-                                                     int ndig, int N, RowMap qp, const ModQ *mods,
-                                                     const ShoupPair *up_inv, const ShoupPair *up_mod,
-                                                     const u64 *own_ntt, long own_s) {
-    // 256 | N, so the CTA's 256 coefficients share one (item, digit): its
-    // conversion constants and row primes are staged in shared memory
-    __shared__ ShoupPair s_mod[4 * 64];   // [s][r], alpha <= 4, rows <= 64
-    __shared__ u64 s_q[64];
-    const long base = (long)blockIdx.x * blockDim.x;
-    const long t = base / N;
-    const int d = (int)(t % ndig), b = (int)(t / ndig);
-    const int rows = level + 1 + alpha;
-    const int i0 = d * alpha;
-    const int ns = min(alpha, level + 1 - i0);
+//
+// blockIdx.y is the digit: a CTA stages that digit's conversion constants
+// and row primes in shared memory once and walks (item, coefficient pair)
+// with a grid stride.  Each thread converts two adjacent coefficients with
+// 16-byte loads and stores; the A lazy Shoup products of a row (each in
+// [0, 2r)) are summed and reduced once.
+static int sm_count(int dev) {
+    static int n[64];
+    dev &= 63;
+    if (!n[dev]) cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev);
+    return n[dev] > 0 ? n[dev] : 1;
+}
+
+template <int A>
+__global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int ndig, int N,
+                                                     RowMap qp, const ModQ *mods, const ShoupPair *up_inv,
+                                                     const ShoupPair *up_mod, const u64 *own_ntt, long own_s) {
+    __shared__ ShoupPair s_mod[A * 64];   // [s][r], rows <= 64
+    __shared__ u64 s_q[64], s_w1[64];
+    const int d = blockIdx.y;
+    const int rows = level + 1 + A;
+    const int i0 = d * A;
+    const int ns = min(A, level + 1 - i0);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const ModQ m = mods[r <= qp.lq ? r : qp.base_p + (r - qp.lq - 1)];   // qp is unshifted
+        s_q[r] = m.q, s_w1[r] = m.wone;
+    }
     for (int e = threadIdx.x; e < ns * rows; e += blockDim.x) {
         const int sd = e / rows, r = e - sd * rows;
-        s_mod[e] = up_mod[((long)d * alpha + sd) * rows + r];
+        s_mod[e] = up_mod[((long)d * A + sd) * rows + r];
     }
-    for (int r = threadIdx.x; r < rows; r += blockDim.x)
-        s_q[r] = mods[r <= qp.lq ? r : qp.base_p + (r - qp.lq - 1)].q;   // qp is unshifted
+    ShoupPair inv[A];
+    u64 qs[A];
+#pragma unroll
+    for (int sd = 0; sd < A; sd++)
+        if (sd < ns) inv[sd] = up_inv[d * A + sd], qs[sd] = mods[i0 + sd].q;
     __syncthreads();
-    const long idx = base + threadIdx.x;
-    if (idx >= (long)B * ndig * N) return;
-    const int x = (int)(idx - t * N);
-    const u64 *cb = coef + (long)b * (level + 1) * N;
-    u64 *ob = out + ((long)b * ndig + d) * rows * N;
-    // alpha <= 4; fixed trip counts keep y in registers
-    u64 y[4] = {0, 0, 0, 0};
+    const int half = N / 2;
+    const long pairs = (long)B * half;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < pairs; idx += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / half);
+        const int x = 2 * (int)(idx - (long)b * half);
+        const u64 *cb = coef + (long)b * (level + 1) * N + x;
+        u64 *ob = out + ((long)b * ndig + d) * rows * N + x;
+        u64 y0[A], y1[A];
 #pragma unroll
-    for (int sd = 0; sd < 4; sd++) {
-        if (sd < ns) {
-            ShoupPair w = up_inv[d * alpha + sd];
-            y[sd] = shoup(cb[(long)(i0 + sd) * N + x], w.w, w.wp, mods[i0 + sd].q);
-        }
-    }
-    for (int r = 0; r < rows; r++) {
-        u64 v;
-        if (r >= i0 && r < i0 + ns) {
-            v = own_ntt ? own_ntt[(long)b * own_s + (long)r * N + x] : cb[(long)r * N + x];
-        } else {
-            const u64 q = s_q[r];
-            v = 0;
-#pragma unroll
-            for (int sd = 0; sd < 4; sd++) {
-                if (sd < ns) {
-                    const ShoupPair w = s_mod[sd * rows + r];
-                    v = addmod(v, shoup(y[sd], w.w, w.wp, q), q);
-                }
+        for (int sd = 0; sd < A; sd++) {
+            y0[sd] = y1[sd] = 0;
+            if (sd < ns) {
+                const ulonglong2 v = *(const ulonglong2 *)(cb + (long)(i0 + sd) * N);
+                y0[sd] = shoup(v.x, inv[sd].w, inv[sd].wp, qs[sd]);
+                y1[sd] = shoup(v.y, inv[sd].w, inv[sd].wp, qs[sd]);
             }
         }
-        ob[(long)r * N + x] = v;
+        for (int r = 0; r < rows; r++) {
+            ulonglong2 o;
+            if (r >= i0 && r < i0 + ns) {   // uniform over the CTA
+                const u64 *src = own_ntt ? own_ntt + (long)b * own_s + (long)r * N + x : cb + (long)r * N;
+                o = *(const ulonglong2 *)src;
+            } else {
+                const u64 q = s_q[r];
+                u64 a0 = 0, a1 = 0;
+#pragma unroll
+                for (int sd = 0; sd < A; sd++) {
+                    if (sd < ns) {
+                        const ShoupPair w = s_mod[sd * rows + r];
+                        a0 += shoup_lazy(y0[sd], w.w, w.wp, q);
+                        a1 += shoup_lazy(y1[sd], w.w, w.wp, q);
+                    }
+                }
+                // a0, a1 < 2 A q <= 8q < 2^64
+                o.x = reduce_any(a0, q, s_w1[r]);
+                o.y = reduce_any(a1, q, s_w1[r]);
+            }
+            *(ulonglong2 *)(ob + (long)r * N) = o;
+        }
     }
 }
+
+static void modup_launch(Ctx *c, const u64 *coef, u64 *out, int B, int level, int nd, const ShoupPair *up_inv,
+                         const ShoupPair *up_mod, const u64 *own_ntt, long own_s, cudaStream_t st) {
+    const long pairs = (long)B * (c->N / 2);
+    // about 8 CTAs of 256 threads per SM over all digits
+    long gx = std::max(1L, (long)sm_count(c->device) * 8 / nd);
+    gx = std::min(gx, (long)nblk(pairs, 256));
+    const dim3 grid((unsigned)gx, (unsigned)nd);
+    const RowMap qp = c->map_qp(level);
+    switch (c->alpha) {
+    case 1: k_modup_bconv<1><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
+    case 2: k_modup_bconv<2><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
+    case 3: k_modup_bconv<3><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
+    default: k_modup_bconv<4><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
+    }
+}
+
 void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cudaStream_t st, const u64 *own_ntt,
                         long own_s) {
     const LevelConsts &L = c->lc(level);
-    long n = (long)B * L.ndig * c->N;
     c->n_launch++;
     cudaEvent_t e0;
     c->trace_begin(3, e0);
-    k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, L.ndig, c->N, c->map_qp(level),
-                                                c->d_mod, L.d_up_inv, L.d_up_mod, own_ntt, own_s);
+    modup_launch(c, coef, out, B, level, L.ndig, L.d_up_inv, L.d_up_mod, own_ntt, own_s, st);
     // the input limbs once, every digit's extended limbs once
     c->trace_end(3, e0, 8.0 * B * c->N * ((level + 1) + (double)L.ndig * c->qp_rows(level)));
 }
@@ -421,11 +461,8 @@ void launch_modup_bconv(Ctx *c, const u64 *coef, u64 *out, int B, int level, cud
 // Same conversion with caller-supplied constants (layout of LevelConsts).
 void launch_modup_bconv_with(Ctx *c, const u64 *coef, u64 *out, int B, int level, const ShoupPair *up_inv,
                              const ShoupPair *up_mod, cudaStream_t st) {
-    int nd = c->ndig(level);
-    long n = (long)B * nd * c->N;
     c->n_launch++;
-    k_modup_bconv<<<nblk(n, 256), 256, 0, st>>>(coef, out, B, level, c->alpha, nd, c->N, c->map_qp(level), c->d_mod,
-                                                up_inv, up_mod, nullptr, 0);
+    modup_launch(c, coef, out, B, level, c->ndig(level), up_inv, up_mod, nullptr, 0, st);
 }
 
 // ----------------------------------------------------- constants per limb
@@ -479,65 +516,114 @@ void launch_centre_i64_q0(Ctx *c, const u64 *a, i64 *out, cudaStream_t st) {
 // ------------------------------------------------------------- ModDown
 // Rounding ModDown (App. A KeySwitch: round(P^-1 x)) as floor((x + h) / P),
 // h = (P-1)/2.  With v_j = u_{p_j} + h mod p_j and y_j = [v_j (P/p_j)^-1]_{p_j},
-// the exact residue (x + h) mod P is sum_j y_j (P/p_j) - e P, where the
-// overflow count e = floor(sum_j y_j / p_j) is evaluated in FP64 (j
-// ascending, correctly rounded conversion, division and addition).
+// the exact residue (x + h) mod P is S - e P with S = sum_j y_j (P/p_j) and
+// the overflow count e = floor(S / P) < A, taken exactly: S is summed in
+// 64-bit limbs and compared with P, 2P, ...
 // conv_r = ((x + h) mod P) - h mod q_r, coefficient form (h is added to
-// every coefficient, so it is folded in here, before the forward NTT).
-// pcoef: [items][alpha][N]; out: [items][l+1][N]
-__global__ void __launch_bounds__(256) k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int alpha,
-                                                       int L, int N, const ModQ *mods, const ShoupPair *pinv,
-                                                       const ShoupPair *pmod, const u64 *hp, const ShoupPair *Pmod,
-                                                       const u64 *hq) {
-    // per-row constants of the conversion, staged once per CTA
-    __shared__ ShoupPair s_pmod[4 * 64], s_P[64];
-    __shared__ u64 s_q[64], s_hq[64];
-    for (int e = threadIdx.x; e < alpha * (level + 1); e += blockDim.x) {
-        const int j = e / (level + 1), r = e - j * (level + 1);
-        s_pmod[e] = pmod[j * (L + 1) + r];
-    }
-    for (int r = threadIdx.x; r <= level; r += blockDim.x) s_q[r] = mods[r].q, s_P[r] = Pmod[r], s_hq[r] = hq[r];
-    __syncthreads();
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)items * N) return;
-    int x = (int)(idx % N);
-    int it = (int)(idx / N);
-    // alpha <= 4; fixed trip counts keep y in registers
-    u64 y[4] = {0, 0, 0, 0};
-    double ef = 0.0;
+// every coefficient, so it is folded in here, before the forward NTT):
+// conv_r = sum_j y_j (P/p_j mod q_r) + E_{e,r} with E_{e,r} = -(e P + h) mod q_r.
+// pcoef: [items][A][N]; out: [items][l+1][N].
+
+// e = floor(S / P) for S = sum_j y[j] (P/p_j): S < A P < 2^(64 A).
+template <int A>
+__device__ __forceinline__ int md_overflow(const u64 (&y)[A], const MdExact &k) {
+    if constexpr (A == 1) {
+        return 0;
+    } else {
+        u64 s[A];
 #pragma unroll
-    for (int j = 0; j < 4; j++) {
-        if (j < alpha) {
-            ShoupPair w = pinv[j];
-            u64 p = mods[L + 1 + j].q;
-            u64 v = addmod(pcoef[((long)it * alpha + j) * N + x], hp[j], p);
-            y[j] = shoup(v, w.w, w.wp, p);
-            ef = __dadd_rn(ef, __ddiv_rn(__ull2double_rn(y[j]), __ull2double_rn(p)));
-        }
-    }
-    u64 e = (u64)floor(ef);
-    for (int r = 0; r <= level; r++) {
-        u64 q = s_q[r], v = 0;
+        for (int i = 0; i < A; i++) s[i] = 0;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (j < alpha) {
-                ShoupPair w = s_pmod[j * (level + 1) + r];
-                v = addmod(v, shoup(y[j], w.w, w.wp, q), q);
+        for (int j = 0; j < A; j++) {
+            u64 carry = 0;
+#pragma unroll
+            for (int i = 0; i < A - 1; i++) {
+                const u64 lo = y[j] * k.phat[j][i], hi = __umul64hi(y[j], k.phat[j][i]);
+                u64 t = s[i] + lo;
+                u64 cy = t < lo ? 1ull : 0ull;
+                t += carry;
+                cy += t < carry ? 1ull : 0ull;
+                s[i] = t;
+                carry = hi + cy;   // hi < 2^62
             }
+            s[A - 1] += carry;     // the partial sums stay below S
         }
-        ShoupPair wP = s_P[r];
-        v = submod(v, shoup(e, wP.w, wP.wp, q), q);
-        v = submod(v, s_hq[r], q);
-        out[((long)it * (level + 1) + r) * N + x] = v;
+        int e = 0;
+#pragma unroll
+        for (int m = 0; m < A - 1; m++) {
+            int cmp = 0;
+#pragma unroll
+            for (int i = A - 1; i >= 0; i--)
+                if (cmp == 0) cmp = s[i] > k.kP[m][i] ? 1 : (s[i] < k.kP[m][i] ? -1 : 0);
+            e += cmp >= 0 ? 1 : 0;
+        }
+        return e;
     }
 }
+
+// Two adjacent coefficients per thread (16-byte loads and stores), a grid
+// stride over (item, pair); per row the lazy Shoup products and E are
+// summed and reduced once.
+template <int A>
+__global__ void __launch_bounds__(256) k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int N,
+                                                       const __grid_constant__ MdExact k, const ModQ *mods,
+                                                       const ShoupPair *pmod, const u64 *E, int L) {
+    __shared__ ShoupPair s_c[A * 64];
+    __shared__ u64 s_E[A * 64], s_q[64], s_w1[64];
+    const int nr = level + 1;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) s_q[r] = mods[r].q, s_w1[r] = mods[r].wone;
+    for (int e = threadIdx.x; e < A * nr; e += blockDim.x) {
+        const int j = e / nr, r = e - j * nr;
+        s_c[e] = pmod[j * (L + 1) + r];
+        s_E[e] = E[j * (L + 1) + r];
+    }
+    __syncthreads();
+    const int half = N / 2;
+    const long pairs = (long)items * half;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < pairs; idx += (long)gridDim.x * blockDim.x) {
+        const int it = (int)(idx / half);
+        const int x = 2 * (int)(idx - (long)it * half);
+        u64 y0[A], y1[A];
+#pragma unroll
+        for (int j = 0; j < A; j++) {
+            const ulonglong2 v = *(const ulonglong2 *)(pcoef + ((long)it * A + j) * N + x);
+            const u64 p = k.p[j];
+            y0[j] = shoup(addmod(v.x, k.hp[j], p), k.pinv[j].w, k.pinv[j].wp, p);
+            y1[j] = shoup(addmod(v.y, k.hp[j], p), k.pinv[j].w, k.pinv[j].wp, p);
+        }
+        const int e0 = md_overflow<A>(y0, k), e1 = md_overflow<A>(y1, k);
+        u64 *op = out + (long)it * nr * N + x;
+        for (int r = 0; r < nr; r++) {
+            const u64 q = s_q[r];
+            u64 a0 = s_E[e0 * nr + r], a1 = s_E[e1 * nr + r];
+#pragma unroll
+            for (int j = 0; j < A; j++) {
+                const ShoupPair w = s_c[j * nr + r];
+                a0 += shoup_lazy(y0[j], w.w, w.wp, q);
+                a1 += shoup_lazy(y1[j], w.w, w.wp, q);
+            }
+            // a0, a1 < (2 A + 1) q <= 9q < 2^64
+            ulonglong2 o;
+            o.x = reduce_any(a0, q, s_w1[r]);
+            o.y = reduce_any(a1, q, s_w1[r]);
+            *(ulonglong2 *)(op + (long)r * N) = o;
+        }
+    }
+}
+
 void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st) {
-    long n = (long)items * c->N;
+    const long pairs = (long)items * (c->N / 2);
+    const unsigned grid = (unsigned)std::min<long>((long)sm_count(c->device) * 8, nblk(pairs, 256));
     c->n_launch++;
     cudaEvent_t e0;
     c->trace_begin(4, e0);
-    k_moddown_bconv<<<nblk(n, 256), 256, 0, st>>>(pcoef, out, items, level, c->alpha, c->L, c->N, c->d_mod,
-                                                  c->d_dn_pinv, c->d_dn_pmod, c->d_dn_hp, c->d_Pmod, c->d_dn_hq);
+    const MdExact &k = c->md_exact;
+    switch (c->alpha) {
+    case 1: k_moddown_bconv<1><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
+    case 2: k_moddown_bconv<2><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
+    case 3: k_moddown_bconv<3><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
+    default: k_moddown_bconv<4><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
+    }
     c->trace_end(4, e0, 8.0 * items * c->N * (c->alpha + level + 1));
 }
 
@@ -658,8 +744,8 @@ __global__ void __launch_bounds__(256, OCC ? OCC : G <= 2 ? 4 : G <= 5 ? 2 : 1) 
 #pragma unroll
             for (int k = 0; k < G; k++) {
                 const u64 *kp = mk.key[k] + (long)d * kd + koff;
-                mac128(a0[k], v, __ldg(kp));
-                mac128(a1[k], v, __ldg(kp + kk));
+                mac128_q(a0[k], v, __ldg(kp), m.q);
+                mac128_q(a1[k], v, __ldg(kp + kk), m.q);
             }
         }
     }
@@ -736,10 +822,10 @@ __global__ void __launch_bounds__(256, OCC) k_multsum_vec(MultiKeys<G> mk, const
             for (int k = 0; k < G; k++) {
                 const ulonglong2 *kp = (const ulonglong2 *)(mk.key[k] + (long)d * kd + koff);
                 const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
-                mac128(acc[0][2 * k], v.x, k0.x);
-                mac128(acc[1][2 * k], v.y, k0.y);
-                mac128(acc[0][2 * k + 1], v.x, k1.x);
-                mac128(acc[1][2 * k + 1], v.y, k1.y);
+                mac128_q(acc[0][2 * k], v.x, k0.x, m.q);
+                mac128_q(acc[1][2 * k], v.y, k0.y, m.q);
+                mac128_q(acc[0][2 * k + 1], v.x, k1.x, m.q);
+                mac128_q(acc[1][2 * k + 1], v.y, k1.y, m.q);
             }
         }
     }
@@ -815,8 +901,8 @@ __global__ void __launch_bounds__(256, OCC) k_multsum_split(const __grid_constan
 #pragma unroll
             for (int k = 0; k < KG; k++) {
                 const u64 *kp = mk.key[kg0 + k] + (long)d * kd + koff;
-                mac128(a0[k], v, __ldg(kp));
-                mac128(a1[k], v, __ldg(kp + kk));
+                mac128_q(a0[k], v, __ldg(kp), m.q);
+                mac128_q(a1[k], v, __ldg(kp + kk), m.q);
             }
         }
     }
@@ -893,10 +979,10 @@ __global__ void __launch_bounds__(256, OCC) k_multsum_splitv(const __grid_consta
             for (int k = 0; k < KG; k++) {
                 const ulonglong2 *kp = (const ulonglong2 *)(mk.key[kg0 + k] + (long)d * kd + koff);
                 const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
-                mac128(acc[0][2 * k], v.x, k0.x);
-                mac128(acc[1][2 * k], v.y, k0.y);
-                mac128(acc[0][2 * k + 1], v.x, k1.x);
-                mac128(acc[1][2 * k + 1], v.y, k1.y);
+                mac128_q(acc[0][2 * k], v.x, k0.x, m.q);
+                mac128_q(acc[1][2 * k], v.y, k0.y, m.q);
+                mac128_q(acc[0][2 * k + 1], v.x, k1.x, m.q);
+                mac128_q(acc[1][2 * k + 1], v.y, k1.y, m.q);
             }
         }
     }
@@ -1182,25 +1268,225 @@ void launch_multsum(Ctx *c, u64 *out, const u64 *digits, const u64 *key, uint32_
     launch_multsum_multi(c, &out, digits, &key, &g, 1, B, level, c0_for_P, c0s, st);
 }
 
+// ------------------------------------------------- C^k babies with masks
+// For k = n1 g + b (b >= 1) the product's C^k step (Sec. 4.1, Table 1
+// "Optimized C^k") needs, over Q_l P,
+//   S_b = m_k (.) rot_qp(A_g; b) + m'_k (.) rot_qp(A'_g; b),
+// rot_qp(X; b) = <kappa_b(digits of X), rtk_b> + (P kappa_b(c0 of X), 0), m_k
+// and m'_k the two column masks (Montgomery form).  The two sources use the
+// same rotation keys: each key word is loaded once for both, and the two
+// hoisted rotations stay in registers, so only S_b reaches memory.  The
+// words equal those of two MultSum launches followed by the masked sum
+// (every value is a canonical residue).
+template <int G>
+struct CkArgs {
+    const u64 *key[G];
+    u64 *out[G];
+    const u64 *m1[G], *m2[G];   // masks over Q_l P, [rows][N]
+    u32 ginv[G];
+};
+
+template <int G>
+__global__ void __launch_bounds__(256, G <= 1 ? 4 : G <= 2 ? 3 : 2)
+    k_multsum_ck(const __grid_constant__ CkArgs<G> ck, const u64 *dig1, const u64 *dig2, int B, int BI, int level,
+                 int alpha, int L, int ndig, int nprimes, int logN, const ModQ *mods, const u64 *c01,
+                 const u64 *c02, long c0s, const ShoupPair *Pmod) {
+    const int N = 1 << logN;
+    const int XW = 256 / BI;
+    const int tx = threadIdx.x % XW, ti = threadIdx.x / XW;
+    const int y = blockIdx.x * XW + tx;
+    const int r = blockIdx.y;
+    const int b = blockIdx.z * BI + ti;
+    if (b >= B || y >= N) return;
+    const int rows = level + 1 + alpha;
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);   // the row's global prime
+    const ModQ m = mods[kr];
+    const long dstride = (long)rows * N;
+    const u64 *dp1 = dig1 + (long)b * ndig * dstride + (long)r * N + y;
+    const u64 *dp2 = dig2 + (long)b * ndig * dstride + (long)r * N + y;
+    const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    U128 acc[G][4];   // (source 1: poly 0, poly 1; source 2: poly 0, poly 1) per key
+    if (m.q < (1ull << 42)) {
+        // residues below 2^42 (uniform over the CTA): 96-bit accumulation
+        u32 x0[4 * G], x1[4 * G], x2[4 * G];
+#pragma unroll
+        for (int k = 0; k < 4 * G; k++) x0[k] = 0, x1[k] = 0, x2[k] = 0;
+        for (int d = 0; d < ndig; d++) {
+            const u64 v1 = __ldg(dp1 + (long)d * dstride), v2 = __ldg(dp2 + (long)d * dstride);
+#pragma unroll
+            for (int k = 0; k < G; k++) {
+                const u64 *kp = ck.key[k] + (long)d * kd + koff;
+                const u64 k0 = __ldg(kp), k1 = __ldg(kp + kk);
+                mac96(x0[4 * k], x1[4 * k], x2[4 * k], v1, k0);
+                mac96(x0[4 * k + 1], x1[4 * k + 1], x2[4 * k + 1], v1, k1);
+                mac96(x0[4 * k + 2], x1[4 * k + 2], x2[4 * k + 2], v2, k0);
+                mac96(x0[4 * k + 3], x1[4 * k + 3], x2[4 * k + 3], v2, k1);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < G; k++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[k][j] = U128{((u64)x1[4 * k + j] << 32) | x0[4 * k + j], x2[4 * k + j]};
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; k++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[k][j] = U128{0, 0};
+        for (int d = 0; d < ndig; d++) {
+            const u64 v1 = __ldg(dp1 + (long)d * dstride), v2 = __ldg(dp2 + (long)d * dstride);
+#pragma unroll
+            for (int k = 0; k < G; k++) {
+                const u64 *kp = ck.key[k] + (long)d * kd + koff;
+                const u64 k0 = __ldg(kp), k1 = __ldg(kp + kk);
+                mac128_q(acc[k][0], v1, k0, m.q);
+                mac128_q(acc[k][1], v1, k1, m.q);
+                mac128_q(acc[k][2], v2, k0, m.q);
+                mac128_q(acc[k][3], v2, k1, m.q);
+            }
+        }
+    }
+    u64 pc1 = 0, pc2 = 0;
+    if (r <= level) {
+        const ShoupPair w = Pmod[r];
+        pc1 = shoup(c01[b * c0s + (long)r * N + y], w.w, w.wp, m.q);
+        pc2 = shoup(c02[b * c0s + (long)r * N + y], w.w, w.wp, m.q);
+    }
+#pragma unroll
+    for (int k = 0; k < G; k++) {
+        const u64 a10 = addmod(redc(acc[k][0].lo, acc[k][0].hi, m), pc1, m.q);
+        const u64 a11 = redc(acc[k][1].lo, acc[k][1].hi, m);
+        const u64 a20 = addmod(redc(acc[k][2].lo, acc[k][2].hi, m), pc2, m.q);
+        const u64 a21 = redc(acc[k][3].lo, acc[k][3].hi, m);
+        const int x = ck.ginv[k] == 1u ? y : auto_index(y, ck.ginv[k], logN);
+        const u64 w1 = __ldg(ck.m1[k] + (long)r * N + x), w2 = __ldg(ck.m2[k] + (long)r * N + x);
+        U128 s0 = {0, 0}, s1 = {0, 0};   // two products below q^2: below q 2^64
+        mac128(s0, w1, a10);
+        mac128(s0, w2, a20);
+        mac128(s1, w1, a11);
+        mac128(s1, w2, a21);
+        u64 *ob = ck.out[k] + (long)b * 2 * rows * N;
+        ob[(long)r * N + x] = redc(s0.lo, s0.hi, m);
+        ob[(long)(rows + r) * N + x] = redc(s1.lo, s1.hi, m);
+    }
+}
+
+template <int G>
+static void multsum_ck_launch_g(Ctx *c, int BI, u64 *const *outs, const u64 *dig1, const u64 *dig2,
+                                const u64 *const *keys, const uint32_t *gs, const u64 *const *m1,
+                                const u64 *const *m2, int B, int level, const u64 *c01, const u64 *c02, long c0s,
+                                cudaStream_t st) {
+    CkArgs<G> ck;
+    const u32 M = 2u * (u32)c->N;
+    for (int k = 0; k < G; k++) {
+        ck.key[k] = keys[k];
+        ck.out[k] = outs[k];
+        ck.m1[k] = m1[k];
+        ck.m2[k] = m2[k];
+        u32 g = gs[k], inv = g;   // inverse of the odd g modulo 2N (Newton on 32-bit words)
+        for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
+        ck.ginv[k] = inv & (M - 1);
+    }
+    const int rows = level + 1 + c->alpha, XW = 256 / BI;
+    dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
+    k_multsum_ck<G><<<grid, 256, 0, st>>>(ck, dig1, dig2, B, BI, level, c->alpha, c->L, c->ndig(level), c->nprimes,
+                                          c->logN, c->d_mod, c01, c02, c0s, c->d_Pmod);
+    c->n_launch++;
+}
+
+void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig2, const u64 *const *keys,
+                       const uint32_t *gs, const u64 *const *m1, const u64 *const *m2, int G, int B, int level,
+                       const u64 *c01, const u64 *c02, long c0s, cudaStream_t st) {
+    if (G <= 0) return;
+    const int rows = level + 1 + c->alpha;
+    auto run = [&](int chunk, int BI, bool traced) {
+        for (int k0 = 0; k0 < G; k0 += chunk) {
+            const int g = std::min(chunk, G - k0);
+            cudaEvent_t e0 = nullptr;
+            if (traced) c->trace_begin(0, e0);
+            switch (g) {
+            case 1: multsum_ck_launch_g<1>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
+            case 2: multsum_ck_launch_g<2>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
+            case 3: multsum_ck_launch_g<3>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
+            default: multsum_ck_launch_g<4>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
+            }
+            if (traced) {
+                // algorithmic bytes: every key and every mask read once, both
+                // sources' digits and c0 read once per item, one output per
+                // (item, key)
+                const double nd = c->ndig(level), W = (double)c->N * 8.0;
+                const double bytes = g * (2.0 * nd * rows + 2.0 * rows) * W +
+                                     (double)B * (2.0 * nd * rows * W + 2.0 * (level + 1) * W + g * 2.0 * rows * W);
+                c->trace_end(0, e0, bytes);
+            }
+        }
+    };
+    int chunk = std::min(G, 4), BI = std::min(B, 8);
+    while (BI > 1 && BI > B) BI >>= 1;
+    if (c->autotune) {
+        auto key3 = std::make_tuple(level, B, G);
+        auto it = c->tune_ck.find(key3);
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        if (it != c->tune_ck.end()) {
+            chunk = it->second >> 8, BI = it->second & 255;
+        } else if (cap == cudaStreamCaptureStatusNone) {
+            // time every (keys per launch, items per CTA) twice on these very
+            // launches (the outputs do not depend on the plan); keep the fastest
+            cudaEvent_t a = c->ev_get(), b = c->ev_get();
+            float best = 1e30f;
+            std::set<std::pair<int, int>> seen;
+            for (int ch : {4, 2, 1}) {
+                for (int bi : {8, 4, 2, 1}) {
+                    const int cc = std::min(ch, G);
+                    int bb = bi;
+                    while (bb > 1 && bb > B) bb >>= 1;
+                    if (!seen.insert(std::make_pair(cc, bb)).second) continue;
+                    float t = 1e30f;
+                    for (int rep = 0; rep < 2; rep++) {
+                        cudaEventRecord(a, st);
+                        run(cc, bb, false);
+                        cudaEventRecord(b, st);
+                        cudaEventSynchronize(b);
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, a, b);
+                        t = std::min(t, ms);
+                    }
+                    if (t < best) best = t, chunk = cc, BI = bb;
+                    char line[128];
+                    snprintf(line, sizeof line, "multsum_ck level %d B %d G %d chunk %d BI %d ms %.4f\n", level, B,
+                             G, cc, bb, t);
+                    c->tune_log += line;
+                }
+            }
+            c->ev_free.push_back(a);
+            c->ev_free.push_back(b);
+            c->tune_ck[key3] = (chunk << 8) | BI;
+        }
+    }
+    run(chunk, BI, true);
+}
+
 // ------------------------------------------------------ double hoisting
 // S[b][k][r][x] = sum_t ptM_t[r][x] * R_t[b][k][r][x] over Q_l P (one REDC).
 struct PtrList {
     const u64 *p[32];
 };
+// The sums of up to 32 products stay below q 2^64 (mac128_q), so one REDC
+// per output word.
 __global__ void k_pmul_acc(u64 *out, PtrList pts, PtrList R, int nterms, int B, int rows, int N, long Rs,
                            RowMap qp, const ModQ *mods) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long per = (long)rows * N;
     if (idx >= per) return;
     int r = (int)(idx / N);
-    const ModQ &m = mods[qp.at(r)];
+    const ModQ m = mods[qp.at(r)];
     for (int b = 0; b < B; b++) {
         U128 a0 = {0, 0}, a1 = {0, 0};
         for (int t = 0; t < nterms; t++) {
-            u64 pv = pts.p[t][idx];
+            const u64 pv = pts.p[t][idx];
             const u64 *rb = R.p[t] + b * Rs;
-            mac128(a0, pv, rb[idx]);
-            mac128(a1, pv, rb[per + idx]);
+            mac128_q(a0, pv, rb[idx], m.q);
+            mac128_q(a1, pv, rb[per + idx], m.q);
         }
         u64 *ob = out + (long)b * 2 * per;
         ob[idx] = redc(a0.lo, a0.hi, m);

@@ -84,6 +84,15 @@ __device__ __forceinline__ void mac128(U128 &acc, u64 a, u64 b) {
     acc.lo = nlo;
 }
 
+// acc += a b for residues a, b < q < 2^60, keeping acc below q 2^64 (the
+// Montgomery reduction's input bound) however many terms are summed: each
+// product is below q 2^60, so after it the high word is below q + q/16 + 1,
+// and subtracting q 2^64 (a multiple of q) once restores the bound.
+__device__ __forceinline__ void mac128_q(U128 &acc, u64 a, u64 b, u64 q) {
+    mac128(acc, a, b);
+    if (acc.hi >= q) acc.hi -= q;
+}
+
 // 96-bit accumulation (w2 w1 w0) of products of residues below 2^42: each
 // product is below 2^84, so a sum of up to 2^12 of them stays below 2^96.
 // (w2 w1 w0) += a b from the four 32 x 32 partial products with the carry

@@ -95,7 +95,7 @@ struct MstAcc<G, true> {
 #pragma unroll
             for (int k = 0; k < 2 * G; k++) x0[i][k] = 0, x1[i][k] = 0, x2[i][k] = 0;
     }
-    __device__ __forceinline__ void mac(int i, int k, u64 v, u64 key) { mac96(x0[i][k], x1[i][k], x2[i][k], v, key); }
+    __device__ __forceinline__ void mac(int i, int k, u64 v, u64 key, u64) { mac96(x0[i][k], x1[i][k], x2[i][k], v, key); }
     __device__ __forceinline__ u64 out(int i, int k, const ModQ &m) const {
         return redc(((u64)x1[i][k] << 32) | x0[i][k], x2[i][k], m);
     }
@@ -109,7 +109,7 @@ struct MstAcc<G, false> {
 #pragma unroll
             for (int k = 0; k < 2 * G; k++) w[i][k] = U128{0, 0};
     }
-    __device__ __forceinline__ void mac(int i, int k, u64 v, u64 key) { mac128(w[i][k], v, key); }
+    __device__ __forceinline__ void mac(int i, int k, u64 v, u64 key, u64 q) { mac128_q(w[i][k], v, key, q); }
     __device__ __forceinline__ u64 out(int i, int k, const ModQ &m) const { return redc(w[i][k].lo, w[i][k].hi, m); }
 };
 
@@ -142,8 +142,8 @@ __device__ __forceinline__ bool mst_tile(const MultiKeys<G> &mk, const MstGeom &
         if (lane == 0) bc_arrive(&empty[s]);
 #pragma unroll
         for (int k = 0; k < 2 * G; k++) {
-            acc.mac(0, k, v0, kv[k]);
-            acc.mac(1, k, v1, kv[k]);
+            acc.mac(0, k, v0, kv[k], m.q);
+            acc.mac(1, k, v1, kv[k], m.q);
         }
     }
     // epilogue: one Montgomery reduction per output word, P c0 on the Q rows
