@@ -452,6 +452,20 @@ int he_trace_enable(he_ctx *ctx, int on);
 int he_bench_butterfly(int iters, double *bfly_per_s);
 int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, double *bytes, int reset);
 
+/* Arithmetic of a traced class since its last reset by he_trace_read:
+ * for class 0 (MultSum) the number of digit-key products accumulated (each
+ * (digit word, key word) pair of every output word); 0 for the other
+ * classes.  Read it before the he_trace_read call that resets the class.
+ * Errors: HE_ERR_ARG. */
+int he_trace_ops(he_ctx *ctx, int cls, double *ops);
+
+/* Integer roofline of MultSum: measured rate (products per second) of the
+ * 96-bit product accumulation of its 40-bit limbs (eight 32-bit
+ * multiply-adds with carries per product) with register operands on the
+ * current device, `iters` rounds of 16 products per thread over 8 CTAs of
+ * 256 threads per SM.  Errors: HE_ERR_ARG, HE_ERR_CUDA. */
+int he_bench_mac(int iters, double *products_per_s);
+
 /* Captured batched products.  he_mm_plan_create runs the jobs once (grouped
  * as he_hmatmul_batch groups them: context, level, block size, schedule) and
  * records every launch of that batched step -- gathers, replication, the

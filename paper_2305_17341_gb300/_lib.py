@@ -135,6 +135,8 @@ SIGNATURES = {
     "he_counters": [vp, llp, llp, llp, llp, ip],
     "he_trace_enable": [vp, ip],
     "he_bench_butterfly": [ip, P(ctypes.c_double)],
+    "he_bench_mac": [ip, P(ctypes.c_double)],
+    "he_trace_ops": [vp, ip, P(ctypes.c_double)],
     "he_trace_read": [vp, ip, llp, P(ctypes.c_double), P(ctypes.c_double), ip],
     "he_mm_plan_create": [P(he_mm_job), ip, P(vp)],
     "he_mm_plan_run": [vp, P(vp)],
@@ -520,9 +522,18 @@ def he_bench_butterfly(iters=2000):
 
 
 def he_trace_read(ctx, cls, reset=False):
-    n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    """Launches, device time (ms), algorithmic bytes and (MultSum) products of
+    a traced kernel class since its last reset."""
+    n, ms, by, ops = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib().he_trace_ops(ctx, cls, ctypes.byref(ops)))
     check(lib().he_trace_read(ctx, cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), 1 if reset else 0))
-    return {"count": n.value, "ms": ms.value, "bytes": by.value}
+    return {"count": n.value, "ms": ms.value, "bytes": by.value, "ops": ops.value}
+
+
+def he_bench_mac(iters=2000):
+    v = ctypes.c_double()
+    check(lib().he_bench_mac(iters, ctypes.byref(v)))
+    return v.value
 
 
 def he_counters(ctx, reset=False):

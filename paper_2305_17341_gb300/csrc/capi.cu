@@ -973,8 +973,22 @@ int he_trace_read(he_ctx *ctx, int cls, long long *count, double *total_ms, doub
     if (bytes) *bytes = t.bytes;
     if (reset) {
         t.count = 0;
-        t.total_ms = t.bytes = 0;
+        t.total_ms = t.bytes = t.ops = 0;
     }
+    return HE_OK;
+}
+
+int he_trace_ops(he_ctx *ctx, int cls, double *ops) {
+    if (!ctx || !ops || cls < 0 || cls > 4) return fail(HE_ERR_ARG, "bad arguments");
+    *ops = ctx->c.tr[cls].ops;
+    return HE_OK;
+}
+
+int he_bench_mac(int iters, double *products_per_s) {
+    if (!products_per_s || iters < 1) return fail(HE_ERR_ARG, "bad arguments");
+    *products_per_s = mac_peak(iters);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HE_ERR_CUDA, cudaGetErrorString(e));
     return HE_OK;
 }
 

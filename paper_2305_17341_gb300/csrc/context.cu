@@ -238,12 +238,13 @@ void Ctx::trace_begin(int cls, cudaEvent_t &e0) {
     cudaEventRecord(e0, stream);
 }
 
-void Ctx::trace_end(int cls, cudaEvent_t e0, double bytes) {
+void Ctx::trace_end(int cls, cudaEvent_t e0, double bytes, double ops) {
     if (!trace || !e0) return;
     cudaEvent_t e1 = ev_get();
     cudaEventRecord(e1, stream);
     tr[cls].pending.push_back({e0, e1});
     tr[cls].bytes += bytes;
+    tr[cls].ops += ops;
     tr[cls].count++;
 }
 

@@ -19,6 +19,7 @@ void encrypt_poly(Ctx *c, const u64 *m_ntt, int level, uint32_t obj, bool refres
 void encode_to(Ctx *c, const double *d_zr, const double *d_zi, double scale, u64 *out, int rows, const RowMap &rm);
 const char *last_error();
 double bfly_peak(int iters);
+double mac_peak(int iters);
 
 void modup(Ctx *c, const u64 *poly, long item_s, int B, int level, u64 *digits);
 // add (may be null, item stride add_s; may equal out): out = add + ModDown(u)

@@ -188,7 +188,7 @@ struct Ctx {
     // launch of a traced class, with the launch's algorithmic bytes
     struct TraceClass {
         std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
-        double total_ms = 0, bytes = 0;
+        double total_ms = 0, bytes = 0, ops = 0;   // ops: digit-key products (MultSum)
         long long count = 0;
     };
     bool trace = false;
@@ -215,7 +215,7 @@ struct Ctx {
     std::vector<cudaEvent_t> ev_free;
     cudaEvent_t ev_get();
     void trace_begin(int cls, cudaEvent_t &e0);
-    void trace_end(int cls, cudaEvent_t e0, double bytes);
+    void trace_end(int cls, cudaEvent_t e0, double bytes, double ops = 0);
     void trace_collect();
 
     // helpers

@@ -1210,7 +1210,7 @@ void launch_multsum_multi(Ctx *c, u64 *const *outs, const u64 *digits, const u64
                 double nd = c->ndig(level), W = (double)c->N * 8.0;
                 double bytes = g * 2.0 * nd * rows * W +
                                (double)B * (nd * rows * W + g * 2.0 * rows * W + (c0_for_P ? (level + 1) * W : 0));
-                c->trace_end(0, e0, bytes);
+                c->trace_end(0, e0, bytes, (double)B * nd * rows * c->N * 2.0 * g);
             }
         }
     };
@@ -1416,7 +1416,7 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
                 const double nd = c->ndig(level), W = (double)c->N * 8.0;
                 const double bytes = g * (2.0 * nd * rows + 2.0 * rows) * W +
                                      (double)B * (2.0 * nd * rows * W + 2.0 * (level + 1) * W + g * 2.0 * rows * W);
-                c->trace_end(0, e0, bytes);
+                c->trace_end(0, e0, bytes, (double)B * nd * rows * c->N * 4.0 * g);
             }
         }
     };

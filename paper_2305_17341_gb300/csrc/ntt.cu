@@ -948,6 +948,52 @@ double bfly_peak(int iters) {
     return bfly / (ms * 1e-3);
 }
 
+// Integer roofline of MultSum: the rate of its inner step on the 40-bit
+// limbs, one digit-key product accumulated into 96 bits (mac96: eight 32-bit
+// multiply-adds with carries), operands in registers, 16 independent
+// accumulators per thread, 8 CTAs of 256 threads per SM.  Only the
+// instruction stream matters; the sums are kept alive through a store that
+// never happens.
+__global__ void k_mac_peak(u64 *sink, int iters, u64 seed) {
+    u32 x0[16], x1[16], x2[16];
+    u64 kk[16];
+    u64 v = (seed ^ threadIdx.x) & ((1ull << 42) - 1);
+#pragma unroll
+    for (int k = 0; k < 16; k++) x0[k] = x1[k] = x2[k] = 0, kk[k] = (seed * (k + 3)) & ((1ull << 42) - 1);
+    for (int it = 0; it < iters; it++) {
+        v = (v + 0x9E3779B97F4A7C15ull) & ((1ull << 42) - 1);
+#pragma unroll
+        for (int k = 0; k < 16; k++) mac96(x0[k], x1[k], x2[k], v, kk[k]);
+    }
+    u32 acc = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc ^= x0[k] ^ x1[k] ^ x2[k];
+    if (acc == 0x1234567u) sink[0] = acc;
+}
+
+double mac_peak(int iters) {
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    u64 *sink;
+    cudaMalloc(&sink, 8);
+    const int blocks = nsm * 8, threads = 256;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_mac_peak<<<blocks, threads>>>(sink, 16, 12345);   // warm-up
+    cudaEventRecord(a);
+    k_mac_peak<<<blocks, threads>>>(sink, iters, 12345);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return (double)blocks * threads * iters * 16.0 / (ms * 1e-3);
+}
+
 // ----------------------------------------------------------------- launch
 static void split(int logN, int &logN1, int &C, int &R) {
     logN1 = logN / 2;

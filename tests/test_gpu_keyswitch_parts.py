@@ -177,3 +177,27 @@ def test_rotation_with_48_digits_equals_oracle(lib):
             lib.he_ct_free(h)
     finally:
         lib.he_ctx_destroy(ctx)
+
+
+def test_multsum_products_are_counted_and_the_product_rate_is_measured(lib):
+    """The MultSum trace counts every digit-key product (one rotation at
+    config 1's top level: 4 digits x 5 rows x N x 2 polynomials), and the
+    product-accumulate microbenchmark runs."""
+    ctx = lib.he_ctx_create(lib.he_params_default(1), 5)
+    try:
+        lib.he_keygen(ctx, [1], want_relin=False)
+        z = np.random.default_rng(2).uniform(-1, 1, 1 << 13)
+        g = lib.he_encrypt_slots(ctx, z, 3, 9)
+        lib.he_ctx_set_autotune(ctx, False)
+        lib.he_trace_enable(ctx, True)
+        for c in range(5):
+            lib.he_trace_read(ctx, c, reset=True)
+        r = lib.he_rotate(ctx, g, 1)
+        t = lib.he_trace_read(ctx, 0, reset=True)
+        lib.he_trace_enable(ctx, False)
+        assert t["count"] == 1 and t["ops"] == 4 * 5 * (1 << 14) * 2
+        for h in (g, r):
+            lib.he_ct_free(h)
+    finally:
+        lib.he_ctx_destroy(ctx)
+    assert lib.he_bench_mac(200) > 1e11
