@@ -356,8 +356,11 @@ void launch_tensor_acc(Ctx *c, u64 *d01, u64 *d2, const u64 *a, const u64 *b, in
 // blockIdx.y is the digit: a CTA stages that digit's conversion constants
 // and row primes in shared memory once and walks (item, coefficient pair)
 // with a grid stride.  Each thread converts two adjacent coefficients with
-// 16-byte loads and stores; the A lazy Shoup products of a row (each in
-// [0, 2r)) are summed and reduced once.
+// 16-byte loads and stores.  When the digit's primes and the row's prime are
+// below 2^42 the products y_i (w_i 2^64 mod r) accumulate in 96 bits with
+// carry-chained 32-bit multiply-adds and one Montgomery reduction ends the
+// row; otherwise the A lazy Shoup products (each in [0, 2r)) are summed and
+// reduced once.
 static int sm_count(int dev) {
     static int n[64];
     dev &= 63;
@@ -370,24 +373,30 @@ __global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, 
                                                      RowMap qp, const ModQ *mods, const ShoupPair *up_inv,
                                                      const ShoupPair *up_mod, const u64 *own_ntt, long own_s) {
     __shared__ ShoupPair s_mod[A * 64];   // [s][r], rows <= 64
-    __shared__ u64 s_q[64], s_w1[64];
+    __shared__ u64 s_mont[A * 64];        // w 2^64 mod r of the same constants
+    __shared__ u64 s_q[64], s_w1[64], s_qinv[64];
     const int d = blockIdx.y;
     const int rows = level + 1 + A;
     const int i0 = d * A;
     const int ns = min(A, level + 1 - i0);
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
         const ModQ m = mods[r <= qp.lq ? r : qp.base_p + (r - qp.lq - 1)];   // qp is unshifted
-        s_q[r] = m.q, s_w1[r] = m.wone;
+        s_q[r] = m.q, s_w1[r] = m.wone, s_qinv[r] = m.qinv;
     }
+    __syncthreads();
     for (int e = threadIdx.x; e < ns * rows; e += blockDim.x) {
         const int sd = e / rows, r = e - sd * rows;
-        s_mod[e] = up_mod[((long)d * A + sd) * rows + r];
+        const ShoupPair w = up_mod[((long)d * A + sd) * rows + r];
+        s_mod[e] = w;
+        // w 2^64 - w' r is in [0, r) and congruent to -w' r modulo 2^64
+        s_mont[e] = (u64)0 - w.wp * s_q[r];
     }
     ShoupPair inv[A];
     u64 qs[A];
+    bool narrow = true;   // every source prime below 2^42 (uniform over the CTA)
 #pragma unroll
     for (int sd = 0; sd < A; sd++)
-        if (sd < ns) inv[sd] = up_inv[d * A + sd], qs[sd] = mods[i0 + sd].q;
+        if (sd < ns) inv[sd] = up_inv[d * A + sd], qs[sd] = mods[i0 + sd].q, narrow = narrow && qs[sd] < (1ull << 42);
     __syncthreads();
     const int half = N / 2;
     const long pairs = (long)B * half;
@@ -411,6 +420,19 @@ __global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, 
             if (r >= i0 && r < i0 + ns) {   // uniform over the CTA
                 const u64 *src = own_ntt ? own_ntt + (long)b * own_s + (long)r * N + x : cb + (long)r * N;
                 o = *(const ulonglong2 *)src;
+            } else if (narrow && s_q[r] < (1ull << 42)) {   // uniform over the CTA
+                // products below 2^84: A of them stay below 2^86 < r 2^64
+                u32 a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
+#pragma unroll
+                for (int sd = 0; sd < A; sd++) {
+                    if (sd < ns) {
+                        const u64 wm = s_mont[sd * rows + r];
+                        mac96(a0, a1, a2, y0[sd], wm);
+                        mac96(c0, c1, c2, y1[sd], wm);
+                    }
+                }
+                o.x = redc_q(((u64)a1 << 32) | a0, a2, s_q[r], s_qinv[r]);
+                o.y = redc_q(((u64)c1 << 32) | c0, c2, s_q[r], s_qinv[r]);
             } else {
                 const u64 q = s_q[r];
                 u64 a0 = 0, a1 = 0;

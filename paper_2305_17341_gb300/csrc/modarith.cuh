@@ -111,6 +111,13 @@ __device__ __forceinline__ void mac96(u32 &w0, u32 &w1, u32 &w2, u64 a, u64 b) {
         : "r"(a0), "r"(a1), "r"(b0), "r"(b1));
 }
 
+// Montgomery REDC with the prime and -q^-1 mod 2^64 given directly.
+__device__ __forceinline__ u64 redc_q(u64 lo, u64 hi, u64 q, u64 qinv) {
+    const u64 t = lo * qinv;
+    const u64 r = hi + mulhi64(t, q) + (lo != 0 ? 1ull : 0ull);
+    return r >= q ? r - q : r;
+}
+
 // Montgomery REDC: x * 2^-64 mod q for x < q 2^64, result in [0, q).
 __device__ __forceinline__ u64 redc(u64 lo, u64 hi, const ModQ &m) {
     u64 t = lo * m.qinv;
