@@ -368,7 +368,32 @@ static int sm_count(int dev) {
     return n[dev] > 0 ? n[dev] : 1;
 }
 
-template <int A>
+// C adjacent words, one 16-byte access for C = 2
+template <int C>
+struct Words {
+    u64 w[C];
+};
+template <int C>
+__device__ __forceinline__ Words<C> load_words(const u64 *p) {
+    Words<C> r;
+    if constexpr (C == 2) {
+        const ulonglong2 v = *(const ulonglong2 *)p;
+        r.w[0] = v.x, r.w[1] = v.y;
+    } else {
+        r.w[0] = *p;
+    }
+    return r;
+}
+template <int C>
+__device__ __forceinline__ void store_words(u64 *p, const Words<C> &r) {
+    if constexpr (C == 2) *(ulonglong2 *)p = make_ulonglong2(r.w[0], r.w[1]);
+    else *p = r.w[0];
+}
+
+// A: special primes per digit; C: adjacent coefficients per thread (2 on
+// launches that fill the GPU, 1 on small ones, where more threads hide more
+// latency).
+template <int A, int C>
 __global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, int B, int level, int ndig, int N,
                                                      RowMap qp, const ModQ *mods, const ShoupPair *up_inv,
                                                      const ShoupPair *up_mod, const u64 *own_ntt, long own_s) {
@@ -398,74 +423,90 @@ __global__ void __launch_bounds__(256) k_modup_bconv(const u64 *coef, u64 *out, 
     for (int sd = 0; sd < A; sd++)
         if (sd < ns) inv[sd] = up_inv[d * A + sd], qs[sd] = mods[i0 + sd].q, narrow = narrow && qs[sd] < (1ull << 42);
     __syncthreads();
-    const int half = N / 2;
-    const long pairs = (long)B * half;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < pairs; idx += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(idx / half);
-        const int x = 2 * (int)(idx - (long)b * half);
+    const int per = N / C;
+    const long units = (long)B * per;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < units; idx += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / per);
+        const int x = C * (int)(idx - (long)b * per);
         const u64 *cb = coef + (long)b * (level + 1) * N + x;
         u64 *ob = out + ((long)b * ndig + d) * rows * N + x;
-        u64 y0[A], y1[A];
+        u64 y[C][A];
 #pragma unroll
         for (int sd = 0; sd < A; sd++) {
-            y0[sd] = y1[sd] = 0;
+#pragma unroll
+            for (int c = 0; c < C; c++) y[c][sd] = 0;
             if (sd < ns) {
-                const ulonglong2 v = *(const ulonglong2 *)(cb + (long)(i0 + sd) * N);
-                y0[sd] = shoup(v.x, inv[sd].w, inv[sd].wp, qs[sd]);
-                y1[sd] = shoup(v.y, inv[sd].w, inv[sd].wp, qs[sd]);
+                const Words<C> v = load_words<C>(cb + (long)(i0 + sd) * N);
+#pragma unroll
+                for (int c = 0; c < C; c++) y[c][sd] = shoup(v.w[c], inv[sd].w, inv[sd].wp, qs[sd]);
             }
         }
         for (int r = 0; r < rows; r++) {
-            ulonglong2 o;
+            Words<C> o;
             if (r >= i0 && r < i0 + ns) {   // uniform over the CTA
-                const u64 *src = own_ntt ? own_ntt + (long)b * own_s + (long)r * N + x : cb + (long)r * N;
-                o = *(const ulonglong2 *)src;
+                o = load_words<C>(own_ntt ? own_ntt + (long)b * own_s + (long)r * N + x : cb + (long)r * N);
             } else if (narrow && s_q[r] < (1ull << 42)) {   // uniform over the CTA
                 // products below 2^84: A of them stay below 2^86 < r 2^64
-                u32 a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
+                u32 w0[C], w1[C], w2[C];
+#pragma unroll
+                for (int c = 0; c < C; c++) w0[c] = w1[c] = w2[c] = 0;
 #pragma unroll
                 for (int sd = 0; sd < A; sd++) {
                     if (sd < ns) {
                         const u64 wm = s_mont[sd * rows + r];
-                        mac96(a0, a1, a2, y0[sd], wm);
-                        mac96(c0, c1, c2, y1[sd], wm);
+#pragma unroll
+                        for (int c = 0; c < C; c++) mac96(w0[c], w1[c], w2[c], y[c][sd], wm);
                     }
                 }
-                o.x = redc_q(((u64)a1 << 32) | a0, a2, s_q[r], s_qinv[r]);
-                o.y = redc_q(((u64)c1 << 32) | c0, c2, s_q[r], s_qinv[r]);
+#pragma unroll
+                for (int c = 0; c < C; c++) o.w[c] = redc_q(((u64)w1[c] << 32) | w0[c], w2[c], s_q[r], s_qinv[r]);
             } else {
                 const u64 q = s_q[r];
-                u64 a0 = 0, a1 = 0;
+                u64 acc[C];
+#pragma unroll
+                for (int c = 0; c < C; c++) acc[c] = 0;
 #pragma unroll
                 for (int sd = 0; sd < A; sd++) {
                     if (sd < ns) {
                         const ShoupPair w = s_mod[sd * rows + r];
-                        a0 += shoup_lazy(y0[sd], w.w, w.wp, q);
-                        a1 += shoup_lazy(y1[sd], w.w, w.wp, q);
+#pragma unroll
+                        for (int c = 0; c < C; c++) acc[c] += shoup_lazy(y[c][sd], w.w, w.wp, q);
                     }
                 }
-                // a0, a1 < 2 A q <= 8q < 2^64
-                o.x = reduce_any(a0, q, s_w1[r]);
-                o.y = reduce_any(a1, q, s_w1[r]);
+                // < 2 A q <= 8q < 2^64
+#pragma unroll
+                for (int c = 0; c < C; c++) o.w[c] = reduce_any(acc[c], q, s_w1[r]);
             }
-            *(ulonglong2 *)(ob + (long)r * N) = o;
+            store_words<C>(ob + (long)r * N, o);
         }
     }
 }
 
-static void modup_launch(Ctx *c, const u64 *coef, u64 *out, int B, int level, int nd, const ShoupPair *up_inv,
-                         const ShoupPair *up_mod, const u64 *own_ntt, long own_s, cudaStream_t st) {
-    const long pairs = (long)B * (c->N / 2);
-    // about 8 CTAs of 256 threads per SM over all digits
-    long gx = std::max(1L, (long)sm_count(c->device) * 8 / nd);
-    gx = std::min(gx, (long)nblk(pairs, 256));
+template <int A>
+static void modup_launch_a(Ctx *c, const u64 *coef, u64 *out, int B, int level, int nd, const ShoupPair *up_inv,
+                           const ShoupPair *up_mod, const u64 *own_ntt, long own_s, cudaStream_t st) {
+    const int nsm = sm_count(c->device);
+    // two coefficients per thread once the launch fills the GPU with 8 CTAs
+    // of 256 threads per SM, one below that
+    const bool wide = (long)B * (c->N / 2) * nd >= (long)nsm * 8 * 256;
+    const long units = (long)B * (c->N / (wide ? 2 : 1));
+    long gx = std::max(1L, (long)nsm * 8 / nd);
+    gx = std::min(gx, (long)nblk(units, 256));
     const dim3 grid((unsigned)gx, (unsigned)nd);
     const RowMap qp = c->map_qp(level);
+    if (wide)
+        k_modup_bconv<A, 2><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s);
+    else
+        k_modup_bconv<A, 1><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s);
+}
+
+static void modup_launch(Ctx *c, const u64 *coef, u64 *out, int B, int level, int nd, const ShoupPair *up_inv,
+                         const ShoupPair *up_mod, const u64 *own_ntt, long own_s, cudaStream_t st) {
     switch (c->alpha) {
-    case 1: k_modup_bconv<1><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
-    case 2: k_modup_bconv<2><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
-    case 3: k_modup_bconv<3><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
-    default: k_modup_bconv<4><<<grid, 256, 0, st>>>(coef, out, B, level, nd, c->N, qp, c->d_mod, up_inv, up_mod, own_ntt, own_s); break;
+    case 1: modup_launch_a<1>(c, coef, out, B, level, nd, up_inv, up_mod, own_ntt, own_s, st); break;
+    case 2: modup_launch_a<2>(c, coef, out, B, level, nd, up_inv, up_mod, own_ntt, own_s, st); break;
+    case 3: modup_launch_a<3>(c, coef, out, B, level, nd, up_inv, up_mod, own_ntt, own_s, st); break;
+    default: modup_launch_a<4>(c, coef, out, B, level, nd, up_inv, up_mod, own_ntt, own_s, st); break;
     }
 }
 
@@ -583,10 +624,11 @@ __device__ __forceinline__ int md_overflow(const u64 (&y)[A], const MdExact &k) 
     }
 }
 
-// Two adjacent coefficients per thread (16-byte loads and stores), a grid
-// stride over (item, pair); per row the lazy Shoup products and E are
-// summed and reduced once.
-template <int A>
+// C adjacent coefficients per thread (2: 16-byte loads and stores, on
+// launches that fill the GPU; 1 on small ones), a grid stride over (item,
+// coefficient group); per row the lazy Shoup products and E are summed and
+// reduced once.
+template <int A, int C>
 __global__ void __launch_bounds__(256) k_moddown_bconv(const u64 *pcoef, u64 *out, int items, int level, int N,
                                                        const __grid_constant__ MdExact k, const ModQ *mods,
                                                        const ShoupPair *pmod, const u64 *E, int L) {
@@ -600,51 +642,65 @@ __global__ void __launch_bounds__(256) k_moddown_bconv(const u64 *pcoef, u64 *ou
         s_E[e] = E[j * (L + 1) + r];
     }
     __syncthreads();
-    const int half = N / 2;
-    const long pairs = (long)items * half;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < pairs; idx += (long)gridDim.x * blockDim.x) {
-        const int it = (int)(idx / half);
-        const int x = 2 * (int)(idx - (long)it * half);
-        u64 y0[A], y1[A];
+    const int per = N / C;
+    const long units = (long)items * per;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < units; idx += (long)gridDim.x * blockDim.x) {
+        const int it = (int)(idx / per);
+        const int x = C * (int)(idx - (long)it * per);
+        u64 y[C][A];
 #pragma unroll
         for (int j = 0; j < A; j++) {
-            const ulonglong2 v = *(const ulonglong2 *)(pcoef + ((long)it * A + j) * N + x);
+            const Words<C> v = load_words<C>(pcoef + ((long)it * A + j) * N + x);
             const u64 p = k.p[j];
-            y0[j] = shoup(addmod(v.x, k.hp[j], p), k.pinv[j].w, k.pinv[j].wp, p);
-            y1[j] = shoup(addmod(v.y, k.hp[j], p), k.pinv[j].w, k.pinv[j].wp, p);
+#pragma unroll
+            for (int c = 0; c < C; c++) y[c][j] = shoup(addmod(v.w[c], k.hp[j], p), k.pinv[j].w, k.pinv[j].wp, p);
         }
-        const int e0 = md_overflow<A>(y0, k), e1 = md_overflow<A>(y1, k);
+        int e[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) e[c] = md_overflow<A>(y[c], k);
         u64 *op = out + (long)it * nr * N + x;
         for (int r = 0; r < nr; r++) {
             const u64 q = s_q[r];
-            u64 a0 = s_E[e0 * nr + r], a1 = s_E[e1 * nr + r];
+            u64 acc[C];
+#pragma unroll
+            for (int c = 0; c < C; c++) acc[c] = s_E[e[c] * nr + r];
 #pragma unroll
             for (int j = 0; j < A; j++) {
                 const ShoupPair w = s_c[j * nr + r];
-                a0 += shoup_lazy(y0[j], w.w, w.wp, q);
-                a1 += shoup_lazy(y1[j], w.w, w.wp, q);
+#pragma unroll
+                for (int c = 0; c < C; c++) acc[c] += shoup_lazy(y[c][j], w.w, w.wp, q);
             }
-            // a0, a1 < (2 A + 1) q <= 9q < 2^64
-            ulonglong2 o;
-            o.x = reduce_any(a0, q, s_w1[r]);
-            o.y = reduce_any(a1, q, s_w1[r]);
-            *(ulonglong2 *)(op + (long)r * N) = o;
+            // < (2 A + 1) q <= 9q < 2^64
+            Words<C> o;
+#pragma unroll
+            for (int c = 0; c < C; c++) o.w[c] = reduce_any(acc[c], q, s_w1[r]);
+            store_words<C>(op + (long)r * N, o);
         }
     }
 }
 
+template <int A>
+static void moddown_launch_a(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st) {
+    const int nsm = sm_count(c->device);
+    const bool wide = (long)items * (c->N / 2) >= (long)nsm * 8 * 256;
+    const long units = (long)items * (c->N / (wide ? 2 : 1));
+    const unsigned grid = (unsigned)std::min<long>((long)nsm * 8, nblk(units, 256));
+    const MdExact &k = c->md_exact;
+    if (wide)
+        k_moddown_bconv<A, 2><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L);
+    else
+        k_moddown_bconv<A, 1><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L);
+}
+
 void launch_moddown_bconv(Ctx *c, const u64 *pcoef, u64 *out, int items, int level, cudaStream_t st) {
-    const long pairs = (long)items * (c->N / 2);
-    const unsigned grid = (unsigned)std::min<long>((long)sm_count(c->device) * 8, nblk(pairs, 256));
     c->n_launch++;
     cudaEvent_t e0;
     c->trace_begin(4, e0);
-    const MdExact &k = c->md_exact;
     switch (c->alpha) {
-    case 1: k_moddown_bconv<1><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
-    case 2: k_moddown_bconv<2><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
-    case 3: k_moddown_bconv<3><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
-    default: k_moddown_bconv<4><<<grid, 256, 0, st>>>(pcoef, out, items, level, c->N, k, c->d_mod, c->d_dn_pmod, c->d_dn_E, c->L); break;
+    case 1: moddown_launch_a<1>(c, pcoef, out, items, level, st); break;
+    case 2: moddown_launch_a<2>(c, pcoef, out, items, level, st); break;
+    case 3: moddown_launch_a<3>(c, pcoef, out, items, level, st); break;
+    default: moddown_launch_a<4>(c, pcoef, out, items, level, st); break;
     }
     c->trace_end(4, e0, 8.0 * items * c->N * (c->alpha + level + 1));
 }
@@ -1493,8 +1549,9 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
 struct PtrList {
     const u64 *p[32];
 };
-// The sums of up to 32 products stay below q 2^64 (mac128_q), so one REDC
-// per output word.
+// One REDC per output word: up to 32 products below q^2 stay below q 2^64
+// for q < 2^59; on wider rows (q_0, the special primes) the sum is kept
+// below it term by term (mac128_q).
 __global__ void k_pmul_acc(u64 *out, PtrList pts, PtrList R, int nterms, int B, int rows, int N, long Rs,
                            RowMap qp, const ModQ *mods) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1502,13 +1559,19 @@ __global__ void k_pmul_acc(u64 *out, PtrList pts, PtrList R, int nterms, int B, 
     if (idx >= per) return;
     int r = (int)(idx / N);
     const ModQ m = mods[qp.at(r)];
+    const bool wide = m.q >= (1ull << 59);   // uniform over the CTA (128 | N)
     for (int b = 0; b < B; b++) {
         U128 a0 = {0, 0}, a1 = {0, 0};
         for (int t = 0; t < nterms; t++) {
             const u64 pv = pts.p[t][idx];
             const u64 *rb = R.p[t] + b * Rs;
-            mac128_q(a0, pv, rb[idx], m.q);
-            mac128_q(a1, pv, rb[per + idx], m.q);
+            if (wide) {
+                mac128_q(a0, pv, rb[idx], m.q);
+                mac128_q(a1, pv, rb[per + idx], m.q);
+            } else {
+                mac128(a0, pv, rb[idx]);
+                mac128(a1, pv, rb[per + idx]);
+            }
         }
         u64 *ob = out + (long)b * 2 * per;
         ob[idx] = redc(a0.lo, a0.hi, m);
