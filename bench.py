@@ -1122,8 +1122,10 @@ def run_transforms(args):
     one 128x128 matrix ciphertext at N = 2^15 (n^2 = slots, no replication),
     chain 60 + 14x40 with 2x60 special primes, n1 in {8, 16}, undecomposed
     (dh-BSGS) and with the Diagonal Convergence Decomposition at maximum
-    diagonal 64 and 32 (depth 2 and 4); the input level is chosen so that
-    every run ends at level 10; device time per transform."""
+    diagonal 64 and 32 (depth 2 and 4), and with the simple key
+    substitution of Sec. 4.2 (heads of 2 and 4 baby keys; Table 2 gives its
+    key counts, Table 3 no times); the input level is chosen so that every
+    run ends at level 10; device time per transform."""
     import numpy as np
     import torch
 
@@ -1138,7 +1140,7 @@ def run_transforms(args):
     for n1 in (8, 16):
         for np_ in (0, 64, 32):
             steps |= set(pk.he_rot_steps_for_sched(n, n1, n1, S, np_, np_))
-    pk.he_keygen(ctx, sorted(steps), False)
+    pk.he_keygen(ctx, sorted(steps), False)     # covers the key-substitution heads too
     A, _ = workloads.matmul_pair(n, 5)
     info = pk.he_ctx_info(ctx)
     out = {}
@@ -1174,6 +1176,32 @@ def run_transforms(args):
                     "ms": ms, "depth": depth, "end_level": lv, "max_abs_err": err,
                     "rotation_keys": keys, "paper_s": PAPER_TABLE3[(name, n1, np_)],
                     "speedup_vs_paper": PAPER_TABLE3[(name, n1, np_)] * 1e3 / ms}
+    # Table 2's SmpKeySub rows (no Table 3 measurement in the paper): the
+    # babies use only the keys of a head of n1' steps, depth 1
+    for name, kind in (("Z", 0), ("T", 1)):
+        for n1 in (8, 16):
+            for head in (2, 4):
+                ct = pk.he_encrypt_matrix(ctx, A, 11, 1)
+                for _ in range(max(2, args.warmup)):
+                    pk.he_ct_free(pk.he_linear_transform_ksub(ctx, ct, kind, n, n1, head))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(tstream)
+                for _ in range(args.steps):
+                    pk.he_ct_free(pk.he_linear_transform_ksub(ctx, ct, kind, n, n1, head))
+                e1.record(tstream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                r = pk.he_linear_transform_ksub(ctx, ct, kind, n, n1, head)
+                d = pk.he_decrypt_matrix(ctx, r, n, n)
+                ref = A[i, (i + j) % n] if kind == 0 else A[(i + j) % n, j]
+                err = float(np.abs(d - ref).max())
+                lv = pk.he_ct_info(r)[0]
+                pk.he_ct_free(r)
+                pk.he_ct_free(ct)
+                keys = len(pk.he_rot_steps_for_ksub(n, kind, n1, head, S))   # n^2 = slots: no replication step
+                out["%s_n1_%d_ksub_head_%d" % (name, n1, head)] = {
+                    "ms": ms, "depth": 1, "end_level": lv, "max_abs_err": err, "rotation_keys": keys}
     # one rotation key: dnum digits x 2 polys x (L+1+alpha) limbs x N words
     N, L, alpha, dnum = info["N"], info["L"], info["alpha"], info["dnum"]
     key_mb = dnum * 2 * (L + 1 + alpha) * N * 8 / 2 ** 20

@@ -223,6 +223,24 @@ int he_rot_steps_for_sched(int n, const he_mm_sched *sched, int slots, int32_t *
 
 int he_rot_steps_for_transpose(int n, int n1, int slots, int32_t *out, int *count);
 
+/* Simple key substitution (Sec. 4.2, Table 2's SmpKeySub rows) for the
+ * double-hoisted BSGS of Z (kind 0, sigma, eq. 5) or T (kind 1, tau, eq. 6):
+ * the babies use only the rotation keys of the head a s, 0 < s < n1_sub, of
+ * their arithmetic progression (a = 1 for Z, n for T).  They are formed in
+ * groups of n1_sub - 1; each later group starts from the last baby of the
+ * previous one, ModDown'd and Decomposed (one more Decompose and ModDown per
+ * group), so the transform needs n1_sub + 2 n/n1 - 2 (Z) or n1_sub + n/n1 - 2
+ * (T) matrix rotation keys instead of n1 + 2 n/n1 - 2 or n1 + n/n1 - 2, at
+ * the same MultSum count.  n1 is a power of two dividing n, 2 <= n1_sub <=
+ * n1 (n1_sub = n1 is the plain transform).  The input is replicated to
+ * period n^2 first when it is not; the output is one level lower.
+ * he_rot_steps_for_ksub lists the slot rotation steps (the transform's and
+ * the replication's): on entry *count is the capacity of out, on return the
+ * number of steps; out may be NULL to ask for the number only.
+ * Errors: HE_ERR_ARG, HE_ERR_LEVEL, HE_ERR_KEY_MISSING, HE_ERR_OOM, HE_ERR_CUDA. */
+int he_linear_transform_ksub(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, int n1_sub, he_ct **out);
+int he_rot_steps_for_ksub(int n, int kind, int n1, int n1_sub, int slots, int32_t *out, int *count);
+
 /* Encode (App. A) a real slot vector z[0..nslots) (rest zero) at scale
  * 2^log_delta and encrypt it (Enc, App. A) at `level` with the public key;
  * the encryption randomness is the Philox stream at object `enc_counter`. */

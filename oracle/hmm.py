@@ -133,6 +133,21 @@ def matmul_rot_steps(n, n1z, n1t, S, dcd_z=0, dcd_t=0):
     return sorted(steps)
 
 
+def ksub_rot_steps(n, kind, n1, n1_sub):
+    """Matrix rotation steps (mod n^2) of Z (kind 0) or T (kind 1) under the
+    simple key substitution (Sec. 4.2): the babies' head a s, 0 < s < n1_sub,
+    and the giants a n1 i (Z: -n2 <= i < n2; T: 0 < i < n2), a = 1 for Z, n
+    for T.  Their number is Table 2's MinRotKeys: n1' + 2 n2 - 2 for Z and
+    n1' + n2 - 2 for T."""
+    n2m, n2 = n * n, n // n1
+    a = 1 if kind == 0 else n
+    steps = {(a * s) % n2m for s in range(1, n1_sub)}
+    giants = range(-n2, n2) if kind == 0 else range(1, n2)
+    steps |= {(a * n1 * i) % n2m for i in giants if i}
+    steps.discard(0)
+    return sorted(steps)
+
+
 def transpose_rot_steps(n, n1g, S):
     n2 = n * n
     a = n - 1
@@ -178,20 +193,37 @@ class HMM:
         m = _c.encode(u.astype(np.complex128), P.N, float(P.q[level]))
         return to_rns(m, P.qp(level))
 
-    def lintrans(self, ct, diag, a, n, n1, giants):
+    def lintrans(self, ct, diag, a, n, n1, giants, n1_sub=0):
         """Double-hoisted BSGS (eq. 3', Sec. 3.3, reading C10):
         U m = sum_i rho( sum_j rho(u_{a(n1 i + j)}; -a n1 i) . rho(m; a j) ; a n1 i ).
         Babies rho(m; a j) share one Decompose and stay in Q_l P; each giant
         group is summed in Q_l P, ModDown'd, rotated (kept in Q_l P) and added;
-        one final ModDown, then Rescale by q_l (plaintexts at scale q_l)."""
+        one final ModDown, then Rescale by q_l (plaintexts at scale q_l).
+
+        n1_sub (simple key substitution, Sec. 4.2): the babies use only the
+        keys a s, 0 < s < n1_sub, of the progression's head.  They come in
+        groups of n1_sub - 1: group 0 rotates m by a s; every later group
+        takes the last baby of the previous one, ModDown'd to a ciphertext
+        and Decomposed, as its source c and rotates it by a s, so baby
+        j = b + s is rho(c; a s) with c = rho(m; a b) (reading C28)."""
         he, P = self.he, self.P
         n2 = n * n
         lv = ct.level
         qp = P.qp(lv)
         digits = he.modup(ct.c1, lv)
         R = [(he.lift_P(ct.c0, lv), he.lift_P(ct.c1, lv))]
-        for j in range(1, n1):
-            R.append(he.rot_qp(ct, digits, (a * j) % n2))
+        if n1_sub and n1_sub < n1:
+            assert n1_sub >= 2
+            src, dg, base = ct, digits, 0
+            for j in range(1, n1):
+                if j - base == n1_sub:
+                    u0, u1 = R[j - 1]
+                    src = Ct(*he.moddown2(u0, u1, lv), lv, ct.scale, ct.period)
+                    dg, base = he.modup(src.c1, lv), j - 1
+                R.append(he.rot_qp(src, dg, (a * (j - base)) % n2))
+        else:
+            for j in range(1, n1):
+                R.append(he.rot_qp(ct, digits, (a * j) % n2))
         acc0 = acc1 = None
         for i in giants:
             pts, idx = [], []
@@ -217,13 +249,13 @@ class HMM:
         out = Ct(*he.moddown2(acc0, acc1, lv), lv, ct.scale, ct.period)
         return he.rescale(out, keep_scale=True)
 
-    def sigma(self, ct, n, n1):
+    def sigma(self, ct, n, n1, n1_sub=0):
         n2 = n // n1
-        return self.lintrans(ct, lambda t: diag_Z(n, t), 1, n, n1, range(-n2, n2))
+        return self.lintrans(ct, lambda t: diag_Z(n, t), 1, n, n1, range(-n2, n2), n1_sub)
 
-    def tau(self, ct, n, n1):
+    def tau(self, ct, n, n1, n1_sub=0):
         n2 = n // n1
-        return self.lintrans(ct, lambda t: diag_T(n, t), n, n, n1, range(0, n2))
+        return self.lintrans(ct, lambda t: diag_T(n, t), n, n, n1, range(0, n2), n1_sub)
 
     # --- Diagonal Convergence Decomposition (Sec. 4.2, DMatrixMult) -------
     def _chain(self, ct, chain, n, a_left, n1, giants_left):

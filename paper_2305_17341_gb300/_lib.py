@@ -130,6 +130,8 @@ SIGNATURES = {
     "he_pca": [vp, P(vp), ip, ip, ip, P(vp), ip, ip, P(ip), ctypes.c_double, P(he_refresh_state), P(vp), P(vp),
                P(ip)],
     "he_ntt": [vp, vp, ctypes.c_longlong, ip, ip],
+    "he_linear_transform_ksub": [vp, vp, ip, ip, ip, ip, P(vp)],
+    "he_rot_steps_for_ksub": [ip, ip, ip, ip, ip, i32p, P(ip)],
     "he_decompose": [vp, vp, ctypes.c_longlong, ip, vp],
     "he_moddown": [vp, vp, ctypes.c_longlong, ip, vp],
     "he_counters": [vp, llp, llp, llp, llp, ip],
@@ -292,6 +294,23 @@ def he_rot_steps_for_transpose(n, n1, slots):
     cnt = ctypes.c_int()
     check(lib().he_rot_steps_for_transpose(n, n1, slots, out.ctypes.data_as(i32p), ctypes.byref(cnt)))
     return [int(x) for x in out[: cnt.value]]
+
+
+def he_rot_steps_for_ksub(n, kind, n1, n1_sub, slots):
+    """Slot rotation steps of sigma (kind 0) or tau (kind 1) with the simple
+    key substitution of head length n1_sub (see include/he.h)."""
+    cnt = ctypes.c_int(0)
+    check(lib().he_rot_steps_for_ksub(n, kind, n1, n1_sub, slots, None, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=np.int32)
+    check(lib().he_rot_steps_for_ksub(n, kind, n1, n1_sub, slots, out.ctypes.data_as(i32p), ctypes.byref(cnt)))
+    return [int(x) for x in out[: cnt.value]]
+
+
+def he_linear_transform_ksub(ctx, ct, kind, n, n1, n1_sub):
+    """sigma (kind 0) or tau (kind 1) with the simple key substitution."""
+    h = vp()
+    check(lib().he_linear_transform_ksub(ctx, ct, kind, n, n1, n1_sub, ctypes.byref(h)))
+    return h
 
 
 def he_encrypt_slots(ctx, z, level, enc_counter):

@@ -904,6 +904,71 @@ int he_linear_transform(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, i
     GUARD_END
 }
 
+// Matrix rotation steps (mod n^2) of Z (kind 0) or T (kind 1) with the
+// simple key substitution: the babies' head a s, 0 < s < n1_sub, and the
+// giants a n1 i.
+static std::vector<long> ksub_steps(int n, int kind, int n1, int n1_sub) {
+    const long n2m = (long)n * n, a = kind == 0 ? 1 : n;
+    const int n2 = n / n1;
+    std::set<long> st;
+    for (int s = 1; s < n1_sub; s++) st.insert(((a * s) % n2m + n2m) % n2m);
+    for (int i = kind == 0 ? -n2 : 1; i < n2; i++)
+        if (i) st.insert(((a * n1 * i) % n2m + n2m) % n2m);
+    st.erase(0);
+    return std::vector<long>(st.begin(), st.end());
+}
+
+static int check_ksub(int n, int kind, int n1, int n1_sub, long slots) {
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (kind < 0 || kind > 1) return fail(HE_ERR_ARG, "kind must be 0 (sigma) or 1 (tau)");
+    if (n < 2 || (long)n * n > slots) return fail(HE_ERR_ARG, "n x n must fit the slots");
+    if (!pow2(n1) || n1 > n || n % n1) return fail(HE_ERR_ARG, "n1 must be a power of two dividing n");
+    if (n1_sub < 2 || n1_sub > n1) return fail(HE_ERR_ARG, "the head length must be in [2, n1]");
+    return HE_OK;
+}
+
+int he_rot_steps_for_ksub(int n, int kind, int n1, int n1_sub, int slots, int32_t *out, int *count) {
+    if (!count) return fail(HE_ERR_ARG, "null count");
+    if (int rc = check_ksub(n, kind, n1, n1_sub, slots)) return rc;
+    std::set<long> st;
+    for (long s : ksub_steps(n, kind, n1, n1_sub)) st.insert(s);
+    for (long r = (long)n * n; r < slots; r *= 2) st.insert(slots - r);   // replication
+    if (out && *count < (int)st.size()) return fail(HE_ERR_ARG, "output array too small");
+    int i = 0;
+    if (out)
+        for (long s : st) out[i++] = (int32_t)s;
+    *count = (int)st.size();
+    return HE_OK;
+}
+
+int he_linear_transform_ksub(he_ctx *ctx, const he_ct *ct, int kind, int n, int n1, int n1_sub, he_ct **out) {
+    if (!ctx || !out) return fail(HE_ERR_ARG, "null argument");
+    Ctx &c = ctx->c;
+    if (int rc = check_ct(c, ct)) return rc;
+    if (int rc = check_ksub(n, kind, n1, n1_sub, c.S)) return rc;
+    if (ct->level < 1) return fail(HE_ERR_LEVEL, "not enough levels for the transform");
+    GUARD_BEGIN
+    he_ct *tmp = clone_ct(c, ct);
+    he_ct *o = nullptr;
+    try {
+        if (tmp->period != n * n) replicate(&c, tmp->d, 1, tmp->level, n);
+        o = new_ct(&c, ct->level - 1, ct->scale, n * n);
+        const int n2 = n / n1;
+        if (kind == 0) lintrans(&c, tmp->d, 1, ct->level, 0, n, 1, n1, -n2, n2, 1.0, o->d, nullptr, n1_sub);
+        else lintrans(&c, tmp->d, 1, ct->level, 1, n, n, n1, 0, n2, 1.0, o->d, nullptr, n1_sub);
+    } catch (...) {
+        free_ct(tmp);
+        free_ct(o);
+        throw;
+    }
+    HE_CUDA_CHECK(cudaStreamSynchronize(c.stream));
+    if (int rc_dev = device_status(&c)) return rc_dev;
+    free_ct(tmp);
+    *out = o;
+    return cuda_status(&c);
+    GUARD_END
+}
+
 int he_ntt(he_ctx *ctx, uint64_t *rows_dev, long long n_rows, int level, int inverse) {
     if (!ctx || (n_rows > 0 && !rows_dev) || n_rows < 0) return fail(HE_ERR_ARG, "bad arguments");
     Ctx &c = ctx->c;

@@ -228,8 +228,14 @@ static long mod_pos(long x, long m) { return ((x % m) + m) % m; }
 // ModDown'd, rotated (kept in Q_l P) and accumulated; one final ModDown and a
 // rescale by q_l (plaintexts at scale q_l keep the ciphertext scale).
 // in: [B][2][l+1][N]; out: [B][2][l][N].
+//
+// n1_sub > 0 (simple key substitution, Sec. 4.2): the babies use only the
+// keys a s, 0 < s < n1_sub.  They come in groups of n1_sub - 1: the first
+// rotates the input by a s; every later group takes the last baby of the
+// previous one, ModDown'd to a ciphertext c and Decomposed, and rotates c by
+// a s, so that baby j = b + s is rho(c; a s) with c = rho(m; a b).
 void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
-              double value, u64 *out, const DcdFactor *fac) {
+              double value, u64 *out, const DcdFactor *fac, int n1_sub) {
     const int N = c->N, nq = level + 1, rows = c->qp_rows(level);
     const long n2 = (long)n * n;
     const size_t qpct = (size_t)2 * rows * N;   // one item over Q_l P
@@ -238,16 +244,28 @@ void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, 
     std::vector<Buf> R;
     R.emplace_back(&c->pool, B * qpct);
     launch_lift_P(c, R[0].p, in, 2 * B, level, (long)nq * N, (long)rows * N, c->stream);
-    std::vector<uint32_t> gs;
-    std::vector<u64 *> outs;
-    for (int j = 1; j < n1; j++) {
-        R.emplace_back(&c->pool, B * qpct);
-        gs.push_back(galois_of_step(c, mod_pos(a * j, n2)));
-        outs.push_back(R[j].p);
-    }
-    rot_qp_multi(c, in, B, level, dg.p, gs.data(), (int)gs.size(), outs.data());
+    for (int j = 1; j < n1; j++) R.emplace_back(&c->pool, B * qpct);
     Buf acc(&c->pool, B * qpct), S(&c->pool, B * qpct), ctmp(&c->pool, (size_t)B * 2 * nq * N),
         dg2(&c->pool, (size_t)B * c->ndig(level) * rows * N), T(&c->pool, B * qpct);
+    const int head = n1_sub > 1 && n1_sub < n1 ? n1_sub : n1;
+    for (int j0 = 1, base = 0; j0 < n1; j0 += head - 1) {
+        const u64 *src = in, *sdg = dg.p;
+        if (j0 > 1) {
+            // the previous group's last baby as the next source
+            base = j0 - 1;
+            moddown(c, R[base].p, 2 * B, level, ctmp.p, (long)nq * N);
+            c->n_md += B;
+            modup(c, ctmp.p + (long)nq * N, 2L * nq * N, B, level, dg2.p);
+            src = ctmp.p, sdg = dg2.p;
+        }
+        std::vector<uint32_t> gs;
+        std::vector<u64 *> outs;
+        for (int j = j0; j < std::min(n1, j0 + head - 1); j++) {
+            gs.push_back(galois_of_step(c, mod_pos(a * (j - base), n2)));
+            outs.push_back(R[j].p);
+        }
+        rot_qp_multi(c, src, B, level, sdg, gs.data(), (int)gs.size(), outs.data());
+    }
     bool have = false;
     RowMap qp = c->map_qp(level);
     for (int i = gi0; i < gi1; i++) {

@@ -39,7 +39,7 @@ void add(Ctx *c, const u64 *a, const u64 *b, int B, int level, u64 *out);
 const u64 *get_pt(Ctx *c, int kind, int n, long t, long rot, double value, int k, int level,
                   const DcdFactor *fac = nullptr);
 void lintrans(Ctx *c, const u64 *in, int B, int level, int kind, int n, long a, int n1, int gi0, int gi1,
-              double value, u64 *out, const DcdFactor *fac = nullptr);
+              double value, u64 *out, const DcdFactor *fac = nullptr, int n1_sub = 0);
 // Decompositions (dcd.cu): which = 0 (Z_1), 1 (Z_2), 2 (T); levels a chain consumes.
 const DcdChain &dcd_chain(Ctx *c, int which, int n, int n_prime);
 // Factors (levels) of the decomposed Z (is_t false) or T; 1 without n'.

@@ -208,3 +208,66 @@ def test_relin_once_with_decomposed_transforms_decrypts():
     cc = HMM(he).hmatmul(ca, cb, n, n1, n1, relin_once=True, dcd_z=n_prime, dcd_t=n_prime)
     assert cc.level == P.L - ((n - 1) // n_prime + 1) - 2
     assert np.abs(he.decrypt_slots(cc).real[: n * n].reshape(n, n) - A @ B).max() < 1e-4
+
+
+@pytest.mark.parametrize("n1,n1_sub", [(8, 2), (8, 3), (8, 5), (4, 3)])
+def test_key_substitution_sigma_tau_decrypt_with_fewer_keys(n1, n1_sub):
+    """Simple key substitution (Sec. 4.2): sigma and tau with only the keys
+    of the babies' head (a s, s < n1') decrypt to the index maps of eq. 5 /
+    eq. 6 within 1e-6.  It keeps the dh-BSGS MultSum count and adds one
+    Decompose and one ModDown per later group of n1' - 1 babies:
+    ceil((n1 - 1)/(n1' - 1)) - 1 of each."""
+    n = 16
+    P = Params(9, [60] + [40] * 4, [60])
+    he = CKKS(P, 4)
+    from oracle.hmm import HMM, ksub_rot_steps
+    r = n * n
+    rep = []
+    while r < P.S:
+        rep.append((-r) % P.S)
+        r *= 2
+    for s in sorted(set(ksub_rot_steps(n, 0, n1, n1_sub)) | set(ksub_rot_steps(n, 1, n1, n1_sub)) | set(rep)):
+        he.gen_rotation_key(s)
+    H = HMM(he)
+    rng = np.random.default_rng(n1 * 10 + n1_sub)
+    A = rng.uniform(-1, 1, (n, n))
+    za = np.zeros(P.S)
+    za[: n * n] = A.ravel()
+    ca = H.replicate(he.encrypt_slots(za, P.L, obj=14), n)
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    extra = -(-(n1 - 1) // (n1_sub - 1)) - 1
+    counts = []
+    for kind in (0, 1):
+        he.cnt.reset()
+        out = H.sigma(ca, n, n1, n1_sub) if kind == 0 else H.tau(ca, n, n1, n1_sub)
+        got = (he.cnt.MS, he.cnt.Dp, he.cnt.MD)
+        want = A[i, (i + j) % n] if kind == 0 else A[(i + j) % n, j]
+        assert out.level == P.L - 1
+        assert np.abs(he.decrypt_slots(out).real[: n * n].reshape(n, n) - want).max() < 1e-6
+        counts.append(got)
+    # the same transforms with all baby keys (dh-BSGS)
+    for s in range(1, n1):
+        he.gen_rotation_key(s % (n * n))
+        he.gen_rotation_key((n * s) % (n * n))
+    for kind in (0, 1):
+        he.cnt.reset()
+        _ = H.sigma(ca, n, n1) if kind == 0 else H.tau(ca, n, n1)
+        ms, dp, md = counts[kind]
+        assert (ms, dp, md) == (he.cnt.MS, he.cnt.Dp + extra, he.cnt.MD + extra)
+
+
+def test_key_substitution_with_the_whole_head_is_dh_bsgs():
+    """n1' = n1 uses every baby key: the transform is the plain double-hoisted
+    BSGS, word for word."""
+    n, n1 = 16, 4
+    P = Params(9, [60] + [40] * 3, [60])
+    he = CKKS(P, 6)
+    from oracle.hmm import HMM, ksub_rot_steps
+    for s in ksub_rot_steps(n, 0, n1, n1):
+        he.gen_rotation_key(s)
+    z = np.random.default_rng(3).uniform(-1, 1, P.S)
+    ca = he.encrypt_slots(z, P.L, obj=15)
+    ca.period = n * n
+    H = HMM(he)
+    a, b = H.sigma(ca, n, n1, n1), H.sigma(ca, n, n1)
+    assert np.array_equal(a.c0, b.c0) and np.array_equal(a.c1, b.c1)

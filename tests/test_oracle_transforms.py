@@ -209,3 +209,16 @@ def test_dcd_table3_key_memory_rows():
         assert round((keys + 1) * key_mib) == int(rtk), line
         seen += 1
     assert seen == 8
+
+
+@pytest.mark.parametrize("n,n1", [(16, 4), (16, 8), (32, 8), (128, 8), (128, 16)])
+def test_key_substitution_key_sets_match_table2(n, n1):
+    """Table 2 SmpKeySub: MinRotKeys n1' + 2 n2 - 2 (Z) and n1' + n2 - 2 (T)
+    for every head length 2 <= n1' <= n1, counted on the step sets the
+    transforms use; n1' = n1 is the plain dh-BSGS row (n1 + 2 n2 - 2,
+    n1 + n2 - 2)."""
+    from oracle.hmm import ksub_rot_steps
+    n2 = n // n1
+    for n1p in range(2, n1 + 1):
+        assert len(ksub_rot_steps(n, 0, n1, n1p)) == n1p + 2 * n2 - 2
+        assert len(ksub_rot_steps(n, 1, n1, n1p)) == n1p + n2 - 2
