@@ -552,10 +552,25 @@ def multsum_picks(log):
         t = float(f[14])
         if key not in best or t < best[key][0]:
             best[key] = (t, int(f[8]), int(f[10]), int(f[12]))
-    return ["level %d B %d G %d: %d keys per launch, %s, %.4f ms" %
-            (k + (v[1], ("variant %d" % (v[2] - 100)) if v[2] > 100 else "%d items per CTA%s" %
-                  (v[2], ", streaming" if v[3] else ""), v[0]))
-            for k, v in sorted(best.items())]
+    picks = ["level %d B %d G %d: %d keys per launch, %s, %.4f ms" %
+             (k + (v[1], ("variant %d" % (v[2] - 100)) if v[2] > 100 else "%d items per CTA%s" %
+                   (v[2], ", streaming" if v[3] else ""), v[0]))
+             for k, v in sorted(best.items())]
+    # the fused C^k babies: "multsum_ck level L B b G g chunk c BI v ms t"
+    # (BI 0: rotations split over the warps)
+    ck = {}
+    for ln in log.splitlines():
+        f = ln.split()
+        if len(f) != 13 or f[0] != "multsum_ck":
+            continue
+        key = (int(f[2]), int(f[4]), int(f[6]))
+        t = float(f[12])
+        if key not in ck or t < ck[key][0]:
+            ck[key] = (t, int(f[8]), int(f[10]))
+    picks += ["C^k fused, level %d B %d G %d: %d keys per launch, %s, %.4f ms" %
+              (k + (v[1], "rotations split over the warps" if v[2] == 0 else "%d items per CTA" % v[2], v[0]))
+              for k, v in sorted(ck.items())]
+    return picks
 
 
 def _cov_keys(pk, ctx, n, n1, S, dcd=0):

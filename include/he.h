@@ -140,7 +140,10 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * coefficients per thread with 16-byte digit and key loads (cached /
  * streaming digit loads), more CTAs per SM, for at most two rotations per
  * launch (more: as 32 / 36); 96, 97: as 64, 65 with two coefficients per
- * thread and 16-byte loads.  Errors: HE_ERR_ARG for other values. */
+ * thread and 16-byte loads.  The fused MultSum of a product's C^k babies
+ * (both sources of a giant with their masks) follows: 96 and 97 pin its
+ * rotations-split-over-warps form, every other variant its
+ * thread-per-word form.  Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without

@@ -1448,6 +1448,102 @@ __global__ void __launch_bounds__(256, G <= 1 ? 4 : G <= 2 ? 3 : 2)
     }
 }
 
+// The same with the rotations split over the warps: warp w takes rotation
+// w / BI of items blockIdx.z BI + w % BI (BI = 8 / G), two adjacent
+// coefficients per thread with 16-byte digit, key and store accesses, so a
+// thread holds 8 accumulators whatever G is (more resident warps than
+// k_multsum_ck at G >= 2).
+template <int G>
+__global__ void __launch_bounds__(256, 3)
+    k_multsum_cks(const __grid_constant__ CkArgs<G> ck, const u64 *dig1, const u64 *dig2, int B, int level,
+                  int alpha, int L, int ndig, int nprimes, int logN, const ModQ *mods, const u64 *c01,
+                  const u64 *c02, long c0s, const ShoupPair *Pmod) {
+    constexpr int BI = 8 / G;
+    const int N = 1 << logN;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int kq = wid / BI, bi = wid % BI;
+    const int y = 2 * (blockIdx.x * 32 + lane);
+    const int r = blockIdx.y;
+    const int b = blockIdx.z * BI + bi;
+    if (b >= B || y >= N) return;
+    const int rows = level + 1 + alpha;
+    const int kr = r <= level ? r : L + 1 + (r - level - 1);
+    const ModQ m = mods[kr];
+    const long dstride = (long)rows * N;
+    const ulonglong2 *dp1 = (const ulonglong2 *)(dig1 + (long)b * ndig * dstride + (long)r * N + y);
+    const ulonglong2 *dp2 = (const ulonglong2 *)(dig2 + (long)b * ndig * dstride + (long)r * N + y);
+    const long koff = (long)kr * N + y, kd = 2L * nprimes * N, kk = (long)nprimes * N;
+    const u64 *key = ck.key[kq];
+    U128 acc[2][4];   // [coefficient][source 1 poly 0, poly 1, source 2 poly 0, poly 1]
+    if (m.q < (1ull << 42)) {
+        u32 x0[2][4], x1[2][4], x2[2][4];
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) x0[c][j] = 0, x1[c][j] = 0, x2[c][j] = 0;
+        for (int d = 0; d < ndig; d++) {
+            const ulonglong2 v1 = __ldg(dp1 + (long)d * dstride / 2), v2 = __ldg(dp2 + (long)d * dstride / 2);
+            const ulonglong2 *kp = (const ulonglong2 *)(key + (long)d * kd + koff);
+            const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
+            mac96(x0[0][0], x1[0][0], x2[0][0], v1.x, k0.x);
+            mac96(x0[1][0], x1[1][0], x2[1][0], v1.y, k0.y);
+            mac96(x0[0][1], x1[0][1], x2[0][1], v1.x, k1.x);
+            mac96(x0[1][1], x1[1][1], x2[1][1], v1.y, k1.y);
+            mac96(x0[0][2], x1[0][2], x2[0][2], v2.x, k0.x);
+            mac96(x0[1][2], x1[1][2], x2[1][2], v2.y, k0.y);
+            mac96(x0[0][3], x1[0][3], x2[0][3], v2.x, k1.x);
+            mac96(x0[1][3], x1[1][3], x2[1][3], v2.y, k1.y);
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[c][j] = U128{((u64)x1[c][j] << 32) | x0[c][j], x2[c][j]};
+    } else {
+#pragma unroll
+        for (int c = 0; c < 2; c++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[c][j] = U128{0, 0};
+        for (int d = 0; d < ndig; d++) {
+            const ulonglong2 v1 = __ldg(dp1 + (long)d * dstride / 2), v2 = __ldg(dp2 + (long)d * dstride / 2);
+            const ulonglong2 *kp = (const ulonglong2 *)(key + (long)d * kd + koff);
+            const ulonglong2 k0 = __ldg(kp), k1 = __ldg(kp + kk / 2);
+            mac128_q(acc[0][0], v1.x, k0.x, m.q);
+            mac128_q(acc[1][0], v1.y, k0.y, m.q);
+            mac128_q(acc[0][1], v1.x, k1.x, m.q);
+            mac128_q(acc[1][1], v1.y, k1.y, m.q);
+            mac128_q(acc[0][2], v2.x, k0.x, m.q);
+            mac128_q(acc[1][2], v2.y, k0.y, m.q);
+            mac128_q(acc[0][3], v2.x, k1.x, m.q);
+            mac128_q(acc[1][3], v2.y, k1.y, m.q);
+        }
+    }
+    const ShoupPair wP = r <= level ? Pmod[r] : ShoupPair{0, 0};
+    u64 *ob = ck.out[kq] + (long)b * 2 * rows * N;
+    const u32 gi = ck.ginv[kq];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const int yc = y + c;
+        u64 pc1 = 0, pc2 = 0;
+        if (r <= level) {
+            pc1 = shoup(c01[b * c0s + (long)r * N + yc], wP.w, wP.wp, m.q);
+            pc2 = shoup(c02[b * c0s + (long)r * N + yc], wP.w, wP.wp, m.q);
+        }
+        const u64 a10 = addmod(redc(acc[c][0].lo, acc[c][0].hi, m), pc1, m.q);
+        const u64 a11 = redc(acc[c][1].lo, acc[c][1].hi, m);
+        const u64 a20 = addmod(redc(acc[c][2].lo, acc[c][2].hi, m), pc2, m.q);
+        const u64 a21 = redc(acc[c][3].lo, acc[c][3].hi, m);
+        const int x = gi == 1u ? yc : auto_index(yc, gi, logN);
+        const u64 w1 = __ldg(ck.m1[kq] + (long)r * N + x), w2 = __ldg(ck.m2[kq] + (long)r * N + x);
+        U128 s0 = {0, 0}, s1 = {0, 0};
+        mac128(s0, w1, a10);
+        mac128(s0, w2, a20);
+        mac128(s1, w1, a11);
+        mac128(s1, w2, a21);
+        ob[(long)r * N + x] = redc(s0.lo, s0.hi, m);
+        ob[(long)(rows + r) * N + x] = redc(s1.lo, s1.hi, m);
+    }
+}
+
 template <int G>
 static void multsum_ck_launch_g(Ctx *c, int BI, u64 *const *outs, const u64 *dig1, const u64 *dig2,
                                 const u64 *const *keys, const uint32_t *gs, const u64 *const *m1,
@@ -1464,7 +1560,19 @@ static void multsum_ck_launch_g(Ctx *c, int BI, u64 *const *outs, const u64 *dig
         for (int it = 0; it < 5; it++) inv *= 2u - g * inv;
         ck.ginv[k] = inv & (M - 1);
     }
-    const int rows = level + 1 + c->alpha, XW = 256 / BI;
+    const int rows = level + 1 + c->alpha;
+    if constexpr (8 % G == 0) {
+        if (BI == 0) {   // rotations split over the warps
+            constexpr int SBI = 8 / G;
+            dim3 grid((unsigned)((c->N / 2 + 31) / 32), (unsigned)rows, (unsigned)((B + SBI - 1) / SBI));
+            k_multsum_cks<G><<<grid, 256, 0, st>>>(ck, dig1, dig2, B, level, c->alpha, c->L, c->ndig(level),
+                                                   c->nprimes, c->logN, c->d_mod, c01, c02, c0s, c->d_Pmod);
+            c->n_launch++;
+            return;
+        }
+    }
+    if (BI == 0) BI = 8;   // G does not divide the warps
+    const int XW = 256 / BI;
     dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
     k_multsum_ck<G><<<grid, 256, 0, st>>>(ck, dig1, dig2, B, BI, level, c->alpha, c->L, c->ndig(level), c->nprimes,
                                           c->logN, c->d_mod, c01, c02, c0s, c->d_Pmod);
@@ -1500,7 +1608,11 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
     };
     int chunk = std::min(G, 4), BI = std::min(B, 8);
     while (BI > 1 && BI > B) BI >>= 1;
-    if (c->autotune) {
+    if (c->force_multsum >= 0) {
+        // a pinned MultSum variant: 96 / 97 (rotations split over the warps)
+        // select the split form here too, every other one the thread-per-word form
+        if (c->force_multsum == 96 || c->force_multsum == 97) BI = 0;
+    } else if (c->autotune) {
         auto key3 = std::make_tuple(level, B, G);
         auto it = c->tune_ck.find(key3);
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1514,10 +1626,11 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
             float best = 1e30f;
             std::set<std::pair<int, int>> seen;
             for (int ch : {4, 2, 1}) {
-                for (int bi : {8, 4, 2, 1}) {
+                for (int bi : {8, 4, 2, 1, 0}) {   // 0: rotations split over the warps
                     const int cc = std::min(ch, G);
                     int bb = bi;
                     while (bb > 1 && bb > B) bb >>= 1;
+                    if (bi == 0 && (8 % cc)) continue;
                     if (!seen.insert(std::make_pair(cc, bb)).second) continue;
                     float t = 1e30f;
                     for (int rep = 0; rep < 2; rep++) {

@@ -120,6 +120,34 @@ def test_alpha2_product_bit_exact_every_multsum_variant(a2, sched):
         pk.he_ct_free(h)
 
 
+def test_alpha2_fused_ck_forms_bit_exact(a2):
+    """n1 = 8 (7 C^k babies per giant: launches of 4 and 3 rotations): the
+    product under the tuner, the thread-per-word fused C^k kernel (variant
+    0) and its rotations-split-over-warps form (variant 96, the 4-rotation
+    launches) equals the oracle word for word."""
+    from oracle.hmm import HMM, matmul_rot_steps
+    pk, ctx, P, he, n, _ = a2
+    n1 = 8
+    steps = sorted(set(matmul_rot_steps(n, n1, n1, P.S)))
+    pk.he_keygen(ctx, steps, want_relin=True)
+    for st in steps:
+        he.gen_rotation_key(st)
+    A, B, ((oa, ga), (ob, gb)) = _encrypted_pair(pk, ctx, P, he, n, 91)
+    want = res(HMM(he).hmatmul(oa, ob, n, n1, n1))
+    try:
+        for v in (-1, 0, 96):
+            pk.he_ctx_set_multsum_variant(ctx, v)
+            gc = pk.he_hmatmul(ctx, ga, gb, n, n1, n1)
+            got = pk.he_ct_export(ctx, gc)
+            assert np.array_equal(got, want), "variant %d: %d of %d words differ" % (v, (got != want).sum(), got.size)
+            assert np.abs(pk.he_decrypt_matrix(ctx, gc, n, n) - A @ B).max() < TOL
+            pk.he_ct_free(gc)
+    finally:
+        pk.he_ctx_set_multsum_variant(ctx, -1)
+    for h in (ga, gb):
+        pk.he_ct_free(h)
+
+
 def test_alpha2_batched_products_at_two_levels(a2):
     """Three products in one he_hmatmul_batch call, two at level 12 and one
     at level 9 (a two-prime last digit): each equals the oracle."""
