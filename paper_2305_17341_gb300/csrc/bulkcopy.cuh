@@ -25,18 +25,16 @@ __device__ __forceinline__ void bc_init_fence() {
 }
 
 __device__ __forceinline__ void bc_arrive(u64 *bar) {
-    u64 state;
+    [[maybe_unused]] u64 state;
     asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(bc_smem(bar)) : "memory");
-    (void)state;
 }
 
 __device__ __forceinline__ void bc_expect_tx(u64 *bar, u32 bytes) {
-    u64 state;
+    [[maybe_unused]] u64 state;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
                  : "=l"(state)
                  : "r"(bc_smem(bar)), "r"(bytes)
                  : "memory");
-    (void)state;
 }
 
 __device__ __forceinline__ bool bc_try_wait(u64 *bar, u32 parity) {
