@@ -250,6 +250,17 @@ __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulong
                 else bf_fwd_nored(x[k], x[k + s], wv.x, wv.y, q);
             }
     }
+    // rows: the per-sequence twiddles of the first two stages after the
+    // transpose do not depend on it, so their loads are issued before its
+    // barrier (the columns' twiddles are shared by the CTA and stay cached)
+    constexpr int SP0 = T / 2, SP1 = T / 4 > 0 ? T / 4 : 1;
+    ulonglong2 w0[8 / SP0], w1[8 / SP1];
+    if constexpr (ROWS) {
+#pragma unroll
+        for (int i = 0; i < 8 / SP0; i++) w0[i] = __ldg(w2_ + (long)(M / (2 * SP0)) * G + (long)t * (8 / SP0) + i);
+#pragma unroll
+        for (int i = 0; i < 8 / SP1; i++) w1[i] = __ldg(w2_ + (long)(M / (2 * SP1)) * G + (long)t * (8 / SP1) + i);
+    }
 #pragma unroll
     for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = x[k];
     pass_sync<CONS>();
@@ -261,7 +272,9 @@ __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulong
 #pragma unroll
         for (int k = 0; k < 16; k++)
             if (!(k & sp)) {
-                const ulonglong2 wv = __ldg(w2_ + mb + k / (2 * sp));
+                const ulonglong2 wv = ROWS && sp == SP0                ? w0[k / (2 * sp)]
+                                      : ROWS && sp == SP1 && SP1 != SP0 ? w1[k / (2 * sp)]
+                                                                         : __ldg(w2_ + mb + k / (2 * sp));
                 if (RED) bf_fwd(x[k], x[k + sp], wv.x, wv.y, q);
                 else bf_fwd_nored(x[k], x[k + sp], wv.x, wv.y, q);
             }
@@ -328,11 +341,16 @@ __global__ void __launch_bounds__(256, MINB) k_ntt_fwd_fast(u64 *data, RowMap rm
         }
         return;
     }
+    // the store addresses are formed again here from an opaque copy of the
+    // base, so that the 16 strided load addresses of the columns are not
+    // kept live through the butterflies
+    u64 *ps = p;
+    asm volatile("" : "+l"(ps));
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         u64 v = sm[G_::sidx(t + T * k, w)];
         if (ROWS) v = red ? reduce4q(v, q) : reduce_any(v, q, wone);
-        p[(long)(t + T * k) * stride] = v;
+        ps[(long)(t + T * k) * stride] = v;
     }
 }
 
