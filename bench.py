@@ -35,13 +35,13 @@ N_MAT = 128
 # DRAM bytes per algorithmic byte, from ncu captures of the same kernels
 # (dram__bytes_read.sum + dram__bytes_write.sum of the launch over the bytes
 # the traced class counts): the forward NTT's two passes each read and write
-# the rows once, plus the row pass's twiddle misses (512-row capture: 1050.20
-# MB against 536.87 MB); MultSum reads the keys, the digits and c0 once and
+# the rows once, plus the row pass's twiddle misses (512-row captures of the
+# two passes: 475.80 + 533.30 MB against 536.87 MB); MultSum reads the keys, the digits and c0 once and
 # writes its outputs once (8 items x 4 hoisted rotations at level 20, the
-# step's largest MultSum launches, compiled for 4 CTAs per SM: 2964.69 MB
+# step's R^k / Z / T baby launches, compiled for 4 CTAs per SM: 2968.30 MB
 # against 2982.15 MB).  Traffic grows with the rows / items of a launch, so
 # per launch it is this ratio times the launch's algorithmic bytes.
-TRAFFIC_RATIO = {"ntt_fwd": 1050.20 / 536.87, "multsum": 2964.69 / 2982.15}
+TRAFFIC_RATIO = {"ntt_fwd": (475.80 + 533.30) / 536.87, "multsum": 2968.30 / 2982.15}
 # baby-step count n1 used for each matrix dimension
 N1_FOR = {16: 4, 32: 8, 64: 8, 128: 16}
 LEVEL = 20

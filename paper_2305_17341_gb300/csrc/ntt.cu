@@ -250,17 +250,6 @@ __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulong
                 else bf_fwd_nored(x[k], x[k + s], wv.x, wv.y, q);
             }
     }
-    // rows: the per-sequence twiddles of the first two stages after the
-    // transpose do not depend on it, so their loads are issued before its
-    // barrier (the columns' twiddles are shared by the CTA and stay cached)
-    constexpr int SP0 = T / 2, SP1 = T / 4 > 0 ? T / 4 : 1;
-    ulonglong2 w0[8 / SP0], w1[8 / SP1];
-    if constexpr (ROWS) {
-#pragma unroll
-        for (int i = 0; i < 8 / SP0; i++) w0[i] = __ldg(w2_ + (long)(M / (2 * SP0)) * G + (long)t * (8 / SP0) + i);
-#pragma unroll
-        for (int i = 0; i < 8 / SP1; i++) w1[i] = __ldg(w2_ + (long)(M / (2 * SP1)) * G + (long)t * (8 / SP1) + i);
-    }
 #pragma unroll
     for (int k = 0; k < 16; k++) sm[G_::sidx(t + T * k, w)] = x[k];
     pass_sync<CONS>();
@@ -272,9 +261,7 @@ __device__ __forceinline__ void fwd_pass_body(u64 (&x)[16], u64 *sm, const ulong
 #pragma unroll
         for (int k = 0; k < 16; k++)
             if (!(k & sp)) {
-                const ulonglong2 wv = ROWS && sp == SP0                ? w0[k / (2 * sp)]
-                                      : ROWS && sp == SP1 && SP1 != SP0 ? w1[k / (2 * sp)]
-                                                                         : __ldg(w2_ + mb + k / (2 * sp));
+                const ulonglong2 wv = __ldg(w2_ + mb + k / (2 * sp));
                 if (RED) bf_fwd(x[k], x[k + sp], wv.x, wv.y, q);
                 else bf_fwd_nored(x[k], x[k + sp], wv.x, wv.y, q);
             }
