@@ -142,8 +142,8 @@ int he_ctx_set_autotune(he_ctx *ctx, int on);
  * launch (more: as 32 / 36); 96, 97: as 64, 65 with two coefficients per
  * thread and 16-byte loads.  The fused MultSum of a product's C^k babies
  * (both sources of a giant with their masks) follows: 96 and 97 pin its
- * rotations-split-over-warps form, every other variant its
- * thread-per-word form.  Errors: HE_ERR_ARG for other values. */
+ * rotations-split-over-warps form (97 with launches of 8 rotations where 8
+ * remain), every other variant its thread-per-word form.  Errors: HE_ERR_ARG for other values. */
 int he_ctx_set_multsum_variant(he_ctx *ctx, int variant);
 
 /* Pins the context's NTT passes (N = 2^14 .. 2^16) to one variant, without

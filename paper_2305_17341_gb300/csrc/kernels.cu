@@ -1462,9 +1462,12 @@ __global__ void __launch_bounds__(256, 3)
     const int N = 1 << logN;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int kq = wid / BI, bi = wid % BI;
-    const int y = 2 * (blockIdx.x * 32 + lane);
+    // one item per CTA (G = 8): the items are the fastest grid index, so the
+    // CTAs of the B items that read the same key words run together
+    const int xb = BI == 1 ? (int)(blockIdx.x / B) : (int)blockIdx.x;
+    const int y = 2 * (xb * 32 + lane);
     const int r = blockIdx.y;
-    const int b = blockIdx.z * BI + bi;
+    const int b = BI == 1 ? (int)(blockIdx.x % B) : (int)blockIdx.z * BI + bi;
     if (b >= B || y >= N) return;
     const int rows = level + 1 + alpha;
     const int kr = r <= level ? r : L + 1 + (r - level - 1);
@@ -1561,22 +1564,27 @@ static void multsum_ck_launch_g(Ctx *c, int BI, u64 *const *outs, const u64 *dig
         ck.ginv[k] = inv & (M - 1);
     }
     const int rows = level + 1 + c->alpha;
+    if constexpr (G > 4) BI = 0;   // eight rotations: the split form only
     if constexpr (8 % G == 0) {
         if (BI == 0) {   // rotations split over the warps
             constexpr int SBI = 8 / G;
-            dim3 grid((unsigned)((c->N / 2 + 31) / 32), (unsigned)rows, (unsigned)((B + SBI - 1) / SBI));
+            const unsigned xblocks = (unsigned)((c->N / 2 + 31) / 32);
+            const dim3 grid = SBI == 1 ? dim3(xblocks * (unsigned)B, (unsigned)rows, 1)
+                                       : dim3(xblocks, (unsigned)rows, (unsigned)((B + SBI - 1) / SBI));
             k_multsum_cks<G><<<grid, 256, 0, st>>>(ck, dig1, dig2, B, level, c->alpha, c->L, c->ndig(level),
                                                    c->nprimes, c->logN, c->d_mod, c01, c02, c0s, c->d_Pmod);
             c->n_launch++;
             return;
         }
     }
-    if (BI == 0) BI = 8;   // G does not divide the warps
-    const int XW = 256 / BI;
-    dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
-    k_multsum_ck<G><<<grid, 256, 0, st>>>(ck, dig1, dig2, B, BI, level, c->alpha, c->L, c->ndig(level), c->nprimes,
-                                          c->logN, c->d_mod, c01, c02, c0s, c->d_Pmod);
-    c->n_launch++;
+    if constexpr (G <= 4) {
+        if (BI == 0) BI = 8;   // G does not divide the warps
+        const int XW = 256 / BI;
+        dim3 grid((unsigned)((c->N + XW - 1) / XW), (unsigned)rows, (unsigned)((B + BI - 1) / BI));
+        k_multsum_ck<G><<<grid, 256, 0, st>>>(ck, dig1, dig2, B, BI, level, c->alpha, c->L, c->ndig(level),
+                                              c->nprimes, c->logN, c->d_mod, c01, c02, c0s, c->d_Pmod);
+        c->n_launch++;
+    }
 }
 
 void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig2, const u64 *const *keys,
@@ -1585,11 +1593,13 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
     if (G <= 0) return;
     const int rows = level + 1 + c->alpha;
     auto run = [&](int chunk, int BI, bool traced) {
-        for (int k0 = 0; k0 < G; k0 += chunk) {
-            const int g = std::min(chunk, G - k0);
+        for (int k0 = 0, g = 0; k0 < G; k0 += g) {
+            g = std::min(chunk, G - k0);
+            if (g > 4 && g != 8) g = 4;   // launches of 1..4 or 8 rotations
             cudaEvent_t e0 = nullptr;
             if (traced) c->trace_begin(0, e0);
             switch (g) {
+            case 8: multsum_ck_launch_g<8>(c, 0, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
             case 1: multsum_ck_launch_g<1>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
             case 2: multsum_ck_launch_g<2>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
             case 3: multsum_ck_launch_g<3>(c, BI, outs + k0, dig1, dig2, keys + k0, gs + k0, m1 + k0, m2 + k0, B, level, c01, c02, c0s, st); break;
@@ -1610,8 +1620,10 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
     while (BI > 1 && BI > B) BI >>= 1;
     if (c->force_multsum >= 0) {
         // a pinned MultSum variant: 96 / 97 (rotations split over the warps)
-        // select the split form here too, every other one the thread-per-word form
+        // select the split form here too (97: launches of 8 rotations where 8
+        // remain), every other one the thread-per-word form
         if (c->force_multsum == 96 || c->force_multsum == 97) BI = 0;
+        if (c->force_multsum == 97) chunk = std::min(G, 8);
     } else if (c->autotune) {
         auto key3 = std::make_tuple(level, B, G);
         auto it = c->tune_ck.find(key3);
@@ -1625,12 +1637,13 @@ void launch_multsum_ck(Ctx *c, u64 *const *outs, const u64 *dig1, const u64 *dig
             cudaEvent_t a = c->ev_get(), b = c->ev_get();
             float best = 1e30f;
             std::set<std::pair<int, int>> seen;
-            for (int ch : {4, 2, 1}) {
+            for (int ch : {8, 4, 2, 1}) {
                 for (int bi : {8, 4, 2, 1, 0}) {   // 0: rotations split over the warps
                     const int cc = std::min(ch, G);
                     int bb = bi;
                     while (bb > 1 && bb > B) bb >>= 1;
-                    if (bi == 0 && (8 % cc)) continue;
+                    if (bi == 0 && (8 % cc) && cc <= 4) continue;
+                    if (cc > 4 && bi != 0) continue;   // more than 4 rotations: the split form only
                     if (!seen.insert(std::make_pair(cc, bb)).second) continue;
                     float t = 1e30f;
                     for (int rep = 0; rep < 2; rep++) {

@@ -290,15 +290,21 @@ def test_alpha2_128x128_benchmark_schedule_bit_exact():
         he.cnt.reset()
         oc = HMM(he).hmatmul(oa, ob, n, n1, n1)
         assert (he.cnt.MS, he.cnt.Dp, he.cnt.MD) == (562, 176, 421)
-        pk.he_counters(ctx, reset=True)
-        gc = pk.he_hmatmul(ctx, ga, gb, n, n1, n1)
-        cnt = pk.he_counters(ctx)
-        assert (cnt["MS"], cnt["Dp"], cnt["MD"]) == (562, 176, 421)
-        got, want = pk.he_ct_export(ctx, gc), res(oc)
-        assert np.array_equal(got, want), "%d of %d words differ" % ((got != want).sum(), got.size)
-        assert pk.he_ct_info(gc)[0] == 1
-        assert np.abs(pk.he_decrypt_matrix(ctx, gc, n, n) - A @ B).max() < TOL
-        for h in (ga, gb, gc):
+        # the tuner's launches, then the fused C^k kernel pinned to its
+        # eight-rotation split form (variant 97: the 15 babies of a giant as
+        # launches of 8, 4 and 3 rotations)
+        for v in (-1, 97):
+            pk.he_ctx_set_multsum_variant(ctx, v)
+            pk.he_counters(ctx, reset=True)
+            gc = pk.he_hmatmul(ctx, ga, gb, n, n1, n1)
+            cnt = pk.he_counters(ctx)
+            assert (cnt["MS"], cnt["Dp"], cnt["MD"]) == (562, 176, 421)
+            got, want = pk.he_ct_export(ctx, gc), res(oc)
+            assert np.array_equal(got, want), "variant %d: %d of %d words differ" % (v, (got != want).sum(), got.size)
+            assert pk.he_ct_info(gc)[0] == 1
+            assert np.abs(pk.he_decrypt_matrix(ctx, gc, n, n) - A @ B).max() < TOL
+            pk.he_ct_free(gc)
+        for h in (ga, gb):
             pk.he_ct_free(h)
     finally:
         pk.he_ctx_destroy(ctx)
