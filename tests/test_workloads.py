@@ -44,3 +44,23 @@ def test_mixed_jobs_ranges():
     for n, logN, level, A, B in jobs:
         assert n in (16, 32, 64, 128) and logN in (15, 16) and 3 <= level <= 20
         assert A.shape == (n, n)
+
+
+def test_multsum_tuner_picks_are_read_from_the_log():
+    """bench.py reports, per (level, items, rotations), the fastest plan of
+    the MultSum tuner's log lines, and the fused C^k kernel's separately."""
+    import bench
+    log = "\n".join([
+        "multsum level 20 B 8 G 15 chunk 8 BI 8 stream 0 ms 2.5000",
+        "multsum level 20 B 8 G 15 chunk 4 BI 116 stream 0 ms 2.1000",
+        "multsum level 18 B 8 G 1 chunk 1 BI 184 stream 0 ms 0.3000",
+        "multsum level 18 B 8 G 1 chunk 1 BI 4 stream 1 ms 0.4000",
+        "multsum_ck level 19 B 8 G 15 chunk 4 BI 8 ms 7.1000",
+        "multsum_ck level 19 B 8 G 15 chunk 8 BI 0 ms 7.5000",
+        "ntt forward logN 16 rows 1024 ctas_per_sm 3 ms 0.7469",
+    ])
+    assert bench.multsum_picks(log) == [
+        "level 18 B 8 G 1: 1 keys per launch, variant 84, 0.3000 ms",
+        "level 20 B 8 G 15: 4 keys per launch, variant 16, 2.1000 ms",
+        "C^k fused, level 19 B 8 G 15: 4 keys per launch, 8 items per CTA, 7.1000 ms",
+    ]
